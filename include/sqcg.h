@@ -1,0 +1,161 @@
+/*
+ * sqcg.h -- C ABI of the GB300 improved-staggered CG library.
+ *
+ * The library solves the even-odd preconditioned improved-staggered normal
+ * equation (sigma - D_eo D_oe) x = b, sigma = 4 m^2, and its multi-shift form,
+ * on one CUDA GPU (the single- and multi-mass staggered CG of arXiv:1611.00728,
+ * Sec. 3; the benchmarked double-precision multi-mass CG of Sec. 4). D is the
+ * staggered Dslash with fat one-hop and long (Naik) three-hop links (Sec. 3,
+ * the generated "staggered dslash" kernel):
+ *
+ *   (D psi)(n) = sum_mu [  s F_mu(n) psi(n+mu) - s' F_mu(n-mu)^+ psi(n-mu)
+ *                        + s L_mu(n) psi(n+3mu) - s' L_mu(n-3mu)^+ psi(n-3mu) ]
+ *
+ * s, s' = eta_mu * boundary sign of the forward hop (eta_x = 1,
+ * eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z); -1 for a forward
+ * hop across the last time slice when the time direction is antiperiodic).
+ *
+ * Conventions shared by every call:
+ *  - Lattice extents dims = {Lx, Ly, Lz, Lt}, all even and >= 4. Sites are
+ *    numbered lex = x + Lx*(y + Ly*(z + Lz*t)); parity = (x+y+z+t) mod 2;
+ *    V = Lx*Ly*Lz*Lt, Vh = V/2.
+ *  - Host gauge fields: double [V][4][3][3][2] (complex, row-major 3x3,
+ *    direction order x, y, z, t, forward links only: the standard MILC storage
+ *    the paper contrasts with its 8-way layout, Sec. 3).
+ *  - Host colour vectors on one parity: double [Vh][3][2], sites of that parity
+ *    in increasing lex order (index lex/2).
+ *  - Device colour vectors on one parity (what sqcg_dslash and the solvers
+ *    take): structure of arrays [3 colour][Vh] of complex, i.e. double2
+ *    (SQCG_F64) or float2 (SQCG_F32); 16-byte (F64) / 8-byte (F32) aligned.
+ *    The caller allocates and owns them (e.g. torch tensors).
+ *  - All work is queued on the context's CUDA stream (set at creation or by
+ *    sqcg_set_stream). Calls that return results to the host (solver info)
+ *    synchronise that stream before returning.
+ *  - Return value: SQCG_OK (0) or a negative SQCG_ERR_* code; sqcg_strerror
+ *    gives a message. Nothing aborts the process and no kernel traps.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SQCG_H
+#define SQCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SQCG_OK 0
+#define SQCG_ERR_INVALID_ARG (-1)    /* odd or too small extent, null pointer, bad flag, tol <= 0 ... */
+#define SQCG_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define SQCG_ERR_NOT_CONVERGED (-3)  /* max_iter reached; x holds the last iterate, info is filled */
+#define SQCG_ERR_BREAKDOWN (-4)      /* <p, A p> <= 0, or NaN/Inf in a reduction */
+#define SQCG_ERR_RECON_REJECTED (-5) /* 12-real long links requested but the links fail the test */
+#define SQCG_ERR_NO_LINKS (-6)       /* operator used before sqcg_load_links */
+#define SQCG_ERR_NO_MEMORY (-7)      /* device allocation failed */
+
+/* ---- sqcg_create flags ---- */
+#define SQCG_ANTIPERIODIC_T 1 /* extra -1 on forward hops across the last time slice */
+#define SQCG_PHASES_FOLDED 2  /* links passed to sqcg_load_links already carry eta and the boundary sign */
+
+/* ---- sqcg_load_links options ---- */
+#define SQCG_RECON12_LONG 1 /* store long links as 2 rows (12 reals) and rebuild row 3 on the fly */
+
+/* ---- precisions ---- */
+#define SQCG_F64 0
+#define SQCG_F32 1
+
+/* ---- solver modes ---- */
+#define SQCG_MODE_F64 0   /* everything in FP64 */
+#define SQCG_MODE_MIXED 1 /* FP32 Dslash and vectors, FP64 x, reductions and reliable updates */
+
+typedef struct sqcg_ctx sqcg_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int iters;             /* CG iterations (Dslash pairs in the Krylov loop) */
+  int reliable_updates;  /* FP64 true-residual recomputations inside the loop */
+  int status;            /* SQCG_OK or SQCG_ERR_* for this system */
+  double true_rel_resid; /* |b - A x| / |b| recomputed in FP64 from the returned x */
+  double seconds;        /* wall time of the solve on the host, including the final sync */
+  int launches;          /* kernels this call launched (including gated-off ones in a captured loop) */
+} sqcg_info;
+
+/* Create a context for one lattice geometry. dims: 4 extents, all even and
+ * >= 4. flags: SQCG_ANTIPERIODIC_T | SQCG_PHASES_FOLDED. cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream). On success *out owns device
+ * memory until sqcg_destroy. Errors: INVALID_ARG, CUDA. */
+int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out);
+
+/* Free everything the context owns (device links, workspace, graphs). NULL is a no-op. */
+int sqcg_destroy(sqcg_ctx* ctx);
+
+/* Change the stream later calls queue their work on. */
+int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
+
+/* Bytes of one device colour vector on one parity in precision prec (Vh * 3 * 2 * sizeof(real)). */
+int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
+
+/* Load fat (one-hop) and long (three-hop) links from host memory in the host
+ * gauge format above. The library folds eta and the boundary sign into its
+ * copies unless the context has SQCG_PHASES_FOLDED, converts them to its
+ * parity-split structure-of-arrays layout and keeps an FP64 and an FP32 copy on
+ * the device (owned by the context, replacing earlier links). The host arrays
+ * are only read during the call.
+ * opts: SQCG_RECON12_LONG stores the long links as their first two rows; it is
+ * accepted only if every long link is s * W with W in SU(3) and one global
+ * real |s| (checked to 1e-12), else SQCG_ERR_RECON_REJECTED and nothing is
+ * loaded. Fat links are always stored in full. */
+int sqcg_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
+
+/* Copy one host colour vector (parity order, complex double [Vh][3]) into a
+ * device vector of precision prec (rounded to nearest for SQCG_F32). */
+int sqcg_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
+
+/* Copy a device vector of precision prec back to host parity order (complex
+ * double [Vh][3]). Synchronises the stream. */
+int sqcg_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host);
+
+/* out = D in on the sites of parity out_parity, reading in on the other
+ * parity (paper Sec. 3, staggered dslash). in and out are device vectors of
+ * precision prec; they must not alias. Asynchronous on the stream. */
+int sqcg_dslash(sqcg_ctx* ctx, int out_parity, int prec, const void* in, void* out);
+
+/* y = (sigma - D_eo D_oe) x on the even sites, FP64 or FP32 device vectors
+ * (x, y must not alias). Asynchronous. */
+int sqcg_normal_op(sqcg_ctx* ctx, double sigma, int prec, const void* x, void* y);
+
+/* Solve (4 mass^2 - D_eo D_oe) x = b on the even sites by CG (paper Sec. 3,
+ * single-mass CG). b, x: FP64 device vectors; x holds the initial guess on
+ * entry (zero it for x0 = 0) and the solution on return. Stops when the FP64
+ * true relative residual |b - A x|/|b| <= tol, or after max_iter iterations
+ * (SQCG_ERR_NOT_CONVERGED, x = last iterate). mode: SQCG_MODE_F64 or
+ * SQCG_MODE_MIXED (FP32 Krylov vectors with FP64 reliable updates). info may
+ * be NULL. Synchronises the stream. */
+int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol, int max_iter,
+                  int mode, sqcg_info* info);
+
+/* Solve (shifts[s] - D_eo D_oe) x[s] = b for nshift shifts at once (1 <= nshift
+ * <= 32) from one Krylov space (paper Sec. 3-4, the multi-mass CG; shifts[s]
+ * plays the role of 4 m_s^2, all >= 0). The smallest shift is the base system;
+ * the shifted systems follow from collinear residuals r_s = zeta_s r with the
+ * FP64 zeta/alpha/beta recurrences of Jegerlehner (hep-lat/9612014). b: FP64
+ * device vector; x: host array of nshift distinct FP64 device vectors
+ * (overwritten; the multi-shift start is x_s = 0); tol[s]: per-shift
+ * tolerance on the FP64 true relative residual. A shift stops when its
+ * iterated residual |zeta_s| |r| / |b| <= tol[s]. Each x_s is then checked on
+ * its FP64 true residual; where that is above tol[s] (expected with FP32
+ * vectors) it is refined by CG of the same mode started from x_s.
+ * info: NULL or an array of nshift (per-shift iterations including refinement,
+ * status, true residual; seconds = whole call). Returns SQCG_OK when every
+ * shift converged, else the first failing status. Synchronises the stream. */
+int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, const void* b,
+                             void* const* x, const double* tol, int max_iter, int mode,
+                             sqcg_info* info);
+
+const char* sqcg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQCG_H */

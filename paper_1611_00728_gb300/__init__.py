@@ -1,0 +1,235 @@
+"""GB300-native improved-staggered CG (arXiv:1611.00728): Python binding.
+
+A thin ctypes layer over the C ABI in ``include/sqcg.h`` (``libsqcg.so``,
+built in-tree by ``paper_1611_00728_gb300.build``). Every step of the Dslash
+and the solvers runs in the library's CUDA kernels; this module only marshals
+arguments. PyTorch provides device memory (tensors) and the CUDA stream.
+
+Device colour vectors are torch tensors of shape ``(3, Vh, 2)`` (colour,
+site, re/im) in float64 (``F64``) or float32 (``F32``): the library's
+structure-of-arrays layout. Host colour vectors are numpy complex128
+``[Vh][3]`` in parity order (sites of one parity in increasing lex order).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
+    "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE",
+]
+
+F64, F32 = 0, 1
+MODE_F64, MODE_MIXED = 0, 1
+ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
+RECON12_LONG = 1
+#: MILC's flop count of one Dslash output site: 16 x 66 (3x3 complex mat-vec) + 15 x 6 (adds)
+FLOPS_PER_SITE = 1146
+
+OK = 0
+ERR_NAMES = {
+    -1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "RECON_REJECTED",
+    -6: "NO_LINKS", -7: "NO_MEMORY",
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libsqcg.so")
+
+
+class SqcgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        self.name = ERR_NAMES.get(code, str(code))
+        msg = library().sqcg_strerror(code).decode()
+        super().__init__(f"{what}: {self.name} ({msg})")
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library():
+    """Load libsqcg.so. There is no fallback: a missing library is an error."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_1611_00728_gb300.build` "
+                               "(the CUDA library is required; there is no CPU path)")
+        lib = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.sqcg_create.argtypes = [P, I, P, ctypes.POINTER(P)]
+        lib.sqcg_destroy.argtypes = [P]
+        lib.sqcg_set_stream.argtypes = [P, P]
+        lib.sqcg_spinor_bytes.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
+        lib.sqcg_load_links.argtypes = [P, P, P, I]
+        lib.sqcg_pack_spinor.argtypes = [P, I, P, P]
+        lib.sqcg_unpack_spinor.argtypes = [P, I, P, P]
+        lib.sqcg_dslash.argtypes = [P, I, I, P, P]
+        lib.sqcg_normal_op.argtypes = [P, D, I, P, P]
+        lib.sqcg_cg_solve.argtypes = [P, D, P, P, D, I, I, ctypes.POINTER(Info)]
+        lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
+        lib.sqcg_strerror.argtypes = [I]
+        lib.sqcg_strerror.restype = ctypes.c_char_p
+        for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
+                     "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
+                     "sqcg_multishift_cg_solve"):
+            getattr(lib, name).restype = I
+        _lib = lib
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise SqcgError(code, what)
+    return code
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class Lattice:
+    """One lattice geometry with its links on the current CUDA device.
+
+    dims = (Lx, Ly, Lz, Lt), all even and >= 4. antiperiodic_t: extra -1 on
+    forward hops across the last time slice. phases_folded: the links passed to
+    load_links already carry the staggered phases and boundary sign."""
+
+    def __init__(self, dims, antiperiodic_t: bool = True, phases_folded: bool = False):
+        torch = _torch()
+        self.dims = tuple(int(v) for v in dims)
+        self.V = int(np.prod(self.dims))
+        self.Vh = self.V // 2
+        flags = (ANTIPERIODIC_T if antiperiodic_t else 0) | (PHASES_FOLDED if phases_folded else 0)
+        d = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream
+        _check(library().sqcg_create(d, flags, ctypes.c_void_p(stream), ctypes.byref(h)), "sqcg_create")
+        self._h = h
+        self.recon12 = False
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().sqcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_stream(self):
+        library().sqcg_set_stream(self._h, ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream))
+
+    # -- data -------------------------------------------------------------
+    def load_links(self, fat: np.ndarray, lng: np.ndarray, recon12: bool = False):
+        """fat, lng: complex128 [V][4][3][3] host arrays (forward links, lex order)."""
+        fat = np.ascontiguousarray(fat, dtype=np.complex128)
+        lng = np.ascontiguousarray(lng, dtype=np.complex128)
+        if fat.shape != (self.V, 4, 3, 3) or lng.shape != (self.V, 4, 3, 3):
+            raise ValueError(f"links must have shape ({self.V}, 4, 3, 3)")
+        self._sync_stream()
+        _check(library().sqcg_load_links(self._h, fat.ctypes.data, lng.ctypes.data, RECON12_LONG if recon12 else 0),
+               "sqcg_load_links")
+        self.recon12 = recon12
+
+    def new_spinor(self, prec: int = F64, count: int | None = None):
+        """Zeroed device colour vector(s) in the library layout: (3, Vh, 2)."""
+        torch = _torch()
+        dt = torch.float64 if prec == F64 else torch.float32
+        shape = (3, self.Vh, 2) if count is None else (count, 3, self.Vh, 2)
+        return torch.zeros(shape, dtype=dt, device="cuda")
+
+    @staticmethod
+    def _check_spinor(t, prec, Vh):
+        torch = _torch()
+        dt = torch.float64 if prec == F64 else torch.float32
+        if t.dtype != dt or tuple(t.shape) != (3, Vh, 2) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA tensor (3, {Vh}, 2) of {dt}, got {t.dtype} {tuple(t.shape)}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def pack(self, host: np.ndarray, prec: int = F64, out=None):
+        """Host parity-order complex [Vh][3] -> device vector (3, Vh, 2)."""
+        host = np.ascontiguousarray(host, dtype=np.complex128)
+        if host.shape != (self.Vh, 3):
+            raise ValueError(f"host field must have shape ({self.Vh}, 3)")
+        out = self.new_spinor(prec) if out is None else out
+        self._sync_stream()
+        _check(library().sqcg_pack_spinor(self._h, prec, host.ctypes.data, self._check_spinor(out, prec, self.Vh)),
+               "sqcg_pack_spinor")
+        return out
+
+    def unpack(self, dev, prec: int = F64, out: np.ndarray | None = None) -> np.ndarray:
+        """Device vector -> host parity-order complex128 [Vh][3] (synchronises)."""
+        out = np.empty((self.Vh, 3), dtype=np.complex128) if out is None else out
+        self._sync_stream()
+        _check(library().sqcg_unpack_spinor(self._h, prec, self._check_spinor(dev, prec, self.Vh), out.ctypes.data),
+               "sqcg_unpack_spinor")
+        return out
+
+    # -- operators --------------------------------------------------------
+    def dslash(self, out_parity: int, inp, out, prec: int = F64):
+        """out = D inp on the sites of out_parity (asynchronous)."""
+        self._sync_stream()
+        _check(library().sqcg_dslash(self._h, out_parity, prec, self._check_spinor(inp, prec, self.Vh),
+                                     self._check_spinor(out, prec, self.Vh)), "sqcg_dslash")
+        return out
+
+    def normal_op(self, sigma: float, x, y, prec: int = F64):
+        """y = (sigma - D_eo D_oe) x on the even sites (asynchronous)."""
+        self._sync_stream()
+        _check(library().sqcg_normal_op(self._h, float(sigma), prec, self._check_spinor(x, prec, self.Vh),
+                                        self._check_spinor(y, prec, self.Vh)), "sqcg_normal_op")
+        return y
+
+    # -- solvers ----------------------------------------------------------
+    def cg_solve(self, mass: float, b, x, tol: float = 1e-8, max_iter: int = 10000, mode: int = MODE_MIXED,
+                 raise_on_error: bool = True) -> Info:
+        """Solve (4 mass^2 - D_eo D_oe) x = b; x holds the initial guess. Returns Info."""
+        info = Info()
+        self._sync_stream()
+        rc = library().sqcg_cg_solve(self._h, float(mass), self._check_spinor(b, F64, self.Vh),
+                                     self._check_spinor(x, F64, self.Vh), float(tol), int(max_iter), int(mode),
+                                     ctypes.byref(info))
+        if raise_on_error:
+            _check(rc, "sqcg_cg_solve")
+        return info
+
+    def multishift_cg_solve(self, shifts, b, xs, tol=1e-8, max_iter: int = 10000, mode: int = MODE_MIXED,
+                            raise_on_error: bool = True):
+        """Solve (shifts[s] - D_eo D_oe) xs[s] = b for all shifts. Returns a list of Info."""
+        n = len(shifts)
+        sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
+        tols = [float(tol)] * n if np.isscalar(tol) else [float(t) for t in tol]
+        tl = (ctypes.c_double * n)(*tols)
+        ptrs = (ctypes.c_void_p * n)(*[self._check_spinor(x, F64, self.Vh).value for x in xs])
+        infos = (Info * n)()
+        self._sync_stream()
+        rc = library().sqcg_multishift_cg_solve(self._h, n, sh, self._check_spinor(b, F64, self.Vh), ptrs, tl,
+                                                int(max_iter), int(mode), infos)
+        if raise_on_error:
+            _check(rc, "sqcg_multishift_cg_solve")
+        return list(infos)

@@ -1,0 +1,249 @@
+// Fused BLAS-1 kernels of the CG iteration (the vector updates and global
+// reductions around the Dslash; paper Sec. 4 notes that multi-mass CG is even
+// more bandwidth bound than CG because of them). Each kernel streams its
+// vectors once; norms and dot products are accumulated in FP64 and reduced
+// deterministically (warp shuffle -> block -> last block in index order),
+// and the scalar CG step runs in the last block.
+#include "solver_device.cuh"
+#include "sqcg_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+// x += alpha p (x FP64); r -= alpha Ap; reduce |r|^2 -> FIN_UPDATE
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restrict__ p,
+            const typename V2<R>::T* __restrict__ Ap, int Vh, SolverState* st, double* partials) {
+  typedef typename V2<R>::T R2;
+  if (!gate_open(st, GATE_ITER)) return;
+  const double alpha = st->alpha;
+  const R ra = (R)alpha;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm = 0.0;
+  if (i < Vh) {
+    R part = R(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      const R2 pc = p[k];
+      const R2 apc = Ap[k];
+      R2 rc = r[k];
+      double2 xc = x[k];
+      xc.x = fma(alpha, (double)pc.x, xc.x);
+      xc.y = fma(alpha, (double)pc.y, xc.y);
+      x[k] = xc;
+      rc.x = fma(-ra, apc.x, rc.x);
+      rc.y = fma(-ra, apc.y, rc.y);
+      r[k] = rc;
+      part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
+    }
+    nrm = (double)part;
+  }
+  grid_reduce_finish(nrm, partials, st, FIN_UPDATE);
+}
+
+// p = r + beta p
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict__ p, int Vh, const SolverState* st) {
+  typedef typename V2<R>::T R2;
+  if (!gate_open(st, GATE_ITER)) return;
+  const R beta = (R)st->beta;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Vh) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const size_t k = (size_t)c * Vh + i;
+    const R2 rc = r[k];
+    R2 pc = p[k];
+    pc.x = fma(beta, pc.x, rc.x);
+    pc.y = fma(beta, pc.y, rc.y);
+    p[k] = pc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_norm2_f64(const double2* __restrict__ v, int Vh, SolverState* st, double* partials, int fin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm = 0.0;
+  if (i < Vh) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = v[(size_t)c * Vh + i];
+      nrm = fma(a.x, a.x, fma(a.y, a.y, nrm));
+    }
+  }
+  grid_reduce_finish(nrm, partials, st, fin);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scale_copy_f64(const double2* __restrict__ src, double2* __restrict__ dst, double a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 s = src[i];
+  dst[i] = make_double2(a * s.x, a * s.y);
+}
+
+// ---------------------------------------------------------------------------
+// multi-shift CG: the base r update with the x_s updates of all shifts, and
+// the p_s updates. The shift scalars come from SolverState (FP64).
+// ---------------------------------------------------------------------------
+struct MSPtrs {
+  double2* x[SQCG_MAX_SHIFTS];
+  void* p[SQCG_MAX_SHIFTS];
+};
+
+// r -= alpha Ap (base); x_s += alpha_s p_s for active shifts; reduce |r|^2 -> FIN_MS_UPDATE
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_ms_update(MSPtrs P, typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restrict__ Ap, int Vh,
+            SolverState* st, double* partials) {
+  typedef typename V2<R>::T R2;
+  if (!gate_open(st, GATE_ITER)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ns = st->nshift;
+  double nrm = 0.0;
+  if (i < Vh) {
+    const R ra = (R)st->alpha;
+    R part = R(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      R2 rc = r[k];
+      const R2 apc = Ap[k];
+      rc.x = fma(-ra, apc.x, rc.x);
+      rc.y = fma(-ra, apc.y, rc.y);
+      r[k] = rc;
+      part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
+    }
+    nrm = (double)part;
+    for (int j = 0; j < ns; ++j) {
+      if (!st->active[j]) continue;
+      const double as = st->alpha_s[j];
+      const R2* ps = static_cast<const R2*>(P.p[j]);
+      double2* xs = P.x[j];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * Vh + i;
+        const R2 pc = ps[k];
+        double2 xc = xs[k];
+        xc.x = fma(as, (double)pc.x, xc.x);
+        xc.y = fma(as, (double)pc.y, xc.y);
+        xs[k] = xc;
+      }
+    }
+  }
+  grid_reduce_finish(nrm, partials, st, FIN_MS_UPDATE);
+}
+
+// p = r + beta p (base, which is also shift 0's direction); p_s = zeta_s r + beta_s p_s (shifts >= 1)
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict__ p, int Vh,
+          const SolverState* st) {
+  typedef typename V2<R>::T R2;
+  if (!gate_open(st, GATE_ITER)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Vh) return;
+  const int ns = st->nshift;
+  R2 rc[3];
+  const R beta = (R)st->beta;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const size_t k = (size_t)c * Vh + i;
+    rc[c] = r[k];
+    R2 pc = p[k];
+    pc.x = fma(beta, pc.x, rc[c].x);
+    pc.y = fma(beta, pc.y, rc[c].y);
+    p[k] = pc;
+  }
+  for (int j = 1; j < ns; ++j) {
+    if (!st->active[j]) continue;
+    const R z = (R)st->zeta[j], bs = (R)st->beta_s[j];
+    R2* ps = static_cast<R2*>(P.p[j]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      R2 pc = ps[k];
+      pc.x = fma(bs, pc.x, z * rc[c].x);
+      pc.y = fma(bs, pc.y, z * rc[c].y);
+      ps[k] = pc;
+    }
+  }
+}
+
+}  // namespace
+
+// variant with an explicit x (the solver's output vector)
+int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
+  if (mixed)
+    k_cg_update<float><<<grid, kThreads, 0, s>>>(x, ctx->r32, ctx->p32, ctx->Ap32, Vh, ctx->st, ctx->partials);
+  else
+    k_cg_update<double><<<grid, kThreads, 0, s>>>(x, ctx->r64, ctx->p64, ctx->Ap64, Vh, ctx->st, ctx->partials);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  if (mixed)
+    k_cg_xpay<float><<<grid, kThreads, 0, s>>>(ctx->r32, ctx->p32, Vh, ctx->st);
+  else
+    k_cg_xpay<double><<<grid, kThreads, 0, s>>>(ctx->r64, ctx->p64, Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
+  k_norm2_f64<<<grid, kThreads, 0, s>>>(v, Vh, ctx->st, ctx->partials, fin);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s) {
+  const int n = ctx->g.Vh * 3;
+  k_scale_copy_f64<<<grid_for(n, kThreads), kThreads, 0, s>>>(src, dst, a, n);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_ms_update_x(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
+  MSPtrs P;
+  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
+    P.x[j] = (j < ctx->ms_nalloc) ? x[j] : nullptr;
+    P.p[j] = (j < ctx->ms_nalloc) ? ctx->ms_p[j] : nullptr;
+  }
+  if (mixed)
+    k_ms_update<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->Ap32, Vh, ctx->st, ctx->partials);
+  else
+    k_ms_update<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, ctx->Ap64, Vh, ctx->st, ctx->partials);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  MSPtrs P;
+  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
+    P.x[j] = nullptr;
+    P.p[j] = (j < ctx->ms_nalloc) ? ctx->ms_p[j] : nullptr;
+  }
+  if (mixed)
+    k_ms_xpay<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->p32, Vh, ctx->st);
+  else
+    k_ms_xpay<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, ctx->p64, Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}

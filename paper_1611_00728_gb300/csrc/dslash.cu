@@ -1,0 +1,298 @@
+// Improved-staggered Dslash on CUDA cores (arXiv:1611.00728 Sec. 3: the
+// generated "staggered dslash" kernel; Sec. 4: its least-data model bandwidth).
+//
+//   (D psi)(n) = sum_mu [ F_mu(n) psi(n+mu) - F_mu(n-mu)^+ psi(n-mu)
+//                       + L_mu(n) psi(n+3mu) - L_mu(n-3mu)^+ psi(n-3mu) ]
+//
+// with eta_mu and the boundary sign already folded into F and L at load time.
+// One thread computes one output site of one parity. Links are stored
+// [parity][mu][elem][Vh] so that a warp reads each matrix element of 32
+// consecutive sites as one contiguous segment; colour vectors are [3][Vh].
+// The backward hop reads the forward link of the neighbour and applies the
+// dagger in registers (forward-only storage, the standard MILC layout).
+// Neighbour indices are computed from the site coordinates (no index tables).
+// With 12-real long links the third row is rebuilt as conj(row0 x row1) / s,
+// s = s0 * eta_mu * boundary sign of that link.
+#include "solver_device.cuh"
+#include "sqcg_internal.cuh"
+
+namespace {
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+template <typename R2>
+__device__ __forceinline__ R2 ldg2(const R2* p) { return __ldg(p); }
+
+template <typename R2>
+__device__ __forceinline__ R2 mk(decltype(R2().x) a, decltype(R2().x) b) { R2 r; r.x = a; r.y = b; return r; }
+
+// acc += U v   (U row-major 3x3 complex)
+template <typename R, typename R2>
+__device__ __forceinline__ void acc_mv(R2 (&acc)[3], const R2 (&U)[9], const R2 (&v)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R2 u = U[a * 3 + b];
+      acc[a].x = fma(u.x, v[b].x, acc[a].x);
+      acc[a].x = fma(-u.y, v[b].y, acc[a].x);
+      acc[a].y = fma(u.x, v[b].y, acc[a].y);
+      acc[a].y = fma(u.y, v[b].x, acc[a].y);
+    }
+  }
+}
+
+// acc -= U^dagger v
+template <typename R, typename R2>
+__device__ __forceinline__ void sub_mdv(R2 (&acc)[3], const R2 (&U)[9], const R2 (&v)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R2 u = U[b * 3 + a];  // conj(U[b][a]) v[b]
+      acc[a].x = fma(-u.x, v[b].x, acc[a].x);
+      acc[a].x = fma(-u.y, v[b].y, acc[a].x);
+      acc[a].y = fma(-u.x, v[b].y, acc[a].y);
+      acc[a].y = fma(u.y, v[b].x, acc[a].y);
+    }
+  }
+}
+
+template <typename R, typename R2, bool RECON>
+__device__ __forceinline__ void load_link(R2 (&U)[9], const R2* __restrict__ base, int stride, int idx, R inv_s) {
+  if (!RECON) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = ldg2(base + (size_t)e * stride + idx);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) U[e] = ldg2(base + (size_t)e * stride + idx);
+    // row2 = conj(row0 x row1) / s
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int k = (j + 1) % 3, l = (j + 2) % 3;
+      const R2 ak = U[k], al = U[l], bk = U[3 + k], bl = U[3 + l];
+      R re = ak.x * bl.x - ak.y * bl.y - (al.x * bk.x - al.y * bk.y);
+      R im = ak.x * bl.y + ak.y * bl.x - (al.x * bk.y + al.y * bk.x);
+      U[6 + j] = mk<R2>(re * inv_s, -im * inv_s);
+    }
+  }
+}
+
+template <typename R2>
+__device__ __forceinline__ void load_vec(R2 (&v)[3], const R2* __restrict__ in, int Vh, int idx) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = ldg2(in + (size_t)c * Vh + idx);
+}
+
+template <typename R>
+struct DArgs {
+  Geom g;
+  int par;                         // output parity
+  const typename V2<R>::T* fat_p;  // fat links of the output parity
+  const typename V2<R>::T* fat_q;  // fat links of the input parity
+  const typename V2<R>::T* lng_p;
+  const typename V2<R>::T* lng_q;
+  int nl;                          // elements per long link (9 or 6)
+  R inv_s0;                        // 1 / global long-link scale (recon)
+  const typename V2<R>::T* in;
+  void* out;
+  void* out2;
+  const void* y;
+  const double2* b;
+  double sigma;
+  const double* sigma_dev;
+  SolverState* st;
+  double* partials;
+  int gate, fin;
+};
+
+// D at output site i of parity a.par; returns the three colour components.
+template <typename R, bool RECON>
+__device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V2<R>::T (&acc)[3]) {
+  typedef typename V2<R>::T R2;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  const int xh = i % g.Lxh;
+  int r = i / g.Lxh;
+  const int y = r % g.Ly;
+  r /= g.Ly;
+  const int z = r % g.Lz;
+  const int t = r / g.Lz;
+  const int x = 2 * xh + ((y + z + t + a.par) & 1);
+  const int row = i - xh;  // half index of (0, y, z, t)
+
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = mk<R2>(R(0), R(0));
+
+  R2 U[9], v[3];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    // eta_mu(n) and the boundary signs, needed only to rebuild 12-real long links
+    R inv_s_f = R(1), inv_s_b = R(1);
+    if (RECON) {
+      int e = 0;
+      if (mu == 1) e = x;
+      if (mu == 2) e = x + y;
+      if (mu == 3) e = x + y + z;
+      const R eta = (e & 1) ? R(-1) : R(1);
+      inv_s_f = eta * a.inv_s0;
+      inv_s_b = eta * a.inv_s0;
+      if (mu == 3 && g.apbc) {
+        if (t + 3 >= g.Lt) inv_s_f = -inv_s_f;
+        if (t < 3) inv_s_b = -inv_s_b;
+      }
+    }
+    const int cmu = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
+    const int Lmu = (mu == 0) ? g.Lx : (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+    const int smu = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int d = (k == 0) ? 1 : 3;
+      int fwd, bwd;
+      if (mu == 0) {
+        int xp = x + d; if (xp >= g.Lx) xp -= g.Lx;
+        int xm = x - d; if (xm < 0) xm += g.Lx;
+        fwd = row + (xp >> 1);
+        bwd = row + (xm >> 1);
+      } else {
+        fwd = i + d * smu; if (cmu + d >= Lmu) fwd -= Lmu * smu;
+        bwd = i - d * smu; if (cmu - d < 0) bwd += Lmu * smu;
+      }
+      if (k == 0) {
+        load_link<R, R2, false>(U, a.fat_p + (size_t)mu * 9 * Vh, Vh, i, R(1));
+        load_vec(v, a.in, Vh, fwd);
+        acc_mv<R>(acc, U, v);
+        load_link<R, R2, false>(U, a.fat_q + (size_t)mu * 9 * Vh, Vh, bwd, R(1));
+        load_vec(v, a.in, Vh, bwd);
+        sub_mdv<R>(acc, U, v);
+      } else {
+        load_link<R, R2, RECON>(U, a.lng_p + (size_t)mu * a.nl * Vh, Vh, i, inv_s_f);
+        load_vec(v, a.in, Vh, fwd);
+        acc_mv<R>(acc, U, v);
+        load_link<R, R2, RECON>(U, a.lng_q + (size_t)mu * a.nl * Vh, Vh, bwd, inv_s_b);
+        load_vec(v, a.in, Vh, bwd);
+        sub_mdv<R>(acc, U, v);
+      }
+    }
+  }
+}
+
+constexpr int kThreads = 128;
+
+template <typename R, typename RO, bool RECON, int EPI>
+__global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
+  typedef typename V2<R>::T R2;
+  typedef typename V2<RO>::T O2;
+  if (!gate_open(a.st, a.gate)) return;
+  const int Vh = a.g.Vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < Vh) {
+    R2 acc[3];
+    dslash_site<R, RECON>(a, i, acc);
+    O2* out = static_cast<O2*>(a.out);
+    if constexpr (EPI == EPI_PLAIN) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = mk<O2>((RO)acc[c].x, (RO)acc[c].y);
+    } else if constexpr (EPI == EPI_NORMAL || EPI == EPI_NORMAL_DOT) {
+      const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
+      const R2* yv = static_cast<const R2*>(a.y);
+      R dot = R(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R2 yc = ldg2(yv + (size_t)c * Vh + i);
+        O2 o = mk<O2>((RO)(sig * yc.x - acc[c].x), (RO)(sig * yc.y - acc[c].y));
+        out[(size_t)c * Vh + i] = o;
+        dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
+      }
+      part = (double)dot;
+    } else {  // EPI_TRUE_RESID: out = b - sigma*x + D in, in FP64
+      const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
+      const double2* xv = static_cast<const double2*>(a.y);
+      O2* out2 = static_cast<O2*>(a.out2);
+      double nrm = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double2 xc = __ldg(xv + (size_t)c * Vh + i);
+        const double2 bc = __ldg(a.b + (size_t)c * Vh + i);
+        const double re = bc.x - sig * xc.x + (double)acc[c].x;
+        const double im = bc.y - sig * xc.y + (double)acc[c].y;
+        O2 o = mk<O2>((RO)re, (RO)im);
+        out[(size_t)c * Vh + i] = o;
+        if (out2) out2[(size_t)c * Vh + i] = o;
+        nrm += re * re + im * im;
+      }
+      part = nrm;
+    }
+  }
+  if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
+    if (a.fin != FIN_NONE) grid_reduce_finish(part, a.partials, a.st, a.fin);
+  }
+}
+
+template <typename R, typename RO, bool RECON>
+int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
+  typedef typename V2<R>::T R2;
+  DArgs<R> a;
+  a.g = ctx->g;
+  a.par = L.out_parity;
+  const int p = L.out_parity, q = 1 - L.out_parity;
+  const size_t Vh = ctx->g.Vh;
+  const int nl = ctx->recon ? 6 : 9;
+  const R2* fat = reinterpret_cast<const R2*>(L.prec == SQCG_F64 ? (const void*)ctx->fat64 : (const void*)ctx->fat32);
+  const R2* lng = reinterpret_cast<const R2*>(L.prec == SQCG_F64 ? (const void*)ctx->lng64 : (const void*)ctx->lng32);
+  a.fat_p = fat + (size_t)p * 4 * 9 * Vh;
+  a.fat_q = fat + (size_t)q * 4 * 9 * Vh;
+  a.lng_p = lng + (size_t)p * 4 * nl * Vh;
+  a.lng_q = lng + (size_t)q * 4 * nl * Vh;
+  a.nl = nl;
+  a.inv_s0 = (R)(ctx->recon ? 1.0 / ctx->long_scale : 1.0);
+  a.in = static_cast<const R2*>(L.in);
+  a.out = L.out;
+  a.out2 = L.out2;
+  a.y = L.y;
+  a.b = static_cast<const double2*>(L.b);
+  a.sigma = L.sigma;
+  a.sigma_dev = L.sigma_dev;
+  a.st = ctx->st;
+  a.partials = ctx->partials;
+  a.gate = L.gate;
+  a.fin = L.fin;
+  if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
+    return SQCG_ERR_INVALID_ARG;
+  const int grid = grid_for(ctx->g.Vh, kThreads);
+  if ((L.epi == EPI_NORMAL_DOT || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE && grid > ctx->max_blocks)
+    return SQCG_ERR_INVALID_ARG;
+  switch (L.epi) {
+    case EPI_PLAIN: k_dslash<R, RO, RECON, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_NORMAL: k_dslash<R, RO, RECON, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
+    default: return SQCG_ERR_INVALID_ARG;
+  }
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+template <typename R, typename RO>
+int launch_r(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
+  return ctx->recon ? launch_t<R, RO, true>(ctx, L, s) : launch_t<R, RO, false>(ctx, L, s);
+}
+
+}  // namespace
+
+int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
+  if (!ctx->have_links) return SQCG_ERR_NO_LINKS;
+  if (L.out_parity != 0 && L.out_parity != 1) return SQCG_ERR_INVALID_ARG;
+  if (L.epi == EPI_TRUE_RESID) {
+    if (L.prec != SQCG_F64 || !L.b || !L.y) return SQCG_ERR_INVALID_ARG;
+    return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
+  }
+  if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT) && !L.y) return SQCG_ERR_INVALID_ARG;
+  if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
+  if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);
+  return SQCG_ERR_INVALID_ARG;
+}

@@ -1,0 +1,171 @@
+// Device-side solver control: gates, deterministic grid reductions and the
+// scalar steps of CG and multi-shift CG that run in the last block of a
+// reduction. All scalars live in SolverState in device memory, so a captured
+// solver iteration needs no host round trip.
+#pragma once
+
+#include <math.h>
+
+#include "sqcg_internal.cuh"
+
+__device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
+  if (gate == GATE_NONE) return true;
+  const volatile SolverState* v = st;
+  if (v->done) return false;
+  if (gate == GATE_UPDATE) return v->need_update != 0;
+  return true;
+}
+
+// sum over the block; the result is valid in thread 0. blockDim.x must be a
+// multiple of 32 and at most 1024. Fixed reduction tree -> deterministic.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // warp_part may still be read by an earlier call
+  if (lane == 0) warp_part[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? warp_part[threadIdx.x] : 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// scalar steps (run by one thread, in the last block of a reduction)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_breakdown(SolverState* s) {
+  s->status = SQCG_ERR_BREAKDOWN;
+  s->done = 1;
+  s->need_update = 0;
+}
+
+__device__ inline void solver_finish(SolverState* s, int fin, double v) {
+  switch (fin) {
+    case FIN_STORE:
+      s->pAp = v;
+      break;
+    case FIN_BB:  // stop thresholds arrive as tol^2 and become tol^2 |b|^2
+      s->bb = v;
+      s->stop_rr *= v;
+      for (int j = 0; j < s->nshift; ++j) s->stop_rr_s[j] *= v;
+      break;
+    case FIN_INIT:  // r = b - A x0 has just been written
+      if (!isfinite(v)) { finish_breakdown(s); break; }
+      s->rr = s->rr_true = s->rr_max = v;
+      s->rr_prev = v;
+      s->iter_last_update = 0;
+      if (v <= s->stop_rr) s->done = 1;
+      break;
+    case FIN_PAP:  // alpha_k = |r_k|^2 / <p_k, A p_k>
+      s->pAp = v;
+      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
+      s->alpha = s->rr / v;
+      break;
+    case FIN_UPDATE: {  // |r_{k+1}|^2 after r -= alpha A p
+      if (!isfinite(v)) { finish_breakdown(s); break; }
+      s->iter += 1;
+      s->rr_prev = s->rr;
+      s->rr = v;
+      s->beta = v / s->rr_prev;
+      if (v > s->rr_max) s->rr_max = v;
+      if (v <= s->stop_rr) {
+        s->need_update = 1;  // confirm on the FP64 true residual
+      } else if (s->mixed && (v < s->delta2 * s->rr_max ||
+                              s->iter - s->iter_last_update >= s->update_interval)) {
+        s->need_update = 1;  // reliable update
+      }
+      if (s->iter >= s->max_iter) s->need_update = 1;  // final true residual, then stop
+      break;
+    }
+    case FIN_TRUE_RESID: {  // r = b - A x recomputed in FP64 and copied to the working r
+      if (!isfinite(v)) { finish_breakdown(s); break; }
+      s->rr_true = v;
+      s->need_update = 0;
+      s->updates += 1;
+      s->iter_last_update = s->iter;
+      s->rr_max = v;
+      if (v <= s->stop_rr) {
+        s->done = 1;
+        s->status = SQCG_OK;
+      } else if (s->iter >= s->max_iter) {
+        s->done = 1;
+        s->status = SQCG_ERR_NOT_CONVERGED;
+      } else {
+        s->beta = v / s->rr_prev;  // continue from the true residual
+        s->rr = v;
+      }
+      break;
+    }
+    case FIN_MS_PAP: {  // base alpha_k, then zeta_{k+1} and alpha^s_k for every shift
+      s->pAp = v;
+      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
+      const double a = s->rr / v;
+      s->alpha = a;
+      for (int j = 0; j < s->nshift; ++j) {
+        if (!s->active[j]) { s->alpha_s[j] = 0.0; continue; }
+        const double zk = s->zeta[j], zkm = s->zeta_prev[j];
+        const double den = a * s->beta_prev * (zkm - zk) + zkm * s->alpha_prev * (1.0 + s->dsig[j] * a);
+        const double znext = zk * zkm * s->alpha_prev / den;
+        s->alpha_s[j] = a * znext / zk;
+        s->beta_s[j] = znext;  // holds zeta_{k+1} until the update step
+      }
+      break;
+    }
+    case FIN_MS_UPDATE: {  // |r_{k+1}|^2, beta_k, beta^s_k, per-shift convergence
+      if (!isfinite(v)) { finish_breakdown(s); break; }
+      s->iter += 1;
+      const double b = v / s->rr;
+      int any = 0;
+      for (int j = 0; j < s->nshift; ++j) {
+        if (!s->active[j]) continue;
+        const double zk = s->zeta[j], znext = s->beta_s[j];
+        s->zeta_prev[j] = zk;
+        s->zeta[j] = znext;
+        s->beta_s[j] = b * (znext / zk) * (znext / zk);
+        s->iters_s[j] = s->iter;
+        if (znext * znext * v <= s->stop_rr_s[j]) s->active[j] = 0;  // shift residual = zeta * r
+        else any = 1;
+      }
+      s->rr_prev = s->rr;
+      s->rr = v;
+      s->beta = b;
+      s->alpha_prev = s->alpha;
+      s->beta_prev = b;
+      if (!any) { s->done = 1; s->status = SQCG_OK; }
+      else if (s->iter >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Grid-wide sum of v with a deterministic order: each block writes its partial,
+// the last block to arrive sums the partials in index order and runs the
+// scalar step. Must be called by every thread of every block.
+__device__ inline void grid_reduce_finish(double v, double* partials, SolverState* st, int fin) {
+  __shared__ bool am_last;
+  const double b = block_sum(v);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b;
+    __threadfence();
+    const unsigned int t = atomicAdd(&st->counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0;
+  const volatile double* vp = partials;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) s += vp[j];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    st->counter = 0;
+    solver_finish(st, fin, s);
+  }
+}

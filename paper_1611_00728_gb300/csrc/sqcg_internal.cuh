@@ -1,0 +1,188 @@
+// Internal declarations of the sqcg CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sqcg.h"
+
+// ---------------------------------------------------------------------------
+// error plumbing: every CUDA call is checked, the code turns into SQCG_ERR_CUDA
+// ---------------------------------------------------------------------------
+#define SQCG_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) {                                  \
+      sqcg_set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return SQCG_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+#define SQCG_TRY(expr)         \
+  do {                         \
+    int _s = (expr);           \
+    if (_s != SQCG_OK) return _s; \
+  } while (0)
+
+void sqcg_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ---------------------------------------------------------------------------
+// geometry of the even-odd half lattice
+// ---------------------------------------------------------------------------
+struct Geom {
+  int Lx, Ly, Lz, Lt;
+  int Lxh;         // Lx / 2
+  int Vh;          // sites per parity
+  int sy, sz, st;  // half-lattice index strides of y, z, t: Lxh, Lxh*Ly, Lxh*Ly*Lz
+  int apbc;        // antiperiodic time direction
+};
+
+// Link storage per field: [parity][mu][elem][Vh] complex, elem = 9 (full) or 6 (two rows).
+template <typename R2>
+struct LinkField {
+  const R2* par[2];  // base of each parity
+  int nelem;         // 9 or 6
+};
+
+// ---------------------------------------------------------------------------
+// solver state kept in device memory (scalars never leave the GPU inside a solve)
+// ---------------------------------------------------------------------------
+#define SQCG_MAX_SHIFTS 32
+
+struct SolverState {
+  double sigma;    // diagonal term of the Krylov system
+  double bb;       // |b|^2
+  double stop_rr;  // tol^2 |b|^2
+  double rr;       // current iterated |r|^2
+  double rr_prev;  // |r|^2 of the previous iteration
+  double rr_true;  // last FP64 true residual |b - A x|^2
+  double rr_max;   // max iterated |r|^2 since the last reliable update
+  double delta2;   // reliable-update trigger: update when |r|^2 < delta2 * rr_max
+  // stop_rr is set to tol^2 by the host and multiplied by |b|^2 in FIN_BB
+  double pAp, alpha, beta;
+  int iter, max_iter;
+  int iter_last_update, update_interval;
+  int done;         // loop finished (converged, breakdown or out of iterations)
+  int status;       // SQCG_OK / SQCG_ERR_*
+  int need_update;  // the FP64 true-residual pass runs in this iteration
+  int updates;      // reliable updates performed inside the loop
+  int mixed;        // working vectors are FP32
+  int pad0;
+  unsigned int counter;  // last-block counter of the grid reductions
+
+  // multi-shift CG (Jegerlehner recurrences; shift s uses sigma + dsig[s])
+  int nshift;
+  int active[SQCG_MAX_SHIFTS];  // shift still iterating
+  double dsig[SQCG_MAX_SHIFTS];
+  double stop_rr_s[SQCG_MAX_SHIFTS];
+  double zeta[SQCG_MAX_SHIFTS], zeta_prev[SQCG_MAX_SHIFTS];
+  double alpha_s[SQCG_MAX_SHIFTS], beta_s[SQCG_MAX_SHIFTS];
+  double alpha_prev, beta_prev;
+  int iters_s[SQCG_MAX_SHIFTS];
+};
+
+// gates: which kernels of a captured iteration actually run
+enum Gate { GATE_NONE = 0, GATE_ITER = 1, GATE_UPDATE = 2 };
+
+// what the last block of a grid reduction does with the total
+enum Finisher {
+  FIN_NONE = 0,
+  FIN_STORE = 1,       // store the total in state->pAp (generic scalar result slot)
+  FIN_BB = 2,          // |b|^2 and the stopping threshold
+  FIN_PAP = 3,         // alpha = rr / <p, A p>
+  FIN_UPDATE = 4,      // new |r|^2, beta, convergence / reliable-update trigger
+  FIN_TRUE_RESID = 5,  // FP64 true residual inside the loop
+  FIN_INIT = 6,        // initial residual r = b - A x0
+  FIN_MS_PAP = 7,      // multi-shift: alpha and the zeta recurrences of every shift
+  FIN_MS_UPDATE = 8,   // multi-shift: new |r|^2, beta, per-shift convergence
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct CGGraph;
+
+struct sqcg_ctx {
+  int L[4];
+  int flags;
+  Geom g;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;  // private stream used only to capture graphs
+
+  bool have_links;
+  bool recon;
+  double long_scale;  // global real scale s0 of the long links (recon)
+
+  // device links, [parity][mu][elem][Vh]
+  double2* fat64;
+  double2* lng64;
+  float2* fat32;
+  float2* lng32;
+
+  // host-copy staging for pack/unpack
+  void* stage;
+  size_t stage_bytes;
+
+  // solver workspace (allocated on first solve)
+  double2 *r64, *p64, *Ap64, *tmp64;
+  float2 *r32, *p32, *Ap32, *tmp32;
+  double* partials;
+  int max_blocks;
+  SolverState* st;       // device
+  SolverState* st_host;  // pinned host mirror
+
+  // multi-shift workspace
+  void* ms_p[SQCG_MAX_SHIFTS];  // per-shift search directions (working precision)
+  int ms_nalloc;
+  int ms_prec;
+
+  CGGraph* graphs;  // cached captured solver loops
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in dslash.cu / blas.cu / layout.cu)
+// ---------------------------------------------------------------------------
+enum DslashEpi {
+  EPI_PLAIN = 0,          // out = D in
+  EPI_NORMAL = 1,         // out = sigma*y - D in
+  EPI_NORMAL_DOT = 2,     // out = sigma*y - D in, reduce Re<y, out>
+  EPI_TRUE_RESID = 3,     // out = b - sigma*y + D in (b, y FP64), reduce |out|^2
+};
+
+struct DslashLaunch {
+  int out_parity;
+  int prec;      // SQCG_F64 / SQCG_F32: precision of links, in and the arithmetic
+  int out_prec;  // precision of out (differs from prec only for EPI_TRUE_RESID)
+  int epi;
+  const void* in;
+  void* out;
+  void* out2;        // EPI_TRUE_RESID: optional second copy of out (same precision as out)
+  const void* y;     // EPI_NORMAL*: vector on out_parity (precision prec); EPI_TRUE_RESID: FP64 x
+  const void* b;     // EPI_TRUE_RESID: FP64 right-hand side
+  double sigma;
+  const double* sigma_dev;  // if non-null, sigma is read from here (solver state)
+  int gate;
+  int fin;
+};
+
+int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
+
+int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
+int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
+int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
+int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
+
+int launch_ms_update_x(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t s);
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
+
+int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
+int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
+int layout_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host);
+int layout_convert(sqcg_ctx* ctx, int from_prec, const void* src, int to_prec, void* dst, cudaStream_t s);
+
+int ensure_workspace(sqcg_ctx* ctx);
+void free_workspace(sqcg_ctx* ctx);
+void free_graphs(sqcg_ctx* ctx);
+
+inline int grid_for(int n, int threads) { return (n + threads - 1) / threads; }

@@ -27,3 +27,32 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def sqcg():
+    """The CUDA library's Python binding, built in-tree if needed (GPU tests only)."""
+    from paper_1611_00728_gb300 import build as _build
+
+    _build.build()
+    import paper_1611_00728_gb300 as pkg
+
+    pkg.library()
+    return pkg
+
+
+_LINK_CACHE = {}
+
+
+@pytest.fixture(scope="session")
+def links_cache():
+    """Seeded fat/long links by (dims, seed), generated once per session."""
+    import synth
+
+    def get(L, seed):
+        key = (tuple(L), seed)
+        if key not in _LINK_CACHE:
+            _LINK_CACHE[key] = synth.fat_long_links(L, seed)
+        return _LINK_CACHE[key]
+
+    return get

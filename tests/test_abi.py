@@ -1,0 +1,78 @@
+"""The C ABI library builds for sm_103a, loads without a GPU, and exports every
+function that include/sqcg.h declares. No compute call is made here."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sqcg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sqcg_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1611_00728_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("sqcg_create", "sqcg_destroy", "sqcg_load_links", "sqcg_dslash", "sqcg_cg_solve",
+                 "sqcg_multishift_cg_solve", "sqcg_strerror"):
+        assert want in names
+
+
+def test_library_loads_and_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_exported_symbols_are_c_linkage(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sqcg_[a-z0-9_]+)\b", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_library_built_for_sm_103a(libpath):
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_strerror_needs_no_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.sqcg_strerror.restype = ctypes.c_char_p
+    assert lib.sqcg_strerror(0) == b"ok"
+    assert b"invalid" in lib.sqcg_strerror(-1)
+    assert b"converged" in lib.sqcg_strerror(-3)
+
+
+def test_create_rejects_bad_extents_without_touching_the_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    h = ctypes.c_void_p()
+    for dims in [(7, 8, 8, 8), (8, 8, 8, 2), (0, 8, 8, 8)]:
+        d = (ctypes.c_int * 4)(*dims)
+        assert lib.sqcg_create(d, 1, None, ctypes.byref(h)) == -1
+    d = (ctypes.c_int * 4)(8, 8, 8, 8)
+    assert lib.sqcg_create(d, 64, None, ctypes.byref(h)) == -1  # unknown flag
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1611_00728_gb300 as pkg
+
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU path"):
+        pkg.library()

@@ -1,0 +1,197 @@
+"""GPU CG and multi-shift CG vs the FP64 oracle, through the C ABI.
+
+Every solve must reach a true relative residual <= tol, recomputed here by the
+oracle in FP64 from the returned x. Where the system is well conditioned
+(m = 0.1 on 4^4 and 8^4) the solution must also lie within 10 tol of the
+oracle's tightly converged solution; for ill-conditioned systems the check is
+the residual, which is the well-posed form of "within 10 tol" (|A(x - x*)| / |b|).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cg_8888_matches_oracle(sqcg, links_cache, mode):
+    """The small single-mass case: 8^4, m = 0.1, tol 1e-8."""
+    L, m, tol = (8, 8, 8, 8), 0.1, 1e-8
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 2100)
+    x_ref, it_ref, res_ref = oracle.cg(L, fat, lng, 4 * m * m, b, tol=1e-13)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db, dx = lat.pack(b), lat.new_spinor()
+        info = lat.cg_solve(m, db, dx, tol=tol, max_iter=1000, mode=mode)
+        x = lat.unpack(dx)
+    assert info.status == 0 and info.true_rel_resid <= tol
+    assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
+    assert rel(x, x_ref) <= 10 * tol
+    if mode == 0:
+        assert abs(info.iters - it_ref) <= 2  # same algorithm, same arithmetic up to rounding order
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cg_4444_matches_dense_lu(sqcg, links_cache, mode):
+    L, m, tol = (4, 4, 4, 4), 0.1, 1e-10
+    fat, lng = links_cache(L, 1001)
+    A = oracle.dense_normal_matrix(L, fat, lng, 4 * m * m)
+    b = synth.gaussian_source(L, 2101)
+    x_lu = np.linalg.solve(A, b.ravel()).reshape(b.shape)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, lat.pack(b), dx, tol=tol, max_iter=1000, mode=mode)
+        x = lat.unpack(dx)
+    assert info.status == 0
+    assert rel(x, x_lu) <= 10 * tol
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cg_ragged_lattice(sqcg, links_cache, mode):
+    L, m, tol = (6, 8, 10, 12), 0.05, 1e-9
+    fat, lng = links_cache(L, 55)
+    b = synth.gaussian_source(L, 9)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, lat.pack(b), dx, tol=tol, max_iter=5000, mode=mode)
+        x = lat.unpack(dx)
+    assert info.status == 0
+    assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
+
+
+def test_cg_initial_guess_and_edge_cases(sqcg, links_cache):
+    L, m = (8, 8, 8, 8), 0.1
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 2100)
+    x_ref, _, _ = oracle.cg(L, fat, lng, 4 * m * m, b, tol=1e-13)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db = lat.pack(b)
+        # starting from the solution: no iteration
+        dx = lat.pack(x_ref)
+        info = lat.cg_solve(m, db, dx, tol=1e-8, mode=1)
+        assert info.status == 0 and info.iters == 0 and info.true_rel_resid <= 1e-8
+        # b = 0 -> x = 0
+        dx = lat.pack(x_ref)
+        info = lat.cg_solve(m, lat.new_spinor(), dx, tol=1e-8)
+        assert info.status == 0 and not np.any(lat.unpack(dx))
+        # max_iter reached: NOT_CONVERGED, info filled, x is the last iterate
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, db, dx, tol=1e-12, max_iter=5, mode=0, raise_on_error=False)
+        assert info.status == -3 and info.iters == 5
+        assert 0 < info.true_rel_resid < 1
+        assert abs(oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(dx)) - info.true_rel_resid) < 1e-10
+        # NaN in the source: breakdown, no hang
+        bn = b.copy()
+        bn[3, 1] = np.nan
+        info = lat.cg_solve(m, lat.pack(bn), lat.new_spinor(), tol=1e-8, raise_on_error=False)
+        assert info.status == -4
+        # invalid arguments
+        with pytest.raises(sqcg.SqcgError) as e:
+            lat.cg_solve(m, db, lat.new_spinor(), tol=0.0)
+        assert e.value.name == "INVALID_ARG"
+        with pytest.raises(ValueError):
+            lat.cg_solve(m, db, lat.new_spinor(1))  # wrong precision for x
+
+
+def test_cg_breakdown_on_zero_mode(sqcg):
+    """sigma = 0 on the free field with a zero-momentum source: <p, A p> = 0."""
+    L = (8, 8, 8, 8)
+    fat, lng = synth.unit_links(L, 1.0, 1.0)
+    b = synth.plane_wave(L, (0, 0, 0, 0), 0, (1, 0, 0), antiperiodic_t=False)
+    with sqcg.Lattice(L, antiperiodic_t=False) as lat:
+        lat.load_links(fat, lng)
+        info = lat.cg_solve(0.0, lat.pack(b), lat.new_spinor(), tol=1e-8, raise_on_error=False)
+    assert info.status == -4
+
+
+def test_no_links_and_bad_dims(sqcg):
+    with sqcg.Lattice((8, 8, 8, 8)) as lat:
+        with pytest.raises(sqcg.SqcgError) as e:
+            lat.cg_solve(0.1, lat.new_spinor(), lat.new_spinor())
+        assert e.value.name == "NO_LINKS"
+    with pytest.raises(sqcg.SqcgError):
+        sqcg.Lattice((8, 8, 8, 5))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_multishift_8888(sqcg, links_cache, mode):
+    L, tol = (8, 8, 8, 8), 1e-8
+    fat, lng = links_cache(L, 1001)
+    shifts = np.logspace(-4, 0, 11)
+    b = synth.gaussian_source(L, 2300)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, lat.pack(b), xs, tol=tol, max_iter=20000, mode=mode)
+        got = [lat.unpack(x) for x in xs]
+    for s, info, x in zip(shifts, infos, got):
+        assert info.status == 0 and info.true_rel_resid <= tol
+        assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
+
+
+def test_multishift_unsorted_shifts_and_free_field(sqcg):
+    L = (16, 16, 16, 16)
+    c1, c3 = 0.9, -1.0 / 24.0
+    fat, lng = synth.unit_links(L, c1, c3)
+    k1, k2 = (1, 0, 0, 0), (2, 3, 1, 2)
+    b = synth.plane_wave(L, k1, 0, (1, 0, 0)) + synth.plane_wave(L, k2, 0, (0, 1, 1j))
+
+    def lam(k):
+        p = np.array([2 * np.pi * k[m] / L[m] for m in range(3)] + [(2 * k[3] + 1) * np.pi / L[3]])
+        return 4.0 * np.sum((c1 * np.sin(p) + c3 * np.sin(3 * p)) ** 2)
+
+    shifts = [0.5, 0.001, 0.05, 1.0]
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, lat.pack(b), xs, tol=[1e-10] * 4, mode=0)
+        for s, info, x in zip(shifts, infos, xs):
+            want = (synth.plane_wave(L, k1, 0, (1, 0, 0)) / (s + lam(k1))
+                    + synth.plane_wave(L, k2, 0, (0, 1, 1j)) / (s + lam(k2)))
+            assert info.status == 0
+            assert rel(lat.unpack(x), want) <= 1e-9
+
+
+def test_cg_32_single_mass_fp64_and_mixed(sqcg, links_cache):
+    """The single-mass benchmark case: 32^4, m = 0.01, both modes to true 1e-8 (oracle-checked)."""
+    L, m, tol = (32, 32, 32, 32), 0.01, 1e-8
+    fat, lng = links_cache(L, 1002)
+    b = synth.gaussian_source(L, 2200)
+    sols = {}
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db = lat.pack(b)
+        for mode in (0, 1):
+            dx = lat.new_spinor()
+            info = lat.cg_solve(m, db, dx, tol=tol, max_iter=20000, mode=mode)
+            assert info.status == 0 and info.true_rel_resid <= tol
+            sols[mode] = lat.unpack(dx)
+    for mode, x in sols.items():
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol, mode
+
+
+def test_multishift_32_mixed(sqcg, links_cache):
+    """The multi-shift benchmark case: 32^4, 11 shifts logspace(-4, 0), mixed precision, per-shift 1e-8."""
+    L, tol = (32, 32, 32, 32), 1e-8
+    fat, lng = links_cache(L, 1003)
+    shifts = np.logspace(-4, 0, 11)
+    b = synth.gaussian_source(L, 2300)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, lat.pack(b), xs, tol=tol, max_iter=20000, mode=1)
+        got = [lat.unpack(x) for x in xs]
+    for s, info, x in zip(shifts, infos, got):
+        assert info.status == 0
+        assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
