@@ -217,13 +217,13 @@ int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, doubl
   return SQCG_OK;
 }
 
-int launch_ms_update_x(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t s) {
+int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
-  if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
+  if (grid > ctx->max_blocks || nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
   MSPtrs P;
   for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
-    P.x[j] = (j < ctx->ms_nalloc) ? x[j] : nullptr;
-    P.p[j] = (j < ctx->ms_nalloc) ? ctx->ms_p[j] : nullptr;
+    P.x[j] = (j < nshift) ? x[j] : nullptr;
+    P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
   }
   if (mixed)
     k_ms_update<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->Ap32, Vh, ctx->st, ctx->partials);
@@ -233,12 +233,13 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t
   return SQCG_OK;
 }
 
-int launch_ms_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  if (nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
   MSPtrs P;
   for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
     P.x[j] = nullptr;
-    P.p[j] = (j < ctx->ms_nalloc) ? ctx->ms_p[j] : nullptr;
+    P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
   }
   if (mixed)
     k_ms_xpay<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->p32, Vh, ctx->st);

@@ -106,7 +106,7 @@ int enqueue_cg_iteration(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaS
   return SQCG_OK;
 }
 
-int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t s) {
+int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
   const int wp = mixed ? SQCG_F32 : SQCG_F64;
   void* p = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
   void* Ap = mixed ? (void*)ctx->Ap32 : (void*)ctx->Ap64;
@@ -118,8 +118,8 @@ int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream
   L.out_parity = 0; L.prec = L.out_prec = wp; L.epi = EPI_NORMAL_DOT; L.in = tmp; L.out = Ap; L.y = p;
   L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_MS_PAP;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  SQCG_TRY(launch_ms_update_x(ctx, mixed, x, s));
-  SQCG_TRY(launch_ms_xpay(ctx, mixed, s));
+  SQCG_TRY(launch_ms_update_x(ctx, mixed, nshift, x, s));
+  SQCG_TRY(launch_ms_xpay(ctx, mixed, nshift, s));
   return SQCG_OK;
 }
 
@@ -131,7 +131,7 @@ int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, i
   int rc = SQCG_OK;
   for (int k = 0; k < kChunk && rc == SQCG_OK; ++k) {
     if (kind == KIND_CG) rc = enqueue_cg_iteration(ctx, mixed, b, x[0], cs);
-    else rc = enqueue_ms_iteration(ctx, mixed, (double2* const*)x, cs);
+    else rc = enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, cs);
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);

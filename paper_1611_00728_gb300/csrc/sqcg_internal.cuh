@@ -173,8 +173,8 @@ int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
 
-int launch_ms_update_x(sqcg_ctx* ctx, int mixed, double2* const* x, cudaStream_t s);
-int launch_ms_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
+int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, cudaStream_t s);
 
 int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
