@@ -178,7 +178,26 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
   }
 }
 
+// One thread: count the WHILE-loop iterations and set its condition. The loop
+// continues while the solve is not done and the hard bound is not reached.
+__global__ void k_loop_control(SolverState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->loop_count += 1;
+  int go = !st->done && st->loop_count < st->loop_limit;
+  if (!go && !st->done) {
+    st->done = 1;
+    st->status = SQCG_ERR_NOT_CONVERGED;
+  }
+  cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, go ? 1u : 0u);
+}
+
 }  // namespace
+
+int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s) {
+  k_loop_control<<<1, 32, 0, s>>>(ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
 
 // variant with an explicit x (the solver's output vector)
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s) {

@@ -2,10 +2,11 @@
 // updates) and multi-mass (multi-shift) CG (paper Sec. 3-4: the single- and
 // multi-mass staggered CG; the multi-mass form is the benchmarked routine).
 //
-// All Krylov scalars stay in device memory (SolverState). The iteration is
-// captured once into a CUDA graph of kChunk iterations; every kernel in it is
-// gated on the device-side state, so iterations after convergence cost only
-// empty launches. The host reads the state once per chunk.
+// All Krylov scalars stay in device memory (SolverState). The whole loop is
+// one CUDA graph launch: a WHILE conditional node runs the iteration body
+// until the device-side state says done (or a hard iteration bound is hit);
+// the FP64 reliable update is an IF node inside the body. The host reads the
+// state once, after the loop.
 #include <chrono>
 #include <math.h>
 #include <stdlib.h>
@@ -15,9 +16,9 @@
 
 namespace {
 
-constexpr int kChunk = 16;
-constexpr int kCGKernelsPerIter = 6;  // enqueue_cg_iteration
-constexpr int kMSKernelsPerIter = 4;  // enqueue_ms_iteration
+constexpr int kCGKernelsPerIter = 5;  // enqueue_cg_head + xpay + loop control
+constexpr int kCGKernelsPerUpdate = 2;  // enqueue_cg_reliable
+constexpr int kMSKernelsPerIter = 5;  // enqueue_ms_iteration + loop control
 
 enum { KIND_CG = 0, KIND_MS = 1 };
 
@@ -28,6 +29,7 @@ struct CGGraph {
   const void* b;
   void* x[SQCG_MAX_SHIFTS];
   cudaGraphExec_t exec;
+  cudaGraphConditionalHandle h_while, h_if;
   CGGraph* next;
 };
 
@@ -72,37 +74,38 @@ void add_graph(sqcg_ctx* ctx, CGGraph* g) {
   ctx->graphs = g;
 }
 
-// kernels of one single-mass CG iteration (see FIN_* in solver_device.cuh)
-int enqueue_cg_iteration(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaStream_t s) {
+// Kernels of one single-mass CG iteration, before the reliable-update node:
+// tmp = D_oe p; Ap = sigma p - D_eo tmp with alpha = |r|^2/<p,Ap>;
+// x += alpha p, r -= alpha Ap with beta and the reliable-update decision.
+int enqueue_cg_head(sqcg_ctx* ctx, int mixed, void* x, cudaStream_t s) {
   const int wp = mixed ? SQCG_F32 : SQCG_F64;
   void* p = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
   void* Ap = mixed ? (void*)ctx->Ap32 : (void*)ctx->Ap64;
   void* tmp = mixed ? (void*)ctx->tmp32 : (void*)ctx->tmp64;
-  void* r = mixed ? (void*)ctx->r32 : (void*)ctx->r64;
-  const double* sigma_dev = &ctx->st->sigma;
-
   DslashLaunch L = {};
-  // tmp_o = D_oe p
   L.out_parity = 1; L.prec = L.out_prec = wp; L.epi = EPI_PLAIN; L.in = p; L.out = tmp; L.gate = GATE_ITER;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  // Ap = sigma p - D_eo tmp; alpha = |r|^2 / <p, Ap>
   L = DslashLaunch{};
   L.out_parity = 0; L.prec = L.out_prec = wp; L.epi = EPI_NORMAL_DOT; L.in = tmp; L.out = Ap; L.y = p;
-  L.sigma_dev = sigma_dev; L.gate = GATE_ITER; L.fin = FIN_PAP;
+  L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_PAP;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  // x += alpha p; r -= alpha Ap; beta, convergence / reliable-update trigger
   SQCG_TRY(launch_cg_update_x(ctx, mixed, (double2*)x, s));
-  // reliable update / final check: r = b - A x in FP64
-  L = DslashLaunch{};
+  return SQCG_OK;
+}
+
+// Body of the reliable-update IF node: r = b - A x in FP64 (written to the
+// working r), which also confirms convergence on the true residual.
+int enqueue_cg_reliable(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaStream_t s) {
+  void* r = mixed ? (void*)ctx->r32 : (void*)ctx->r64;
+  DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
   L.gate = GATE_UPDATE;
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
-  L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = wp; L.epi = EPI_TRUE_RESID; L.in = ctx->tmp64; L.out = r;
-  L.y = x; L.b = b; L.sigma_dev = sigma_dev; L.gate = GATE_UPDATE; L.fin = FIN_TRUE_RESID;
+  L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = mixed ? SQCG_F32 : SQCG_F64; L.epi = EPI_TRUE_RESID;
+  L.in = ctx->tmp64; L.out = r; L.y = x; L.b = b; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_UPDATE;
+  L.fin = FIN_TRUE_RESID;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  // p = r + beta p
-  SQCG_TRY(launch_cg_xpay(ctx, mixed, s));
   return SQCG_OK;
 }
 
@@ -123,27 +126,93 @@ int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x
   return SQCG_OK;
 }
 
+// Build the solver graph: one WHILE node whose body is one iteration followed
+// by the loop-control kernel. For single-mass CG the FP64 reliable update sits
+// in an IF node inside the body, so iterations without an update launch no
+// FP64 kernels. The conditional handles are passed to the kernels through the
+// device state (h_while, h_if).
+int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, cudaGraph_t body,
+                 cudaGraphConditionalHandle* hif, cudaGraph_t* ifbody) {
+  cudaStream_t cs = ctx->cap_stream;
+  SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = SQCG_OK;
+  if (kind == KIND_CG) {
+    rc = enqueue_cg_head(ctx, mixed, x[0], cs);
+    if (rc == SQCG_OK) {
+      cudaStreamCaptureStatus status;
+      cudaGraph_t capg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      cudaGraphNode_t inode = nullptr;
+      cudaGraphNodeParams ip = {};
+      if (cudaStreamGetCaptureInfo(cs, &status, nullptr, &capg, &deps, nullptr, &ndeps) != cudaSuccess ||
+          cudaGraphConditionalHandleCreate(hif, capg, 0, 0) != cudaSuccess) {
+        rc = SQCG_ERR_CUDA;
+      } else {
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = *hif;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        if (cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                cudaSuccess)
+          rc = SQCG_ERR_CUDA;
+        else
+          *ifbody = ip.conditional.phGraph_out[0];
+      }
+    }
+    if (rc == SQCG_OK) rc = launch_cg_xpay(ctx, mixed, cs);
+  } else {
+    rc = enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, cs);
+  }
+  if (rc == SQCG_OK) rc = launch_loop_control(ctx, cs);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "conditional node", __FILE__, __LINE__);
+  if (rc != SQCG_OK) return rc;
+  if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+  if (kind == KIND_CG) {
+    SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, *ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_cg_reliable(ctx, mixed, b, x[0], cs);
+    e = cudaStreamEndCapture(cs, &out);
+    if (rc != SQCG_OK) return rc;
+    if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+  }
+  return SQCG_OK;
+}
+
 int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, CGGraph** out) {
   CGGraph* g = find_graph(ctx, kind, mixed, b, x, nx);
   if (g) { *out = g; return SQCG_OK; }
-  cudaStream_t cs = ctx->cap_stream;
-  SQCG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t top = nullptr;
+  SQCG_CUDA_TRY(cudaGraphCreate(&top, 0));
+  cudaGraphConditionalHandle hw = 0, hif = 0;
+  cudaGraph_t ifbody = nullptr;
   int rc = SQCG_OK;
-  for (int k = 0; k < kChunk && rc == SQCG_OK; ++k) {
-    if (kind == KIND_CG) rc = enqueue_cg_iteration(ctx, mixed, b, x[0], cs);
-    else rc = enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, cs);
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wnode = nullptr;
+  if (cudaGraphConditionalHandleCreate(&hw, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    rc = SQCG_ERR_CUDA;
+  } else {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) rc = SQCG_ERR_CUDA;
   }
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(cs, &graph);
-  if (rc != SQCG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-  if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+  if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "WHILE node", __FILE__, __LINE__);
+  if (rc == SQCG_OK) rc = capture_body(ctx, kind, mixed, b, x, nx, wp.conditional.phGraph_out[0], &hif, &ifbody);
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+  if (rc == SQCG_OK) {
+    cudaError_t e = cudaGraphInstantiate(&exec, top, 0);
+    if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); rc = SQCG_ERR_CUDA; }
+  }
+  cudaGraphDestroy(top);
+  if (rc != SQCG_OK) return rc;
   g = (CGGraph*)calloc(1, sizeof(CGGraph));
   if (!g) { cudaGraphExecDestroy(exec); return SQCG_ERR_NO_MEMORY; }
   g->kind = kind; g->mixed = mixed; g->nshift = nx; g->b = b; g->exec = exec;
+  g->h_while = hw; g->h_if = hif;
   for (int j = 0; j < nx; ++j) g->x[j] = x[j];
   add_graph(ctx, g);
   *out = g;
@@ -161,16 +230,19 @@ int write_state(sqcg_ctx* ctx, cudaStream_t s) {
   return SQCG_OK;
 }
 
-// run chunks of the captured loop until the device state says done; *chunks = graphs launched
-int run_loop(sqcg_ctx* ctx, CGGraph* g, int max_iter, cudaStream_t s, int* chunks) {
-  const long max_chunks = (long)max_iter / kChunk + 8;
-  *chunks = 0;
-  for (long c = 0; c < max_chunks; ++c) {
-    SQCG_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-    *chunks += 1;
-    SQCG_TRY(read_state(ctx, s));
-    if (ctx->st_host->done) return SQCG_OK;
-  }
+// Run the whole device-side loop with one graph launch, then read the state.
+// *iters_run = WHILE-loop iterations executed (for the launch count).
+int run_loop(sqcg_ctx* ctx, CGGraph* g, int max_iter, cudaStream_t s, int* iters_run) {
+  SolverState* h = ctx->st_host;
+  h->h_while = g->h_while;
+  h->h_if = g->h_if;
+  h->use_if = (g->kind == KIND_CG) ? 1 : 0;
+  h->loop_count = 0;
+  h->loop_limit = max_iter + 4;
+  SQCG_TRY(write_state(ctx, s));
+  SQCG_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+  SQCG_TRY(read_state(ctx, s));
+  *iters_run = h->loop_count;
   return SQCG_OK;
 }
 
@@ -235,7 +307,7 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   SQCG_TRY(read_state(ctx, s));
 
   int status = SQCG_OK;
-  int launches = 3, chunks = 0;
+  int launches = 3, loops = 0;
   if (h->bb == 0.0) {  // b = 0: the solution is x = 0
     SQCG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)ctx->g.Vh * 3 * sizeof(double2), s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -250,8 +322,8 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
     CGGraph* g = nullptr;
     void* xs[1] = {x};
     SQCG_TRY(capture(ctx, KIND_CG, mixed, b, xs, 1, &g));
-    SQCG_TRY(run_loop(ctx, g, max_iter, s, &chunks));
-    launches += chunks * kChunk * kCGKernelsPerIter;
+    SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+    launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
     status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   } else {
     status = h->status;  // x0 already solves the system (or breakdown on a non-finite residual)
@@ -362,9 +434,9 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
 
   CGGraph* g = nullptr;
   SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
-  int chunks = 0;
-  SQCG_TRY(run_loop(ctx, g, max_iter, s, &chunks));
-  int launches = 1 + 1 + nshift + chunks * kChunk * kMSKernelsPerIter;
+  int loops = 0;
+  SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+  int launches = 1 + 1 + nshift + loops * kMSKernelsPerIter;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];
   for (int j = 0; j < nshift; ++j) iters_s[j] = h->iters_s[j];

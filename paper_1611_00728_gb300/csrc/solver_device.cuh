@@ -80,6 +80,7 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
         s->need_update = 1;  // reliable update
       }
       if (s->iter >= s->max_iter) s->need_update = 1;  // final true residual, then stop
+      if (s->use_if) cudaGraphSetConditional((cudaGraphConditionalHandle)s->h_if, s->need_update ? 1u : 0u);
       break;
     }
     case FIN_TRUE_RESID: {  // r = b - A x recomputed in FP64 and copied to the working r
@@ -160,9 +161,13 @@ __device__ inline void grid_reduce_finish(double v, double* partials, SolverStat
   __syncthreads();
   if (!am_last) return;
   __threadfence();
+  // L2-only loads (the partials come from other SMs); not volatile, so the
+  // compiler can issue several before the adds. Each thread adds its share in
+  // index order, so the total does not depend on timing.
   double s = 0.0;
-  const volatile double* vp = partials;
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) s += vp[j];
+  const int n = (int)gridDim.x;
+#pragma unroll 8
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += __ldcg(partials + j);
   s = block_sum(s);
   if (threadIdx.x == 0) {
     st->counter = 0;

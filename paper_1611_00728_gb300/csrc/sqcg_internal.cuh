@@ -68,8 +68,12 @@ struct SolverState {
   int need_update;  // the FP64 true-residual pass runs in this iteration
   int updates;      // reliable updates performed inside the loop
   int mixed;        // working vectors are FP32
-  int pad0;
+  int use_if;       // the reliable-update pass is an IF node whose condition FIN_UPDATE sets
   unsigned int counter;  // last-block counter of the grid reductions
+  int loop_count;        // iterations of the device-side WHILE loop so far
+  int loop_limit;        // hard bound on loop_count (the loop always ends)
+  unsigned long long h_while;  // conditional handle of the WHILE node (cudaGraphConditionalHandle)
+  unsigned long long h_if;     // conditional handle of the reliable-update IF node
 
   // multi-shift CG (Jegerlehner recurrences; shift s uses sigma + dsig[s])
   int nshift;
@@ -169,6 +173,7 @@ struct DslashLaunch {
 int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
 
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
+int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);

@@ -1,0 +1,71 @@
+"""The benchmark's multi-rank path on CPU (gloo, world size 2).
+
+The CG does not shard across GPUs here (replicas only): each rank solves its
+own system, and the process group only provides the barrier, the sum of the
+work and the max of the time. These tests run that host logic with two gloo
+ranks; nothing touches a GPU.
+"""
+
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update({"WORLD_SIZE": str(world), "RANK": str(rank), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import bench
+
+    ranks = bench.Ranks()
+    try:
+        assert ranks.backend == "gloo"
+        ranks.barrier()
+        # rank r did (r + 1) GFLOP in (r + 1) * 0.5 s
+        rate, tmax = bench.whole_job_rate((rank + 1) * 1e9, (rank + 1) * 0.5, ranks)
+        q.put((rank, rate, tmax))
+        # the reference arm runs on rank 0 only; other ranks return without work
+        if rank != 0:
+            class A:
+                steps, warmup, gpus = 1, 0, world
+
+            bench.run_reference(A(), ranks)
+            q.put((rank, "ref-skipped", None))
+    finally:
+        ranks.close()
+
+
+def test_whole_job_rate_two_gloo_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    out = [q.get(timeout=5) for _ in range(3)]
+    rates = [o for o in out if o[1] != "ref-skipped"]
+    assert len(rates) == 2
+    for _, rate, tmax in rates:
+        assert tmax == pytest.approx(1.0)          # max over ranks
+        assert rate == pytest.approx(3.0)          # (1 + 2) GFLOP / 1.0 s
+    assert any(o[1] == "ref-skipped" and o[0] == 1 for o in out)
+
+
+def test_single_rank_needs_no_process_group(monkeypatch):
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    import bench
+
+    ranks = bench.Ranks()
+    assert ranks.dist is None
+    rate, tmax = bench.whole_job_rate(2e9, 0.5, ranks)
+    assert rate == pytest.approx(4.0) and tmax == 0.5
