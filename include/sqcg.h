@@ -34,6 +34,11 @@
  *  - Return value: SQCG_OK (0) or a negative SQCG_ERR_* code; sqcg_strerror
  *    gives a message. Nothing aborts the process and no kernel traps.
  *  - A context is not thread-safe: one host thread at a time per context.
+ *  - Solver loops run on the device as one CUDA graph launch (conditional
+ *    WHILE/IF nodes). With the environment variable SQCG_LAUNCH_MODE=eager the
+ *    single-mass and multi-shift solvers launch the same kernels one at a time
+ *    with a host round trip per iteration instead (kernel-level profilers do
+ *    not list kernels inside conditional graph nodes); results are identical.
  */
 #ifndef SQCG_H
 #define SQCG_H
@@ -151,6 +156,31 @@ int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol
 int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, const void* b,
                              void* const* x, const double* tol, int max_iter, int mode,
                              sqcg_info* info);
+
+/* Batched CG: solve (4 mass[k]^2 - D_eo D_oe) x = b for nrhs[k] right-hand
+ * sides on each of nctx lattices (1 <= nctx <= 16, sum of nrhs <= 256) in one
+ * device-side loop, mixed precision (FP32 Dslash and Krylov vectors, FP64 x,
+ * reductions and reliable updates). This applies the paper's single-mass CG
+ * (Sec. 3) to many sources at once; batching is not in the paper. Each link is
+ * loaded once per block of W right-hand sides. W (1..16) and the site-block
+ * size are picked on the first call for a given set of lattices by timing the
+ * multi-RHS Dslash (cached per process, and in the file named by the
+ * environment variable SQCG_TUNE_CACHE if set).
+ * ctx[k]: distinct contexts with links loaded, all on the current device; the
+ * work runs on ctx[0]'s stream. b[k], x[k]: device arrays of nrhs[k]
+ * consecutive FP64 device vectors ([nrhs][3][Vh] complex double); x[k] holds
+ * the initial guesses and receives the solutions. tol: FP64 true relative
+ * residual target for every RHS. info: NULL or sum(nrhs) entries, lattice-major.
+ * Workspace (about 48 bytes per site and RHS) is cached with ctx[0] for
+ * repeated calls with the same arguments. Returns SQCG_OK when every RHS
+ * converged, else the first failing status. Synchronises the stream. */
+int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
+                          const void* const* b, void* const* x, double tol, int max_iter,
+                          sqcg_info* info);
+
+/* RHS block width W and site-block size T chosen by the autotuner for the
+ * batched solve cached with ctx (the ctx passed first to the last batched call). */
+int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T);
 
 const char* sqcg_strerror(int status);
 

@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = [
     "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
-    "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE",
+    "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
+    "batched_tuning",
 ]
 
 F64, F32 = 0, 1
@@ -81,11 +82,13 @@ def library():
         lib.sqcg_normal_op.argtypes = [P, D, I, P, P]
         lib.sqcg_cg_solve.argtypes = [P, D, P, P, D, I, I, ctypes.POINTER(Info)]
         lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
+        lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
+        lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.sqcg_strerror.argtypes = [I]
         lib.sqcg_strerror.restype = ctypes.c_char_p
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
-                     "sqcg_multishift_cg_solve"):
+                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning"):
             getattr(lib, name).restype = I
         _lib = lib
     return _lib
@@ -233,3 +236,48 @@ class Lattice:
         if raise_on_error:
             _check(rc, "sqcg_multishift_cg_solve")
         return list(infos)
+
+
+def cg_solve_batched(lattices, masses, bs, xs, tol: float = 1e-8, max_iter: int = 10000,
+                     raise_on_error: bool = True):
+    """Batched mixed-precision CG over several lattices and many right-hand sides.
+
+    lattices: list of Lattice (links loaded); masses: one mass per lattice;
+    bs[k], xs[k]: contiguous CUDA float64 tensors (nrhs_k, 3, Vh_k, 2) holding
+    the sources and the initial guesses / solutions. Returns a list (one per
+    lattice) of lists of Info (one per RHS)."""
+    n = len(lattices)
+    if not (len(masses) == len(bs) == len(xs) == n):
+        raise ValueError("one mass, b and x per lattice")
+    torch = _torch()
+    nrhs = []
+    for lat, b, x in zip(lattices, bs, xs):
+        for t in (b, x):
+            if t.dtype != torch.float64 or t.dim() != 4 or tuple(t.shape[1:]) != (3, lat.Vh, 2) or not t.is_cuda \
+                    or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous CUDA float64 tensor (nrhs, 3, {lat.Vh}, 2)")
+        if b.shape[0] != x.shape[0]:
+            raise ValueError("b and x must hold the same number of right-hand sides")
+        nrhs.append(int(b.shape[0]))
+    lattices[0]._sync_stream()
+    ctxs = (ctypes.c_void_p * n)(*[lat._h.value for lat in lattices])
+    nr = (ctypes.c_int * n)(*nrhs)
+    ms = (ctypes.c_double * n)(*[float(m) for m in masses])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (Info * sum(nrhs))()
+    rc = library().sqcg_cg_solve_batched(n, ctxs, nr, ms, bp, xp, float(tol), int(max_iter), infos)
+    if raise_on_error:
+        _check(rc, "sqcg_cg_solve_batched")
+    out, k = [], 0
+    for r in nrhs:
+        out.append(list(infos[k:k + r]))
+        k += r
+    return out
+
+
+def batched_tuning(lattice) -> tuple[int, int]:
+    """(RHS block width, site block size) the autotuner chose for the last batched solve led by lattice."""
+    W, T = ctypes.c_int(), ctypes.c_int()
+    _check(library().sqcg_batched_tuning(lattice._h, ctypes.byref(W), ctypes.byref(T)), "sqcg_batched_tuning")
+    return W.value, T.value

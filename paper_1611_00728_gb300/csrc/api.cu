@@ -95,6 +95,7 @@ int sqcg_destroy(sqcg_ctx* ctx) {
   if (!ctx) return SQCG_OK;
   cudaStreamSynchronize(ctx->stream);
   free_graphs(ctx);
+  free_batch_plan(ctx);
   free_workspace(ctx);
   cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
   cudaFree(ctx->stage);

@@ -1,0 +1,995 @@
+// Batched multi-RHS CG over several lattices of different volumes in one
+// device-side loop (the single-mass CG of arXiv:1611.00728 Sec. 3 applied to
+// many sources at once; mixed precision with FP64 reliable updates).
+//
+// Work decomposition: a tile is (lattice, RHS block of width W, block of T
+// sites). One launch per phase covers the tiles of every lattice, so the small
+// lattices ride along with the large one instead of paying their own launch
+// and tail. Within a tile each thread owns one site and applies every link it
+// loads to the W right-hand sides of the block, so the link stream (96% of the
+// single-RHS bytes) is paid once per W sources: 1152/W + 48 bytes per
+// site-RHS in FP32. Tiles are ordered with the RHS blocks of one site block
+// adjacent, so when W < nrhs the other blocks find the links in L2.
+//
+// Every RHS has its own CG scalars in BatchState; the per-RHS dot products are
+// reduced deterministically per RHS block (warp shuffle -> block -> last tile
+// of the block in site-block order). The loop is one CUDA graph: a WHILE node
+// around [D_oe p, A p with <p,Ap>, x/r update, IF(reliable update in FP64),
+// p update, loop control]. W and T are chosen by a small autotuner that times
+// the FP32 multi-RHS Dslash over the whole batch and caches the choice.
+#include <chrono>
+#include <map>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <string>
+
+#include "solver_device.cuh"
+#include "sqcg_internal.cuh"
+
+namespace {
+
+constexpr int kMaxT = 256;    // largest site block (threads per CTA)
+constexpr int kMinT = 64;     // smallest site block
+constexpr int kW64 = 4;       // RHS per pass in the FP64 kernels (register budget)
+
+struct LatDev {
+  Geom g;
+  const float2* fat32[2];
+  const float2* lng32[2];
+  const double2* fat64[2];
+  const double2* lng64[2];
+  int nl, recon;
+  float inv_s0_f;
+  double inv_s0_d;
+  int rhs0, nrhs;  // global index of the first RHS, count
+  int nsb;         // site blocks of T sites
+  int nrb, rb0;    // FP32 RHS blocks of width W, global index of the first
+  int nrb64, rb640;  // FP64 RHS blocks of width min(W, kW64)
+  int tile0, tile640;  // first FP32 / FP64 tile
+  float2 *r, *p, *Ap, *tmp;  // [nrhs][3][Vh]
+  double2* x;
+  double2* tmp64;
+  const double2* b;
+};
+
+template <typename R> struct V2;
+template <> struct V2<double> { typedef double2 T; };
+template <> struct V2<float> { typedef float2 T; };
+
+template <typename R2>
+__device__ __forceinline__ R2 mk2(decltype(R2().x) a, decltype(R2().x) b) { R2 r; r.x = a; r.y = b; return r; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// decode a tile into (lattice, RHS block, site block); RHS blocks fastest
+__device__ __forceinline__ int find_lat(const LatDev* lats, int nlat, int tile, bool fp64) {
+  int k = 0;
+  for (int j = 1; j < nlat; ++j)
+    if (tile >= (fp64 ? lats[j].tile640 : lats[j].tile0)) k = j;
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// per-RHS CG scalar steps (same rules as the single-mass solver)
+// ---------------------------------------------------------------------------
+enum BFin { BFIN_BB = 1, BFIN_INIT = 2, BFIN_PAP = 3, BFIN_UPDATE = 4, BFIN_TRUE = 5 };
+
+__device__ void rhs_finish(RhsScalars& s, const BatchState* st, int fin, double v) {
+  switch (fin) {
+    case BFIN_BB:
+      s.bb = v;
+      s.stop_rr *= v;
+      break;
+    case BFIN_INIT:
+      if (!isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; break; }
+      s.rr = s.rr_true = s.rr_max = s.rr_prev = v;
+      s.iter_last_update = 0;
+      if (v <= s.stop_rr) { s.active = 0; s.status = SQCG_OK; }
+      break;
+    case BFIN_PAP:
+      if (!s.active) break;
+      s.pAp = v;
+      if (!(v > 0.0) || !isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; s.need_update = 0; break; }
+      s.alpha = s.rr / v;
+      break;
+    case BFIN_UPDATE:
+      if (!s.active) break;
+      if (!isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; s.need_update = 0; break; }
+      s.iter += 1;
+      s.rr_prev = s.rr;
+      s.rr = v;
+      s.beta = v / s.rr_prev;
+      if (v > s.rr_max) s.rr_max = v;
+      if (v <= s.stop_rr || v < st->delta2 * s.rr_max || s.iter - s.iter_last_update >= st->update_interval ||
+          s.iter >= st->max_iter)
+        s.need_update = 1;
+      break;
+    case BFIN_TRUE:  // every active RHS of an updated block takes the FP64 residual
+      if (!s.active) break;
+      if (!isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; s.need_update = 0; break; }
+      s.rr_true = v;
+      s.need_update = 0;
+      s.updates += 1;
+      s.iter_last_update = s.iter;
+      s.rr_max = v;
+      if (v <= s.stop_rr) { s.active = 0; s.status = SQCG_OK; }
+      else if (s.iter >= st->max_iter) { s.active = 0; s.status = SQCG_ERR_NOT_CONVERGED; }
+      else { s.beta = v / s.rr_prev; s.rr = v; }
+      break;
+    default:
+      break;
+  }
+}
+
+// Reduce W per-thread values over the tile, then over all site blocks of the
+// RHS block (last tile of the block sums the partials in order) and run the
+// per-RHS step. counter: index of this RHS block's arrival counter.
+template <int W>
+__device__ void rhs_block_reduce(double (&v)[W], const LatDev& L, int rb, int wbase, int nw, int sb, BatchState* st,
+                                 double* partials, int max_nsb, int counter, int fin) {
+  __shared__ double red[W][kMaxT / 32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const double t = warp_sum(v[w]);
+    if (lane == 0) red[w][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nw) {
+    double t = 0.0;
+    for (int j = 0; j < nwarps; ++j) t += red[threadIdx.x][j];
+    partials[(size_t)(L.rhs0 + wbase + threadIdx.x) * max_nsb + sb] = t;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(&st->counter[counter], 1u);
+    am_last = (t == (unsigned)L.nsb - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int w = wid; w < nw; w += nwarps) {
+    const int g = L.rhs0 + wbase + w;
+    double s = 0.0;
+    for (int j = lane; j < L.nsb; j += 32) s += __ldcg(partials + (size_t)g * max_nsb + j);
+    s = warp_sum(s);
+    if (lane == 0) rhs_finish(st->r[g], st, fin, s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st->counter[counter] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// multi-RHS Dslash
+// ---------------------------------------------------------------------------
+template <typename R, bool RECONS>
+__device__ __forceinline__ void load_link_m(typename V2<R>::T (&U)[9], const typename V2<R>::T* __restrict__ base,
+                                            int Vh, int idx, bool recon, R inv_s) {
+  typedef typename V2<R>::T R2;
+  if (!recon) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = __ldg(base + (size_t)e * Vh + idx);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) U[e] = __ldg(base + (size_t)e * Vh + idx);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int k = (j + 1) % 3, l = (j + 2) % 3;
+      const R2 ak = U[k], al = U[l], bk = U[3 + k], bl = U[3 + l];
+      const R re = ak.x * bl.x - ak.y * bl.y - (al.x * bk.x - al.y * bk.y);
+      const R im = ak.x * bl.y + ak.y * bl.x - (al.x * bk.y + al.y * bk.x);
+      U[6 + j] = mk2<R2>(re * inv_s, -im * inv_s);
+    }
+  }
+}
+
+template <typename R, int W, bool DAG>
+__device__ __forceinline__ void apply_w(typename V2<R>::T (&acc)[W][3], const typename V2<R>::T (&U)[9],
+                                        const typename V2<R>::T* __restrict__ in, int Vh, int idx, int nw) {
+  typedef typename V2<R>::T R2;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    if (w < nw) {
+      R2 v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] = __ldg(in + ((size_t)w * 3 + c) * Vh + idx);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (!DAG) {
+            const R2 u = U[a * 3 + b];
+            acc[w][a].x = fma(u.x, v[b].x, acc[w][a].x);
+            acc[w][a].x = fma(-u.y, v[b].y, acc[w][a].x);
+            acc[w][a].y = fma(u.x, v[b].y, acc[w][a].y);
+            acc[w][a].y = fma(u.y, v[b].x, acc[w][a].y);
+          } else {
+            const R2 u = U[b * 3 + a];
+            acc[w][a].x = fma(-u.x, v[b].x, acc[w][a].x);
+            acc[w][a].x = fma(-u.y, v[b].y, acc[w][a].x);
+            acc[w][a].y = fma(-u.x, v[b].y, acc[w][a].y);
+            acc[w][a].y = fma(u.y, v[b].x, acc[w][a].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+// acc[w] = D in[w] at site i of parity par, for nw <= W right-hand sides
+template <typename R, int W>
+__device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i, const typename V2<R>::T* in,
+                                                 int nw, typename V2<R>::T (&acc)[W][3]) {
+  typedef typename V2<R>::T R2;
+  const Geom& g = L.g;
+  const int Vh = g.Vh;
+  const int xh = i % g.Lxh;
+  int rr = i / g.Lxh;
+  const int y = rr % g.Ly;
+  rr /= g.Ly;
+  const int z = rr % g.Lz;
+  const int t = rr / g.Lz;
+  const int x = 2 * xh + ((y + z + t + par) & 1);
+  const int row = i - xh;
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[w][c] = mk2<R2>(R(0), R(0));
+  const R2* fat_p;
+  const R2* fat_q;
+  const R2* lng_p;
+  const R2* lng_q;
+  R inv_s0;
+  if constexpr (sizeof(R) == 8) {
+    fat_p = L.fat64[par]; fat_q = L.fat64[1 - par]; lng_p = L.lng64[par]; lng_q = L.lng64[1 - par];
+    inv_s0 = (R)L.inv_s0_d;
+  } else {
+    fat_p = L.fat32[par]; fat_q = L.fat32[1 - par]; lng_p = L.lng32[par]; lng_q = L.lng32[1 - par];
+    inv_s0 = (R)L.inv_s0_f;
+  }
+  const bool recon = L.recon != 0;
+  R2 U[9];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    R inv_f = inv_s0, inv_b = inv_s0;
+    if (recon) {
+      int e = 0;
+      if (mu == 1) e = x;
+      if (mu == 2) e = x + y;
+      if (mu == 3) e = x + y + z;
+      if (e & 1) { inv_f = -inv_f; inv_b = -inv_b; }
+      if (mu == 3 && g.apbc) {
+        if (t + 3 >= g.Lt) inv_f = -inv_f;
+        if (t < 3) inv_b = -inv_b;
+      }
+    }
+    const int cmu = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
+    const int Lmu = (mu == 0) ? g.Lx : (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+    const int smu = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int d = (k == 0) ? 1 : 3;
+      int fwd, bwd;
+      if (mu == 0) {
+        int xp = x + d; if (xp >= g.Lx) xp -= g.Lx;
+        int xm = x - d; if (xm < 0) xm += g.Lx;
+        fwd = row + (xp >> 1);
+        bwd = row + (xm >> 1);
+      } else {
+        fwd = i + d * smu; if (cmu + d >= Lmu) fwd -= Lmu * smu;
+        bwd = i - d * smu; if (cmu - d < 0) bwd += Lmu * smu;
+      }
+      if (k == 0) {
+        load_link_m<R, false>(U, fat_p + (size_t)mu * 9 * Vh, Vh, i, false, R(1));
+        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw);
+        load_link_m<R, false>(U, fat_q + (size_t)mu * 9 * Vh, Vh, bwd, false, R(1));
+        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
+      } else {
+        load_link_m<R, true>(U, lng_p + (size_t)mu * L.nl * Vh, Vh, i, recon, inv_f);
+        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw);
+        load_link_m<R, true>(U, lng_q + (size_t)mu * L.nl * Vh, Vh, bwd, recon, inv_b);
+        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
+      }
+    }
+  }
+}
+
+enum MEpi { M_PLAIN = 0, M_NORMAL_DOT = 1, M_TRUE_RESID = 2 };
+enum MVec { V_P = 0, V_TMP = 1, V_X = 2, V_TMP64 = 3 };
+
+struct MArgs {
+  const LatDev* lats;
+  int nlat;
+  int par;       // output parity
+  int in_vec;    // MVec of the input
+  int epi;
+  int gate;      // GATE_NONE, GATE_ITER (RHS block active), GATE_UPDATE (RHS block needs update)
+  BatchState* st;
+  double* partials;
+  int max_nsb;
+  int W;         // RHS block width of the FP32 blocks (gates refer to these blocks)
+  int write_p;   // M_TRUE_RESID at initialisation: also copy r into p
+};
+
+template <typename R, int W>
+__global__ void __launch_bounds__(kMaxT) k_mrhs_dslash(MArgs a) {
+  typedef typename V2<R>::T R2;
+  constexpr bool F64 = sizeof(R) == 8;
+  const int tile = blockIdx.x;
+  const int k = find_lat(a.lats, a.nlat, tile, F64);
+  const LatDev& L = a.lats[k];
+  const int local = tile - (F64 ? L.tile640 : L.tile0);
+  const int nrb = F64 ? L.nrb64 : L.nrb;
+  const int rb = local % nrb, sb = local / nrb;
+  const int wbase = rb * W;
+  const int nw = min(W, L.nrhs - wbase);
+  const int blk = L.rb0 + wbase / a.W;  // FP32 block that holds these RHS
+  if (a.gate == GATE_ITER && !a.st->blk_active[blk]) return;
+  if (a.gate == GATE_UPDATE && !a.st->blk_update[blk]) return;
+  const int Vh = L.g.Vh;
+  const int i = sb * blockDim.x + threadIdx.x;
+  double part[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) part[w] = 0.0;
+  const R2* in;
+  if constexpr (F64) in = (a.in_vec == V_X ? (const R2*)L.x : (const R2*)L.tmp64);
+  else in = (a.in_vec == V_P ? (const R2*)L.p : (const R2*)L.tmp);
+  in += (size_t)wbase * 3 * Vh;
+  if (i < Vh) {
+    R2 acc[W][3];
+    dslash_mrhs_site<R, W>(L, a.par, i, in, nw, acc);
+    if (a.epi == M_PLAIN) {
+      R2* out = (F64 ? (R2*)L.tmp64 : (R2*)L.tmp) + (size_t)wbase * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        if (w < nw)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
+    } else if constexpr (!F64) {  // M_NORMAL_DOT (FP32): Ap = sigma p - D tmp, <p, Ap>
+      const R2* y = (const R2*)L.p + (size_t)wbase * 3 * Vh;
+      R2* out = (R2*)L.Ap + (size_t)wbase * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        if (w < nw) {
+          const R sig = (R)a.st->r[L.rhs0 + wbase + w].sigma;
+          R dot = R(0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const size_t o = ((size_t)w * 3 + c) * Vh + i;
+            const R2 yc = __ldg(y + o);
+            const R2 v = mk2<R2>(sig * yc.x - acc[w][c].x, sig * yc.y - acc[w][c].y);
+            out[o] = v;
+            dot = fma(yc.x, v.x, fma(yc.y, v.y, dot));
+          }
+          part[w] = (double)dot;
+        }
+      }
+    } else {  // M_TRUE_RESID (FP64): r = b - sigma x + D tmp64, |r|^2; r (FP32) and optionally p
+      const double2* xb = L.x + (size_t)wbase * 3 * Vh;
+      const double2* bb = L.b + (size_t)wbase * 3 * Vh;
+      float2* rb32 = L.r + (size_t)wbase * 3 * Vh;
+      float2* pb32 = L.p + (size_t)wbase * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        if (w < nw) {
+          const double sig = a.st->r[L.rhs0 + wbase + w].sigma;
+          double n2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const size_t o = ((size_t)w * 3 + c) * Vh + i;
+            const double2 xc = __ldg(xb + o), bc = __ldg(bb + o);
+            const double re = bc.x - sig * xc.x + (double)acc[w][c].x;
+            const double im = bc.y - sig * xc.y + (double)acc[w][c].y;
+            const float2 f = make_float2((float)re, (float)im);
+            rb32[o] = f;
+            if (a.write_p) pb32[o] = f;
+            n2 += re * re + im * im;
+          }
+          part[w] = n2;
+        }
+      }
+    }
+  }
+  if (a.epi != M_PLAIN) {
+    const int fin = (a.epi == M_NORMAL_DOT) ? BFIN_PAP : (a.write_p ? BFIN_INIT : BFIN_TRUE);
+    const int counter = F64 ? (SQCG_MAX_BATCH_RHS + L.rb640 + rb) : (L.rb0 + rb);
+    rhs_block_reduce<W>(part, L, rb, wbase, nw, sb, a.st, a.partials, a.max_nsb, counter, fin);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multi-RHS BLAS: x += alpha p, r -= alpha Ap (|r|^2); p = r + beta p; |b|^2
+// ---------------------------------------------------------------------------
+enum MBlas { B_UPDATE = 0, B_XPAY = 1, B_NORM_B = 2 };
+
+struct BArgs {
+  const LatDev* lats;
+  int nlat;
+  int op;
+  BatchState* st;
+  double* partials;
+  int max_nsb;
+  int W;
+};
+
+template <int W>
+__global__ void __launch_bounds__(kMaxT) k_mrhs_blas(BArgs a) {
+  const int tile = blockIdx.x;
+  const int k = find_lat(a.lats, a.nlat, tile, false);
+  const LatDev& L = a.lats[k];
+  const int local = tile - L.tile0;
+  const int rb = local % L.nrb, sb = local / L.nrb;
+  const int wbase = rb * W;
+  const int nw = min(W, L.nrhs - wbase);
+  const int blk = L.rb0 + rb;
+  if (a.op != B_NORM_B && !a.st->blk_active[blk]) return;
+  const int Vh = L.g.Vh;
+  const int i = sb * blockDim.x + threadIdx.x;
+  double part[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) part[w] = 0.0;
+  if (i < Vh) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      if (w >= nw) continue;
+      const RhsScalars& s = a.st->r[L.rhs0 + wbase + w];
+      const size_t base = (size_t)(wbase + w) * 3 * Vh;
+      if (a.op == B_NORM_B) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 v = L.b[base + (size_t)c * Vh + i];
+          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
+        }
+        part[w] = n2;
+      } else if (!s.active) {
+        continue;
+      } else if (a.op == B_UPDATE) {
+        const double al = s.alpha;
+        const float fa = (float)al;
+        float n2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = base + (size_t)c * Vh + i;
+          const float2 pc = L.p[o], apc = L.Ap[o];
+          float2 rc = L.r[o];
+          double2 xc = L.x[o];
+          xc.x = fma(al, (double)pc.x, xc.x);
+          xc.y = fma(al, (double)pc.y, xc.y);
+          L.x[o] = xc;
+          rc.x = fmaf(-fa, apc.x, rc.x);
+          rc.y = fmaf(-fa, apc.y, rc.y);
+          L.r[o] = rc;
+          n2 = fmaf(rc.x, rc.x, fmaf(rc.y, rc.y, n2));
+        }
+        part[w] = (double)n2;
+      } else {  // B_XPAY
+        const float be = (float)s.beta;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = base + (size_t)c * Vh + i;
+          const float2 rc = L.r[o];
+          float2 pc = L.p[o];
+          pc.x = fmaf(be, pc.x, rc.x);
+          pc.y = fmaf(be, pc.y, rc.y);
+          L.p[o] = pc;
+        }
+      }
+    }
+  }
+  if (a.op != B_XPAY)
+    rhs_block_reduce<W>(part, L, rb, wbase, nw, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb,
+                        a.op == B_UPDATE ? BFIN_UPDATE : BFIN_BB);
+}
+
+// One thread: which RHS blocks need the FP64 reliable update -> IF condition
+__global__ void k_batch_ctl_update(BatchState* st, const LatDev* lats, int nlat, int W) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int any = 0;
+  for (int k = 0; k < nlat; ++k) {
+    const LatDev& L = lats[k];
+    for (int rb = 0; rb < L.nrb; ++rb) {
+      int u = 0;
+      for (int w = rb * W; w < min((rb + 1) * W, L.nrhs); ++w) u |= st->r[L.rhs0 + w].need_update;
+      st->blk_update[L.rb0 + rb] = u;
+      any |= u;
+    }
+  }
+  st->if_runs += any;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_if, any ? 1u : 0u);
+}
+
+// One thread: active RHS blocks, loop count and the WHILE condition
+__global__ void k_batch_ctl_loop(BatchState* st, const LatDev* lats, int nlat, int W) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->loop_count += 1;
+  int any = 0;
+  for (int k = 0; k < nlat; ++k) {
+    const LatDev& L = lats[k];
+    for (int rb = 0; rb < L.nrb; ++rb) {
+      int a = 0;
+      for (int w = rb * W; w < min((rb + 1) * W, L.nrhs); ++w) a |= st->r[L.rhs0 + w].active;
+      st->blk_active[L.rb0 + rb] = a;
+      any |= a;
+    }
+  }
+  const int go = any && st->loop_count < st->loop_limit;
+  if (!go && any) {  // hard bound reached: stop every RHS that is still running
+    for (int j = 0; j < st->nrhs; ++j)
+      if (st->r[j].active) { st->r[j].active = 0; st->r[j].status = SQCG_ERR_NOT_CONVERGED; }
+  }
+  cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, go ? 1u : 0u);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  int nlat;
+  sqcg_ctx* ctx[SQCG_MAX_LATTICES];
+  unsigned long long gen[SQCG_MAX_LATTICES];
+  int nrhs[SQCG_MAX_LATTICES];
+  const void* b[SQCG_MAX_LATTICES];
+  void* x[SQCG_MAX_LATTICES];
+  int W, T;              // tuned RHS block width and site block
+  int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
+  int nblk;              // FP32 RHS blocks over all lattices
+  int max_nsb;
+  int nrhs_total;
+  LatDev host[SQCG_MAX_LATTICES];
+  LatDev* dev;           // device copy of host[]
+  void* work[SQCG_MAX_LATTICES];  // per lattice: r, p, Ap, tmp (FP32) and tmp64 (FP64)
+  double* partials;
+  BatchState* st;
+  BatchState* st_host;
+  cudaGraphExec_t exec;
+  cudaGraphConditionalHandle h_while, h_if;
+};
+
+extern unsigned long long sqcg_links_generation(const sqcg_ctx* ctx);
+
+namespace {
+
+std::map<std::string, std::pair<int, int>>& tune_cache() {
+  static std::map<std::string, std::pair<int, int>> m;
+  return m;
+}
+
+bool tune_file_loaded = false;
+
+void tune_file_load() {
+  if (tune_file_loaded) return;
+  tune_file_loaded = true;
+  const char* path = getenv("SQCG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[512];
+  int W, T;
+  while (fscanf(f, "%511s %d %d", key, &W, &T) == 3) tune_cache()[key] = {W, T};
+  fclose(f);
+}
+
+void tune_file_store(const std::string& key, int W, int T) {
+  const char* path = getenv("SQCG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d\n", key.c_str(), W, T);
+  fclose(f);
+}
+
+std::string tune_key(const BatchPlan& P) {
+  std::string k = "mrhs_dslash_f32";
+  char buf[128];
+  for (int j = 0; j < P.nlat; ++j) {
+    const Geom& g = P.host[j].g;
+    snprintf(buf, sizeof(buf), ":%dx%dx%dx%d/r%d/n%d", g.Lx, g.Ly, g.Lz, g.Lt, P.host[j].recon, P.nrhs[j]);
+    k += buf;
+  }
+  return k;
+}
+
+// tiles, blocks and first indices for a given W and T
+void layout_tiles(BatchPlan& P, int W, int T) {
+  int tile = 0, tile64 = 0, rb0 = 0, rb640 = 0;
+  const int W64 = W < kW64 ? W : kW64;
+  for (int k = 0; k < P.nlat; ++k) {
+    LatDev& L = P.host[k];
+    L.nsb = grid_for(L.g.Vh, T);
+    L.nrb = grid_for(L.nrhs, W);
+    L.nrb64 = grid_for(L.nrhs, W64);
+    L.rb0 = rb0;
+    L.rb640 = rb640;
+    L.tile0 = tile;
+    L.tile640 = tile64;
+    tile += L.nsb * L.nrb;
+    tile64 += L.nsb * L.nrb64;
+    rb0 += L.nrb;
+    rb640 += L.nrb64;
+  }
+  P.W = W;
+  P.T = T;
+  P.ntiles = tile;
+  P.ntiles64 = tile64;
+  P.nblk = rb0;
+}
+
+template <typename R>
+int launch_mrhs_dslash_w(int W, int grid, int T, cudaStream_t s, const MArgs& a) {
+  switch (W) {
+    case 1: k_mrhs_dslash<R, 1><<<grid, T, 0, s>>>(a); break;
+    case 2: k_mrhs_dslash<R, 2><<<grid, T, 0, s>>>(a); break;
+    case 4: k_mrhs_dslash<R, 4><<<grid, T, 0, s>>>(a); break;
+    case 8: if constexpr (sizeof(R) == 4) { k_mrhs_dslash<R, 8><<<grid, T, 0, s>>>(a); break; } else return SQCG_ERR_INVALID_ARG;
+    case 16: if constexpr (sizeof(R) == 4) { k_mrhs_dslash<R, 16><<<grid, T, 0, s>>>(a); break; } else return SQCG_ERR_INVALID_ARG;
+    default: return SQCG_ERR_INVALID_ARG;
+  }
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_mrhs_blas(const BatchPlan& P, int op, cudaStream_t s) {
+  BArgs a;
+  a.lats = P.dev; a.nlat = P.nlat; a.op = op; a.st = P.st; a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W;
+  switch (P.W) {
+    case 1: k_mrhs_blas<1><<<P.ntiles, P.T, 0, s>>>(a); break;
+    case 2: k_mrhs_blas<2><<<P.ntiles, P.T, 0, s>>>(a); break;
+    case 4: k_mrhs_blas<4><<<P.ntiles, P.T, 0, s>>>(a); break;
+    case 8: k_mrhs_blas<8><<<P.ntiles, P.T, 0, s>>>(a); break;
+    case 16: k_mrhs_blas<16><<<P.ntiles, P.T, 0, s>>>(a); break;
+    default: return SQCG_ERR_INVALID_ARG;
+  }
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+MArgs margs(const BatchPlan& P, int par, int in_vec, int epi, int gate, int write_p) {
+  MArgs a;
+  a.lats = P.dev; a.nlat = P.nlat; a.par = par; a.in_vec = in_vec; a.epi = epi; a.gate = gate; a.st = P.st;
+  a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W; a.write_p = write_p;
+  return a;
+}
+
+int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
+  return launch_mrhs_dslash_w<float>(P.W, P.ntiles, P.T, s, margs(P, par, in_vec, epi, gate, 0));
+}
+
+int launch_f64(const BatchPlan& P, int par, int in_vec, int epi, int gate, int write_p, cudaStream_t s) {
+  const int W64 = P.W < kW64 ? P.W : kW64;
+  return launch_mrhs_dslash_w<double>(W64, P.ntiles64, P.T, s, margs(P, par, in_vec, epi, gate, write_p));
+}
+
+int upload_lats(BatchPlan& P, cudaStream_t s) {
+  SQCG_CUDA_TRY(cudaMemcpyAsync(P.dev, P.host, sizeof(LatDev) * P.nlat, cudaMemcpyHostToDevice, s));
+  return SQCG_OK;
+}
+
+// time the FP32 multi-RHS Dslash over the batch for each (W, T); keep the fastest
+int autotune(BatchPlan& P, cudaStream_t s) {
+  tune_file_load();
+  const std::string key = tune_key(P);
+  auto it = tune_cache().find(key);
+  int maxr = 0;
+  for (int k = 0; k < P.nlat; ++k) maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
+  if (it != tune_cache().end()) {
+    layout_tiles(P, it->second.first, it->second.second);
+    return upload_lats(P, s);
+  }
+  cudaEvent_t e0, e1;
+  SQCG_CUDA_TRY(cudaEventCreate(&e0));
+  SQCG_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestW = 1, bestT = 128;
+  const int Ws[] = {1, 2, 4, 8, 16};
+  const int Ts[] = {64, 128, 256};
+  int rc = SQCG_OK;
+  for (int W : Ws) {
+    if (W > 1 && W / 2 >= maxr) break;  // wider blocks than any lattice's RHS count only add idle lanes
+    for (int T : Ts) {
+      layout_tiles(P, W, T);
+      if ((rc = upload_lats(P, s)) != SQCG_OK) break;
+      for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+      if (rc != SQCG_OK) break;
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 5 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+      cudaEventRecord(e1, s);
+      if (rc != SQCG_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestW = W; bestT = T; }
+    }
+    if (rc != SQCG_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SQCG_OK) return rc;
+  tune_cache()[key] = {bestW, bestT};
+  tune_file_store(key, bestW, bestT);
+  layout_tiles(P, bestW, bestT);
+  return upload_lats(P, s);
+}
+
+void destroy_plan(BatchPlan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  for (int k = 0; k < P->nlat; ++k) cudaFree(P->work[k]);
+  cudaFree(P->dev);
+  cudaFree(P->partials);
+  cudaFree(P->st);
+  if (P->st_host) cudaFreeHost(P->st_host);
+  free(P);
+}
+
+int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b, void* const* x,
+               BatchPlan** out, cudaStream_t s) {
+  BatchPlan* P = (BatchPlan*)calloc(1, sizeof(BatchPlan));
+  if (!P) return SQCG_ERR_NO_MEMORY;
+  P->nlat = nctx;
+  int total = 0, max_vh = 0;
+  for (int k = 0; k < nctx; ++k) {
+    sqcg_ctx* c = ctx[k];
+    P->ctx[k] = c;
+    P->gen[k] = sqcg_links_generation(c);
+    P->nrhs[k] = nrhs[k];
+    P->b[k] = b[k];
+    P->x[k] = x[k];
+    LatDev& L = P->host[k];
+    L.g = c->g;
+    const size_t Vh = c->g.Vh;
+    const int nl = c->recon ? 6 : 9;
+    for (int par = 0; par < 2; ++par) {
+      L.fat32[par] = c->fat32 + (size_t)par * 4 * 9 * Vh;
+      L.lng32[par] = c->lng32 + (size_t)par * 4 * nl * Vh;
+      L.fat64[par] = c->fat64 + (size_t)par * 4 * 9 * Vh;
+      L.lng64[par] = c->lng64 + (size_t)par * 4 * nl * Vh;
+    }
+    L.nl = nl;
+    L.recon = c->recon ? 1 : 0;
+    L.inv_s0_f = (float)(c->recon ? 1.0 / c->long_scale : 1.0);
+    L.inv_s0_d = c->recon ? 1.0 / c->long_scale : 1.0;
+    L.rhs0 = total;
+    L.nrhs = nrhs[k];
+    L.b = (const double2*)b[k];
+    L.x = (double2*)x[k];
+    const size_t n = (size_t)nrhs[k] * 3 * Vh;
+    if (cudaMalloc(&P->work[k], n * (4 * sizeof(float2) + sizeof(double2))) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_plan(P);
+      return SQCG_ERR_NO_MEMORY;
+    }
+    float2* w = (float2*)P->work[k];
+    L.r = w; L.p = w + n; L.Ap = w + 2 * n; L.tmp = w + 3 * n;
+    L.tmp64 = (double2*)(w + 4 * n);
+    total += nrhs[k];
+    if ((int)Vh > max_vh) max_vh = (int)Vh;
+  }
+  P->nrhs_total = total;
+  P->max_nsb = grid_for(max_vh, kMinT);
+  bool ok = cudaMalloc((void**)&P->dev, sizeof(LatDev) * nctx) == cudaSuccess &&
+            cudaMalloc((void**)&P->partials, sizeof(double) * (size_t)total * P->max_nsb) == cudaSuccess &&
+            cudaMalloc((void**)&P->st, sizeof(BatchState)) == cudaSuccess &&
+            cudaMallocHost((void**)&P->st_host, sizeof(BatchState)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    destroy_plan(P);
+    return SQCG_ERR_NO_MEMORY;
+  }
+  SQCG_CUDA_TRY(cudaMemsetAsync(P->st, 0, sizeof(BatchState), s));
+  for (int k = 0; k < nctx; ++k)
+    SQCG_CUDA_TRY(cudaMemsetAsync(P->work[k], 0, (size_t)nrhs[k] * 3 * ctx[k]->g.Vh * (4 * sizeof(float2) + sizeof(double2)), s));
+  int rc = autotune(*P, s);
+  if (rc != SQCG_OK) { destroy_plan(P); return rc; }
+  *out = P;
+  return SQCG_OK;
+}
+
+// Capture the loop: WHILE { D_oe p; A p + <p,Ap>; x,r update; ctl; IF { FP64 r = b - A x }; p update; ctl }
+int capture_plan(BatchPlan& P) {
+  cudaStream_t cs = P.ctx[0]->cap_stream;
+  cudaGraph_t top = nullptr;
+  SQCG_CUDA_TRY(cudaGraphCreate(&top, 0));
+  int rc = SQCG_OK;
+  cudaGraphConditionalHandle hw = 0, hif = 0;
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wnode = nullptr;
+  cudaGraph_t ifbody = nullptr;
+  do {
+    if (cudaGraphConditionalHandleCreate(&hw, top, 1, cudaGraphCondAssignDefault) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_ITER, cs);
+    if (rc == SQCG_OK) rc = launch_f32(P, 0, V_TMP, M_NORMAL_DOT, GATE_ITER, cs);
+    if (rc == SQCG_OK) rc = launch_mrhs_blas(P, B_UPDATE, cs);
+    if (rc == SQCG_OK) {
+      k_batch_ctl_update<<<1, 32, 0, cs>>>(P.st, P.dev, P.nlat, P.W);
+      if (cudaGetLastError() != cudaSuccess) rc = SQCG_ERR_CUDA;
+    }
+    if (rc == SQCG_OK) {
+      cudaStreamCaptureStatus status;
+      cudaGraph_t capg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      cudaGraphNodeParams ip = {};
+      cudaGraphNode_t inode = nullptr;
+      if (cudaStreamGetCaptureInfo(cs, &status, nullptr, &capg, &deps, nullptr, &ndeps) != cudaSuccess ||
+          cudaGraphConditionalHandleCreate(&hif, capg, 0, 0) != cudaSuccess) {
+        rc = SQCG_ERR_CUDA;
+      } else {
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hif;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        if (cudaGraphAddNode(&inode, capg, deps, nullptr, ndeps, &ip) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+          rc = SQCG_ERR_CUDA;
+        else
+          ifbody = ip.conditional.phGraph_out[0];
+      }
+    }
+    if (rc == SQCG_OK) rc = launch_mrhs_blas(P, B_XPAY, cs);
+    if (rc == SQCG_OK) {
+      k_batch_ctl_loop<<<1, 32, 0, cs>>>(P.st, P.dev, P.nlat, P.W);
+      if (cudaGetLastError() != cudaSuccess) rc = SQCG_ERR_CUDA;
+    }
+    cudaGraph_t got = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &got);
+    if (rc != SQCG_OK) break;
+    if (e != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    if (cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    rc = launch_f64(P, 1, V_X, M_PLAIN, GATE_UPDATE, 0, cs);
+    if (rc == SQCG_OK) rc = launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_UPDATE, 0, cs);
+    e = cudaStreamEndCapture(cs, &got);
+    if (rc != SQCG_OK) break;
+    if (e != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    if (cudaGraphInstantiate(&P.exec, top, 0) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+  } while (0);
+  if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "batched graph", __FILE__, __LINE__);
+  cudaGraphDestroy(top);
+  P.h_while = hw;
+  P.h_if = hif;
+  return rc;
+}
+
+bool plan_matches(const BatchPlan* P, int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b,
+                  void* const* x) {
+  if (!P || P->nlat != nctx) return false;
+  for (int k = 0; k < nctx; ++k)
+    if (P->ctx[k] != ctx[k] || P->gen[k] != sqcg_links_generation(ctx[k]) || P->nrhs[k] != nrhs[k] ||
+        P->b[k] != b[k] || P->x[k] != x[k])
+      return false;
+  return true;
+}
+
+}  // namespace
+
+void free_batch_plan(sqcg_ctx* ctx) {
+  destroy_plan(ctx->batch);
+  ctx->batch = nullptr;
+}
+
+extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
+                                     const void* const* b, void* const* x, double tol, int max_iter,
+                                     sqcg_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nctx < 1 || nctx > SQCG_MAX_LATTICES || !ctx || !nrhs || !mass || !b || !x || !(tol > 0) || max_iter <= 0)
+    return SQCG_ERR_INVALID_ARG;
+  int total = 0;
+  for (int k = 0; k < nctx; ++k) {
+    if (!ctx[k] || nrhs[k] < 1 || !isfinite(mass[k]) || !b[k] || !x[k] || b[k] == x[k]) return SQCG_ERR_INVALID_ARG;
+    if (((uintptr_t)b[k] | (uintptr_t)x[k]) & 15) return SQCG_ERR_INVALID_ARG;
+    if (!ctx[k]->have_links) return SQCG_ERR_NO_LINKS;
+    for (int j = 0; j < k; ++j)
+      if (ctx[j] == ctx[k] || x[j] == x[k]) return SQCG_ERR_INVALID_ARG;
+    total += nrhs[k];
+  }
+  if (total > SQCG_MAX_BATCH_RHS) return SQCG_ERR_INVALID_ARG;
+  sqcg_ctx* c0 = ctx[0];
+  cudaStream_t s = c0->stream;
+  if (!plan_matches(c0->batch, nctx, ctx, nrhs, b, x)) {
+    SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+    free_batch_plan(c0);
+    SQCG_TRY(build_plan(nctx, ctx, nrhs, b, x, &c0->batch, s));
+  }
+  BatchPlan& P = *c0->batch;
+
+  // state: per-RHS scalars
+  BatchState* h = P.st_host;
+  memset(h, 0, sizeof(BatchState));
+  h->nrhs = total;
+  h->nblk = P.nblk;
+  h->max_iter = max_iter;
+  h->update_interval = 100;
+  h->delta2 = 0.01;
+  for (int k = 0; k < nctx; ++k)
+    for (int j = 0; j < nrhs[k]; ++j) {
+      RhsScalars& r = h->r[P.host[k].rhs0 + j];
+      r.sigma = 4.0 * mass[k] * mass[k];
+      r.stop_rr = tol * tol;
+      r.active = 1;
+      r.status = SQCG_OK;
+    }
+  for (int j = 0; j < P.nblk; ++j) h->blk_active[j] = 1;
+  SQCG_CUDA_TRY(cudaMemcpyAsync(P.st, h, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+  // |b|^2 per RHS; r = b - A x0 in FP64 (x holds the initial guess), p = r
+  SQCG_TRY(launch_mrhs_blas(P, B_NORM_B, s));
+  for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 1;
+  SQCG_CUDA_TRY(cudaMemcpyAsync(P.st->blk_update, h->blk_update, sizeof(int) * P.nblk, cudaMemcpyHostToDevice, s));
+  SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_NONE, 0, s));
+  SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_NONE, 1, s));
+  SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+  SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+  int launches = 3;
+  int any = 0;
+  for (int j = 0; j < total; ++j) {
+    if (h->r[j].bb == 0.0 && h->r[j].active) {  // b = 0: x = 0 is the solution
+      h->r[j].active = 0;
+      h->r[j].status = SQCG_OK;
+    }
+    any |= h->r[j].active;
+  }
+  for (int k = 0; k < nctx; ++k)
+    for (int j = 0; j < nrhs[k]; ++j)
+      if (h->r[P.host[k].rhs0 + j].bb == 0.0)
+        SQCG_CUDA_TRY(cudaMemsetAsync((double2*)x[k] + (size_t)j * 3 * ctx[k]->g.Vh, 0,
+                                      (size_t)3 * ctx[k]->g.Vh * sizeof(double2), s));
+  if (any) {
+    if (!P.exec) SQCG_TRY(capture_plan(P));
+    for (int k = 0; k < P.nlat; ++k)
+      for (int rb = 0; rb < P.host[k].nrb; ++rb) {
+        int a = 0;
+        for (int w = rb * P.W; w < (rb + 1) * P.W && w < P.host[k].nrhs; ++w) a |= h->r[P.host[k].rhs0 + w].active;
+        h->blk_active[P.host[k].rb0 + rb] = a;
+      }
+    for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 0;
+    for (int j = 0; j < total; ++j) h->r[j].need_update = 0;
+    h->h_while = P.h_while;
+    h->h_if = P.h_if;
+    h->loop_count = 0;
+    h->loop_limit = max_iter + 4;
+    SQCG_CUDA_TRY(cudaMemcpyAsync(P.st, h, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+    SQCG_CUDA_TRY(cudaGraphLaunch(P.exec, s));
+    SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+    SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+    launches += h->loop_count * 6 + h->if_runs * 2;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = SQCG_OK;
+  for (int j = 0; j < total; ++j) {
+    const RhsScalars& r = h->r[j];
+    int st = r.active ? SQCG_ERR_NOT_CONVERGED : r.status;
+    if (info) {
+      info[j].iters = r.iter;
+      info[j].reliable_updates = r.updates;
+      info[j].status = st;
+      info[j].true_rel_resid = r.bb > 0 ? sqrt(r.rr_true / r.bb) : 0.0;
+      info[j].seconds = secs;
+      info[j].launches = launches;
+    }
+    if (st != SQCG_OK && worst == SQCG_OK) worst = st;
+  }
+  return worst;
+}
+
+extern "C" int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T) {
+  if (!ctx || !ctx->batch || !W || !T) return SQCG_ERR_INVALID_ARG;
+  *W = ctx->batch->W;
+  *T = ctx->batch->T;
+  return SQCG_OK;
+}

@@ -246,6 +246,41 @@ int run_loop(sqcg_ctx* ctx, CGGraph* g, int max_iter, cudaStream_t s, int* iters
   return SQCG_OK;
 }
 
+// The same iterations launched one kernel at a time, with the host reading
+// the device state after each step (SQCG_LAUNCH_MODE=eager). Kernel-level
+// profilers do not see kernels inside conditional graph nodes; this mode
+// gives them the identical kernel sequence to list. Results are the same.
+bool eager_mode() {
+  const char* m = getenv("SQCG_LAUNCH_MODE");
+  return m && strcmp(m, "eager") == 0;
+}
+
+int run_eager(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, int max_iter,
+              cudaStream_t s, int* iters_run) {
+  SolverState* h = ctx->st_host;
+  h->use_if = 0;  // no graph: the kernels must not touch conditional handles
+  SQCG_TRY(write_state(ctx, s));
+  int it = 0;
+  for (; it < max_iter + 4; ++it) {
+    if (kind == KIND_CG) {
+      SQCG_TRY(enqueue_cg_head(ctx, mixed, x[0], s));
+      SQCG_TRY(read_state(ctx, s));
+      if (!h->done && h->need_update) {
+        SQCG_TRY(enqueue_cg_reliable(ctx, mixed, b, x[0], s));
+        SQCG_TRY(read_state(ctx, s));
+      }
+      if (h->done) break;
+      SQCG_TRY(launch_cg_xpay(ctx, mixed, s));
+    } else {
+      SQCG_TRY(enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, s));
+      SQCG_TRY(read_state(ctx, s));
+      if (h->done) break;
+    }
+  }
+  *iters_run = it + 1;
+  return SQCG_OK;
+}
+
 // |b - (sigma - D_eo D_oe) x|^2 in FP64 (r64 as scratch); result in *rr
 int true_residual2(sqcg_ctx* ctx, double sigma, const void* b, const void* x, double* rr, cudaStream_t s) {
   DslashLaunch L = {};
@@ -319,10 +354,14 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
     return SQCG_OK;
   }
   if (!h->done) {
-    CGGraph* g = nullptr;
     void* xs[1] = {x};
-    SQCG_TRY(capture(ctx, KIND_CG, mixed, b, xs, 1, &g));
-    SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+    if (eager_mode()) {
+      SQCG_TRY(run_eager(ctx, KIND_CG, mixed, b, xs, 1, max_iter, s, &loops));
+    } else {
+      CGGraph* g = nullptr;
+      SQCG_TRY(capture(ctx, KIND_CG, mixed, b, xs, 1, &g));
+      SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+    }
     launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
     status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   } else {
@@ -432,10 +471,14 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
   h->rr = h->rr_prev = h->bb;
   SQCG_TRY(write_state(ctx, s));
 
-  CGGraph* g = nullptr;
-  SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
   int loops = 0;
-  SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+  if (eager_mode()) {
+    SQCG_TRY(run_eager(ctx, KIND_MS, mixed, b, xs, nshift, max_iter, s, &loops));
+  } else {
+    CGGraph* g = nullptr;
+    SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
+    SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+  }
   int launches = 1 + 1 + nshift + loops * kMSKernelsPerIter;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];

@@ -178,6 +178,7 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   ctx->fat32 = ctx->lng32 = nullptr;
   ctx->have_links = false;
   free_graphs(ctx);
+  free_batch_plan(ctx);
 
   void* raw = nullptr;
   bool ok = cudaMalloc((void**)&ctx->fat64, nfat * sizeof(double2)) == cudaSuccess &&
@@ -214,6 +215,8 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   ctx->recon = recon;
   ctx->long_scale = s0;
   ctx->have_links = true;
+  static unsigned long long generation = 0;
+  ctx->links_gen = __atomic_add_fetch(&generation, 1ULL, __ATOMIC_RELAXED);
   return SQCG_OK;
 }
 
@@ -262,3 +265,5 @@ int layout_convert(sqcg_ctx* ctx, int from_prec, const void* src, int to_prec, v
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }
+
+unsigned long long sqcg_links_generation(const sqcg_ctx* ctx) { return ctx->links_gen; }

@@ -86,6 +86,33 @@ struct SolverState {
   int iters_s[SQCG_MAX_SHIFTS];
 };
 
+// ---------------------------------------------------------------------------
+// batched multi-RHS CG over several lattices (one state entry per RHS)
+// ---------------------------------------------------------------------------
+#define SQCG_MAX_BATCH_RHS 256
+#define SQCG_MAX_LATTICES 16
+
+struct RhsScalars {
+  double sigma, bb, stop_rr, rr, rr_prev, rr_true, rr_max, pAp, alpha, beta;
+  int iter, iter_last_update, active, status, need_update, updates;
+};
+
+struct BatchState {
+  int nrhs, nblk;   // right-hand sides; FP32 RHS blocks over all lattices
+  int max_iter, update_interval;
+  double delta2;
+  int loop_count, loop_limit;
+  int if_runs;  // executions of the reliable-update IF body
+  int pad;
+  unsigned long long h_while, h_if;
+  RhsScalars r[SQCG_MAX_BATCH_RHS];
+  int blk_active[SQCG_MAX_BATCH_RHS];  // RHS block has an active RHS
+  int blk_update[SQCG_MAX_BATCH_RHS];  // RHS block runs the FP64 reliable update
+  unsigned int counter[3 * SQCG_MAX_BATCH_RHS];
+};
+
+struct BatchPlan;  // defined in batched.cu
+
 // gates: which kernels of a captured iteration actually run
 enum Gate { GATE_NONE = 0, GATE_ITER = 1, GATE_UPDATE = 2 };
 
@@ -116,6 +143,7 @@ struct sqcg_ctx {
 
   bool have_links;
   bool recon;
+  unsigned long long links_gen;  // process-wide counter value of the last sqcg_load_links
   double long_scale;  // global real scale s0 of the long links (recon)
 
   // device links, [parity][mu][elem][Vh]
@@ -142,7 +170,10 @@ struct sqcg_ctx {
   int ms_prec;
 
   CGGraph* graphs;  // cached captured solver loops
+  BatchPlan* batch;  // cached batched-solve workspace and graph (owned by the first context of a batch)
 };
+
+void free_batch_plan(sqcg_ctx* ctx);
 
 // ---------------------------------------------------------------------------
 // launchers (defined in dslash.cu / blas.cu / layout.cu)

@@ -1,0 +1,114 @@
+"""Batched multi-RHS CG over lattices of different volumes, through the C ABI.
+
+Every right-hand side must reach a true relative residual <= tol, recomputed
+here by the FP64 oracle from the returned x; a batched solve must agree with
+the single-RHS solver. The full batched workload (16 sources each on 16^4,
+24^4 and 32^3x64, m = 0.02) is checked on the solver's reported residuals for
+all 48 sources and on the oracle for a sample of them.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(sq, lat, srcs):
+    b = torch.stack([lat.pack(s) for s in srcs]).contiguous()
+    x = torch.zeros_like(b)
+    return b, x
+
+
+@pytest.mark.parametrize("recon", [False, True])
+def test_batched_small_uneven(sqcg, links_cache, recon):
+    specs = [((8, 8, 8, 8), 3, 0.1), ((6, 8, 10, 12), 5, 0.05), ((4, 4, 4, 8), 2, 0.2)]
+    tol = 1e-9
+    lats, bs, xs, srcs, links = [], [], [], [], []
+    for n, (L, nr, m) in enumerate(specs):
+        fat, lng = links_cache(L, 400 + n)
+        lat = sqcg.Lattice(L)
+        lat.load_links(fat, lng, recon12=recon and n == 1)
+        s = [synth.gaussian_source(L, 5000 + 10 * n + j) for j in range(nr)]
+        b, x = make_batch(sqcg, lat, s)
+        lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
+    infos = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=tol, max_iter=5000)
+    W, T = sqcg.batched_tuning(lats[0])
+    assert W in (1, 2, 4, 8, 16) and T in (64, 128, 256)
+    for n, (L, nr, m) in enumerate(specs):
+        fat, lng = links[n]
+        for j in range(nr):
+            assert infos[n][j].status == 0 and infos[n][j].true_rel_resid <= tol
+            x = lats[n].unpack(xs[n][j])
+            assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], x) <= tol
+    # agrees with the single-RHS solver on the same system
+    L, nr, m = specs[0]
+    dx = lats[0].new_spinor()
+    lats[0].cg_solve(m, bs[0][1], dx, tol=1e-12, max_iter=5000, mode=0)
+    ref = lats[0].unpack(dx)
+    got = lats[0].unpack(xs[0][1])
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 10 * tol
+    # a second call with the same arguments reuses the cached plan and graph
+    for x in xs:
+        x.zero_()
+    infos2 = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=tol, max_iter=5000)
+    assert [i.iters for i in infos2[1]] == [i.iters for i in infos[1]]
+    for lat in lats:
+        lat.close()
+
+
+def test_batched_edge_cases(sqcg, links_cache):
+    L = (8, 8, 8, 8)
+    fat, lng = links_cache(L, 1001)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        srcs = [synth.gaussian_source(L, 7000 + j) for j in range(3)]
+        srcs[1] = np.zeros_like(srcs[1])  # zero source -> x = 0
+        b, x = make_batch(sqcg, lat, srcs)
+        x.fill_(1.0)  # initial guesses (the zero source must still give x = 0)
+        infos = sqcg.cg_solve_batched([lat], [0.1], [b], [x], tol=1e-8)[0]
+        assert all(i.status == 0 for i in infos)
+        assert not torch.any(x[1])
+        for j in (0, 2):
+            assert oracle.true_rel_residual(L, fat, lng, 0.04, srcs[j], lat.unpack(x[j])) <= 1e-8
+        # max_iter reached
+        x.zero_()
+        infos = sqcg.cg_solve_batched([lat], [0.1], [b], [x], tol=1e-14, max_iter=4, raise_on_error=False)[0]
+        assert infos[0].status == -3 and infos[0].iters <= 4
+        # NaN source -> breakdown for that RHS only
+        bad = [s.copy() for s in srcs]
+        bad[2][5, 0] = np.nan
+        b2, x2 = make_batch(sqcg, lat, bad)
+        infos = sqcg.cg_solve_batched([lat], [0.1], [b2], [x2], tol=1e-8, raise_on_error=False)[0]
+        assert infos[0].status == 0 and infos[2].status == -4
+        # invalid arguments
+        with pytest.raises(sqcg.SqcgError):
+            sqcg.cg_solve_batched([lat, lat], [0.1, 0.1], [b, b], [x, x2])  # same context twice
+
+
+def test_batched_full_workload(sqcg, links_cache):
+    """16 sources each on 16^4, 24^4 and 32^3x64 at m = 0.02, FP32 with FP64 reliable updates, tol 1e-8."""
+    specs = [(16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 64)]
+    m, tol, nr = 0.02, 1e-8, 16
+    lats, bs, xs, srcs, links = [], [], [], [], []
+    for n, L in enumerate(specs):
+        fat, lng = links_cache(L, 1004 + n)
+        lat = sqcg.Lattice(L)
+        lat.load_links(fat, lng)
+        s = synth.gaussian_source(L, 2400 + 10 * n, nrhs=nr)
+        b, x = make_batch(sqcg, lat, list(s))
+        lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
+    infos = sqcg.cg_solve_batched(lats, [m] * 3, bs, xs, tol=tol, max_iter=20000)
+    for n in range(3):
+        assert all(i.status == 0 and i.true_rel_resid <= tol for i in infos[n])
+    rng = np.random.default_rng(1)
+    for n, L in enumerate(specs):
+        fat, lng = links[n]
+        for j in rng.choice(nr, 2, replace=False):
+            x = lats[n].unpack(xs[n][j])
+            assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], x) <= tol
+    for lat in lats:
+        lat.close()

@@ -197,3 +197,30 @@ def test_multishift_32_mixed(sqcg, links_cache):
     for s, info, x in zip(shifts, infos, got):
         assert info.status == 0
         assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
+
+
+def test_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch):
+    """The device-side loop (one graph launch) and the eager profiling mode run the
+    same kernels with deterministic reductions: identical iterates, bit for bit."""
+    L, m = (8, 10, 12, 14), 0.02
+    fat, lng = links_cache(L, 88)
+    b = synth.gaussian_source(L, 4)
+    out = {}
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db = lat.pack(b)
+        for mode in ("graph", "eager"):
+            if mode == "eager":
+                monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
+            else:
+                monkeypatch.delenv("SQCG_LAUNCH_MODE", raising=False)
+            dx = lat.new_spinor()
+            info = lat.cg_solve(m, db, dx, tol=1e-10, max_iter=5000, mode=1)
+            xs = [lat.new_spinor() for _ in range(3)]
+            ms = lat.multishift_cg_solve([0.01, 0.1, 1.0], db, xs, tol=1e-9, mode=1)
+            out[mode] = (info.iters, info.reliable_updates, lat.unpack(dx), [i.iters for i in ms],
+                         [lat.unpack(x) for x in xs])
+    g, e = out["graph"], out["eager"]
+    assert g[0] == e[0] and g[1] == e[1] and g[3] == e[3]
+    assert np.array_equal(g[2], e[2])
+    assert all(np.array_equal(a, c) for a, c in zip(g[4], e[4]))
