@@ -58,6 +58,7 @@ extern "C" {
 #define SQCG_ERR_RECON_REJECTED (-5) /* 12-real long links requested but the links fail the test */
 #define SQCG_ERR_NO_LINKS (-6)       /* operator used before sqcg_load_links */
 #define SQCG_ERR_NO_MEMORY (-7)      /* device allocation failed */
+#define SQCG_ERR_SCRATCH_TOO_SMALL (-8) /* lattice larger than the fixed scratch of sqcg_normal_op_noalloc */
 
 /* ---- sqcg_create flags ---- */
 #define SQCG_ANTIPERIODIC_T 1 /* extra -1 on forward hops across the last time slice */
@@ -128,6 +129,26 @@ int sqcg_dslash(sqcg_ctx* ctx, int out_parity, int prec, const void* in, void* o
 /* y = (sigma - D_eo D_oe) x on the even sites, FP64 or FP32 device vectors
  * (x, y must not alias). Asynchronous. */
 int sqcg_normal_op(sqcg_ctx* ctx, double sigma, int prec, const void* x, void* y);
+
+/* Same result as sqcg_normal_op, but this call allocates no device memory.
+ * The paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc when they apply the operator, such as host applications that give
+ * all device memory to their own allocator or pool up front (a new cudaMalloc
+ * would fail or break their budget) and latency-bound loops that cannot accept
+ * an allocation, which may synchronise the device. sqcg_normal_op keeps its
+ * intermediate D_oe x in the context's workspace, which is allocated on first
+ * use; this call keeps it in one fixed 8 MiB array compiled into the library
+ * (held on every GPU that loads the library until the process exits), so the
+ * lattice may have at most 174762 sites per parity in SQCG_F64 and 349525 in
+ * SQCG_F32; larger lattices get SQCG_ERR_SCRATCH_TOO_SMALL. The context must
+ * already exist with its links loaded; x and y are the caller's device vectors
+ * as for sqcg_normal_op. The first call on each device looks up the device
+ * address of that array (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture. Every call on a device shares the
+ * array and it keeps the last call's contents (nothing in it has to start at
+ * zero: each call overwrites what it reads); calls that overlap on the GPU
+ * (other streams or host threads) race on it. Asynchronous on the stream. */
+int sqcg_normal_op_noalloc(sqcg_ctx* ctx, double sigma, int prec, const void* x, void* y);
 
 /* Solve (4 mass^2 - D_eo D_oe) x = b on the even sites by CG (paper Sec. 3,
  * single-mass CG). b, x: FP64 device vectors; x holds the initial guess on

@@ -34,7 +34,7 @@ FLOPS_PER_SITE = 1146
 OK = 0
 ERR_NAMES = {
     -1: "INVALID_ARG", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "RECON_REJECTED",
-    -6: "NO_LINKS", -7: "NO_MEMORY",
+    -6: "NO_LINKS", -7: "NO_MEMORY", -8: "SCRATCH_TOO_SMALL",
 }
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -80,6 +80,7 @@ def library():
         lib.sqcg_unpack_spinor.argtypes = [P, I, P, P]
         lib.sqcg_dslash.argtypes = [P, I, I, P, P]
         lib.sqcg_normal_op.argtypes = [P, D, I, P, P]
+        lib.sqcg_normal_op_noalloc.argtypes = [P, D, I, P, P]
         lib.sqcg_cg_solve.argtypes = [P, D, P, P, D, I, I, ctypes.POINTER(Info)]
         lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
@@ -88,6 +89,7 @@ def library():
         lib.sqcg_strerror.restype = ctypes.c_char_p
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
+                     "sqcg_normal_op_noalloc",
                      "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning"):
             getattr(lib, name).restype = I
         _lib = lib
@@ -206,6 +208,15 @@ class Lattice:
         self._sync_stream()
         _check(library().sqcg_normal_op(self._h, float(sigma), prec, self._check_spinor(x, prec, self.Vh),
                                         self._check_spinor(y, prec, self.Vh)), "sqcg_normal_op")
+        return y
+
+    def normal_op_noalloc(self, sigma: float, x, y, prec: int = F64):
+        """y = (sigma - D_eo D_oe) x without allocating device memory: the
+        intermediate lives in a fixed scratch array of the library (for callers
+        that cannot allocate; see sqcg_normal_op_noalloc in include/sqcg.h)."""
+        self._sync_stream()
+        _check(library().sqcg_normal_op_noalloc(self._h, float(sigma), prec, self._check_spinor(x, prec, self.Vh),
+                                                self._check_spinor(y, prec, self.Vh)), "sqcg_normal_op_noalloc")
         return y
 
     # -- solvers ----------------------------------------------------------

@@ -175,6 +175,9 @@ const char* sqcg_strerror(int status) {
     case SQCG_ERR_RECON_REJECTED: return "12-real long links rejected: links are not a global scale times SU(3)";
     case SQCG_ERR_NO_LINKS: return "no links loaded";
     case SQCG_ERR_NO_MEMORY: return "device allocation failed";
+    case SQCG_ERR_SCRATCH_TOO_SMALL:
+      return "lattice too large for the fixed 8 MiB scratch of sqcg_normal_op_noalloc "
+             "(at most 174762 sites per parity in FP64, 349525 in FP32)";
     default: return "unknown status";
   }
 }
