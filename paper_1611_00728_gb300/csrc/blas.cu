@@ -45,7 +45,7 @@ k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const ty
     }
     nrm = (double)part;
   }
-  grid_reduce_finish(nrm, partials, st, FIN_UPDATE);
+  block_partial(nrm, partials);
 }
 
 // p = r + beta p
@@ -79,7 +79,7 @@ k_norm2_f64(const double2* __restrict__ v, int Vh, SolverState* st, double* part
       nrm = fma(a.x, a.x, fma(a.y, a.y, nrm));
     }
   }
-  grid_reduce_finish(nrm, partials, st, fin);
+  block_partial(nrm, partials);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -139,7 +139,7 @@ k_ms_update(MSPtrs P, typename V2<R>::T* __restrict__ r, const typename V2<R>::T
       }
     }
   }
-  grid_reduce_finish(nrm, partials, st, FIN_MS_UPDATE);
+  block_partial(nrm, partials);
 }
 
 // p = r + beta p (base, which is also shift 0's direction); p_s = zeta_s r + beta_s p_s (shifts >= 1)
@@ -178,6 +178,13 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
   }
 }
 
+// Second stage of a grid reduction: sum the block partials, run the scalar step.
+__global__ void __launch_bounds__(kFinishThreads) k_finish(SolverState* st, const double* partials, int n, int fin,
+                                                           int gate) {
+  if (!gate_open(st, gate)) return;
+  finish_partials(st, partials, n, fin);
+}
+
 // One thread: count the WHILE-loop iterations and set its condition. The loop
 // continues while the solve is not done and the hard bound is not reached.
 __global__ void k_loop_control(SolverState* st) {
@@ -192,6 +199,12 @@ __global__ void k_loop_control(SolverState* st) {
 }
 
 }  // namespace
+
+int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
+  k_finish<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
 
 int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s) {
   k_loop_control<<<1, 32, 0, s>>>(ctx->st);
@@ -208,7 +221,7 @@ int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s) {
   else
     k_cg_update<double><<<grid, kThreads, 0, s>>>(x, ctx->r64, ctx->p64, ctx->Ap64, Vh, ctx->st, ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
-  return SQCG_OK;
+  return launch_finish(ctx, grid, FIN_UPDATE, GATE_ITER, s);
 }
 
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
@@ -226,7 +239,7 @@ int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s) {
   if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
   k_norm2_f64<<<grid, kThreads, 0, s>>>(v, Vh, ctx->st, ctx->partials, fin);
   SQCG_CUDA_TRY(cudaGetLastError());
-  return SQCG_OK;
+  return launch_finish(ctx, grid, fin, GATE_NONE, s);
 }
 
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s) {
@@ -249,7 +262,7 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
   else
     k_ms_update<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, ctx->Ap64, Vh, ctx->st, ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
-  return SQCG_OK;
+  return launch_finish(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s);
 }
 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, cudaStream_t s) {

@@ -16,9 +16,9 @@
 
 namespace {
 
-constexpr int kCGKernelsPerIter = 5;  // enqueue_cg_head + xpay + loop control
-constexpr int kCGKernelsPerUpdate = 2;  // enqueue_cg_reliable
-constexpr int kMSKernelsPerIter = 5;  // enqueue_ms_iteration + loop control
+constexpr int kCGKernelsPerIter = 7;  // enqueue_cg_head (3 + 2 finishers) + xpay + loop control
+constexpr int kCGKernelsPerUpdate = 3;  // enqueue_cg_reliable (2 + finisher)
+constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control
 
 enum { KIND_CG = 0, KIND_MS = 1 };
 
@@ -342,7 +342,7 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   SQCG_TRY(read_state(ctx, s));
 
   int status = SQCG_OK;
-  int launches = 3, loops = 0;
+  int launches = 5, loops = 0;
   if (h->bb == 0.0) {  // b = 0: the solution is x = 0
     SQCG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)ctx->g.Vh * 3 * sizeof(double2), s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -479,7 +479,7 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
     SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
   }
-  int launches = 1 + 1 + nshift + loops * kMSKernelsPerIter;
+  int launches = 2 + 1 + nshift + loops * kMSKernelsPerIter;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];
   for (int j = 0; j < nshift; ++j) iters_s[j] = h->iters_s[j];
@@ -493,7 +493,7 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     double rr = 0.0;
     int st = (loop_status == SQCG_ERR_BREAKDOWN) ? SQCG_ERR_BREAKDOWN : SQCG_OK;
     SQCG_TRY(true_residual2(ctx, sig, b, xs[j], &rr, s));
-    launches += 2;
+    launches += 3;
     double rel = sqrt(rr / bb);
     int extra = 0, updates = 0;
     if (st == SQCG_OK && !(rel <= tol[u])) {

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
     }
   }
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
-    if (a.fin != FIN_NONE) grid_reduce_finish(part, a.partials, a.st, a.fin);
+    if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
 }
 
@@ -273,6 +273,8 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
+  if ((L.epi == EPI_NORMAL_DOT || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE)
+    return launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
 }
 

@@ -146,31 +146,23 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
   }
 }
 
-// Grid-wide sum of v with a deterministic order: each block writes its partial,
-// the last block to arrive sums the partials in index order and runs the
-// scalar step. Must be called by every thread of every block.
-__device__ inline void grid_reduce_finish(double v, double* partials, SolverState* st, int fin) {
-  __shared__ bool am_last;
+// First stage of a grid-wide sum: each block writes its partial sum to
+// partials[blockIdx.x]. The second stage is k_finish (one block, launched
+// right after on the same stream), which adds the partials in index order and
+// runs the scalar step, so the total does not depend on timing. The kernel
+// boundary makes the partials visible without fences or atomics.
+__device__ __forceinline__ void block_partial(double v, double* partials) {
   const double b = block_sum(v);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = b;
-    __threadfence();
-    const unsigned int t = atomicAdd(&st->counter, 1u);
-    am_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // L2-only loads (the partials come from other SMs); not volatile, so the
-  // compiler can issue several before the adds. Each thread adds its share in
-  // index order, so the total does not depend on timing.
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+// Second stage: one block of kFinishThreads threads.
+constexpr int kFinishThreads = 256;
+
+__device__ __forceinline__ void finish_partials(SolverState* st, const double* partials, int n, int fin) {
   double s = 0.0;
-  const int n = (int)gridDim.x;
 #pragma unroll 8
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s += __ldcg(partials + j);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += partials[j];
   s = block_sum(s);
-  if (threadIdx.x == 0) {
-    st->counter = 0;
-    solver_finish(st, fin, s);
-  }
+  if (threadIdx.x == 0) solver_finish(st, fin, s);
 }

@@ -205,6 +205,7 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
 
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
 int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
+int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
