@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
+    ap.add_argument("--workload", choices=["single", "multishift", "batched", "learned"], default="single",
+                    help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
 
 
@@ -408,10 +410,249 @@ def run_ours(args, ranks: Ranks):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# other forms of the solve, each against plain FP64 GPU CG at the same residual
+# ---------------------------------------------------------------------------
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.current_stream()
+    e0.record(s)
+    out = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_multishift(args):
+    """32^4, 11 shifts logspace(-4, 0), one Gaussian source, per-shift tol 1e-8."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    sq.build_if_needed()
+    fat, lng = synth.fat_long_links(LATTICE, 1003)
+    b_host = synth.gaussian_source(LATTICE, 2300)
+    shifts = list(np.logspace(-4, 0, 11))
+    lat = sq.Lattice(LATTICE)
+    lat.load_links(fat, lng)
+    b = lat.pack(b_host)
+    xs = [lat.new_spinor() for _ in shifts]
+    res = {}
+    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+        for _ in range(max(args.warmup, 1)):
+            lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode)
+        times, infos = [], None
+        for _ in range(args.steps):
+            infos, ms = _timed(torch, lambda: lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode))
+            times.append(ms)
+        res[name] = {"ms": statistics.median(times), "iters": [i.iters for i in infos],
+                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+    # plain FP64 CG, one solve per shift
+    x = lat.new_spinor()
+    total, iters = 0.0, []
+    for sg in shifts:
+        info, ms = _timed(torch, lambda sg=sg: _solve_sigma(lat, sg, b, x, sq))
+        total += ms
+        iters.append(info.iters)
+    res["fp64_cg_per_shift"] = {"ms": total, "iters": iters}
+    lat.close()
+    Vh = int(np.prod(LATTICE)) // 2
+    line = {"metric": "multi-shift CG time to per-shift true residual 1e-8 vs plain FP64 CG", "unit": "ms",
+            "value": res["mixed"]["ms"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "32^4 multi-shift CG, 11 shifts logspace(-4,0), 1 source (seeds 1003/2300)",
+                       "vh": Vh, "shifts": shifts},
+            "multishift_mixed": res["mixed"], "multishift_fp64": res["fp64"],
+            "fp64_cg_one_per_shift": res["fp64_cg_per_shift"],
+            "speedup_vs_fp64_cg_per_shift": res["fp64_cg_per_shift"]["ms"] / res["mixed"]["ms"],
+            "speedup_vs_fp64_multishift": res["fp64"]["ms"] / res["mixed"]["ms"]}
+    print(json.dumps(line), flush=True)
+
+
+def _solve_sigma(lat, sigma, b, x, sq):
+    """Plain FP64 CG of (sigma - D_eo D_oe) x = b (mass = sqrt(sigma) / 2)."""
+    x.zero_()
+    return lat.cg_solve(float(np.sqrt(sigma) / 2), b, x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
+
+
+def run_batched(args):
+    """16 sources each on 16^4, 24^4, 32^3x64, m = 0.02, one batched solve vs FP64 CG per source."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    sq.build_if_needed()
+    specs = [(16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 64)]
+    m, nr = 0.02, 16
+    lats, bs, xs = [], [], []
+    for n, L in enumerate(specs):
+        fat, lng = synth.fat_long_links(L, 1004 + n)
+        lat = sq.Lattice(L)
+        lat.load_links(fat, lng)
+        src = synth.gaussian_source(L, 2400 + 10 * n, nrhs=nr)
+        b = torch.stack([lat.pack(s) for s in src]).contiguous()
+        lats.append(lat); bs.append(b); xs.append(torch.zeros_like(b))
+
+    def solve():
+        for x in xs:
+            x.zero_()
+        return sq.cg_solve_batched(lats, [m] * 3, bs, xs, tol=TOL, max_iter=20000)
+
+    for _ in range(max(args.warmup, 1)):
+        solve()
+    times, infos = [], None
+    for _ in range(args.steps):
+        infos, ms = _timed(torch, solve)
+        times.append(ms)
+    t_batched = statistics.median(times)
+    W, T = sq.batched_tuning(lats[0])
+    # plain FP64 CG and single-RHS mixed CG, one source at a time
+    t64, tmix, it64 = 0.0, 0.0, []
+    for lat, b in zip(lats, bs):
+        x = lat.new_spinor()
+        for j in range(nr):
+            def f64():
+                x.zero_()
+                return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
+            def fmx():
+                x.zero_()
+                return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_MIXED)
+            i64, ms = _timed(torch, f64)
+            t64 += ms
+            it64.append(i64.iters)
+            _, ms = _timed(torch, fmx)
+            tmix += ms
+    site_rhs = sum(nr * int(np.prod(L)) // 2 for L in specs)
+    apps = sum(2 * (i.iters + i.reliable_updates + 1) * int(np.prod(L)) // 2
+               for L, lst in zip(specs, infos) for i in lst)
+    line = {"metric": "batched CG time to true residual 1e-8 (48 sources, 3 lattices) vs plain FP64 CG", "unit": "ms",
+            "value": t_batched, "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "16 Gaussian sources each on 16^4, 24^4, 32^3x64, m=0.02 (gauge seeds 1004-1006)",
+                       "site_rhs": site_rhs},
+            "batched_ms": t_batched, "tuned_W": W, "tuned_T": T,
+            "dslash_gflops_in_solve": FLOPS_PER_SITE * apps / (t_batched / 1e3) / 1e9,
+            "max_iters": max(i.iters for lst in infos for i in lst),
+            "max_true_rel_resid": max(i.true_rel_resid for lst in infos for i in lst),
+            "fp64_cg_one_per_source_ms": t64, "mixed_cg_one_per_source_ms": tmix,
+            "speedup_vs_fp64_cg": t64 / t_batched, "speedup_vs_mixed_cg_sequential": tmix / t_batched}
+    for lat in lats:
+        lat.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned preconditioner: train at 16^4 on CG pairs, flexible CG on held-out seeds at 16^4 and 32^4."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    sq.build_if_needed()
+    m, sigma = 0.005, 4 * 0.005 ** 2
+    Ltr = (16, 16, 16, 16)
+    t0 = time.perf_counter()
+    # training pairs: CG iterates x_k (CG from 0 truncated at k) against a tight x*, 8 gauge seeds x 4 sources
+    ks = [0, 1, 2, 4, 8, 16, 32, 64, 128, 256]
+    R, E = [], []
+    nets = []
+    for gseed in range(8):
+        fat, lng = synth.fat_long_links(Ltr, gseed)
+        lat = sq.Lattice(Ltr)
+        lat.load_links(fat, lng)
+        net = sq.Network(lat)
+        for src in range(4):
+            b = lat.pack(synth.gaussian_source(Ltr, 5000 + 10 * gseed + src))
+            xs = lat.new_spinor()
+            lat.cg_solve(m, b, xs, tol=1e-12, max_iter=50000, mode=sq.MODE_MIXED)
+            for k in ks:
+                xk = lat.new_spinor()
+                if k > 0:
+                    lat.cg_solve(m, b, xk, tol=1e-30, max_iter=k, mode=sq.MODE_F64, raise_on_error=False)
+                r32, e32 = lat.new_spinor(sq.F32), lat.new_spinor(sq.F32)
+                net.make_pair(sigma, b, xk, xs, r32, e32)
+                R.append(r32); E.append(e32)
+        nets.append((lat, net))
+    t_data = time.perf_counter() - t0
+    # train on the first lattice's network (weights are lattice independent) against all pairs: the pairs'
+    # A-norm needs their own links, so train per gauge field in turn and share the parameters
+    rng = np.random.default_rng(0)
+    params = None
+    t0 = time.perf_counter()
+    per = len(ks) * 4
+    losses = []
+    for epoch in range(3):
+        for g in rng.permutation(8):
+            lat, net = nets[g]
+            if params is not None:
+                net.set_params(params)
+            Rg = torch.stack(R[g * per:(g + 1) * per]).contiguous()
+            Eg = torch.stack(E[g * per:(g + 1) * per]).contiguous()
+            if params is None:
+                net.set_params(_init_net_params())
+            first, last = net.train(sigma, Rg, Eg, steps=60, batch=8, lr=1e-2, seed=int(g) + 1 + 100 * epoch)
+            losses.append((first, last))
+            params = net.get_params()
+    t_train = time.perf_counter() - t0
+    for lat, net in nets:
+        net.close()
+        lat.close()
+    results = {}
+    for L in (Ltr, (32, 32, 32, 32)):
+        fat, lng = synth.fat_long_links(L, 9000)
+        lat = sq.Lattice(L)
+        lat.load_links(fat, lng)
+        net = sq.Network(lat)
+        net.set_params(params)
+        b = lat.pack(synth.gaussian_source(L, 9100))
+        x = lat.new_spinor()
+        out = {}
+        for name, fn in (("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64)),
+                         ("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
+                         ("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))):
+            x.zero_()
+            fn()
+            x.zero_()
+            info, ms = _timed(torch, fn)
+            out[name] = {"ms": ms, "iters": info.iters, "true_rel_resid": info.true_rel_resid,
+                         "fallback": getattr(info, "fallback", 0)}
+        results["x".join(map(str, L))] = out
+        net.close()
+        lat.close()
+    line = {"metric": "learned-preconditioned flexible CG time to true residual 1e-8 vs plain FP64 CG", "unit": "ms",
+            "value": results["32x32x32x32"]["fcg_nn"]["ms"], "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32/bf16",
+            "config": {"workload": "train 16^4 (gauge seeds 0-7, 4 sources each, CG iterates k in "
+                                   f"{ks}), held-out gauge seed 9000 at 16^4 and 32^4, m=0.005",
+                       "pairs": len(R)},
+            "train_loss_first_last": [losses[0][0], losses[-1][1]], "seconds_data": t_data,
+            "seconds_train": t_train, "results": results}
+    print(json.dumps(line), flush=True)
+
+
+def _init_net_params():
+    """Small seeded initial weights (numpy; layout as in include/sqcg.h)."""
+    rng = np.random.default_rng(12345)
+    p = np.zeros(1472, dtype=np.float32)
+    for lo, hi, cin in ((0, 144, 1), (144, 1296, 8), (1296, 1440, 8)):
+        p[lo:hi] = rng.standard_normal(hi - lo) * 0.3 / np.sqrt(9 * cin)
+    p[1440:1448] = -0.5
+    p[1448:1456] = 1.0
+    p[1456:1464] = -0.5
+    p[1464:1472] = 1.0
+    return p
+
+
 def main():
     args = parse()
     if args.steps < 1:
         raise SystemExit("--steps must be >= 1")
+    if args.workload != "single":
+        {"multishift": run_multishift, "batched": run_batched, "learned": run_learned}[args.workload](args)
+        return
     ranks = Ranks()
     try:
         if args.impl == "reference":

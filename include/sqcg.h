@@ -84,6 +84,7 @@ typedef struct {
   double true_rel_resid; /* |b - A x| / |b| recomputed in FP64 from the returned x */
   double seconds;        /* wall time of the solve on the host, including the final sync */
   int launches;          /* kernels this call launched (including gated-off ones in a captured loop) */
+  int fallback;          /* sqcg_fcg_solve_nn only: 1 if plain CG took over from the flexible CG */
 } sqcg_info;
 
 /* Create a context for one lattice geometry. dims: 4 extents, all even and
@@ -198,6 +199,60 @@ int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, co
 int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
                           const void* const* b, void* const* x, double tol, int max_iter,
                           sqcg_info* info);
+
+/* ---- learned gauge-covariant preconditioner and flexible CG ----
+ * Not in the paper: a learned preconditioner for a flexible CG built around
+ * the paper's single-mass CG (Sec. 3). The network N has three
+ * parallel-transport convolution layers over the fat links (channels
+ * 1 -> 8 -> 8 -> 1; taps: self and the 8 one-hop neighbours; complex weights
+ * that mix channels only, stored in BF16 with FP32 accumulation), a gate
+ * h <- h sigmoid(a |h|^2 + b) after layers 1 and 2, and an input scaled to
+ * unit RMS with the output scaled back, so N(c r) = c N(r). It is exactly
+ * gauge covariant. Parameters (SQCG_NN_NPARAMS floats, host layout):
+ *   [0, 144)     layer 1 weights [tap][out 8][in 1][re, im]
+ *   [144, 1296)  layer 2 weights [tap][out 8][in 8][re, im]
+ *   [1296, 1440) layer 3 weights [tap][out 1][in 8][re, im]
+ *   [1440, 1472) gate 1 a[8], b[8], gate 2 a[8], b[8]
+ * taps: 0 self, 1 + 2 mu = F_mu(n) h(n + mu), 2 + 2 mu = F_mu(n - mu)^+ h(n - mu),
+ * with F the fat links carrying the staggered phases and boundary sign.
+ * Vectors given to these calls are FP32 device vectors on the even sites. */
+typedef struct sqcg_nn sqcg_nn;
+#define SQCG_NN_NPARAMS 1472
+
+/* Network bound to ctx (its links and geometry); parameters start at zero. */
+int sqcg_nn_create(sqcg_ctx* ctx, sqcg_nn** out);
+int sqcg_nn_destroy(sqcg_nn* nn);
+int sqcg_nn_nparams(void);
+/* Copy parameters in (host floats, layout above; resets the optimiser state) or
+ * out (bf16_rounded != 0: the weights as the forward pass uses them). */
+int sqcg_nn_set_params(sqcg_nn* nn, const float* params);
+int sqcg_nn_get_params(const sqcg_nn* nn, float* params, int bf16_rounded);
+/* z = N(r). Asynchronous. */
+int sqcg_nn_apply(sqcg_nn* nn, const void* r, void* z);
+/* Training loss of one (residual r, error e) pair, L = <d, A d> / <e, r>,
+ * d = N(r) - e, A = sigma - D_eo D_oe (the A-norm of the preconditioned error
+ * relative to that of e), and its gradient (host floats, parameter layout,
+ * complex entries as dL/dRe + i dL/dIm). Synchronises. */
+int sqcg_nn_loss_grad(sqcg_nn* nn, double sigma, const void* r, const void* e, double* loss, float* grad);
+/* Adam (lr, beta1 0.9, beta2 0.999) over `steps` mini-batches of `batch` pairs
+ * drawn from npairs pairs (r, e: npairs consecutive FP32 even vectors each)
+ * with a seeded generator. loss_first / loss_last: mean batch loss of the
+ * first and last step. Synchronises. */
+int sqcg_nn_train(sqcg_nn* nn, double sigma, int npairs, const void* r, const void* e, int steps, int batch,
+                  double lr, unsigned long long seed, double* loss_first, double* loss_last);
+/* One training pair from a CG iterate: r = b - (sigma - D_eo D_oe) x_k in FP64,
+ * e = x_star - x_k, both rounded to FP32 (b, x_k, x_star: FP64 device vectors). */
+int sqcg_make_training_pair(sqcg_ctx* ctx, double sigma, const void* b, const void* x_k, const void* x_star,
+                            void* r_out, void* e_out);
+/* Flexible CG (Notay's FCG with one stored direction, Polak-Ribiere beta)
+ * preconditioned by nn, FP32 vectors with FP64 x and reliable updates, for
+ * (4 mass^2 - D_eo D_oe) x = b (FP64 device vectors; x = initial guess in,
+ * solution out). On breakdown (<p,Ap> <= 0, <z,r> <= 0, non-finite) or
+ * without convergence it hands over to the mixed-precision CG from the
+ * current iterate (info->fallback = 1), which also confirms the answer on the
+ * FP64 true residual. nn must be bound to ctx. Synchronises. */
+int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const void* b, void* x, double tol, int max_iter,
+                      sqcg_info* info);
 
 /* RHS block width W and site-block size T chosen by the autotuner for the
  * batched solve cached with ctx (the ctx passed first to the last batched call). */

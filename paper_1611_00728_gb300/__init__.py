@@ -21,13 +21,15 @@ import numpy as np
 __all__ = [
     "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
-    "batched_tuning",
+    "batched_tuning", "Network", "NN_NPARAMS",
 ]
 
 F64, F32 = 0, 1
 MODE_F64, MODE_MIXED = 0, 1
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
+#: parameters of the preconditioner network (see include/sqcg.h for the layout)
+NN_NPARAMS = 1472
 #: MILC's flop count of one Dslash output site: 16 x 66 (3x3 complex mat-vec) + 15 x 6 (adds)
 FLOPS_PER_SITE = 1146
 
@@ -55,10 +57,18 @@ class SqcgError(RuntimeError):
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
-                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int)]
+                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int),
+                ("fallback", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build_if_needed():
+    """Compile libsqcg.so in-tree when it is missing or older than its sources."""
+    from . import build as _b
+
+    return _b.build()
 
 
 def library():
@@ -85,11 +95,24 @@ def library():
         lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
         lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.sqcg_nn_create.argtypes = [P, ctypes.POINTER(P)]
+        lib.sqcg_nn_destroy.argtypes = [P]
+        lib.sqcg_nn_nparams.argtypes = []
+        lib.sqcg_nn_set_params.argtypes = [P, P]
+        lib.sqcg_nn_get_params.argtypes = [P, P, I]
+        lib.sqcg_nn_apply.argtypes = [P, P, P]
+        lib.sqcg_nn_loss_grad.argtypes = [P, D, P, P, ctypes.POINTER(D), P]
+        lib.sqcg_nn_train.argtypes = [P, D, I, P, P, I, I, D, ctypes.c_ulonglong, ctypes.POINTER(D),
+                                      ctypes.POINTER(D)]
+        lib.sqcg_make_training_pair.argtypes = [P, D, P, P, P, P, P]
+        lib.sqcg_fcg_solve_nn.argtypes = [P, P, D, P, P, D, I, ctypes.POINTER(Info)]
         lib.sqcg_strerror.argtypes = [I]
         lib.sqcg_strerror.restype = ctypes.c_char_p
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
-                     "sqcg_normal_op_noalloc",
+                     "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
+                     "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_loss_grad", "sqcg_nn_train",
+                     "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
                      "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning"):
             getattr(lib, name).restype = I
         _lib = lib
@@ -292,3 +315,96 @@ def batched_tuning(lattice) -> tuple[int, int]:
     W, T = ctypes.c_int(), ctypes.c_int()
     _check(library().sqcg_batched_tuning(lattice._h, ctypes.byref(W), ctypes.byref(T)), "sqcg_batched_tuning")
     return W.value, T.value
+
+
+class Network:
+    """The gauge-covariant preconditioner network bound to one Lattice (its links).
+
+    Vectors are FP32 even-site device vectors (3, Vh, 2) float32."""
+
+    def __init__(self, lattice: Lattice):
+        self.lattice = lattice
+        h = ctypes.c_void_p()
+        _check(library().sqcg_nn_create(lattice._h, ctypes.byref(h)), "sqcg_nn_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().sqcg_nn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (NN_NPARAMS,):
+            raise ValueError(f"expected {NN_NPARAMS} parameters")
+        self.lattice._sync_stream()
+        _check(library().sqcg_nn_set_params(self._h, p.ctypes.data), "sqcg_nn_set_params")
+
+    def get_params(self, bf16_rounded: bool = False) -> np.ndarray:
+        p = np.empty(NN_NPARAMS, dtype=np.float32)
+        self.lattice._sync_stream()
+        _check(library().sqcg_nn_get_params(self._h, p.ctypes.data, int(bf16_rounded)), "sqcg_nn_get_params")
+        return p
+
+    def apply(self, r, z):
+        lat = self.lattice
+        lat._sync_stream()
+        _check(library().sqcg_nn_apply(self._h, lat._check_spinor(r, F32, lat.Vh), lat._check_spinor(z, F32, lat.Vh)),
+               "sqcg_nn_apply")
+        return z
+
+    def loss_grad(self, sigma: float, r, e):
+        lat = self.lattice
+        loss = ctypes.c_double()
+        grad = np.empty(NN_NPARAMS, dtype=np.float32)
+        lat._sync_stream()
+        _check(library().sqcg_nn_loss_grad(self._h, float(sigma), lat._check_spinor(r, F32, lat.Vh),
+                                           lat._check_spinor(e, F32, lat.Vh), ctypes.byref(loss), grad.ctypes.data),
+               "sqcg_nn_loss_grad")
+        return loss.value, grad
+
+    def train(self, sigma: float, r_pairs, e_pairs, steps: int, batch: int = 8, lr: float = 1e-2, seed: int = 1):
+        """r_pairs, e_pairs: CUDA float32 tensors (npairs, 3, Vh, 2). Returns (first, last) batch loss."""
+        lat = self.lattice
+        torch = _torch()
+        for t in (r_pairs, e_pairs):
+            if t.dtype != torch.float32 or t.dim() != 4 or tuple(t.shape[1:]) != (3, lat.Vh, 2) or not t.is_cuda \
+                    or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous CUDA float32 tensor (npairs, 3, {lat.Vh}, 2)")
+        if r_pairs.shape[0] != e_pairs.shape[0]:
+            raise ValueError("as many errors as residuals")
+        first, last = ctypes.c_double(), ctypes.c_double()
+        lat._sync_stream()
+        _check(library().sqcg_nn_train(self._h, float(sigma), int(r_pairs.shape[0]), r_pairs.data_ptr(),
+                                       e_pairs.data_ptr(), int(steps), int(batch), float(lr), int(seed),
+                                       ctypes.byref(first), ctypes.byref(last)), "sqcg_nn_train")
+        return first.value, last.value
+
+    def make_pair(self, sigma: float, b, x_k, x_star, r_out, e_out):
+        """r = b - A x_k (FP64, rounded to FP32), e = x_star - x_k (FP32)."""
+        lat = self.lattice
+        lat._sync_stream()
+        _check(library().sqcg_make_training_pair(lat._h, float(sigma), lat._check_spinor(b, F64, lat.Vh),
+                                                 lat._check_spinor(x_k, F64, lat.Vh),
+                                                 lat._check_spinor(x_star, F64, lat.Vh),
+                                                 lat._check_spinor(r_out, F32, lat.Vh),
+                                                 lat._check_spinor(e_out, F32, lat.Vh)), "sqcg_make_training_pair")
+
+    def fcg_solve(self, mass: float, b, x, tol: float = 1e-8, max_iter: int = 10000,
+                  raise_on_error: bool = True) -> Info:
+        """Flexible CG preconditioned by this network on its lattice."""
+        lat = self.lattice
+        info = Info()
+        lat._sync_stream()
+        rc = library().sqcg_fcg_solve_nn(lat._h, self._h, float(mass), lat._check_spinor(b, F64, lat.Vh),
+                                         lat._check_spinor(x, F64, lat.Vh), float(tol), int(max_iter),
+                                         ctypes.byref(info))
+        if raise_on_error:
+            _check(rc, "sqcg_fcg_solve_nn")
+        return info

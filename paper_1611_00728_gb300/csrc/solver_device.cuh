@@ -141,8 +141,31 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       else if (s->iter >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; }
       break;
     }
+    case FIN_NN_SCALE:  // |r|^2 of the network input
+      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); s->nn_s = s->nn_inv_s = 0.0; break; }
+      s->nn_s = sqrt(3.0 * (double)s->vh / v);
+      s->nn_inv_s = 1.0 / s->nn_s;
+      break;
+    case FIN_FCG_PAP:  // alpha = <z_k, r_k> / <p_k, A p_k>
+      s->pAp = v;
+      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
+      s->alpha = s->rz / v;
+      break;
+    case FIN_FCG_INIT:
+      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
+      s->rz = v;
+      break;
     default:
       break;
+  }
+}
+
+// scalar steps that take two sums (a = first, b = second)
+__device__ inline void solver_finish2(SolverState* s, int fin, double a, double b) {
+  if (fin == FIN_FCG_BETA) {  // a = <z_{k+1}, r_{k+1}>, b = <z_{k+1}, r_k>
+    if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) { finish_breakdown(s); return; }
+    s->beta = (a - b) / s->rz;  // Polak-Ribiere (flexible) beta
+    s->rz = a;
   }
 }
 
@@ -156,13 +179,34 @@ __device__ __forceinline__ void block_partial(double v, double* partials) {
   if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 
-// Second stage: one block of kFinishThreads threads.
-constexpr int kFinishThreads = 256;
+// Second stage: one block of kFinishThreads threads (each adds only a few partials).
+constexpr int kFinishThreads = 1024;
 
 __device__ __forceinline__ void finish_partials(SolverState* st, const double* partials, int n, int fin) {
   double s = 0.0;
-#pragma unroll 8
+#pragma unroll 4
   for (int j = threadIdx.x; j < n; j += blockDim.x) s += partials[j];
   s = block_sum(s);
   if (threadIdx.x == 0) solver_finish(st, fin, s);
+}
+
+// two sums at once: block partials of the second sum follow those of the first (offset n)
+__device__ __forceinline__ void block_partial2(double v, double w, double* partials) {
+  const double a = block_sum(v);
+  const double b = block_sum(w);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = b;
+  }
+}
+
+__device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    a += partials[j];
+    b += partials[n + j];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) solver_finish2(st, fin, a, b);
 }

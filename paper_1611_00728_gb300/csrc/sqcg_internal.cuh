@@ -68,12 +68,18 @@ struct SolverState {
   int need_update;  // the FP64 true-residual pass runs in this iteration
   int updates;      // reliable updates performed inside the loop
   int mixed;        // working vectors are FP32
+  int vh;           // sites per parity (network input scale)
   int use_if;       // the reliable-update pass is an IF node whose condition FIN_UPDATE sets
   unsigned int counter;  // last-block counter of the grid reductions
   int loop_count;        // iterations of the device-side WHILE loop so far
   int loop_limit;        // hard bound on loop_count (the loop always ends)
   unsigned long long h_while;  // conditional handle of the WHILE node (cudaGraphConditionalHandle)
   unsigned long long h_if;     // conditional handle of the reliable-update IF node
+
+  // flexible CG with the network preconditioner
+  double rz;          // <z_k, r_k>
+  double nn_s;        // network input scale sqrt(3 Vh) / |r|
+  double nn_inv_s;    // 1 / nn_s
 
   // multi-shift CG (Jegerlehner recurrences; shift s uses sigma + dsig[s])
   int nshift;
@@ -127,6 +133,10 @@ enum Finisher {
   FIN_INIT = 6,        // initial residual r = b - A x0
   FIN_MS_PAP = 7,      // multi-shift: alpha and the zeta recurrences of every shift
   FIN_MS_UPDATE = 8,   // multi-shift: new |r|^2, beta, per-shift convergence
+  FIN_NN_SCALE = 9,    // network input scale from |r|^2
+  FIN_FCG_PAP = 10,    // flexible CG: alpha = <z,r> / <p,Ap>
+  FIN_FCG_BETA = 11,   // flexible CG (two sums): beta = (<z,r> - <z,r_old>) / <z_old,r_old>
+  FIN_FCG_INIT = 12,   // flexible CG: <z_0, r_0>
 };
 
 // ---------------------------------------------------------------------------
@@ -206,6 +216,7 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
 int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
+int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);

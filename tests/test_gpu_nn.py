@@ -1,0 +1,166 @@
+"""Preconditioner network and flexible CG on the GPU vs the FP64 numpy oracle (oracle/nn.py).
+
+Forward pass and training gradient are compared element by element with the
+oracle evaluated on the same BF16-rounded weights; the GPU accumulates in FP32,
+so the bars are relative errors of 1e-5 (forward) and 1e-4 (loss, gradient).
+Flexible-CG solutions must reach the true relative residual tol recomputed by
+the FP64 oracle; the fallback to plain CG is exercised with a network that
+outputs zero.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.nn as onn
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def flat_to_params(p):
+    """Host parameter layout (include/sqcg.h) -> oracle parameter dict."""
+    p = np.asarray(p, dtype=np.float64)
+    c = p[:1440].reshape(-1, 2)
+    w = c[:, 0] + 1j * c[:, 1]
+    return {"W": [w[:72].reshape(9, 8, 1), w[72:648].reshape(9, 8, 8), w[648:720].reshape(9, 1, 8)],
+            "gates": [(p[1440:1448], p[1448:1456]), (p[1456:1464], p[1464:1472])]}
+
+
+def params_to_flat(d):
+    out = np.zeros(1472)
+    w = np.concatenate([d["W"][0].ravel(), d["W"][1].ravel(), d["W"][2].ravel()])
+    out[:1440:2], out[1:1440:2] = w.real, w.imag
+    out[1440:1448], out[1448:1456] = d["gates"][0]
+    out[1456:1464], out[1464:1472] = d["gates"][1]
+    return out.astype(np.float32)
+
+
+def to_f32(x):
+    return np.asarray(x, dtype=np.complex64).astype(np.complex128)
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 6), (8, 8, 8, 8), (6, 8, 10, 12)])
+def test_network_forward_matches_oracle(sqcg, links_cache, L):
+    fat, lng = links_cache(L, 51)
+    r = to_f32(synth.gaussian_source(L, 52))
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(5, scale=0.6)))
+        z = net.apply(lat.pack(r, sqcg.F32), lat.new_spinor(sqcg.F32))
+        got = lat.unpack(z, sqcg.F32)
+        want = onn.apply(L, fat, flat_to_params(net.get_params(bf16_rounded=True)), r)
+        net.close()
+    assert rel(got, want) <= 1e-5
+
+
+def test_network_gauge_covariance_on_gpu(sqcg, links_cache):
+    L = (8, 8, 8, 8)
+    fat, lng = links_cache(L, 53)
+    G = synth.random_gauge(L, 54)
+    r = synth.gaussian_source(L, 55)
+    params = params_to_flat(onn.init_params(6, scale=0.6))
+    outs = []
+    for f, l, src in [(fat, lng, r), (synth.gauge_transform_links(L, fat, G, 1), synth.gauge_transform_links(L, lng, G, 3),
+                                      synth.gauge_transform_parity_field(L, r, G, 0))]:
+        with sqcg.Lattice(L) as lat:
+            lat.load_links(f, l)
+            net = sqcg.Network(lat)
+            net.set_params(params)
+            outs.append(lat.unpack(net.apply(lat.pack(src, sqcg.F32), lat.new_spinor(sqcg.F32)), sqcg.F32))
+            net.close()
+    assert rel(outs[1], synth.gauge_transform_parity_field(L, outs[0], G, 0)) <= 1e-5
+
+
+def test_loss_and_gradient_match_oracle(sqcg, links_cache):
+    L, sigma = (4, 4, 4, 6), 0.05
+    fat, lng = links_cache(L, 56)
+    r = to_f32(synth.gaussian_source(L, 57))
+    e = to_f32(np.linalg.solve(oracle.dense_normal_matrix(L, fat, lng, sigma), r.ravel()).reshape(r.shape))
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(7, scale=0.7)))
+        loss, grad = net.loss_grad(sigma, lat.pack(r, sqcg.F32), lat.pack(e, sqcg.F32))
+        p = flat_to_params(net.get_params(bf16_rounded=True))
+        net.close()
+    want_loss, g = onn.loss_and_grad(L, fat, lng, p, r, e, sigma)
+    want = params_to_flat(g).astype(np.float64)
+    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    assert rel(grad.astype(np.float64), want) <= 1e-4
+    for lo, hi in [(0, 144), (144, 1296), (1296, 1440), (1440, 1472)]:  # every block of parameters
+        assert rel(grad[lo:hi].astype(np.float64), want[lo:hi]) <= 1e-3
+
+
+def make_pairs(sqcg, lat, net, fat, lng, m, seeds, ks):
+    """(r_k, e_k) pairs from CG iterates x_k (CG from 0 truncated at k iterations) and a tight x*."""
+    sigma = 4 * m * m
+    rs, es = [], []
+    for sd in seeds:
+        b = lat.pack(synth.gaussian_source(lat.dims, sd))
+        xs = lat.new_spinor()
+        lat.cg_solve(m, b, xs, tol=1e-12, max_iter=20000, mode=0)
+        for k in ks:
+            xk = lat.new_spinor()
+            if k > 0:  # the k-th CG iterate from x0 = 0 (k = 0: x0 itself)
+                lat.cg_solve(m, b, xk, tol=1e-30, max_iter=k, mode=0, raise_on_error=False)
+            r32, e32 = lat.new_spinor(sqcg.F32), lat.new_spinor(sqcg.F32)
+            net.make_pair(sigma, b, xk, xs, r32, e32)
+            rs.append(r32)
+            es.append(e32)
+    return torch.stack(rs).contiguous(), torch.stack(es).contiguous()
+
+
+def test_training_pair_matches_oracle(sqcg, links_cache):
+    L, m = (8, 8, 8, 8), 0.05
+    fat, lng = links_cache(L, 58)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        b = synth.gaussian_source(L, 59)
+        xk = synth.gaussian_source(L, 60)
+        xs = synth.gaussian_source(L, 61)
+        r32, e32 = lat.new_spinor(sqcg.F32), lat.new_spinor(sqcg.F32)
+        net.make_pair(4 * m * m, lat.pack(b), lat.pack(xk), lat.pack(xs), r32, e32)
+        assert rel(lat.unpack(r32, sqcg.F32), b - oracle.normal_op(L, fat, lng, 4 * m * m, xk)) <= 1e-6
+        assert rel(lat.unpack(e32, sqcg.F32), xs - xk) <= 1e-6
+        net.close()
+
+
+def test_training_lowers_loss_and_fcg_converges(sqcg, links_cache):
+    L, m, tol = (8, 8, 8, 8), 0.02, 1e-8
+    fat, lng = links_cache(L, 62)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(8, scale=0.3)))
+        R, E = make_pairs(sqcg, lat, net, fat, lng, m, seeds=[70, 71, 72], ks=[0, 2, 5, 10, 20])
+        first, last = net.train(4 * m * m, R, E, steps=150, batch=4, lr=2e-2, seed=3)
+        assert last < first
+        # held-out source: flexible CG preconditioned by the trained network
+        b = synth.gaussian_source(L, 90)
+        x = lat.new_spinor()
+        info = net.fcg_solve(m, lat.pack(b), x, tol=tol, max_iter=2000)
+        assert info.status == 0 and info.true_rel_resid <= tol
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
+        net.close()
+
+
+def test_fcg_falls_back_to_plain_cg(sqcg, links_cache):
+    L, m, tol = (8, 8, 8, 8), 0.05, 1e-8
+    fat, lng = links_cache(L, 63)
+    b = synth.gaussian_source(L, 91)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)  # all parameters zero: N(r) = 0, so <z, r> = 0 (breakdown)
+        x = lat.new_spinor()
+        info = net.fcg_solve(m, lat.pack(b), x, tol=tol, max_iter=2000)
+        assert info.fallback == 1 and info.status == 0
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
+        net.close()
