@@ -65,7 +65,7 @@ extern "C" {
 #define SQCG_PHASES_FOLDED 2  /* links passed to sqcg_load_links already carry eta and the boundary sign */
 
 /* ---- sqcg_load_links options ---- */
-#define SQCG_RECON12_LONG 1 /* store long links as 2 rows (12 reals) and rebuild row 3 on the fly */
+#define SQCG_RECON12_LONG 1 /* FP32 long links as 2 rows (12 reals), row 3 rebuilt on the fly */
 
 /* ---- precisions ---- */
 #define SQCG_F64 0
@@ -108,10 +108,12 @@ int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
  * parity-split structure-of-arrays layout and keeps an FP64 and an FP32 copy on
  * the device (owned by the context, replacing earlier links). The host arrays
  * are only read during the call.
- * opts: SQCG_RECON12_LONG stores the long links as their first two rows; it is
- * accepted only if every long link is s * W with W in SU(3) and one global
- * real |s| (checked to 1e-12), else SQCG_ERR_RECON_REJECTED and nothing is
- * loaded. Fat links are always stored in full. */
+ * opts: SQCG_RECON12_LONG stores the FP32 copy of the long links as their
+ * first two rows (the FP32 Dslash rebuilds the third); it is accepted only if
+ * every long link is s * W with W in SU(3) and one global real |s| (checked to
+ * 1e-12), else SQCG_ERR_RECON_REJECTED and nothing is loaded. The FP64 copy
+ * and the fat links are always stored in full (the FP64 Dslash is bound by
+ * FP64 arithmetic, which the reconstruction would add to). */
 int sqcg_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 
 /* Copy one host colour vector (parity order, complex double [Vh][3]) into a
@@ -187,7 +189,8 @@ int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, co
  * loaded once per block of W right-hand sides. W (1..16) and the site-block
  * size are picked on the first call for a given set of lattices by timing the
  * multi-RHS Dslash (cached per process, and in the file named by the
- * environment variable SQCG_TUNE_CACHE if set).
+ * environment variable SQCG_TUNE_CACHE if set; SQCG_TUNE_VERBOSE=1 prints each
+ * timed candidate to stderr).
  * ctx[k]: distinct contexts with links loaded, all on the current device; the
  * work runs on ctx[0]'s stream. b[k], x[k]: device arrays of nrhs[k]
  * consecutive FP64 device vectors ([nrhs][3][Vh] complex double); x[k] holds

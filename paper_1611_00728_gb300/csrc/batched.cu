@@ -40,7 +40,7 @@ struct LatDev {
   const float2* lng32[2];
   const double2* fat64[2];
   const double2* lng64[2];
-  int nl, recon;
+  int nl32, recon;  // the 12-real long-link form exists for the FP32 copy only
   float inv_s0_f;
   double inv_s0_d;
   int rhs0, nrhs;  // global index of the first RHS, count
@@ -255,7 +255,8 @@ __device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i
     fat_p = L.fat32[par]; fat_q = L.fat32[1 - par]; lng_p = L.lng32[par]; lng_q = L.lng32[1 - par];
     inv_s0 = (R)L.inv_s0_f;
   }
-  const bool recon = L.recon != 0;
+  const bool recon = (sizeof(R) == 4) && L.recon != 0;
+  const int nl = recon ? 6 : 9;
   R2 U[9];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
@@ -293,9 +294,9 @@ __device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i
         load_link_m<R, false>(U, fat_q + (size_t)mu * 9 * Vh, Vh, bwd, false, R(1));
         apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
       } else {
-        load_link_m<R, true>(U, lng_p + (size_t)mu * L.nl * Vh, Vh, i, recon, inv_f);
+        load_link_m<R, true>(U, lng_p + (size_t)mu * nl * Vh, Vh, i, recon, inv_f);
         apply_w<R, W, false>(acc, U, in, Vh, fwd, nw);
-        load_link_m<R, true>(U, lng_q + (size_t)mu * L.nl * Vh, Vh, bwd, recon, inv_b);
+        load_link_m<R, true>(U, lng_q + (size_t)mu * nl * Vh, Vh, bwd, recon, inv_b);
         apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
       }
     }
@@ -708,6 +709,7 @@ int autotune(BatchPlan& P, cudaStream_t s) {
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
+      if (getenv("SQCG_TUNE_VERBOSE")) fprintf(stderr, "sqcg tune %s W=%d T=%d %.4f ms\n", key.c_str(), W, T, ms / 5);
       if (ms < best) { best = ms; bestW = W; bestT = T; }
     }
     if (rc != SQCG_OK) break;
@@ -748,14 +750,14 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     LatDev& L = P->host[k];
     L.g = c->g;
     const size_t Vh = c->g.Vh;
-    const int nl = c->recon ? 6 : 9;
+    const int nl32 = c->recon ? 6 : 9;
     for (int par = 0; par < 2; ++par) {
       L.fat32[par] = c->fat32 + (size_t)par * 4 * 9 * Vh;
-      L.lng32[par] = c->lng32 + (size_t)par * 4 * nl * Vh;
+      L.lng32[par] = c->lng32 + (size_t)par * 4 * nl32 * Vh;
       L.fat64[par] = c->fat64 + (size_t)par * 4 * 9 * Vh;
-      L.lng64[par] = c->lng64 + (size_t)par * 4 * nl * Vh;
+      L.lng64[par] = c->lng64 + (size_t)par * 4 * 9 * Vh;
     }
-    L.nl = nl;
+    L.nl32 = nl32;
     L.recon = c->recon ? 1 : 0;
     L.inv_s0_f = (float)(c->recon ? 1.0 / c->long_scale : 1.0);
     L.inv_s0_d = c->recon ? 1.0 / c->long_scale : 1.0;

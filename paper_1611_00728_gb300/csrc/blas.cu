@@ -99,15 +99,14 @@ struct MSPtrs {
   void* p[SQCG_MAX_SHIFTS];
 };
 
-// r -= alpha Ap (base); x_s += alpha_s p_s for active shifts; reduce |r|^2 -> FIN_MS_UPDATE
+// r -= alpha Ap (base), reduce |r|^2 -> FIN_MS_UPDATE
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_ms_update(MSPtrs P, typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restrict__ Ap, int Vh,
-            SolverState* st, double* partials) {
+k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restrict__ Ap, int Vh, SolverState* st,
+            double* partials) {
   typedef typename V2<R>::T R2;
   if (!gate_open(st, GATE_ITER)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ns = st->nshift;
   double nrm = 0.0;
   if (i < Vh) {
     const R ra = (R)st->alpha;
@@ -123,57 +122,53 @@ k_ms_update(MSPtrs P, typename V2<R>::T* __restrict__ r, const typename V2<R>::T
       part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
     }
     nrm = (double)part;
-    for (int j = 0; j < ns; ++j) {
-      if (!st->active[j]) continue;
-      const double as = st->alpha_s[j];
-      const R2* ps = static_cast<const R2*>(P.p[j]);
-      double2* xs = P.x[j];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t k = (size_t)c * Vh + i;
-        const R2 pc = ps[k];
-        double2 xc = xs[k];
-        xc.x = fma(as, (double)pc.x, xc.x);
-        xc.y = fma(as, (double)pc.y, xc.y);
-        xs[k] = xc;
-      }
-    }
   }
   block_partial(nrm, partials);
 }
 
-// p = r + beta p (base, which is also shift 0's direction); p_s = zeta_s r + beta_s p_s (shifts >= 1)
+// One pass over every shift's direction: x_s += alpha_s p_s (the old p_s; for
+// every shift with an update this iteration, including one that just
+// converged), then p_s = zeta_s r + beta_s p_s for shifts still iterating.
+// Shift 0 is the base system: its direction is the base p = r + beta p.
+// Runs while the loop goes on, and once more in the iteration that ends it.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict__ p, int Vh,
           const SolverState* st) {
   typedef typename V2<R>::T R2;
-  if (!gate_open(st, GATE_ITER)) return;
+  const volatile SolverState* vs = st;
+  const int done = vs->done;
+  if (done && !vs->ms_final) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Vh) return;
   const int ns = st->nshift;
   R2 rc[3];
-  const R beta = (R)st->beta;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const size_t k = (size_t)c * Vh + i;
-    rc[c] = r[k];
-    R2 pc = p[k];
-    pc.x = fma(beta, pc.x, rc[c].x);
-    pc.y = fma(beta, pc.y, rc[c].y);
-    p[k] = pc;
-  }
-  for (int j = 1; j < ns; ++j) {
-    if (!st->active[j]) continue;
-    const R z = (R)st->zeta[j], bs = (R)st->beta_s[j];
-    R2* ps = static_cast<R2*>(P.p[j]);
+  for (int c = 0; c < 3; ++c) rc[c] = r[(size_t)c * Vh + i];
+  for (int j = 0; j < ns; ++j) {
+    const int act = st->active[j];
+    const bool upd_p = !done && (j == 0 || act == 1);  // the base direction moves while the loop runs
+    if (!act && !upd_p) continue;
+    R2* ps = (j == 0) ? p : static_cast<R2*>(P.p[j]);
+    const double as = st->alpha_s[j];
+    const R z = (j == 0) ? R(1) : (R)st->zeta[j];
+    const R bs = (j == 0) ? (R)st->beta : (R)st->beta_s[j];
+    double2* xs = P.x[j];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * Vh + i;
       R2 pc = ps[k];
-      pc.x = fma(bs, pc.x, z * rc[c].x);
-      pc.y = fma(bs, pc.y, z * rc[c].y);
-      ps[k] = pc;
+      if (act) {
+        double2 xc = xs[k];
+        xc.x = fma(as, (double)pc.x, xc.x);
+        xc.y = fma(as, (double)pc.y, xc.y);
+        xs[k] = xc;
+      }
+      if (upd_p) {
+        pc.x = fma(bs, pc.x, z * rc[c].x);
+        pc.y = fma(bs, pc.y, z * rc[c].y);
+        ps[k] = pc;
+      }
     }
   }
 }
@@ -269,20 +264,21 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
     P.x[j] = (j < nshift) ? x[j] : nullptr;
     P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
   }
+  (void)P;
   if (mixed)
-    k_ms_update<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->Ap32, Vh, ctx->st, ctx->partials);
+    k_ms_update<float><<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, Vh, ctx->st, ctx->partials);
   else
-    k_ms_update<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, ctx->Ap64, Vh, ctx->st, ctx->partials);
+    k_ms_update<double><<<grid, kThreads, 0, s>>>(ctx->r64, ctx->Ap64, Vh, ctx->st, ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
   return launch_finish(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s);
 }
 
-int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, cudaStream_t s) {
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
   if (nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
   MSPtrs P;
   for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
-    P.x[j] = nullptr;
+    P.x[j] = (j < nshift) ? x[j] : nullptr;
     P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
   }
   if (mixed)

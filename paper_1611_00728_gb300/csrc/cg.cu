@@ -122,7 +122,7 @@ int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x
   L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_MS_PAP;
   SQCG_TRY(launch_dslash(ctx, L, s));
   SQCG_TRY(launch_ms_update_x(ctx, mixed, nshift, x, s));
-  SQCG_TRY(launch_ms_xpay(ctx, mixed, nshift, s));
+  SQCG_TRY(launch_ms_xpay(ctx, mixed, nshift, x, s));
   return SQCG_OK;
 }
 

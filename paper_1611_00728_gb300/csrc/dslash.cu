@@ -11,8 +11,8 @@
 // The backward hop reads the forward link of the neighbour and applies the
 // dagger in registers (forward-only storage, the standard MILC layout).
 // Neighbour indices are computed from the site coordinates (no index tables).
-// With 12-real long links the third row is rebuilt as conj(row0 x row1) / s,
-// s = s0 * eta_mu * boundary sign of that link.
+// With 12-real long links (FP32 copy only) the third row is rebuilt as
+// conj(row0 x row1) / s, s = s0 * eta_mu * boundary sign of that link.
 #include "solver_device.cuh"
 #include "sqcg_internal.cuh"
 
@@ -240,7 +240,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   a.par = L.out_parity;
   const int p = L.out_parity, q = 1 - L.out_parity;
   const size_t Vh = ctx->g.Vh;
-  const int nl = ctx->recon ? 6 : 9;
+  const int nl = RECON ? 6 : 9;  // the 12-real form exists for the FP32 copy only
   const R2* fat = reinterpret_cast<const R2*>(L.prec == SQCG_F64 ? (const void*)ctx->fat64 : (const void*)ctx->fat32);
   const R2* lng = reinterpret_cast<const R2*>(L.prec == SQCG_F64 ? (const void*)ctx->lng64 : (const void*)ctx->lng32);
   a.fat_p = fat + (size_t)p * 4 * 9 * Vh;
@@ -248,7 +248,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   a.lng_p = lng + (size_t)p * 4 * nl * Vh;
   a.lng_q = lng + (size_t)q * 4 * nl * Vh;
   a.nl = nl;
-  a.inv_s0 = (R)(ctx->recon ? 1.0 / ctx->long_scale : 1.0);
+  a.inv_s0 = (R)(RECON ? 1.0 / ctx->long_scale : 1.0);
   a.in = static_cast<const R2*>(L.in);
   a.out = L.out;
   a.out2 = L.out2;
@@ -280,7 +280,10 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
 
 template <typename R, typename RO>
 int launch_r(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
-  return ctx->recon ? launch_t<R, RO, true>(ctx, L, s) : launch_t<R, RO, false>(ctx, L, s);
+  if constexpr (sizeof(R) == 4) {
+    if (ctx->recon) return launch_t<R, RO, true>(ctx, L, s);
+  }
+  return launch_t<R, RO, false>(ctx, L, s);
 }
 
 }  // namespace

@@ -23,8 +23,9 @@ __device__ __forceinline__ void coords_of(const Geom& g, long n, int& x, int& y,
   t = (int)(n / g.Lz);
 }
 
-// one thread per (mu, site): raw[n][mu][9] -> out[par][mu][e][n/2] (e < nelem)
-__global__ void k_pack_links(const double2* __restrict__ raw, Geom g, int fold, int hop, int nelem,
+// one thread per (mu, site): raw[n][mu][9] -> out64[par][mu][e][n/2] (e < 9) and
+// out32[par][mu][e][n/2] (e < nelem32: 9, or 6 for the 12-real form)
+__global__ void k_pack_links(const double2* __restrict__ raw, Geom g, int fold, int hop, int nelem32,
                              double2* __restrict__ out64, float2* __restrict__ out32) {
   const long V = 2L * g.Vh;
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,12 +46,14 @@ __global__ void k_pack_links(const double2* __restrict__ raw, Geom g, int fold, 
     if (mu == 3 && g.apbc && t + hop >= g.Lt) f = -f;
   }
   const double2* src = raw + (n * 4 + mu) * 9;
-  const size_t base = ((size_t)par * 4 + mu) * nelem * g.Vh;
-  for (int e = 0; e < nelem; ++e) {
+  const size_t base64 = ((size_t)par * 4 + mu) * 9 * g.Vh;
+  const size_t base32 = ((size_t)par * 4 + mu) * nelem32 * g.Vh;
+  for (int e = 0; e < 9; ++e) {
     const double2 u = src[e];
     const double2 v = make_double2(f * u.x, f * u.y);
-    out64[base + (size_t)e * g.Vh + ih] = v;
-    out32[base + (size_t)e * g.Vh + ih] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    out64[base64 + (size_t)e * g.Vh + ih] = v;
+    if (e < nelem32)
+      out32[base32 + (size_t)e * g.Vh + ih] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
   }
 }
 
@@ -167,8 +170,10 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   if (recon && !recon_check(ctx, lng, &s0)) return SQCG_ERR_RECON_REJECTED;
 
   const size_t Vh = ctx->g.Vh, V = 2 * Vh;
-  const int nl = recon ? 6 : 9;
-  const size_t nfat = 2 * 4 * 9 * Vh, nlng = 2 * 4 * (size_t)nl * Vh;
+  // the 12-real form is used for the FP32 copy only: on this GPU the FP64 Dslash is
+  // bound by FP64 arithmetic, which rebuilding the third row would only add to
+  const int nl32 = recon ? 6 : 9;
+  const size_t nfat = 2 * 4 * 9 * Vh, nlng64 = 2 * 4 * 9 * Vh, nlng32 = 2 * 4 * (size_t)nl32 * Vh;
   cudaStream_t s = ctx->stream;
 
   // drop earlier links
@@ -182,9 +187,9 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
 
   void* raw = nullptr;
   bool ok = cudaMalloc((void**)&ctx->fat64, nfat * sizeof(double2)) == cudaSuccess &&
-            cudaMalloc((void**)&ctx->lng64, nlng * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->lng64, nlng64 * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->fat32, nfat * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&ctx->lng32, nlng * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->lng32, nlng32 * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&raw, V * 4 * 9 * sizeof(double2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -203,7 +208,7 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
     k_pack_links<<<grid, kThreads, 0, s>>>((const double2*)raw, ctx->g, fold, 1, 9, ctx->fat64, ctx->fat32);
     if (cudaGetLastError() != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     if (cudaMemcpyAsync(raw, lng, V * 4 * 9 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-    k_pack_links<<<grid, kThreads, 0, s>>>((const double2*)raw, ctx->g, fold, 3, nl, ctx->lng64, ctx->lng32);
+    k_pack_links<<<grid, kThreads, 0, s>>>((const double2*)raw, ctx->g, fold, 3, nl32, ctx->lng64, ctx->lng32);
     if (cudaGetLastError() != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
   } while (0);

@@ -104,6 +104,8 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
     }
     case FIN_MS_PAP: {  // base alpha_k, then zeta_{k+1} and alpha^s_k for every shift
       s->pAp = v;
+      for (int j = 0; j < s->nshift; ++j)
+        if (s->active[j] == 2) s->active[j] = 0;  // its final x update was applied last iteration
       if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
       const double a = s->rr / v;
       s->alpha = a;
@@ -123,13 +125,14 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       const double b = v / s->rr;
       int any = 0;
       for (int j = 0; j < s->nshift; ++j) {
-        if (!s->active[j]) continue;
+        if (s->active[j] != 1) continue;
         const double zk = s->zeta[j], znext = s->beta_s[j];
         s->zeta_prev[j] = zk;
         s->zeta[j] = znext;
         s->beta_s[j] = b * (znext / zk) * (znext / zk);
         s->iters_s[j] = s->iter;
-        if (znext * znext * v <= s->stop_rr_s[j]) s->active[j] = 0;  // shift residual = zeta * r
+        // shift residual = zeta * r; a converged shift still takes this iteration's x update (state 2)
+        if (znext * znext * v <= s->stop_rr_s[j]) s->active[j] = 2;
         else any = 1;
       }
       s->rr_prev = s->rr;
@@ -137,8 +140,8 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       s->beta = b;
       s->alpha_prev = s->alpha;
       s->beta_prev = b;
-      if (!any) { s->done = 1; s->status = SQCG_OK; }
-      else if (s->iter >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; }
+      if (!any) { s->done = 1; s->status = SQCG_OK; s->ms_final = 1; }
+      else if (s->iter >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; s->ms_final = 1; }
       break;
     }
     case FIN_NN_SCALE:  // |r|^2 of the network input

@@ -83,7 +83,8 @@ struct SolverState {
 
   // multi-shift CG (Jegerlehner recurrences; shift s uses sigma + dsig[s])
   int nshift;
-  int active[SQCG_MAX_SHIFTS];  // shift still iterating
+  int ms_final;  // the loop has just ended: the fused update still applies the last x_s updates
+  int active[SQCG_MAX_SHIFTS];  // 1 iterating, 2 converged with its last x update pending, 0 done
   double dsig[SQCG_MAX_SHIFTS];
   double stop_rr_s[SQCG_MAX_SHIFTS];
   double zeta[SQCG_MAX_SHIFTS], zeta_prev[SQCG_MAX_SHIFTS];
@@ -222,7 +223,7 @@ int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
 
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
-int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, cudaStream_t s);
+int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 
 int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
