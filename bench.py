@@ -440,7 +440,7 @@ def run_multishift(args):
     b_host = synth.gaussian_source(LATTICE, 2300)
     shifts = list(np.logspace(-4, 0, 11))
     lat = sq.Lattice(LATTICE)
-    lat.load_links(fat, lng)
+    lat.load_links(fat, lng, recon12=True)
     b = lat.pack(b_host)
     xs = [lat.new_spinor() for _ in shifts]
     res = {}
@@ -495,7 +495,7 @@ def run_batched(args):
     for n, L in enumerate(specs):
         fat, lng = synth.fat_long_links(L, 1004 + n)
         lat = sq.Lattice(L)
-        lat.load_links(fat, lng)
+        lat.load_links(fat, lng, recon12=True)
         src = synth.gaussian_source(L, 2400 + 10 * n, nrhs=nr)
         b = torch.stack([lat.pack(s) for s in src]).contiguous()
         lats.append(lat); bs.append(b); xs.append(torch.zeros_like(b))
@@ -568,8 +568,9 @@ def run_learned(args):
     for gseed in range(8):
         fat, lng = synth.fat_long_links(Ltr, gseed)
         lat = sq.Lattice(Ltr)
-        lat.load_links(fat, lng)
+        lat.load_links(fat, lng, recon12=True)
         net = sq.Network(lat)
+        net.set_loss(2)
         for src in range(4):
             b = lat.pack(synth.gaussian_source(Ltr, 5000 + 10 * gseed + src))
             xs = lat.new_spinor()
@@ -610,7 +611,7 @@ def run_learned(args):
     for L in (Ltr, (32, 32, 32, 32)):
         fat, lng = synth.fat_long_links(L, 9000)
         lat = sq.Lattice(L)
-        lat.load_links(fat, lng)
+        lat.load_links(fat, lng, recon12=True)
         net = sq.Network(lat)
         net.set_params(params)
         b = lat.pack(synth.gaussian_source(L, 9100))

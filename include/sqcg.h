@@ -232,10 +232,13 @@ int sqcg_nn_set_params(sqcg_nn* nn, const float* params);
 int sqcg_nn_get_params(const sqcg_nn* nn, float* params, int bf16_rounded);
 /* z = N(r). Asynchronous. */
 int sqcg_nn_apply(sqcg_nn* nn, const void* r, void* z);
-/* Training loss of one (residual r, error e) pair, L = <d, A d> / <e, r>,
- * d = N(r) - e, A = sigma - D_eo D_oe (the A-norm of the preconditioned error
- * relative to that of e), and its gradient (host floats, parameter layout,
- * complex entries as dL/dRe + i dL/dIm). Synchronises. */
+/* Training loss of one (residual r, error e) pair, d = N(r) - e,
+ * A = sigma - D_eo D_oe, in the norm chosen by sqcg_nn_set_loss:
+ *   1 (default): L = <d, A d> / <e, r>  (A-norm of the error relative to that of e)
+ *   2:           L = <A d, A d> / <r, r> (A^2-norm: |A N(r) - r|^2 / |r|^2, since A e = r)
+ * and its gradient (host floats, parameter layout, complex entries as
+ * dL/dRe + i dL/dIm). Synchronises. */
+int sqcg_nn_set_loss(sqcg_nn* nn, int norm);
 int sqcg_nn_loss_grad(sqcg_nn* nn, double sigma, const void* r, const void* e, double* loss, float* grad);
 /* Adam (lr, beta1 0.9, beta2 0.999) over `steps` mini-batches of `batch` pairs
  * drawn from npairs pairs (r, e: npairs consecutive FP32 even vectors each)

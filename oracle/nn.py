@@ -24,9 +24,11 @@ single-mass CG (Sec. 3). Definition, written out plainly:
 Gauge covariance holds because the weights mix channels only (colour-blind),
 links carry colour, and the gate depends on the gauge-invariant |h|.
 
-Training loss for one (residual r, error e) pair with e = A^-1 r:
-    L = <d, A d> / <e, r>,  d = N(r) - e,   A = sigma - D_eo D_oe,
-i.e. the squared A-norm of the preconditioned error relative to that of e.
+Training loss for one (residual r, error e) pair with e = A^-1 r, d = N(r) - e,
+A = sigma - D_eo D_oe, in one of two norms:
+    norm 1:  L = <d, A d> / <e, r>         (A-norm of the error relative to that of e)
+    norm 2:  L = <A d, A d> / <r, r>       (A^2-norm: the residual of the preconditioned
+                                            step, |A N(r) - r|^2 / |r|^2, since A e = r)
 """
 
 from __future__ import annotations
@@ -168,17 +170,23 @@ def gate_backward(h, a, b, cache, gout):
     return grad_h, grad_a, grad_b
 
 
-def loss_and_grad(L, fat, lng, params, r_even, e_even, sigma, antiperiodic_t: bool = True):
-    """Loss L = <d, A d>/<e, r> for one (r, e) pair and its gradient w.r.t. every parameter.
+def loss_and_grad(L, fat, lng, params, r_even, e_even, sigma, antiperiodic_t: bool = True, norm: int = 1):
+    """Training loss of one (r, e) pair (norm 1 or 2, see the module docstring) and its
+    gradient w.r.t. every parameter.
 
     The loss is invariant under (r, e) -> (c r, c e) because N(c r) = c N(r)."""
     U = folded_fat(L, fat, antiperiodic_t)
     z, c = forward(L, U, params, r_even)
     d = z - e_even
     Ad = oracle.normal_op(L, fat, lng, sigma, d, antiperiodic_t)
-    er = np.real(np.vdot(e_even, r_even))
-    loss = float(np.real(np.vdot(d, Ad)) / er)
-    gz = 2.0 * Ad / er  # dL/dz (complex convention: dL/dRe z + i dL/dIm z)
+    if norm == 1:
+        er = np.real(np.vdot(e_even, r_even))
+        loss = float(np.real(np.vdot(d, Ad)) / er)
+        gz = 2.0 * Ad / er  # dL/dz (complex convention: dL/dRe z + i dL/dIm z)
+    else:
+        rr = np.real(np.vdot(r_even, r_even))
+        loss = float(np.real(np.vdot(Ad, Ad)) / rr)
+        gz = 2.0 * oracle.normal_op(L, fat, lng, sigma, Ad, antiperiodic_t) / rr
     par = c["par"]
     W, gates = params["W"], params["gates"]
     g3 = np.zeros((1, par.size, 3), dtype=np.complex128)

@@ -101,6 +101,7 @@ def library():
         lib.sqcg_nn_set_params.argtypes = [P, P]
         lib.sqcg_nn_get_params.argtypes = [P, P, I]
         lib.sqcg_nn_apply.argtypes = [P, P, P]
+        lib.sqcg_nn_set_loss.argtypes = [P, I]
         lib.sqcg_nn_loss_grad.argtypes = [P, D, P, P, ctypes.POINTER(D), P]
         lib.sqcg_nn_train.argtypes = [P, D, I, P, P, I, I, D, ctypes.c_ulonglong, ctypes.POINTER(D),
                                       ctypes.POINTER(D)]
@@ -111,7 +112,7 @@ def library():
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
-                     "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_loss_grad", "sqcg_nn_train",
+                     "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
                      "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning"):
             getattr(lib, name).restype = I
@@ -351,6 +352,10 @@ class Network:
         self.lattice._sync_stream()
         _check(library().sqcg_nn_get_params(self._h, p.ctypes.data, int(bf16_rounded)), "sqcg_nn_get_params")
         return p
+
+    def set_loss(self, norm: int):
+        """Training loss norm: 1 = A-norm of the error (default), 2 = A^2-norm (preconditioned residual)."""
+        _check(library().sqcg_nn_set_loss(self._h, int(norm)), "sqcg_nn_set_loss")
 
     def apply(self, r, z):
         lat = self.lattice

@@ -11,7 +11,9 @@
 //
 // Training minimises L = <d, A d> / <e, r>, d = N(r) - e, over (residual,
 // error) pairs produced by plain CG: the A-norm of the preconditioned error
-// relative to that of e. dL/dz = 2 A d / <e, r> is back-propagated with
+// relative to that of e (or, selectable, the A^2-norm <A d, A d> / <r, r>,
+// the residual of the preconditioned step). dL/dz (2 A d / <e, r>, or
+// 2 A A d / <r, r>) is back-propagated with
 // hand-written kernels (adjoint convolutions, gate backward, weight-gradient
 // reductions) and the weights follow Adam (FP32 master, BF16 forward copy).
 //
@@ -522,6 +524,7 @@ struct sqcg_nn {
   float2 *d, *Ad, *tmp, *zbuf;  // even FP32 vectors (training) / odd temp
   float2 *r_old, *z;       // flexible CG vectors
   bool train_ready;
+  int loss_norm;           // 1: A-norm of the error, 2: A^2-norm (preconditioned residual)
 };
 
 namespace {
@@ -670,9 +673,22 @@ int nn_pair(sqcg_nn* nn, double sigma, const float2* r, const float2* e, cudaStr
   L.out_parity = 0; L.epi = EPI_NORMAL; L.in = nn->tmp; L.out = nn->Ad; L.y = nn->d; L.sigma = sigma;
   SQCG_TRY(launch_dslash(ctx, L, s));
   const int grid = (Vh + kRedThreads - 1) / kRedThreads;
-  k_dot2<<<grid, kRedThreads, 0, s>>>(nn->d, nn->Ad, e, r, Vh, nn->partials);
-  k_nn_finish<<<1, kRedThreads, 0, s>>>(nn->partials, grid, nn->scal, 1, Vh);
-  k_dz<<<nn_grid(3 * Vh), kThreads, 0, s>>>(nn->Ad, nn->g3, Vh, nn->scal);
+  if (nn->loss_norm == 2) {
+    // L = <Ad, Ad> / <r, r>; dL/dz = 2 A (A d) / <r, r>   (A e = r: the preconditioned residual)
+    L = DslashLaunch{};
+    L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = nn->Ad; L.out = nn->tmp;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    L.out_parity = 0; L.epi = EPI_NORMAL; L.in = nn->tmp; L.out = nn->zbuf; L.y = nn->Ad; L.sigma = sigma;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    k_dot2<<<grid, kRedThreads, 0, s>>>(nn->Ad, nn->Ad, r, r, Vh, nn->partials);
+    k_nn_finish<<<1, kRedThreads, 0, s>>>(nn->partials, grid, nn->scal, 1, Vh);
+    k_dz<<<nn_grid(3 * Vh), kThreads, 0, s>>>(nn->zbuf, nn->g3, Vh, nn->scal);
+  } else {
+    // L = <d, A d> / <e, r>; dL/dz = 2 A d / <e, r>
+    k_dot2<<<grid, kRedThreads, 0, s>>>(nn->d, nn->Ad, e, r, Vh, nn->partials);
+    k_nn_finish<<<1, kRedThreads, 0, s>>>(nn->partials, grid, nn->scal, 1, Vh);
+    k_dz<<<nn_grid(3 * Vh), kThreads, 0, s>>>(nn->Ad, nn->g3, Vh, nn->scal);
+  }
   SQCG_CUDA_TRY(cudaGetLastError());
   // layer 3: dW3, dL/dh2
   SQCG_TRY((wgrad<CH, 1>(nn, IN_FULL, nn->h2, nn->g3, 1, OFF_W3, s)));
@@ -698,6 +714,7 @@ int sqcg_nn_create(sqcg_ctx* ctx, sqcg_nn** out) {
   sqcg_nn* nn = (sqcg_nn*)calloc(1, sizeof(sqcg_nn));
   if (!nn) return SQCG_ERR_NO_MEMORY;
   nn->ctx = ctx;
+  nn->loss_norm = 1;
   const size_t Vh = ctx->g.Vh;
   const size_t full = (size_t)CH * 2 * 3 * Vh;
   // partials: enough for the largest reduction (weight gradients: 1024 blocks x 1152 doubles)
@@ -743,6 +760,12 @@ int sqcg_nn_destroy(sqcg_nn* nn) {
 }
 
 int sqcg_nn_nparams(void) { return NPARAM; }
+
+int sqcg_nn_set_loss(sqcg_nn* nn, int norm) {
+  if (!nn || (norm != 1 && norm != 2)) return SQCG_ERR_INVALID_ARG;
+  nn->loss_norm = norm;
+  return SQCG_OK;
+}
 
 int sqcg_nn_set_params(sqcg_nn* nn, const float* params) {
   if (!nn || !params) return SQCG_ERR_INVALID_ARG;

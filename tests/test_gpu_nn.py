@@ -78,7 +78,8 @@ def test_network_gauge_covariance_on_gpu(sqcg, links_cache):
     assert rel(outs[1], synth.gauge_transform_parity_field(L, outs[0], G, 0)) <= 1e-5
 
 
-def test_loss_and_gradient_match_oracle(sqcg, links_cache):
+@pytest.mark.parametrize("norm", [1, 2])
+def test_loss_and_gradient_match_oracle(sqcg, links_cache, norm):
     L, sigma = (4, 4, 4, 6), 0.05
     fat, lng = links_cache(L, 56)
     r = to_f32(synth.gaussian_source(L, 57))
@@ -87,10 +88,11 @@ def test_loss_and_gradient_match_oracle(sqcg, links_cache):
         lat.load_links(fat, lng)
         net = sqcg.Network(lat)
         net.set_params(params_to_flat(onn.init_params(7, scale=0.7)))
+        net.set_loss(norm)
         loss, grad = net.loss_grad(sigma, lat.pack(r, sqcg.F32), lat.pack(e, sqcg.F32))
         p = flat_to_params(net.get_params(bf16_rounded=True))
         net.close()
-    want_loss, g = onn.loss_and_grad(L, fat, lng, p, r, e, sigma)
+    want_loss, g = onn.loss_and_grad(L, fat, lng, p, r, e, sigma, norm=norm)
     want = params_to_flat(g).astype(np.float64)
     assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
     assert rel(grad.astype(np.float64), want) <= 1e-4
@@ -140,6 +142,7 @@ def test_training_lowers_loss_and_fcg_converges(sqcg, links_cache):
         lat.load_links(fat, lng)
         net = sqcg.Network(lat)
         net.set_params(params_to_flat(onn.init_params(8, scale=0.3)))
+        net.set_loss(2)
         R, E = make_pairs(sqcg, lat, net, fat, lng, m, seeds=[70, 71, 72], ks=[0, 2, 5, 10, 20])
         first, last = net.train(4 * m * m, R, E, steps=150, batch=4, lr=2e-2, seed=3)
         assert last < first

@@ -5,8 +5,9 @@
   and weights +1 / -1 on the forward / backward hops of layers 1 and 2 (identity
   layer 3), the network is D_fat D_fat, i.e. -(D_eo D_oe) with zero long links;
 * scale covariance N(c r) = c N(r);
-* finite-difference checks of the loss gradient for weights of every layer,
-  real and imaginary parts, and for the gate parameters.
+* finite-difference checks of the loss gradient (both loss norms) for weights of
+  every layer, real and imaginary parts, and for the gate parameters;
+* the A^2-norm loss equals |A N(r) - r|^2 / |r|^2 computed directly.
 """
 
 import numpy as np
@@ -67,20 +68,21 @@ def _perturbed(params, which, eps):
     return p
 
 
+@pytest.mark.parametrize("norm", [1, 2])
 @pytest.mark.parametrize("which", [
     ("W", (0, 0, 3, 0), "re"), ("W", (0, 5, 1, 0), "im"), ("W", (1, 2, 4, 6), "re"), ("W", (1, 7, 0, 3), "im"),
     ("W", (2, 0, 0, 5), "im"), ("W", (2, 8, 0, 2), "re"), ("G", (0, 0, 2), None), ("G", (0, 1, 5), None),
     ("G", (1, 0, 7), None), ("G", (1, 1, 1), None)])
-def test_gradient_matches_finite_differences(which):
+def test_gradient_matches_finite_differences(which, norm):
     fat, lng = synth.fat_long_links(L, 10)
     sigma = 0.05
     params = nn.init_params(3, scale=0.7)
     r = synth.gaussian_source(L, 11)
     e = np.linalg.solve(oracle.dense_normal_matrix(L, fat, lng, sigma), r.ravel()).reshape(r.shape)
-    loss, grads = nn.loss_and_grad(L, fat, lng, params, r, e, sigma)
+    loss, grads = nn.loss_and_grad(L, fat, lng, params, r, e, sigma, norm=norm)
     eps = 1e-6
-    lp, _ = nn.loss_and_grad(L, fat, lng, _perturbed(params, which, eps), r, e, sigma)
-    lm, _ = nn.loss_and_grad(L, fat, lng, _perturbed(params, which, -eps), r, e, sigma)
+    lp, _ = nn.loss_and_grad(L, fat, lng, _perturbed(params, which, eps), r, e, sigma, norm=norm)
+    lm, _ = nn.loss_and_grad(L, fat, lng, _perturbed(params, which, -eps), r, e, sigma, norm=norm)
     fd = (lp - lm) / (2 * eps)
     kind, idx, part = which
     if kind == "W":
@@ -91,3 +93,15 @@ def test_gradient_matches_finite_differences(which):
         l, ab, c = idx
         an = grads["gates"][l][ab][c]
     assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_residual_norm_loss_is_the_preconditioned_residual():
+    fat, lng = synth.fat_long_links(L, 12)
+    sigma = 0.05
+    params = nn.init_params(4, scale=0.5)
+    r = synth.gaussian_source(L, 13)
+    e = np.linalg.solve(oracle.dense_normal_matrix(L, fat, lng, sigma), r.ravel()).reshape(r.shape)
+    loss, _ = nn.loss_and_grad(L, fat, lng, params, r, e, sigma, norm=2)
+    z = nn.apply(L, fat, params, r)
+    want = np.linalg.norm(oracle.normal_op(L, fat, lng, sigma, z) - r) ** 2 / np.linalg.norm(r) ** 2
+    assert abs(loss - want) <= 1e-10 * want
