@@ -46,9 +46,11 @@ SOURCE_SEED = 2200  # 2000 + 100 * workload number + rhs
 BYTES_PER_SITE = {"f64": 16 * 144 + 2 * 48, "f32": 16 * 72 + 2 * 24, "f32_recon12": 8 * 72 + 8 * 48 + 2 * 24}
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch of the FP32 Dslash measured by ncu, with the hash of
-# the kernel sources they were taken on (null once the sources change).
-NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None, "lattice": None}
+# DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
+# at 32^4, measured by ncu (profiles/dslash_f32_recon12_32x32x32x32.md), with the
+# hash of the kernel sources they were taken on (reported as null once those change).
+NCU_TRAFFIC = {"sources_sha256": "8e98da2cd236035f8c10bc948b311b5843f75e0760f830bdc7a905f7bc3fb574",
+               "bytes_per_launch": 525859328 + 11529728, "lattice": [32, 32, 32, 32]}
 
 
 def parse():
@@ -165,13 +167,15 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+DSLASH_SOURCES = ("dslash.cu", "solver_device.cuh", "sqcg_internal.cuh")  # what k_dslash is compiled from
+
+
 def sources_sha256() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1611_00728_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in DSLASH_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()
 
 

@@ -30,8 +30,9 @@
 
 namespace {
 
-constexpr int kMaxT = 256;    // largest site block (threads per CTA)
-constexpr int kMinT = 64;     // smallest site block
+constexpr int kMaxT = 256;    // largest site block (threads along x)
+constexpr int kMaxThreads = 512;  // largest CTA (site block x RHS groups)
+constexpr int kMinT = 32;     // smallest site block
 constexpr int kW64 = 4;       // RHS per pass in the FP64 kernels (register budget)
 
 struct LatDev {
@@ -127,44 +128,49 @@ __device__ void rhs_finish(RhsScalars& s, const BatchState* st, int fin, double 
   }
 }
 
-// Reduce W per-thread values over the tile, then over all site blocks of the
-// RHS block (last tile of the block sums the partials in order) and run the
-// per-RHS step. counter: index of this RHS block's arrival counter.
-template <int W>
-__device__ void rhs_block_reduce(double (&v)[W], const LatDev& L, int rb, int wbase, int nw, int sb, BatchState* st,
+// Reduce per-RHS values over the tile, then over all site blocks of the RHS
+// block (the last tile of the block sums the partials in site-block order) and
+// run the per-RHS step. Blocks are (sites x RHS groups): thread (x, y) holds
+// the WT values of RHS y*WT .. y*WT+WT-1 of the tile; blockDim.x is a multiple
+// of 32, so every warp belongs to one group. counter: this RHS block's
+// arrival counter.
+template <int WT>
+__device__ void rhs_block_reduce(double (&v)[WT], const LatDev& L, int wbase, int nw_tile, int sb, BatchState* st,
                                  double* partials, int max_nsb, int counter, int fin) {
-  __shared__ double red[W][kMaxT / 32];
+  __shared__ double red[16][kMaxT / 32];
   __shared__ bool am_last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wx = threadIdx.x >> 5, nwx = blockDim.x >> 5;
+  const int nwarps = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
-  for (int w = 0; w < W; ++w) {
+  for (int w = 0; w < WT; ++w) {
     const double t = warp_sum(v[w]);
-    if (lane == 0) red[w][wid] = t;
+    if (lane == 0) red[threadIdx.y * WT + w][wx] = t;
   }
   __syncthreads();
-  if (threadIdx.x < nw) {
+  if (tid < nw_tile) {
     double t = 0.0;
-    for (int j = 0; j < nwarps; ++j) t += red[threadIdx.x][j];
-    partials[(size_t)(L.rhs0 + wbase + threadIdx.x) * max_nsb + sb] = t;
+    for (int j = 0; j < nwx; ++j) t += red[tid][j];
+    partials[(size_t)(L.rhs0 + wbase + tid) * max_nsb + sb] = t;
     __threadfence();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     const unsigned int t = atomicAdd(&st->counter[counter], 1u);
     am_last = (t == (unsigned)L.nsb - 1);
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  for (int w = wid; w < nw; w += nwarps) {
+  for (int w = tid >> 5; w < nw_tile; w += nwarps) {
     const int g = L.rhs0 + wbase + w;
-    double s = 0.0;
-    for (int j = lane; j < L.nsb; j += 32) s += __ldcg(partials + (size_t)g * max_nsb + j);
-    s = warp_sum(s);
-    if (lane == 0) rhs_finish(st->r[g], st, fin, s);
+    double sum = 0.0;
+    for (int j = lane; j < L.nsb; j += 32) sum += __ldcg(partials + (size_t)g * max_nsb + j);
+    sum = warp_sum(sum);
+    if (lane == 0) rhs_finish(st->r[g], st, fin, sum);
   }
   __syncthreads();
-  if (threadIdx.x == 0) st->counter[counter] = 0;
+  if (tid == 0) st->counter[counter] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -320,8 +326,11 @@ struct MArgs {
   int write_p;   // M_TRUE_RESID at initialisation: also copy r into p
 };
 
-template <typename R, int W>
-__global__ void __launch_bounds__(kMaxT) k_mrhs_dslash(MArgs a) {
+// Thread (x, y) of a tile: site sb*blockDim.x + x, right-hand sides y*WT .. y*WT+WT-1
+// of the tile's RHS block (width WT*blockDim.y). The groups y of one site
+// block load the same links, which the first group brings into L1.
+template <typename R, int WT>
+__global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   typedef typename V2<R>::T R2;
   constexpr bool F64 = sizeof(R) == 8;
   const int tile = blockIdx.x;
@@ -330,37 +339,40 @@ __global__ void __launch_bounds__(kMaxT) k_mrhs_dslash(MArgs a) {
   const int local = tile - (F64 ? L.tile640 : L.tile0);
   const int nrb = F64 ? L.nrb64 : L.nrb;
   const int rb = local % nrb, sb = local / nrb;
-  const int wbase = rb * W;
-  const int nw = min(W, L.nrhs - wbase);
+  const int Wtile = WT * blockDim.y;
+  const int wbase = rb * Wtile;
+  const int nw_tile = min(Wtile, L.nrhs - wbase);
+  const int w0 = wbase + threadIdx.y * WT;            // first RHS of this thread (within the lattice)
+  const int nw = max(0, min(WT, L.nrhs - w0));
   const int blk = L.rb0 + wbase / a.W;  // FP32 block that holds these RHS
   if (a.gate == GATE_ITER && !a.st->blk_active[blk]) return;
   if (a.gate == GATE_UPDATE && !a.st->blk_update[blk]) return;
   const int Vh = L.g.Vh;
   const int i = sb * blockDim.x + threadIdx.x;
-  double part[W];
+  double part[WT];
 #pragma unroll
-  for (int w = 0; w < W; ++w) part[w] = 0.0;
+  for (int w = 0; w < WT; ++w) part[w] = 0.0;
   const R2* in;
   if constexpr (F64) in = (a.in_vec == V_X ? (const R2*)L.x : (const R2*)L.tmp64);
   else in = (a.in_vec == V_P ? (const R2*)L.p : (const R2*)L.tmp);
-  in += (size_t)wbase * 3 * Vh;
-  if (i < Vh) {
-    R2 acc[W][3];
-    dslash_mrhs_site<R, W>(L, a.par, i, in, nw, acc);
+  in += (size_t)w0 * 3 * Vh;
+  if (i < Vh && nw > 0) {
+    R2 acc[WT][3];
+    dslash_mrhs_site<R, WT>(L, a.par, i, in, nw, acc);
     if (a.epi == M_PLAIN) {
-      R2* out = (F64 ? (R2*)L.tmp64 : (R2*)L.tmp) + (size_t)wbase * 3 * Vh;
+      R2* out = (F64 ? (R2*)L.tmp64 : (R2*)L.tmp) + (size_t)w0 * 3 * Vh;
 #pragma unroll
-      for (int w = 0; w < W; ++w)
+      for (int w = 0; w < WT; ++w)
         if (w < nw)
 #pragma unroll
           for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
     } else if constexpr (!F64) {  // M_NORMAL_DOT (FP32): Ap = sigma p - D tmp, <p, Ap>
-      const R2* y = (const R2*)L.p + (size_t)wbase * 3 * Vh;
-      R2* out = (R2*)L.Ap + (size_t)wbase * 3 * Vh;
+      const R2* y = (const R2*)L.p + (size_t)w0 * 3 * Vh;
+      R2* out = (R2*)L.Ap + (size_t)w0 * 3 * Vh;
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
+      for (int w = 0; w < WT; ++w) {
         if (w < nw) {
-          const R sig = (R)a.st->r[L.rhs0 + wbase + w].sigma;
+          const R sig = (R)a.st->r[L.rhs0 + w0 + w].sigma;
           R dot = R(0);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -374,14 +386,14 @@ __global__ void __launch_bounds__(kMaxT) k_mrhs_dslash(MArgs a) {
         }
       }
     } else {  // M_TRUE_RESID (FP64): r = b - sigma x + D tmp64, |r|^2; r (FP32) and optionally p
-      const double2* xb = L.x + (size_t)wbase * 3 * Vh;
-      const double2* bb = L.b + (size_t)wbase * 3 * Vh;
-      float2* rb32 = L.r + (size_t)wbase * 3 * Vh;
-      float2* pb32 = L.p + (size_t)wbase * 3 * Vh;
+      const double2* xb = L.x + (size_t)w0 * 3 * Vh;
+      const double2* bb = L.b + (size_t)w0 * 3 * Vh;
+      float2* rb32 = L.r + (size_t)w0 * 3 * Vh;
+      float2* pb32 = L.p + (size_t)w0 * 3 * Vh;
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
+      for (int w = 0; w < WT; ++w) {
         if (w < nw) {
-          const double sig = a.st->r[L.rhs0 + wbase + w].sigma;
+          const double sig = a.st->r[L.rhs0 + w0 + w].sigma;
           double n2 = 0.0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -402,7 +414,7 @@ __global__ void __launch_bounds__(kMaxT) k_mrhs_dslash(MArgs a) {
   if (a.epi != M_PLAIN) {
     const int fin = (a.epi == M_NORMAL_DOT) ? BFIN_PAP : (a.write_p ? BFIN_INIT : BFIN_TRUE);
     const int counter = F64 ? (SQCG_MAX_BATCH_RHS + L.rb640 + rb) : (L.rb0 + rb);
-    rhs_block_reduce<W>(part, L, rb, wbase, nw, sb, a.st, a.partials, a.max_nsb, counter, fin);
+    rhs_block_reduce<WT>(part, L, wbase, nw_tile, sb, a.st, a.partials, a.max_nsb, counter, fin);
   }
 }
 
@@ -487,7 +499,7 @@ __global__ void __launch_bounds__(kMaxT) k_mrhs_blas(BArgs a) {
     }
   }
   if (a.op != B_XPAY)
-    rhs_block_reduce<W>(part, L, rb, wbase, nw, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb,
+    rhs_block_reduce<W>(part, L, wbase, nw, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb,
                         a.op == B_UPDATE ? BFIN_UPDATE : BFIN_BB);
 }
 
@@ -542,7 +554,8 @@ struct BatchPlan {
   int nrhs[SQCG_MAX_LATTICES];
   const void* b[SQCG_MAX_LATTICES];
   void* x[SQCG_MAX_LATTICES];
-  int W, T;              // tuned RHS block width and site block
+  int W, T;              // tuned RHS block width and site block (threads along x)
+  int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
   int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
   int nblk;              // FP32 RHS blocks over all lattices
   int max_nsb;
@@ -561,8 +574,12 @@ extern unsigned long long sqcg_links_generation(const sqcg_ctx* ctx);
 
 namespace {
 
-std::map<std::string, std::pair<int, int>>& tune_cache() {
-  static std::map<std::string, std::pair<int, int>> m;
+struct TuneChoice {
+  int W, WT, T;
+};
+
+std::map<std::string, TuneChoice>& tune_cache() {
+  static std::map<std::string, TuneChoice> m;
   return m;
 }
 
@@ -576,22 +593,22 @@ void tune_file_load() {
   FILE* f = fopen(path, "r");
   if (!f) return;
   char key[512];
-  int W, T;
-  while (fscanf(f, "%511s %d %d", key, &W, &T) == 3) tune_cache()[key] = {W, T};
+  int W, WT, T;
+  while (fscanf(f, "%511s %d %d %d", key, &W, &WT, &T) == 4) tune_cache()[key] = {W, WT, T};
   fclose(f);
 }
 
-void tune_file_store(const std::string& key, int W, int T) {
+void tune_file_store(const std::string& key, const TuneChoice& c) {
   const char* path = getenv("SQCG_TUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d\n", key.c_str(), W, T);
+  fprintf(f, "%s %d %d %d\n", key.c_str(), c.W, c.WT, c.T);
   fclose(f);
 }
 
 std::string tune_key(const BatchPlan& P) {
-  std::string k = "mrhs_dslash_f32";
+  std::string k = "mrhs_dslash2_f32";
   char buf[128];
   for (int j = 0; j < P.nlat; ++j) {
     const Geom& g = P.host[j].g;
@@ -602,7 +619,7 @@ std::string tune_key(const BatchPlan& P) {
 }
 
 // tiles, blocks and first indices for a given W and T
-void layout_tiles(BatchPlan& P, int W, int T) {
+void layout_tiles(BatchPlan& P, int W, int WT, int T) {
   int tile = 0, tile64 = 0, rb0 = 0, rb640 = 0;
   const int W64 = W < kW64 ? W : kW64;
   for (int k = 0; k < P.nlat; ++k) {
@@ -620,6 +637,7 @@ void layout_tiles(BatchPlan& P, int W, int T) {
     rb640 += L.nrb64;
   }
   P.W = W;
+  P.WT = WT;
   P.T = T;
   P.ntiles = tile;
   P.ntiles64 = tile64;
@@ -627,13 +645,13 @@ void layout_tiles(BatchPlan& P, int W, int T) {
 }
 
 template <typename R>
-int launch_mrhs_dslash_w(int W, int grid, int T, cudaStream_t s, const MArgs& a) {
-  switch (W) {
-    case 1: k_mrhs_dslash<R, 1><<<grid, T, 0, s>>>(a); break;
-    case 2: k_mrhs_dslash<R, 2><<<grid, T, 0, s>>>(a); break;
-    case 4: k_mrhs_dslash<R, 4><<<grid, T, 0, s>>>(a); break;
-    case 8: if constexpr (sizeof(R) == 4) { k_mrhs_dslash<R, 8><<<grid, T, 0, s>>>(a); break; } else return SQCG_ERR_INVALID_ARG;
-    case 16: if constexpr (sizeof(R) == 4) { k_mrhs_dslash<R, 16><<<grid, T, 0, s>>>(a); break; } else return SQCG_ERR_INVALID_ARG;
+int launch_mrhs_dslash_w(int WT, int G, int grid, int T, cudaStream_t s, const MArgs& a) {
+  const dim3 block(T, G);
+  if (T * G > kMaxThreads || T % 32) return SQCG_ERR_INVALID_ARG;
+  switch (WT) {
+    case 1: k_mrhs_dslash<R, 1><<<grid, block, 0, s>>>(a); break;
+    case 2: k_mrhs_dslash<R, 2><<<grid, block, 0, s>>>(a); break;
+    case 4: k_mrhs_dslash<R, 4><<<grid, block, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -663,12 +681,12 @@ MArgs margs(const BatchPlan& P, int par, int in_vec, int epi, int gate, int writ
 }
 
 int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
-  return launch_mrhs_dslash_w<float>(P.W, P.ntiles, P.T, s, margs(P, par, in_vec, epi, gate, 0));
+  return launch_mrhs_dslash_w<float>(P.WT, P.W / P.WT, P.ntiles, P.T, s, margs(P, par, in_vec, epi, gate, 0));
 }
 
 int launch_f64(const BatchPlan& P, int par, int in_vec, int epi, int gate, int write_p, cudaStream_t s) {
   const int W64 = P.W < kW64 ? P.W : kW64;
-  return launch_mrhs_dslash_w<double>(W64, P.ntiles64, P.T, s, margs(P, par, in_vec, epi, gate, write_p));
+  return launch_mrhs_dslash_w<double>(W64, 1, P.ntiles64, P.T, s, margs(P, par, in_vec, epi, gate, write_p));
 }
 
 int upload_lats(BatchPlan& P, cudaStream_t s) {
@@ -676,7 +694,7 @@ int upload_lats(BatchPlan& P, cudaStream_t s) {
   return SQCG_OK;
 }
 
-// time the FP32 multi-RHS Dslash over the batch for each (W, T); keep the fastest
+// time the FP32 multi-RHS Dslash over the batch for each (W, WT, T); keep the fastest
 int autotune(BatchPlan& P, cudaStream_t s) {
   tune_file_load();
   const std::string key = tune_key(P);
@@ -684,42 +702,50 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   int maxr = 0;
   for (int k = 0; k < P.nlat; ++k) maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
   if (it != tune_cache().end()) {
-    layout_tiles(P, it->second.first, it->second.second);
+    layout_tiles(P, it->second.W, it->second.WT, it->second.T);
     return upload_lats(P, s);
   }
   cudaEvent_t e0, e1;
   SQCG_CUDA_TRY(cudaEventCreate(&e0));
   SQCG_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bestW = 1, bestT = 128;
+  TuneChoice bestc = {1, 1, 128};
   const int Ws[] = {1, 2, 4, 8, 16};
-  const int Ts[] = {64, 128, 256};
+  const int WTs[] = {1, 2, 4};
+  const int Ts[] = {32, 64, 128, 256};
   int rc = SQCG_OK;
   for (int W : Ws) {
     if (W > 1 && W / 2 >= maxr) break;  // wider blocks than any lattice's RHS count only add idle lanes
-    for (int T : Ts) {
-      layout_tiles(P, W, T);
-      if ((rc = upload_lats(P, s)) != SQCG_OK) break;
-      for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+    for (int WT : WTs) {
+      if (WT > W) break;
+      const int G = W / WT;
+      for (int T : Ts) {
+        if (T * G > kMaxThreads) break;
+        layout_tiles(P, W, WT, T);
+        if ((rc = upload_lats(P, s)) != SQCG_OK) break;
+        for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+        if (rc != SQCG_OK) break;
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 5 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+        cudaEventRecord(e1, s);
+        if (rc != SQCG_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (getenv("SQCG_TUNE_VERBOSE"))
+          fprintf(stderr, "sqcg tune %s W=%d WT=%d T=%d %.4f ms\n", key.c_str(), W, WT, T, ms / 5);
+        if (ms < best) { best = ms; bestc = {W, WT, T}; }
+      }
       if (rc != SQCG_OK) break;
-      cudaEventRecord(e0, s);
-      for (int rep = 0; rep < 5 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
-      cudaEventRecord(e1, s);
-      if (rc != SQCG_OK) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (getenv("SQCG_TUNE_VERBOSE")) fprintf(stderr, "sqcg tune %s W=%d T=%d %.4f ms\n", key.c_str(), W, T, ms / 5);
-      if (ms < best) { best = ms; bestW = W; bestT = T; }
     }
     if (rc != SQCG_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != SQCG_OK) return rc;
-  tune_cache()[key] = {bestW, bestT};
-  tune_file_store(key, bestW, bestT);
-  layout_tiles(P, bestW, bestT);
+  tune_cache()[key] = bestc;
+  tune_file_store(key, bestc);
+  layout_tiles(P, bestc.W, bestc.WT, bestc.T);
   return upload_lats(P, s);
 }
 
@@ -778,7 +804,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     if ((int)Vh > max_vh) max_vh = (int)Vh;
   }
   P->nrhs_total = total;
-  P->max_nsb = grid_for(max_vh, kMinT);
+  P->max_nsb = grid_for(max_vh, kMinT);  // the smallest site block the tuner tries
   bool ok = cudaMalloc((void**)&P->dev, sizeof(LatDev) * nctx) == cudaSuccess &&
             cudaMalloc((void**)&P->partials, sizeof(double) * (size_t)total * P->max_nsb) == cudaSuccess &&
             cudaMalloc((void**)&P->st, sizeof(BatchState)) == cudaSuccess &&
