@@ -96,12 +96,13 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
-// U v (dag = false) or U^dag v (dag = true), U: 9 FP32 complex at stride Vh
-__device__ __forceinline__ void transport(const float2* __restrict__ U, int Vh, int idx, bool dag, const float2 (&v)[3],
-                                          float2 (&out)[3]) {
-  float2 u[9];
+__device__ __forceinline__ void load_link9(const float2* __restrict__ U, int Vh, int idx, float2 (&u)[9]) {
 #pragma unroll
   for (int e = 0; e < 9; ++e) u[e] = __ldg(U + (size_t)e * Vh + idx);
+}
+
+// U v (dag = false) or U^dag v (dag = true) for a link already in registers
+__device__ __forceinline__ void apply_link(const float2 (&u)[9], bool dag, const float2 (&v)[3], float2 (&out)[3]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float2 acc = make_float2(0.f, 0.f);
@@ -141,7 +142,7 @@ struct ConvArgs {
 };
 
 template <int CIN, int COUT, int IN, int OUT>
-__global__ void __launch_bounds__(kThreads) k_conv(ConvArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
   __shared__ float2 W[NT * COUT * CIN];
   for (int j = threadIdx.x; j < NT * COUT * CIN; j += blockDim.x) W[j] = a.W[j];
@@ -192,22 +193,23 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvArgs a) {
       mix(0, v, ci);
     }
   }
-  // hops (input of the other parity)
+  // hops (input of the other parity); each link is loaded once and applied to every channel
   if (IN == IN_FULL || q == 0) {
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const int jf = nbr(g, s, mu, +1), jb = nbr(g, s, mu, -1);
-      const float2* Uf = a.fat[par] + (size_t)mu * 9 * Vh;  // F_mu(n)
-      const float2* Ub = a.fat[q] + (size_t)mu * 9 * Vh;    // F_mu(n - mu)
 #pragma unroll
-      for (int ci = 0; ci < CIN; ++ci) {
-        float2 v[3], t[3];
-        load_in(ci, q, jf, v);
-        transport(Uf, Vh, i, false, v, t);
-        mix(1 + 2 * mu, t, ci);
-        load_in(ci, q, jb, v);
-        transport(Ub, Vh, jb, true, v, t);
-        mix(2 + 2 * mu, t, ci);
+      for (int dir = 0; dir < 2; ++dir) {
+        const int j = nbr(g, s, mu, dir == 0 ? +1 : -1);
+        float2 u[9];
+        if (dir == 0) load_link9(a.fat[par] + (size_t)mu * 9 * Vh, Vh, i, u);  // F_mu(n)
+        else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);             // F_mu(n - mu)
+#pragma unroll 2
+        for (int ci = 0; ci < CIN; ++ci) {
+          float2 v[3], t[3];
+          load_in(ci, q, j, v);
+          apply_link(u, dir == 1, v, t);
+          mix(1 + 2 * mu + dir, t, ci);
+        }
       }
     }
   }
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gate_bwd(const float2* __restri
 
 // the 9 tap fields of an input field, for every site: T[tap][ci][par][3][Vh]
 template <int CIN, int IN>
-__global__ void __launch_bounds__(kThreads) k_taps(ConvArgs a, float2* __restrict__ T) {
+__global__ void __launch_bounds__(kThreads, 4) k_taps(ConvArgs a, float2* __restrict__ T) {
   const Geom& g = a.g;
   const int Vh = g.Vh;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -318,18 +320,25 @@ __global__ void __launch_bounds__(kThreads) k_taps(ConvArgs a, float2* __restric
   };
 #pragma unroll
   for (int ci = 0; ci < CIN; ++ci) {
-    float2 v[3], t[3];
+    float2 v[3];
     load_in(ci, par, i, v);
     store(0, ci, v);
+  }
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const int jf = nbr(g, s, mu, +1), jb = nbr(g, s, mu, -1);
-      load_in(ci, q, jf, v);
-      transport(a.fat[par] + (size_t)mu * 9 * Vh, Vh, i, false, v, t);
-      store(1 + 2 * mu, ci, t);
-      load_in(ci, q, jb, v);
-      transport(a.fat[q] + (size_t)mu * 9 * Vh, Vh, jb, true, v, t);
-      store(2 + 2 * mu, ci, t);
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      const int j = nbr(g, s, mu, dir == 0 ? +1 : -1);
+      float2 u[9];
+      if (dir == 0) load_link9(a.fat[par] + (size_t)mu * 9 * Vh, Vh, i, u);
+      else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) {
+        float2 v[3], t[3];
+        load_in(ci, q, j, v);
+        apply_link(u, dir == 1, v, t);
+        store(1 + 2 * mu + dir, ci, t);
+      }
     }
   }
 }
