@@ -99,6 +99,13 @@ int sqcg_destroy(sqcg_ctx* ctx);
 /* Change the stream later calls queue their work on. */
 int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
 
+/* Reliable-update trigger of the mixed-precision solvers on this context: the
+ * FP64 true residual is recomputed when the iterated |r| falls below
+ * delta * (max |r| since the last update), or after `interval` iterations,
+ * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.1 and 100).
+ * The batched solve uses the settings of its first context. */
+int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval);
+
 /* Bytes of one device colour vector on one parity in precision prec (Vh * 3 * 2 * sizeof(real)). */
 int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
 

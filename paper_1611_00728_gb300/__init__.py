@@ -84,6 +84,7 @@ def library():
         lib.sqcg_create.argtypes = [P, I, P, ctypes.POINTER(P)]
         lib.sqcg_destroy.argtypes = [P]
         lib.sqcg_set_stream.argtypes = [P, P]
+        lib.sqcg_set_reliable_update.argtypes = [P, D, I]
         lib.sqcg_spinor_bytes.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
         lib.sqcg_load_links.argtypes = [P, P, P, I]
         lib.sqcg_pack_spinor.argtypes = [P, I, P, P]
@@ -109,7 +110,8 @@ def library():
         lib.sqcg_fcg_solve_nn.argtypes = [P, P, D, P, P, D, I, ctypes.POINTER(Info)]
         lib.sqcg_strerror.argtypes = [I]
         lib.sqcg_strerror.restype = ctypes.c_char_p
-        for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_spinor_bytes", "sqcg_load_links",
+        for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_set_reliable_update", "sqcg_spinor_bytes",
+                     "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
                      "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
@@ -169,6 +171,11 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_reliable_update(self, delta: float = 0.1, interval: int = 100):
+        """Mixed-precision trigger: FP64 true residual when |r| < delta * max|r| since the last one, or every
+        `interval` iterations."""
+        _check(library().sqcg_set_reliable_update(self._h, float(delta), int(interval)), "sqcg_set_reliable_update")
 
     def _sync_stream(self):
         library().sqcg_set_stream(self._h, ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream))

@@ -82,6 +82,8 @@ int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out)
   g.st = g.Lxh * g.Ly * g.Lz;
   g.apbc = (flags & SQCG_ANTIPERIODIC_T) ? 1 : 0;
   c->stream = (cudaStream_t)cuda_stream;
+  c->ru_delta = 0.1;
+  c->ru_interval = 100;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     sqcg_set_last_cuda_error(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);
     free(c);
@@ -107,6 +109,13 @@ int sqcg_destroy(sqcg_ctx* ctx) {
 int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream) {
   if (!ctx) return SQCG_ERR_INVALID_ARG;
   ctx->stream = (cudaStream_t)cuda_stream;
+  return SQCG_OK;
+}
+
+int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval) {
+  if (!ctx || !(delta > 0.0) || !(delta < 1.0) || interval < 1) return SQCG_ERR_INVALID_ARG;
+  ctx->ru_delta = delta;
+  ctx->ru_interval = interval;
   return SQCG_OK;
 }
 

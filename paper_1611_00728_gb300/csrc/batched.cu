@@ -32,6 +32,7 @@ namespace {
 
 constexpr int kMaxT = 256;    // largest site block (threads along x)
 constexpr int kMaxThreads = 512;  // largest CTA (site block x RHS groups)
+constexpr int kMaxTSmem = 128;    // largest site block of the shared-memory FP32 Dslash (144 KB of links)
 constexpr int kMinT = 32;     // smallest site block
 constexpr int kW64 = 4;       // RHS per pass in the FP64 kernels (register budget)
 
@@ -418,6 +419,155 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   }
 }
 
+// FP32 multi-RHS Dslash with the links of the tile staged in shared memory.
+// Thread (x, y): site sb*blockDim.x + x, right-hand sides y*WT .. y*WT+WT-1 of
+// the tile's RHS block (width W = WT*blockDim.y). First the block copies the 16
+// links of each of its sites (8 fat, 8 long; 12-real long links rebuilt here)
+// from global memory into shared memory, the RHS groups sharing the work; then
+// every group applies them to its own right-hand sides. Each link is read from
+// global memory once per RHS block, whatever W is.
+constexpr int kHops = 16;
+
+template <int WT>
+__global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
+  extern __shared__ float2 sU[];  // [kHops][9][blockDim.x]
+  const int tile = blockIdx.x;
+  const int k = find_lat(a.lats, a.nlat, tile, false);
+  const LatDev& L = a.lats[k];
+  const int local = tile - L.tile0;
+  const int rb = local % L.nrb, sb = local / L.nrb;
+  const int TX = blockDim.x, G = blockDim.y;
+  const int Wtile = WT * G;
+  const int wbase = rb * Wtile;
+  const int nw_tile = min(Wtile, L.nrhs - wbase);
+  const int w0 = wbase + threadIdx.y * WT;
+  const int nw = max(0, min(WT, L.nrhs - w0));
+  const int blk = L.rb0 + rb;
+  if (a.gate == GATE_ITER && !a.st->blk_active[blk]) return;
+  const Geom& g = L.g;
+  const int Vh = g.Vh;
+  const int par = a.par, q = 1 - par;
+  const int i = sb * TX + threadIdx.x;
+  const bool valid = i < Vh;
+  // site coordinates
+  int x = 0, y = 0, z = 0, t = 0, row = 0;
+  if (valid) {
+    const int xh = i % g.Lxh;
+    int rr = i / g.Lxh;
+    y = rr % g.Ly;
+    rr /= g.Ly;
+    z = rr % g.Lz;
+    t = rr / g.Lz;
+    x = 2 * xh + ((y + z + t + par) & 1);
+    row = i - xh;
+  }
+  auto nbr = [&](int mu, int d) {  // half index of n + d mu
+    if (mu == 0) {
+      int xp = x + d;
+      if (xp >= g.Lx) xp -= g.Lx;
+      if (xp < 0) xp += g.Lx;
+      return row + (xp >> 1);
+    }
+    const int c = (mu == 1) ? y : (mu == 2) ? z : t;
+    const int Lm = (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+    const int sm = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+    int j = i + d * sm;
+    if (c + d >= Lm) j -= Lm * sm;
+    if (c + d < 0) j += Lm * sm;
+    return j;
+  };
+  // ---- stage the links: hop h = 4 * mu + 2 * (long) + (backward) ----
+  const bool recon = L.recon != 0;
+  const int nl = recon ? 6 : 9;
+  for (int h = threadIdx.y; h < kHops; h += G) {
+    const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
+    const int d = lng ? 3 : 1;
+    float2 u[9];
+    if (valid) {
+      const float2* base = lng ? (bwd ? L.lng32[q] : L.lng32[par]) : (bwd ? L.fat32[q] : L.fat32[par]);
+      base += (size_t)mu * (lng ? nl : 9) * Vh;
+      const int idx = bwd ? nbr(mu, -d) : i;
+      const int ne = lng ? nl : 9;
+#pragma unroll
+      for (int e = 0; e < 9; ++e)
+        if (e < ne) u[e] = __ldg(base + (size_t)e * Vh + idx);
+      if (lng && recon) {  // third row = conj(row0 x row1) / s, s = s0 * eta_mu * boundary sign
+        int ep = 0;
+        if (mu == 1) ep = x;
+        if (mu == 2) ep = x + y;
+        if (mu == 3) ep = x + y + z;
+        float inv_s = (ep & 1) ? -L.inv_s0_f : L.inv_s0_f;
+        if (mu == 3 && g.apbc && (bwd ? (t < 3) : (t + 3 >= g.Lt))) inv_s = -inv_s;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int kk = (jj + 1) % 3, ll = (jj + 2) % 3;
+          const float2 ak = u[kk], al = u[ll], bk = u[3 + kk], bl = u[3 + ll];
+          const float re = ak.x * bl.x - ak.y * bl.y - (al.x * bk.x - al.y * bk.y);
+          const float im = ak.x * bl.y + ak.y * bl.x - (al.x * bk.y + al.y * bk.x);
+          u[6 + jj] = make_float2(re * inv_s, -im * inv_s);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) u[e] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) sU[(h * 9 + e) * TX + threadIdx.x] = u[e];
+  }
+  __syncthreads();
+  // ---- apply to this thread's right-hand sides ----
+  double part[WT];
+#pragma unroll
+  for (int w = 0; w < WT; ++w) part[w] = 0.0;
+  const float2* in = (a.in_vec == V_P ? (const float2*)L.p : (const float2*)L.tmp) + (size_t)w0 * 3 * Vh;
+  if (valid && nw > 0) {
+    float2 acc[WT][3];
+#pragma unroll
+    for (int w = 0; w < WT; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[w][c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < kHops; ++h) {
+      const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
+      const int j = nbr(mu, bwd ? (lng ? -3 : -1) : (lng ? 3 : 1));
+      float2 U[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) U[e] = sU[(h * 9 + e) * TX + threadIdx.x];
+      if (bwd) apply_w<float, WT, true>(acc, U, in, Vh, j, nw);
+      else apply_w<float, WT, false>(acc, U, in, Vh, j, nw);
+    }
+    if (a.epi == M_PLAIN) {
+      float2* out = L.tmp + (size_t)w0 * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < WT; ++w)
+        if (w < nw)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
+    } else {  // M_NORMAL_DOT: Ap = sigma p - D tmp, <p, Ap>
+      const float2* yv = L.p + (size_t)w0 * 3 * Vh;
+      float2* out = L.Ap + (size_t)w0 * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < WT; ++w) {
+        if (w < nw) {
+          const float sig = (float)a.st->r[L.rhs0 + w0 + w].sigma;
+          float dot = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const size_t o = ((size_t)w * 3 + c) * Vh + i;
+            const float2 yc = __ldg(yv + o);
+            const float2 v = make_float2(sig * yc.x - acc[w][c].x, sig * yc.y - acc[w][c].y);
+            out[o] = v;
+            dot = fmaf(yc.x, v.x, fmaf(yc.y, v.y, dot));
+          }
+          part[w] = (double)dot;
+        }
+      }
+    }
+  }
+  if (a.epi != M_PLAIN)
+    rhs_block_reduce<WT>(part, L, wbase, nw_tile, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb, BFIN_PAP);
+}
+
 // ---------------------------------------------------------------------------
 // multi-RHS BLAS: x += alpha p, r -= alpha Ap (|r|^2); p = r + beta p; |b|^2
 // ---------------------------------------------------------------------------
@@ -608,7 +758,7 @@ void tune_file_store(const std::string& key, const TuneChoice& c) {
 }
 
 std::string tune_key(const BatchPlan& P) {
-  std::string k = "mrhs_dslash2_f32";
+  std::string k = "mrhs_dslash_smem_f32";
   char buf[128];
   for (int j = 0; j < P.nlat; ++j) {
     const Geom& g = P.host[j].g;
@@ -681,7 +831,30 @@ MArgs margs(const BatchPlan& P, int par, int in_vec, int epi, int gate, int writ
 }
 
 int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
-  return launch_mrhs_dslash_w<float>(P.WT, P.W / P.WT, P.ntiles, P.T, s, margs(P, par, in_vec, epi, gate, 0));
+  const int G = P.W / P.WT, T = P.T;
+  if (T * G > kMaxThreads || T % 32) return SQCG_ERR_INVALID_ARG;
+  const size_t smem = (size_t)kHops * 9 * T * sizeof(float2);
+  static bool attr_set[3] = {false, false, false};  // per WT instantiation
+  const MArgs a = margs(P, par, in_vec, epi, gate, 0);
+  const dim3 block(T, G);
+  switch (P.WT) {
+    case 1:
+      if (!attr_set[0]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[0] = true; }
+      k_mrhs_dslash_smem<1><<<P.ntiles, block, smem, s>>>(a);
+      break;
+    case 2:
+      if (!attr_set[1]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[1] = true; }
+      k_mrhs_dslash_smem<2><<<P.ntiles, block, smem, s>>>(a);
+      break;
+    case 4:
+      if (!attr_set[2]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[2] = true; }
+      k_mrhs_dslash_smem<4><<<P.ntiles, block, smem, s>>>(a);
+      break;
+    default:
+      return SQCG_ERR_INVALID_ARG;
+  }
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
 }
 
 int launch_f64(const BatchPlan& P, int par, int in_vec, int epi, int gate, int write_p, cudaStream_t s) {
@@ -720,7 +893,7 @@ int autotune(BatchPlan& P, cudaStream_t s) {
       if (WT > W) break;
       const int G = W / WT;
       for (int T : Ts) {
-        if (T * G > kMaxThreads) break;
+        if (T * G > kMaxThreads || T > kMaxTSmem) break;
         layout_tiles(P, W, WT, T);
         if ((rc = upload_lats(P, s)) != SQCG_OK) break;
         for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
@@ -943,8 +1116,8 @@ extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* 
   h->nrhs = total;
   h->nblk = P.nblk;
   h->max_iter = max_iter;
-  h->update_interval = 100;
-  h->delta2 = 0.01;
+  h->update_interval = c0->ru_interval;
+  h->delta2 = c0->ru_delta * c0->ru_delta;
   for (int k = 0; k < nctx; ++k)
     for (int j = 0; j < nrhs[k]; ++j) {
       RhsScalars& r = h->r[P.host[k].rhs0 + j];

@@ -322,9 +322,9 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   memset(h, 0, sizeof(SolverState));
   h->sigma = sigma;
   h->stop_rr = tol * tol;  // times |b|^2 on the device
-  h->delta2 = 0.1 * 0.1;
+  h->delta2 = ctx->ru_delta * ctx->ru_delta;
   h->max_iter = max_iter;
-  h->update_interval = mixed ? 100 : (1 << 30);
+  h->update_interval = mixed ? ctx->ru_interval : (1 << 30);
   h->mixed = mixed;
   h->status = SQCG_OK;
   SQCG_TRY(write_state(ctx, s));

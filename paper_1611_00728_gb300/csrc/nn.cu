@@ -1103,9 +1103,9 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
   memset(h, 0, sizeof(SolverState));
   h->sigma = sigma;
   h->stop_rr = tol * tol;
-  h->delta2 = 0.01;
+  h->delta2 = ctx->ru_delta * ctx->ru_delta;
   h->max_iter = max_iter;
-  h->update_interval = 100;
+  h->update_interval = ctx->ru_interval;
   h->mixed = 1;
   h->vh = Vh;
   h->status = SQCG_OK;

@@ -180,6 +180,8 @@ struct sqcg_ctx {
   int ms_nalloc;
   int ms_prec;
 
+  double ru_delta;     // reliable update when |r| < ru_delta * max |r| since the last one
+  int ru_interval;     // ... or after this many iterations
   CGGraph* graphs;  // cached captured solver loops
   BatchPlan* batch;  // cached batched-solve workspace and graph (owned by the first context of a batch)
 };

@@ -37,7 +37,7 @@ def test_batched_small_uneven(sqcg, links_cache, recon):
         lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
     infos = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=tol, max_iter=5000)
     W, T = sqcg.batched_tuning(lats[0])
-    assert W in (1, 2, 4, 8, 16) and T in (64, 128, 256)
+    assert W in (1, 2, 4, 8, 16) and T in (32, 64, 128, 256)
     for n, (L, nr, m) in enumerate(specs):
         fat, lng = links[n]
         for j in range(nr):

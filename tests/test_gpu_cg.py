@@ -224,3 +224,23 @@ def test_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch)
     assert g[0] == e[0] and g[1] == e[1] and g[3] == e[3]
     assert np.array_equal(g[2], e[2])
     assert all(np.array_equal(a, c) for a, c in zip(g[4], e[4]))
+
+
+@pytest.mark.parametrize("delta,interval", [(0.01, 100), (0.5, 5), (0.1, 1000)])
+def test_reliable_update_settings(sqcg, links_cache, delta, interval):
+    """Any trigger setting still ends on the FP64 true residual; the count follows the setting."""
+    L, m, tol = (8, 10, 12, 14), 0.01, 1e-9
+    fat, lng = links_cache(L, 88)
+    b = synth.gaussian_source(L, 4)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        lat.set_reliable_update(delta, interval)
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, lat.pack(b), dx, tol=tol, max_iter=5000, mode=1)
+        x = lat.unpack(dx)
+        with pytest.raises(sqcg.SqcgError):
+            lat.set_reliable_update(1.5, 10)
+    assert info.status == 0
+    assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
+    if interval == 5:
+        assert info.reliable_updates >= info.iters // 5
