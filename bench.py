@@ -364,6 +364,13 @@ def run_ours(args, ranks: Ranks):
     lat_f.load_links(fat, lng)
     t32 = time_dslash(torch, lat_f, sq, sq.F32, 50)
     lat_f.close()
+    # 8-way storage of the FP32 links (backward links at the site that uses them)
+    t8 = {}
+    for rc in (False, True):
+        lat8 = sq.Lattice(LATTICE)
+        lat8.load_links(fat, lng, recon12=rc, eight_way=True)
+        t8[rc] = time_dslash(torch, lat8, sq, sq.F32, 50)
+        lat8.close()
     ach = BYTES_PER_SITE["f32_recon12"] * Vh / t32r / 1e9
     traffic = None
     if NCU_TRAFFIC["sources_sha256"] == sources_sha256() and NCU_TRAFFIC["lattice"] == list(LATTICE):
@@ -377,6 +384,12 @@ def run_ours(args, ranks: Ranks):
               "f32_recon12": {"ms": t32r * 1e3, "gflops": FLOPS_PER_SITE * Vh / t32r / 1e9,
                               "gbs": BYTES_PER_SITE["f32_recon12"] * Vh / t32r / 1e9,
                               "frac_hbm": BYTES_PER_SITE["f32_recon12"] * Vh / t32r / 1e9 / peak},
+              "f32_8way": {"ms": t8[False] * 1e3, "gflops": FLOPS_PER_SITE * Vh / t8[False] / 1e9,
+                           "gbs": BYTES_PER_SITE["f32"] * Vh / t8[False] / 1e9,
+                           "frac_hbm": BYTES_PER_SITE["f32"] * Vh / t8[False] / 1e9 / peak},
+              "f32_8way_recon12": {"ms": t8[True] * 1e3, "gflops": FLOPS_PER_SITE * Vh / t8[True] / 1e9,
+                                   "gbs": BYTES_PER_SITE["f32_recon12"] * Vh / t8[True] / 1e9,
+                                   "frac_hbm": BYTES_PER_SITE["f32_recon12"] * Vh / t8[True] / 1e9 / peak},
               "f64": {"ms": t64d * 1e3, "gflops": FLOPS_PER_SITE * Vh / t64d / 1e9,
                       "gbs": BYTES_PER_SITE["f64"] * Vh / t64d / 1e9,
                       "frac_hbm": BYTES_PER_SITE["f64"] * Vh / t64d / 1e9 / peak}}

@@ -66,6 +66,7 @@ extern "C" {
 
 /* ---- sqcg_load_links options ---- */
 #define SQCG_RECON12_LONG 1 /* FP32 long links as 2 rows (12 reals), row 3 rebuilt on the fly */
+#define SQCG_EIGHT_WAY 2    /* FP32 copy also stores the backward links -F(n-mu)^+, -L(n-3mu)^+ at n */
 
 /* ---- precisions ---- */
 #define SQCG_F64 0
@@ -102,7 +103,7 @@ int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
 /* Reliable-update trigger of the mixed-precision solvers on this context: the
  * FP64 true residual is recomputed when the iterated |r| falls below
  * delta * (max |r| since the last update), or after `interval` iterations,
- * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.1 and 100).
+ * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.01 and 100).
  * The batched solve uses the settings of its first context. */
 int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval);
 
@@ -120,7 +121,12 @@ int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
  * every long link is s * W with W in SU(3) and one global real |s| (checked to
  * 1e-12), else SQCG_ERR_RECON_REJECTED and nothing is loaded. The FP64 copy
  * and the fat links are always stored in full (the FP64 Dslash is bound by
- * FP64 arithmetic, which the reconstruction would add to). */
+ * FP64 arithmetic, which the reconstruction would add to).
+ * SQCG_EIGHT_WAY additionally stores, for the FP32 copy, the daggered and
+ * negated backward links at the site that uses them (the paper's 8-way gauge
+ * storage, Sec. 3): every FP32 link read is then at the thread's own index, at
+ * twice the FP32 link memory. Combined with SQCG_RECON12_LONG the backward
+ * long links are stored as two rows too. */
 int sqcg_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 
 /* Copy one host colour vector (parity order, complex double [Vh][3]) into a

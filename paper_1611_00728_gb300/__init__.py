@@ -28,6 +28,7 @@ F64, F32 = 0, 1
 MODE_F64, MODE_MIXED = 0, 1
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
+EIGHT_WAY = 2
 #: parameters of the preconditioner network (see include/sqcg.h for the layout)
 NN_NPARAMS = 1472
 #: MILC's flop count of one Dslash output site: 16 x 66 (3x3 complex mat-vec) + 15 x 6 (adds)
@@ -172,7 +173,7 @@ class Lattice:
     def __exit__(self, *exc):
         self.close()
 
-    def set_reliable_update(self, delta: float = 0.1, interval: int = 100):
+    def set_reliable_update(self, delta: float = 0.01, interval: int = 100):
         """Mixed-precision trigger: FP64 true residual when |r| < delta * max|r| since the last one, or every
         `interval` iterations."""
         _check(library().sqcg_set_reliable_update(self._h, float(delta), int(interval)), "sqcg_set_reliable_update")
@@ -181,15 +182,16 @@ class Lattice:
         library().sqcg_set_stream(self._h, ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream))
 
     # -- data -------------------------------------------------------------
-    def load_links(self, fat: np.ndarray, lng: np.ndarray, recon12: bool = False):
-        """fat, lng: complex128 [V][4][3][3] host arrays (forward links, lex order)."""
+    def load_links(self, fat: np.ndarray, lng: np.ndarray, recon12: bool = False, eight_way: bool = False):
+        """fat, lng: complex128 [V][4][3][3] host arrays (forward links, lex order). recon12: FP32 long links
+        as two rows (checked); eight_way: FP32 copy also stores the backward links at the site that uses them."""
         fat = np.ascontiguousarray(fat, dtype=np.complex128)
         lng = np.ascontiguousarray(lng, dtype=np.complex128)
         if fat.shape != (self.V, 4, 3, 3) or lng.shape != (self.V, 4, 3, 3):
             raise ValueError(f"links must have shape ({self.V}, 4, 3, 3)")
         self._sync_stream()
-        _check(library().sqcg_load_links(self._h, fat.ctypes.data, lng.ctypes.data, RECON12_LONG if recon12 else 0),
-               "sqcg_load_links")
+        opts = (RECON12_LONG if recon12 else 0) | (EIGHT_WAY if eight_way else 0)
+        _check(library().sqcg_load_links(self._h, fat.ctypes.data, lng.ctypes.data, opts), "sqcg_load_links")
         self.recon12 = recon12
 
     def new_spinor(self, prec: int = F64, count: int | None = None):

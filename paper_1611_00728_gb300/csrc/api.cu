@@ -82,7 +82,7 @@ int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out)
   g.st = g.Lxh * g.Ly * g.Lz;
   g.apbc = (flags & SQCG_ANTIPERIODIC_T) ? 1 : 0;
   c->stream = (cudaStream_t)cuda_stream;
-  c->ru_delta = 0.1;
+  c->ru_delta = 0.01;
   c->ru_interval = 100;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     sqcg_set_last_cuda_error(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);
@@ -100,6 +100,7 @@ int sqcg_destroy(sqcg_ctx* ctx) {
   free_batch_plan(ctx);
   free_workspace(ctx);
   cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
+  cudaFree(ctx->fatb32); cudaFree(ctx->lngb32);
   cudaFree(ctx->stage);
   cudaStreamDestroy(ctx->cap_stream);
   free(ctx);

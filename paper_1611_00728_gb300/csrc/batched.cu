@@ -112,8 +112,8 @@ __device__ void rhs_finish(RhsScalars& s, const BatchState* st, int fin, double 
           s.iter >= st->max_iter)
         s.need_update = 1;
       break;
-    case BFIN_TRUE:  // every active RHS of an updated block takes the FP64 residual
-      if (!s.active) break;
+    case BFIN_TRUE:  // only the RHS that asked for the update were recomputed
+      if (!s.need_update || !s.active) break;
       if (!isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; s.need_update = 0; break; }
       s.rr_true = v;
       s.need_update = 0;
@@ -200,11 +200,12 @@ __device__ __forceinline__ void load_link_m(typename V2<R>::T (&U)[9], const typ
 
 template <typename R, int W, bool DAG>
 __device__ __forceinline__ void apply_w(typename V2<R>::T (&acc)[W][3], const typename V2<R>::T (&U)[9],
-                                        const typename V2<R>::T* __restrict__ in, int Vh, int idx, int nw) {
+                                        const typename V2<R>::T* __restrict__ in, int Vh, int idx, int nw,
+                                        unsigned mask = 0xffffffffu) {
   typedef typename V2<R>::T R2;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    if (w < nw) {
+    if (w < nw && ((mask >> w) & 1u)) {
       R2 v[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) v[c] = __ldg(in + ((size_t)w * 3 + c) * Vh + idx);
@@ -234,7 +235,8 @@ __device__ __forceinline__ void apply_w(typename V2<R>::T (&acc)[W][3], const ty
 // acc[w] = D in[w] at site i of parity par, for nw <= W right-hand sides
 template <typename R, int W>
 __device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i, const typename V2<R>::T* in,
-                                                 int nw, typename V2<R>::T (&acc)[W][3]) {
+                                                 int nw, typename V2<R>::T (&acc)[W][3],
+                                                 unsigned mask = 0xffffffffu) {
   typedef typename V2<R>::T R2;
   const Geom& g = L.g;
   const int Vh = g.Vh;
@@ -297,14 +299,14 @@ __device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i
       }
       if (k == 0) {
         load_link_m<R, false>(U, fat_p + (size_t)mu * 9 * Vh, Vh, i, false, R(1));
-        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw);
+        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw, mask);
         load_link_m<R, false>(U, fat_q + (size_t)mu * 9 * Vh, Vh, bwd, false, R(1));
-        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
+        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw, mask);
       } else {
         load_link_m<R, true>(U, lng_p + (size_t)mu * nl * Vh, Vh, i, recon, inv_f);
-        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw);
+        apply_w<R, W, false>(acc, U, in, Vh, fwd, nw, mask);
         load_link_m<R, true>(U, lng_q + (size_t)mu * nl * Vh, Vh, bwd, recon, inv_b);
-        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw);
+        apply_w<R, W, true>(acc, U, in, Vh, bwd, nw, mask);
       }
     }
   }
@@ -357,14 +359,22 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   if constexpr (F64) in = (a.in_vec == V_X ? (const R2*)L.x : (const R2*)L.tmp64);
   else in = (a.in_vec == V_P ? (const R2*)L.p : (const R2*)L.tmp);
   in += (size_t)w0 * 3 * Vh;
-  if (i < Vh && nw > 0) {
+  // in a reliable-update pass only the RHS that asked for one are computed (FP64 work is the cost here)
+  unsigned mask = 0xffffffffu;
+  if (a.gate == GATE_UPDATE) {
+    mask = 0u;
+#pragma unroll
+    for (int w = 0; w < WT; ++w)
+      if (w < nw && a.st->r[L.rhs0 + w0 + w].need_update && a.st->r[L.rhs0 + w0 + w].active) mask |= 1u << w;
+  }
+  if (i < Vh && nw > 0 && mask) {
     R2 acc[WT][3];
-    dslash_mrhs_site<R, WT>(L, a.par, i, in, nw, acc);
+    dslash_mrhs_site<R, WT>(L, a.par, i, in, nw, acc, mask);
     if (a.epi == M_PLAIN) {
       R2* out = (F64 ? (R2*)L.tmp64 : (R2*)L.tmp) + (size_t)w0 * 3 * Vh;
 #pragma unroll
       for (int w = 0; w < WT; ++w)
-        if (w < nw)
+        if (w < nw && ((mask >> w) & 1u))
 #pragma unroll
           for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
     } else if constexpr (!F64) {  // M_NORMAL_DOT (FP32): Ap = sigma p - D tmp, <p, Ap>
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
       float2* pb32 = L.p + (size_t)w0 * 3 * Vh;
 #pragma unroll
       for (int w = 0; w < WT; ++w) {
-        if (w < nw) {
+        if (w < nw && ((mask >> w) & 1u)) {
           const double sig = a.st->r[L.rhs0 + w0 + w].sigma;
           double n2 = 0.0;
 #pragma unroll

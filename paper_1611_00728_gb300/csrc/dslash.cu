@@ -9,7 +9,8 @@
 // [parity][mu][elem][Vh] so that a warp reads each matrix element of 32
 // consecutive sites as one contiguous segment; colour vectors are [3][Vh].
 // The backward hop reads the forward link of the neighbour and applies the
-// dagger in registers (forward-only storage, the standard MILC layout).
+// dagger in registers (forward-only storage, the standard MILC layout), or,
+// with the 8-way option of the FP32 copy, reads -U^+ stored at the site itself.
 // Neighbour indices are computed from the site coordinates (no index tables).
 // With 12-real long links (FP32 copy only) the third row is rebuilt as
 // conj(row0 x row1) / s, s = s0 * eta_mu * boundary sign of that link.
@@ -94,6 +95,8 @@ struct DArgs {
   const typename V2<R>::T* fat_q;  // fat links of the input parity
   const typename V2<R>::T* lng_p;
   const typename V2<R>::T* lng_q;
+  const typename V2<R>::T* fatb_p;  // 8-way: -F_mu(n - mu)^+ stored at the output site n
+  const typename V2<R>::T* lngb_p;  // 8-way: -L_mu(n - 3mu)^+ stored at n
   int nl;                          // elements per long link (9 or 6)
   R inv_s0;                        // 1 / global long-link scale (recon)
   const typename V2<R>::T* in;
@@ -109,7 +112,8 @@ struct DArgs {
 };
 
 // D at output site i of parity a.par; returns the three colour components.
-template <typename R, bool RECON>
+// EIGHT: the backward links are read, already daggered and negated, at i.
+template <typename R, bool RECON, bool EIGHT>
 __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V2<R>::T (&acc)[3]) {
   typedef typename V2<R>::T R2;
   const Geom& g = a.g;
@@ -164,16 +168,26 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
         load_link<R, R2, false>(U, a.fat_p + (size_t)mu * 9 * Vh, Vh, i, R(1));
         load_vec(v, a.in, Vh, fwd);
         acc_mv<R>(acc, U, v);
-        load_link<R, R2, false>(U, a.fat_q + (size_t)mu * 9 * Vh, Vh, bwd, R(1));
         load_vec(v, a.in, Vh, bwd);
-        sub_mdv<R>(acc, U, v);
+        if (EIGHT) {
+          load_link<R, R2, false>(U, a.fatb_p + (size_t)mu * 9 * Vh, Vh, i, R(1));
+          acc_mv<R>(acc, U, v);
+        } else {
+          load_link<R, R2, false>(U, a.fat_q + (size_t)mu * 9 * Vh, Vh, bwd, R(1));
+          sub_mdv<R>(acc, U, v);
+        }
       } else {
         load_link<R, R2, RECON>(U, a.lng_p + (size_t)mu * a.nl * Vh, Vh, i, inv_s_f);
         load_vec(v, a.in, Vh, fwd);
         acc_mv<R>(acc, U, v);
-        load_link<R, R2, RECON>(U, a.lng_q + (size_t)mu * a.nl * Vh, Vh, bwd, inv_s_b);
         load_vec(v, a.in, Vh, bwd);
-        sub_mdv<R>(acc, U, v);
+        if (EIGHT) {  // -L^+ = (-s) V^+: its third row is rebuilt with the scale -s
+          load_link<R, R2, RECON>(U, a.lngb_p + (size_t)mu * a.nl * Vh, Vh, i, -inv_s_b);
+          acc_mv<R>(acc, U, v);
+        } else {
+          load_link<R, R2, RECON>(U, a.lng_q + (size_t)mu * a.nl * Vh, Vh, bwd, inv_s_b);
+          sub_mdv<R>(acc, U, v);
+        }
       }
     }
   }
@@ -181,7 +195,7 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
 
 constexpr int kThreads = 128;
 
-template <typename R, typename RO, bool RECON, int EPI>
+template <typename R, typename RO, bool RECON, bool EIGHT, int EPI>
 __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   typedef typename V2<R>::T R2;
   typedef typename V2<RO>::T O2;
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   double part = 0.0;
   if (i < Vh) {
     R2 acc[3];
-    dslash_site<R, RECON>(a, i, acc);
+    dslash_site<R, RECON, EIGHT>(a, i, acc);
     O2* out = static_cast<O2*>(a.out);
     if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
@@ -232,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   }
 }
 
-template <typename R, typename RO, bool RECON>
+template <typename R, typename RO, bool RECON, bool EIGHT>
 int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   typedef typename V2<R>::T R2;
   DArgs<R> a;
@@ -247,6 +261,8 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   a.fat_q = fat + (size_t)q * 4 * 9 * Vh;
   a.lng_p = lng + (size_t)p * 4 * nl * Vh;
   a.lng_q = lng + (size_t)q * 4 * nl * Vh;
+  a.fatb_p = EIGHT ? reinterpret_cast<const R2*>(ctx->fatb32) + (size_t)p * 4 * 9 * Vh : nullptr;
+  a.lngb_p = EIGHT ? reinterpret_cast<const R2*>(ctx->lngb32) + (size_t)p * 4 * nl * Vh : nullptr;
   a.nl = nl;
   a.inv_s0 = (R)(RECON ? 1.0 / ctx->long_scale : 1.0);
   a.in = static_cast<const R2*>(L.in);
@@ -266,10 +282,10 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.epi == EPI_NORMAL_DOT || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE && grid > ctx->max_blocks)
     return SQCG_ERR_INVALID_ARG;
   switch (L.epi) {
-    case EPI_PLAIN: k_dslash<R, RO, RECON, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
-    case EPI_NORMAL: k_dslash<R, RO, RECON, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
-    case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
-    case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -280,10 +296,12 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
 
 template <typename R, typename RO>
 int launch_r(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
-  if constexpr (sizeof(R) == 4) {
-    if (ctx->recon) return launch_t<R, RO, true>(ctx, L, s);
+  if constexpr (sizeof(R) == 4) {  // 12-real and 8-way forms exist for the FP32 copy only
+    if (ctx->eightway)
+      return ctx->recon ? launch_t<R, RO, true, true>(ctx, L, s) : launch_t<R, RO, false, true>(ctx, L, s);
+    if (ctx->recon) return launch_t<R, RO, true, false>(ctx, L, s);
   }
-  return launch_t<R, RO, false>(ctx, L, s);
+  return launch_t<R, RO, false, false>(ctx, L, s);
 }
 
 }  // namespace

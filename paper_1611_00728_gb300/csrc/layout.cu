@@ -94,6 +94,37 @@ __global__ void k_convert(const I2* __restrict__ in, O2* __restrict__ out, int n
   out[i] = o;
 }
 
+// 8-way FP32 backward links: out[p][mu][e][n_h] = -(U_mu(n - d mu))^dagger, from the
+// folded FP64 forward links; e < nelem (6: first two rows for the 12-real form)
+__global__ void k_pack_backward(const double2* __restrict__ fwd64, Geom g, int d, int nelem, float2* __restrict__ out) {
+  const long V = 2L * g.Vh;
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 4 * V) return;
+  const int mu = (int)(tid / V);
+  const long n = tid % V;
+  int c[4];
+  long m = n;
+  c[0] = (int)(m % g.Lx); m /= g.Lx;
+  c[1] = (int)(m % g.Ly); m /= g.Ly;
+  c[2] = (int)(m % g.Lz);
+  c[3] = (int)(m / g.Lz);
+  const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int Ls[4] = {g.Lx, g.Ly, g.Lz, g.Lt};
+  int cb[4] = {c[0], c[1], c[2], c[3]};
+  cb[mu] = ((c[mu] - d) % Ls[mu] + Ls[mu]) % Ls[mu];
+  const long nb = cb[0] + (long)g.Lx * (cb[1] + (long)g.Ly * (cb[2] + (long)g.Lz * cb[3]));
+  const int q = 1 - par;
+  const size_t src = ((size_t)q * 4 + mu) * 9 * g.Vh + (nb >> 1);
+  const size_t dst = ((size_t)par * 4 + mu) * nelem * g.Vh + (n >> 1);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const int e = a * 3 + b;
+      if (e >= nelem) continue;
+      const double2 u = fwd64[src + (size_t)(b * 3 + a) * g.Vh];  // element (b, a) of the forward link
+      out[dst + (size_t)e * g.Vh] = make_float2(__double2float_rn(-u.x), __double2float_rn(u.y));
+    }
+}
+
 typedef std::complex<double> cd;
 
 // 12-real eligibility: every long link is s * W, W in SU(3), |s| global.
@@ -164,8 +195,9 @@ int ensure_stage(sqcg_ctx* ctx, size_t bytes) {
 
 int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts) {
   if (!fat || !lng) return SQCG_ERR_INVALID_ARG;
-  if (opts & ~SQCG_RECON12_LONG) return SQCG_ERR_INVALID_ARG;
+  if (opts & ~(SQCG_RECON12_LONG | SQCG_EIGHT_WAY)) return SQCG_ERR_INVALID_ARG;
   const bool recon = (opts & SQCG_RECON12_LONG) != 0;
+  const bool eightway = (opts & SQCG_EIGHT_WAY) != 0;
   double s0 = 1.0;
   if (recon && !recon_check(ctx, lng, &s0)) return SQCG_ERR_RECON_REJECTED;
 
@@ -179,8 +211,11 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   // drop earlier links
   SQCG_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
+  cudaFree(ctx->fatb32); cudaFree(ctx->lngb32);
   ctx->fat64 = ctx->lng64 = nullptr;
   ctx->fat32 = ctx->lng32 = nullptr;
+  ctx->fatb32 = ctx->lngb32 = nullptr;
+  ctx->eightway = false;
   ctx->have_links = false;
   free_graphs(ctx);
   free_batch_plan(ctx);
@@ -213,10 +248,23 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
   } while (0);
   cudaFree(raw);
+  if (rc == SQCG_OK && eightway) {
+    if (cudaMalloc((void**)&ctx->fatb32, nfat * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->lngb32, nlng32 * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->fatb32); cudaFree(ctx->lngb32);
+      ctx->fatb32 = ctx->lngb32 = nullptr;
+      return SQCG_ERR_NO_MEMORY;
+    }
+    k_pack_backward<<<grid, kThreads, 0, s>>>(ctx->fat64, ctx->g, 1, 9, ctx->fatb32);
+    k_pack_backward<<<grid, kThreads, 0, s>>>(ctx->lng64, ctx->g, 3, nl32, ctx->lngb32);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = SQCG_ERR_CUDA;
+  }
   if (rc != SQCG_OK) {
     sqcg_set_last_cuda_error(cudaGetLastError(), "load_links", __FILE__, __LINE__);
     return rc;
   }
+  ctx->eightway = eightway;
   ctx->recon = recon;
   ctx->long_scale = s0;
   ctx->have_links = true;

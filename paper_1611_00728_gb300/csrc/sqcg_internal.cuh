@@ -162,6 +162,10 @@ struct sqcg_ctx {
   double2* lng64;
   float2* fat32;
   float2* lng32;
+  // 8-way option (FP32 only): backward links -F_mu(n-mu)^+, -L_mu(n-3mu)^+ stored at n
+  bool eightway;
+  float2* fatb32;
+  float2* lngb32;
 
   // host-copy staging for pack/unpack
   void* stage;

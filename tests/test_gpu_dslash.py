@@ -52,6 +52,27 @@ def test_dslash_matches_oracle(sqcg, links_cache, L, prec, recon):
             assert rel(got, want) <= TOL[prec], (L, prec, recon, out_par, rel(got, want))
 
 
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 8, 10, 12)])
+@pytest.mark.parametrize("recon", [False, True])
+@pytest.mark.parametrize("apbc", [False, True])
+def test_dslash_eight_way_matches_oracle(sqcg, links_cache, L, recon, apbc):
+    """8-way FP32 storage (backward links at the site that uses them) gives the same D."""
+    fat, lng = links_cache(L, 1001)
+    with sqcg.Lattice(L, antiperiodic_t=apbc) as lat:
+        lat.load_links(fat, lng, recon12=recon, eight_way=True)
+        for out_par in (0, 1):
+            psi = synth.gaussian_source(L, 2000 + out_par)
+            out = lat.new_spinor(1)
+            lat.dslash(out_par, lat.pack(psi, 1), out, 1)
+            want = oracle.dslash(L, fat, lng, psi, out_par, apbc)
+            assert rel(lat.unpack(out, 1), want) <= TOL[1]
+        # FP64 stays forward-only and exact
+        out = lat.new_spinor(0)
+        psi = synth.gaussian_source(L, 3)
+        lat.dslash(0, lat.pack(psi), out)
+        assert rel(lat.unpack(out), oracle.dslash(L, fat, lng, psi, 0, apbc)) <= TOL[0]
+
+
 @pytest.mark.parametrize("apbc", [False, True])
 def test_dslash_periodic_and_folded_phases(sqcg, links_cache, apbc):
     L = (6, 8, 10, 12)
