@@ -12,8 +12,9 @@
 // adjacent, so when W < nrhs the other blocks find the links in L2.
 //
 // Every RHS has its own CG scalars in BatchState; the per-RHS dot products are
-// reduced deterministically per RHS block (warp shuffle -> block -> last tile
-// of the block in site-block order). The loop is one CUDA graph: a WHILE node
+// reduced deterministically in two stages (warp shuffle -> block partial per
+// tile, then one block per RHS adds the partials in site-block order). The
+// BLAS kernels use their own 256-site tiles, independent of the Dslash tile. The loop is one CUDA graph: a WHILE node
 // around [D_oe p, A p with <p,Ap>, x/r update, IF(reliable update in FP64),
 // p update, loop control]. W and T are chosen by a small autotuner that times
 // the FP32 multi-RHS Dslash over the whole batch and caches the choice.
@@ -35,6 +36,7 @@ constexpr int kMaxThreads = 512;  // largest CTA (site block x RHS groups)
 constexpr int kMaxTSmem = 128;    // largest site block of the shared-memory FP32 Dslash (144 KB of links)
 constexpr int kMinT = 32;     // smallest site block
 constexpr int kW64 = 4;       // RHS per pass in the FP64 kernels (register budget)
+constexpr int kTB = 256;      // site block of the BLAS kernels (independent of the tuned Dslash tile)
 
 struct LatDev {
   Geom g;
@@ -50,6 +52,7 @@ struct LatDev {
   int nrb, rb0;    // FP32 RHS blocks of width W, global index of the first
   int nrb64, rb640;  // FP64 RHS blocks of width min(W, kW64)
   int tile0, tile640;  // first FP32 / FP64 tile
+  int nsb_b, tile0_b;  // BLAS tiling: site blocks of kTB sites, first BLAS tile
   float2 *r, *p, *Ap, *tmp;  // [nrhs][3][Vh]
   double2* x;
   double2* tmp64;
@@ -129,20 +132,17 @@ __device__ void rhs_finish(RhsScalars& s, const BatchState* st, int fin, double 
   }
 }
 
-// Reduce per-RHS values over the tile, then over all site blocks of the RHS
-// block (the last tile of the block sums the partials in site-block order) and
-// run the per-RHS step. Blocks are (sites x RHS groups): thread (x, y) holds
-// the WT values of RHS y*WT .. y*WT+WT-1 of the tile; blockDim.x is a multiple
-// of 32, so every warp belongs to one group. counter: this RHS block's
-// arrival counter.
+// First stage of the per-RHS sums: reduce the tile's values per RHS and write
+// partials[rhs][site block]. Blocks are (sites x RHS groups): thread (x, y)
+// holds the WT values of RHS y*WT .. y*WT+WT-1 of the tile; blockDim.x is a
+// multiple of 32, so every warp belongs to one group. The second stage is
+// k_batch_finish, launched right after on the same stream.
 template <int WT>
-__device__ void rhs_block_reduce(double (&v)[WT], const LatDev& L, int wbase, int nw_tile, int sb, BatchState* st,
-                                 double* partials, int max_nsb, int counter, int fin) {
+__device__ void rhs_block_partial(double (&v)[WT], const LatDev& L, int wbase, int nw_tile, int sb,
+                                  double* partials, int max_nsb) {
   __shared__ double red[16][kMaxT / 32];
-  __shared__ bool am_last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, wx = threadIdx.x >> 5, nwx = blockDim.x >> 5;
-  const int nwarps = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
   for (int w = 0; w < WT; ++w) {
     const double t = warp_sum(v[w]);
@@ -153,25 +153,24 @@ __device__ void rhs_block_reduce(double (&v)[WT], const LatDev& L, int wbase, in
     double t = 0.0;
     for (int j = 0; j < nwx; ++j) t += red[tid][j];
     partials[(size_t)(L.rhs0 + wbase + tid) * max_nsb + sb] = t;
-    __threadfence();
   }
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned int t = atomicAdd(&st->counter[counter], 1u);
-    am_last = (t == (unsigned)L.nsb - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  for (int w = tid >> 5; w < nw_tile; w += nwarps) {
-    const int g = L.rhs0 + wbase + w;
-    double sum = 0.0;
-    for (int j = lane; j < L.nsb; j += 32) sum += __ldcg(partials + (size_t)g * max_nsb + j);
-    sum = warp_sum(sum);
-    if (lane == 0) rhs_finish(st->r[g], st, fin, sum);
-  }
-  __syncthreads();
-  if (tid == 0) st->counter[counter] = 0;
+}
+
+// Second stage: one block per RHS adds its partials in site-block order and
+// runs the per-RHS scalar step (deterministic). blas: the partials come from
+// the BLAS tiling (nsb_b site blocks) rather than the Dslash tiling (nsb).
+__global__ void __launch_bounds__(256) k_batch_finish(BatchState* st, const LatDev* lats, int nlat,
+                                                      const double* partials, int max_nsb, int fin, int blas) {
+  const int g = blockIdx.x;
+  int k = 0;
+  for (int j = 1; j < nlat; ++j)
+    if (g >= lats[j].rhs0) k = j;
+  const LatDev& L = lats[k];
+  const int n = blas ? L.nsb_b : L.nsb;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += partials[(size_t)g * max_nsb + j];
+  s = block_sum(s);
+  if (threadIdx.x == 0) rhs_finish(st->r[g], st, fin, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,8 +423,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   }
   if (a.epi != M_PLAIN) {
     const int fin = (a.epi == M_NORMAL_DOT) ? BFIN_PAP : (a.write_p ? BFIN_INIT : BFIN_TRUE);
-    const int counter = F64 ? (SQCG_MAX_BATCH_RHS + L.rb640 + rb) : (L.rb0 + rb);
-    rhs_block_reduce<WT>(part, L, wbase, nw_tile, sb, a.st, a.partials, a.max_nsb, counter, fin);
+    (void)fin;
+    rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
   }
 }
 
@@ -575,7 +574,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
     }
   }
   if (a.epi != M_PLAIN)
-    rhs_block_reduce<WT>(part, L, wbase, nw_tile, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb, BFIN_PAP);
+    rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
 }
 
 // ---------------------------------------------------------------------------
@@ -594,11 +593,13 @@ struct BArgs {
 };
 
 template <int W>
-__global__ void __launch_bounds__(kMaxT) k_mrhs_blas(BArgs a) {
+__global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
   const int tile = blockIdx.x;
-  const int k = find_lat(a.lats, a.nlat, tile, false);
+  int k = 0;
+  for (int j = 1; j < a.nlat; ++j)
+    if (tile >= a.lats[j].tile0_b) k = j;
   const LatDev& L = a.lats[k];
-  const int local = tile - L.tile0;
+  const int local = tile - L.tile0_b;
   const int rb = local % L.nrb, sb = local / L.nrb;
   const int wbase = rb * W;
   const int nw = min(W, L.nrhs - wbase);
@@ -658,9 +659,7 @@ __global__ void __launch_bounds__(kMaxT) k_mrhs_blas(BArgs a) {
       }
     }
   }
-  if (a.op != B_XPAY)
-    rhs_block_reduce<W>(part, L, wbase, nw, sb, a.st, a.partials, a.max_nsb, L.rb0 + rb,
-                        a.op == B_UPDATE ? BFIN_UPDATE : BFIN_BB);
+  if (a.op != B_XPAY) rhs_block_partial<W>(part, L, wbase, nw, sb, a.partials, a.max_nsb);
 }
 
 // One thread: which RHS blocks need the FP64 reliable update -> IF condition
@@ -717,6 +716,7 @@ struct BatchPlan {
   int W, T;              // tuned RHS block width and site block (threads along x)
   int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
   int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
+  int ntiles_b;          // BLAS tiles over all lattices
   int nblk;              // FP32 RHS blocks over all lattices
   int max_nsb;
   int nrhs_total;
@@ -780,7 +780,7 @@ std::string tune_key(const BatchPlan& P) {
 
 // tiles, blocks and first indices for a given W and T
 void layout_tiles(BatchPlan& P, int W, int WT, int T) {
-  int tile = 0, tile64 = 0, rb0 = 0, rb640 = 0;
+  int tile = 0, tile64 = 0, tileb = 0, rb0 = 0, rb640 = 0;
   const int W64 = W < kW64 ? W : kW64;
   for (int k = 0; k < P.nlat; ++k) {
     LatDev& L = P.host[k];
@@ -791,6 +791,9 @@ void layout_tiles(BatchPlan& P, int W, int WT, int T) {
     L.rb640 = rb640;
     L.tile0 = tile;
     L.tile640 = tile64;
+    L.nsb_b = grid_for(L.g.Vh, kTB);
+    L.tile0_b = tileb;
+    tileb += L.nsb_b * L.nrb;
     tile += L.nsb * L.nrb;
     tile64 += L.nsb * L.nrb64;
     rb0 += L.nrb;
@@ -801,6 +804,7 @@ void layout_tiles(BatchPlan& P, int W, int WT, int T) {
   P.T = T;
   P.ntiles = tile;
   P.ntiles64 = tile64;
+  P.ntiles_b = tileb;
   P.nblk = rb0;
 }
 
@@ -822,11 +826,11 @@ int launch_mrhs_blas(const BatchPlan& P, int op, cudaStream_t s) {
   BArgs a;
   a.lats = P.dev; a.nlat = P.nlat; a.op = op; a.st = P.st; a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W;
   switch (P.W) {
-    case 1: k_mrhs_blas<1><<<P.ntiles, P.T, 0, s>>>(a); break;
-    case 2: k_mrhs_blas<2><<<P.ntiles, P.T, 0, s>>>(a); break;
-    case 4: k_mrhs_blas<4><<<P.ntiles, P.T, 0, s>>>(a); break;
-    case 8: k_mrhs_blas<8><<<P.ntiles, P.T, 0, s>>>(a); break;
-    case 16: k_mrhs_blas<16><<<P.ntiles, P.T, 0, s>>>(a); break;
+    case 1: k_mrhs_blas<1><<<P.ntiles_b, kTB, 0, s>>>(a); break;
+    case 2: k_mrhs_blas<2><<<P.ntiles_b, kTB, 0, s>>>(a); break;
+    case 4: k_mrhs_blas<4><<<P.ntiles_b, kTB, 0, s>>>(a); break;
+    case 8: k_mrhs_blas<8><<<P.ntiles_b, kTB, 0, s>>>(a); break;
+    case 16: k_mrhs_blas<16><<<P.ntiles_b, kTB, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -838,6 +842,12 @@ MArgs margs(const BatchPlan& P, int par, int in_vec, int epi, int gate, int writ
   a.lats = P.dev; a.nlat = P.nlat; a.par = par; a.in_vec = in_vec; a.epi = epi; a.gate = gate; a.st = P.st;
   a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W; a.write_p = write_p;
   return a;
+}
+
+int launch_finish_b(const BatchPlan& P, int fin, int blas, cudaStream_t s) {
+  k_batch_finish<<<P.nrhs_total, 256, 0, s>>>(P.st, P.dev, P.nlat, P.partials, P.max_nsb, fin, blas);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
 }
 
 int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
@@ -1027,7 +1037,9 @@ int capture_plan(BatchPlan& P) {
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_ITER, cs);
     if (rc == SQCG_OK) rc = launch_f32(P, 0, V_TMP, M_NORMAL_DOT, GATE_ITER, cs);
+    if (rc == SQCG_OK) rc = launch_finish_b(P, BFIN_PAP, 0, cs);
     if (rc == SQCG_OK) rc = launch_mrhs_blas(P, B_UPDATE, cs);
+    if (rc == SQCG_OK) rc = launch_finish_b(P, BFIN_UPDATE, 1, cs);
     if (rc == SQCG_OK) {
       k_batch_ctl_update<<<1, 32, 0, cs>>>(P.st, P.dev, P.nlat, P.W);
       if (cudaGetLastError() != cudaSuccess) rc = SQCG_ERR_CUDA;
@@ -1066,6 +1078,7 @@ int capture_plan(BatchPlan& P) {
     if (cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     rc = launch_f64(P, 1, V_X, M_PLAIN, GATE_UPDATE, 0, cs);
     if (rc == SQCG_OK) rc = launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_UPDATE, 0, cs);
+    if (rc == SQCG_OK) rc = launch_finish_b(P, BFIN_TRUE, 0, cs);
     e = cudaStreamEndCapture(cs, &got);
     if (rc != SQCG_OK) break;
     if (e != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
@@ -1140,13 +1153,15 @@ extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* 
   SQCG_CUDA_TRY(cudaMemcpyAsync(P.st, h, sizeof(BatchState), cudaMemcpyHostToDevice, s));
   // |b|^2 per RHS; r = b - A x0 in FP64 (x holds the initial guess), p = r
   SQCG_TRY(launch_mrhs_blas(P, B_NORM_B, s));
+  SQCG_TRY(launch_finish_b(P, BFIN_BB, 1, s));
   for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 1;
   SQCG_CUDA_TRY(cudaMemcpyAsync(P.st->blk_update, h->blk_update, sizeof(int) * P.nblk, cudaMemcpyHostToDevice, s));
   SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_NONE, 0, s));
   SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_NONE, 1, s));
+  SQCG_TRY(launch_finish_b(P, BFIN_INIT, 0, s));
   SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
   SQCG_CUDA_TRY(cudaStreamSynchronize(s));
-  int launches = 3;
+  int launches = 6;
   int any = 0;
   for (int j = 0; j < total; ++j) {
     if (h->r[j].bb == 0.0 && h->r[j].active) {  // b = 0: x = 0 is the solution
@@ -1178,7 +1193,7 @@ extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* 
     SQCG_CUDA_TRY(cudaGraphLaunch(P.exec, s));
     SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
-    launches += h->loop_count * 6 + h->if_runs * 2;
+    launches += h->loop_count * 8 + h->if_runs * 3;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int worst = SQCG_OK;

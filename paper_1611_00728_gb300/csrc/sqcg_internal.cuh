@@ -115,7 +115,6 @@ struct BatchState {
   RhsScalars r[SQCG_MAX_BATCH_RHS];
   int blk_active[SQCG_MAX_BATCH_RHS];  // RHS block has an active RHS
   int blk_update[SQCG_MAX_BATCH_RHS];  // RHS block runs the FP64 reliable update
-  unsigned int counter[3 * SQCG_MAX_BATCH_RHS];
 };
 
 struct BatchPlan;  // defined in batched.cu
