@@ -49,8 +49,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
 # at 32^4, measured by ncu (profiles/dslash_f32_recon12_32x32x32x32.md), with the
 # hash of the kernel sources they were taken on (reported as null once those change).
-NCU_TRAFFIC = {"sources_sha256": "8e98da2cd236035f8c10bc948b311b5843f75e0760f830bdc7a905f7bc3fb574",
-               "bytes_per_launch": 525859328 + 11529728, "lattice": [32, 32, 32, 32]}
+NCU_TRAFFIC = {"sources_sha256": "b327f0b141b85bfff29ea9420e2938b9768f8ebd6edcb4aff31d6918e4871d14",
+               "bytes_per_launch": 526045952 + 11590144, "lattice": [32, 32, 32, 32]}
 
 
 def parse():
@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
-    ap.add_argument("--workload", choices=["single", "multishift", "batched", "learned"], default="single",
+    ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned"], default="single",
                     help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
 
@@ -375,12 +375,13 @@ def run_ours(args, ranks: Ranks):
     traffic = None
     if NCU_TRAFFIC["sources_sha256"] == sources_sha256() and NCU_TRAFFIC["lattice"] == list(LATTICE):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    roofline = {"bound": "hbm", "kernel": "k_dslash<float, float, 1, 0> (FP32 Dslash, 12-real long links)",
+    roofline = {"bound": "hbm", "kernel": "k_dslash<float, float, 1, 0, 0> (FP32 Dslash, 12-real long links)",
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "traffic": traffic,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE["f32_recon12"] * Vh, "ms_per_launch": t32r * 1e3}
     dslash = {"f32": {"ms": t32 * 1e3, "gflops": FLOPS_PER_SITE * Vh / t32 / 1e9,
-                      "gbs": ach, "frac_hbm": ach / peak},
+                      "gbs": BYTES_PER_SITE["f32"] * Vh / t32 / 1e9,
+                      "frac_hbm": BYTES_PER_SITE["f32"] * Vh / t32 / 1e9 / peak},
               "f32_recon12": {"ms": t32r * 1e3, "gflops": FLOPS_PER_SITE * Vh / t32r / 1e9,
                               "gbs": BYTES_PER_SITE["f32_recon12"] * Vh / t32r / 1e9,
                               "frac_hbm": BYTES_PER_SITE["f32_recon12"] * Vh / t32r / 1e9 / peak},
@@ -489,6 +490,47 @@ def run_multishift(args):
             "fp64_cg_one_per_shift": res["fp64_cg_per_shift"],
             "speedup_vs_fp64_cg_per_shift": res["fp64_cg_per_shift"]["ms"] / res["mixed"]["ms"],
             "speedup_vs_fp64_multishift": res["fp64"]["ms"] / res["mixed"]["ms"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_rational(args):
+    """32^4, m=0.01: one application of a 12-pole rational approximation of (4m^2 - D_eo D_oe)^(-1/2)
+    to a Gaussian source (the RHMC use of the multi-shift solver), per-pole tol 1e-8."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    sq.build_if_needed()
+    m = 0.01
+    fat, lng = synth.fat_long_links(LATTICE, 1003)
+    b_host = synth.gaussian_source(LATTICE, 2300)
+    a0, a, beta = synth.inverse_sqrt_rational(12, 4 * m * m, 16.0)
+    shifts = 4 * m * m + beta
+    lat = sq.Lattice(LATTICE)
+    lat.load_links(fat, lng, recon12=True)
+    b = lat.pack(b_host)
+    out = lat.new_spinor()
+    res = {}
+    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+        for _ in range(max(args.warmup, 1)):
+            lat.rational_apply(shifts, a, a0, b, out, tol=TOL, max_iter=20000, mode=mode)
+        times, infos = [], None
+        for _ in range(args.steps):
+            infos, ms = _timed(torch, lambda: lat.rational_apply(shifts, a, a0, b, out, tol=TOL, max_iter=20000,
+                                                                 mode=mode))
+            times.append(ms)
+        res[name] = {"ms": statistics.median(times), "iters": max(i.iters for i in infos),
+                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+    lat.close()
+    line = {"metric": "rational-function application r(A) b (12 poles) time, every pole to true residual 1e-8",
+            "unit": "ms", "value": res["mixed"]["ms"], "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "32^4, m=0.01, 12-pole Gauss-Legendre approximation of x^(-1/2) on [4m^2, 16], "
+                                   "1 source (seeds 1003/2300)", "vh": int(np.prod(LATTICE)) // 2,
+                       "shifts": [float(v) for v in shifts]},
+            "rational_mixed": res["mixed"], "rational_fp64": res["fp64"],
+            "speedup_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"]}
     print(json.dumps(line), flush=True)
 
 
@@ -675,7 +717,7 @@ def main():
     if args.steps < 1:
         raise SystemExit("--steps must be >= 1")
     if args.workload != "single":
-        {"multishift": run_multishift, "batched": run_batched, "learned": run_learned}[args.workload](args)
+        {"multishift": run_multishift, "rational": run_rational, "batched": run_batched, "learned": run_learned}[args.workload](args)
         return
     ranks = Ranks()
     try:

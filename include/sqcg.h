@@ -194,6 +194,19 @@ int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, co
                              void* const* x, const double* tol, int max_iter, int mode,
                              sqcg_info* info);
 
+/* Rational-function application, the multi-mass CG's use inside RHMC evolution
+ * (paper Sec. 4: su3_rhmc_hisq, about nine masses):
+ *   out = a0 b + sum_s residues[s] (shifts[s] - D_eo D_oe)^-1 b,
+ * from one multi-shift solve (sqcg_multishift_cg_solve rules: shifts >= 0, each
+ * shift solved to FP64 true relative residual tol, mixed mode refined as
+ * needed), combined in FP64. For a rational approximation
+ * r(x) = a0 + sum_s a_s / (x + beta_s) of a function of M^+M = 4 m^2 - D_eo D_oe
+ * the shifts are 4 m^2 + beta_s. b, out: FP64 device vectors (distinct). The
+ * per-shift solutions are kept in library-owned buffers (freed with the
+ * context). info: NULL or nshift entries. Synchronises the stream. */
+int sqcg_rational_apply(sqcg_ctx* ctx, int nshift, const double* shifts, const double* residues, double a0,
+                        const void* b, void* out, double tol, int max_iter, int mode, sqcg_info* info);
+
 /* Batched CG: solve (4 mass[k]^2 - D_eo D_oe) x = b for nrhs[k] right-hand
  * sides on each of nctx lattices (1 <= nctx <= 16, sum of nrhs <= 256) in one
  * device-side loop, mixed precision (FP32 Dslash and Krylov vectors, FP64 x,

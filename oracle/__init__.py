@@ -180,6 +180,16 @@ def multishift_solutions(L, fat, lng, shifts, b_even, tol: float = 1e-12, max_it
     return out
 
 
+def rational_apply(L, fat, lng, shifts, residues, a0, b_even, tol: float = 1e-12, max_iter: int = 100000,
+                   antiperiodic_t: bool = True, nthreads: int = 0):
+    """Expected rational-function application by definition: a0 b + sum_s a_s (sigma_s - D_eo D_oe)^-1 b."""
+    out = float(a0) * np.asarray(b_even, dtype=np.complex128)
+    for (x, _, _), a in zip(multishift_solutions(L, fat, lng, shifts, b_even, tol, max_iter, antiperiodic_t,
+                                                 nthreads), residues):
+        out = out + float(a) * x
+    return out
+
+
 def dense_normal_matrix(L, fat, lng, sigma: float, antiperiodic_t: bool = True):
     """The normal operator as a dense matrix, one column per unit vector (tiny lattices only)."""
     Ld = _dims(L)

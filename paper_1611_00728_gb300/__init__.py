@@ -95,6 +95,7 @@ def library():
         lib.sqcg_normal_op_noalloc.argtypes = [P, D, I, P, P]
         lib.sqcg_cg_solve.argtypes = [P, D, P, P, D, I, I, ctypes.POINTER(Info)]
         lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
+        lib.sqcg_rational_apply.argtypes = [P, I, P, P, D, P, P, D, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
         lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.sqcg_nn_create.argtypes = [P, ctypes.POINTER(P)]
@@ -117,7 +118,7 @@ def library():
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
                      "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
-                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning"):
+                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply"):
             getattr(lib, name).restype = I
         _lib = lib
     return _lib
@@ -264,6 +265,23 @@ class Lattice:
         if raise_on_error:
             _check(rc, "sqcg_cg_solve")
         return info
+
+    def rational_apply(self, shifts, residues, a0: float, b, out, tol: float = 1e-8, max_iter: int = 10000,
+                       mode: int = MODE_MIXED, raise_on_error: bool = True):
+        """out = a0 b + sum_s residues[s] (shifts[s] - D_eo D_oe)^-1 b (one multi-shift solve). Returns Info per shift."""
+        n = len(shifts)
+        if len(residues) != n:
+            raise ValueError("one residue per shift")
+        sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+        rs = (ctypes.c_double * n)(*[float(v) for v in residues])
+        infos = (Info * n)()
+        self._sync_stream()
+        rc = library().sqcg_rational_apply(self._h, n, sh, rs, float(a0), self._check_spinor(b, F64, self.Vh),
+                                           self._check_spinor(out, F64, self.Vh), float(tol), int(max_iter), int(mode),
+                                           infos)
+        if raise_on_error:
+            _check(rc, "sqcg_rational_apply")
+        return list(infos)
 
     def multishift_cg_solve(self, shifts, b, xs, tol=1e-8, max_iter: int = 10000, mode: int = MODE_MIXED,
                             raise_on_error: bool = True):

@@ -51,6 +51,9 @@ void free_workspace(sqcg_ctx* ctx) {
   for (int j = 1; j < ctx->ms_nalloc; ++j) cudaFree(ctx->ms_p[j]);
   for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) ctx->ms_p[j] = nullptr;
   ctx->ms_nalloc = 0;
+  for (int j = 0; j < ctx->rat_n; ++j) cudaFree(ctx->rat_x[j]);
+  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) ctx->rat_x[j] = nullptr;
+  ctx->rat_n = 0;
 }
 
 extern "C" {

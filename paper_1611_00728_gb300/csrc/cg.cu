@@ -522,3 +522,72 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     }
   return worst;
 }
+
+// ---------------------------------------------------------------------------
+// rational-function application (the multi-mass CG's use inside RHMC)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Coeffs {
+  const double2* x[SQCG_MAX_SHIFTS];
+  double a[SQCG_MAX_SHIFTS];
+};
+
+// out = a0 b + sum_s a_s x_s, FP64
+__global__ void k_rational_combine(Coeffs C, int nshift, double a0, const double2* __restrict__ b,
+                                   double2* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 bv = b[i];
+  double re = a0 * bv.x, im = a0 * bv.y;
+  for (int j = 0; j < nshift; ++j) {
+    const double2 v = C.x[j][i];
+    re = fma(C.a[j], v.x, re);
+    im = fma(C.a[j], v.y, im);
+  }
+  out[i] = make_double2(re, im);
+}
+
+}  // namespace
+
+extern "C" int sqcg_rational_apply(sqcg_ctx* ctx, int nshift, const double* shifts, const double* residues, double a0,
+                                   const void* b, void* out, double tol, int max_iter, int mode, sqcg_info* info) {
+  if (!ctx || nshift < 1 || nshift > SQCG_MAX_SHIFTS || !shifts || !residues || !isfinite(a0) || !out || out == b ||
+      !(tol > 0))
+    return SQCG_ERR_INVALID_ARG;
+  SQCG_TRY(validate_vec(b, SQCG_F64));
+  SQCG_TRY(validate_vec(out, SQCG_F64));
+  for (int j = 0; j < nshift; ++j)
+    if (!isfinite(residues[j])) return SQCG_ERR_INVALID_ARG;
+  if (!ctx->have_links) return SQCG_ERR_NO_LINKS;
+  // per-shift solutions in library-owned FP64 buffers
+  const size_t bytes = (size_t)ctx->g.Vh * 3 * sizeof(double2);
+  if (ctx->rat_n < nshift) {
+    SQCG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < ctx->rat_n; ++j) cudaFree(ctx->rat_x[j]);
+    ctx->rat_n = 0;
+    free_graphs(ctx);
+    for (int j = 0; j < nshift; ++j) {
+      if (cudaMalloc(&ctx->rat_x[j], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        for (int k = 0; k < j; ++k) cudaFree(ctx->rat_x[k]);
+        return SQCG_ERR_NO_MEMORY;
+      }
+    }
+    ctx->rat_n = nshift;
+  }
+  double tols[SQCG_MAX_SHIFTS];
+  for (int j = 0; j < nshift; ++j) tols[j] = tol;
+  const int rc = sqcg_multishift_cg_solve(ctx, nshift, shifts, b, ctx->rat_x, tols, max_iter, mode, info);
+  if (rc == SQCG_ERR_CUDA || rc == SQCG_ERR_INVALID_ARG || rc == SQCG_ERR_NO_MEMORY) return rc;
+  Coeffs C;
+  for (int j = 0; j < nshift; ++j) {
+    C.x[j] = (const double2*)ctx->rat_x[j];
+    C.a[j] = residues[j];
+  }
+  const int n = ctx->g.Vh * 3;
+  k_rational_combine<<<grid_for(n, 256), 256, 0, ctx->stream>>>(C, nshift, a0, (const double2*)b, (double2*)out, n);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  SQCG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return rc;
+}

@@ -180,6 +180,8 @@ struct sqcg_ctx {
 
   // multi-shift workspace
   void* ms_p[SQCG_MAX_SHIFTS];  // per-shift search directions (working precision)
+  void* rat_x[SQCG_MAX_SHIFTS];  // per-shift solutions of sqcg_rational_apply (FP64)
+  int rat_n;
   int ms_nalloc;
   int ms_prec;
 

@@ -36,6 +36,7 @@ __all__ = [
     "random_gauge",
     "gauge_transform_links",
     "gauge_transform_parity_field",
+    "inverse_sqrt_rational",
 ]
 
 # Gell-Mann matrices: a basis of the traceless Hermitian 3x3 matrices.
@@ -172,3 +173,19 @@ def gauge_transform_parity_field(L, psi: np.ndarray, G: np.ndarray, parity: int)
     """psi(n) -> G(n) psi(n) for a [Vh][3] field on one parity."""
     Gp = G[parity_sites(L, parity)]
     return np.einsum("nij,nj->ni", Gp, psi)
+
+
+def inverse_sqrt_rational(npoles: int, lo: float, hi: float):
+    """Poles and residues of a rational approximation r(x) = a0 + sum_k a_k / (x + beta_k) of x^(-1/2)
+    for x in [lo, hi] (an RHMC-style input: apply it to M^+M with shifts 4 m^2 + beta_k).
+
+    From x^(-1/2) = (2/pi) int_0^(pi/2) d(theta) / (sin^2 theta + x cos^2 theta) with c = sqrt(lo hi),
+    x -> x / c and Gauss-Legendre nodes theta_k, weights w_k on [0, pi/2]:
+    a_k = sqrt(c) (2/pi) w_k / cos^2 theta_k, beta_k = c tan^2 theta_k, a0 = 0. Returns (a0, a, beta)."""
+    c = np.sqrt(lo * hi)
+    u, w = np.polynomial.legendre.leggauss(npoles)
+    theta = (u + 1.0) * np.pi / 4.0
+    wt = w * np.pi / 4.0
+    a = np.sqrt(c) * (2.0 / np.pi) * wt / np.cos(theta) ** 2
+    beta = c * np.tan(theta) ** 2
+    return 0.0, a, beta

@@ -244,3 +244,42 @@ def test_reliable_update_settings(sqcg, links_cache, delta, interval):
     assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
     if interval == 5:
         assert info.reliable_updates >= info.iters // 5
+
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rational_apply_matches_oracle(sqcg, links_cache, mode):
+    """RHMC use of the multi-mass CG: a0 b + sum_s a_s (sigma_s - D_eo D_oe)^-1 b with 9 poles."""
+    L, m, tol = (8, 8, 8, 8), 0.1, 1e-9
+    fat, lng = links_cache(L, 1001)
+    a0, a, beta = synth.inverse_sqrt_rational(9, 4 * m * m, 64.0)
+    shifts = 4 * m * m + beta
+    b = synth.gaussian_source(L, 2500)
+    want = oracle.rational_apply(L, fat, lng, shifts, a, 0.25, b, tol=1e-13)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        out = lat.new_spinor()
+        infos = lat.rational_apply(shifts, a, 0.25, lat.pack(b), out, tol=tol, mode=mode)
+        got = lat.unpack(out)
+    assert all(i.status == 0 and i.true_rel_resid <= tol for i in infos)
+    # kappa(A_s) <= ~57 / 4m^2 here, so each x_s is within ~1.5e3 tol of the exact one
+    assert rel(got, want) <= 2e3 * tol
+
+
+def test_rational_apply_free_field_on_gpu(sqcg):
+    L = (16, 16, 16, 16)
+    c1, c3 = 0.9, -1.0 / 24.0
+    fat, lng = synth.unit_links(L, c1, c3)
+    m = 0.02
+    a0, a, beta = synth.inverse_sqrt_rational(9, 4 * m * m, 64.0)
+    shifts = 4 * m * m + beta
+    k = (3, 1, 2, 5)
+    b = synth.plane_wave(L, k, 0, (1.0, 0.5j, -0.25))
+    p = np.array([2 * np.pi * k[mu] / L[mu] for mu in range(3)] + [(2 * k[3] + 1) * np.pi / L[3]])
+    lam = 4.0 * np.sum((c1 * np.sin(p) + c3 * np.sin(3 * p)) ** 2)
+    want = (np.sum(a / (shifts + lam))) * b
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        out = lat.new_spinor()
+        lat.rational_apply(shifts, a, 0.0, lat.pack(b), out, tol=1e-10, mode=0)
+        assert rel(lat.unpack(out), want) <= 1e-8

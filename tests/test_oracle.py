@@ -203,3 +203,28 @@ def test_parity_layout_roundtrip():
     assert np.array_equal(oracle.to_parity(L, oracle.to_full(L, f, 1), 1), f)
     # the oracle's parity order agrees with the generators' (lex order within a parity)
     assert np.array_equal(np.nonzero(oracle.parity_of_sites(L) == 1)[0], synth.parity_sites(L, 1))
+
+
+def test_rational_apply_free_field_closed_form():
+    """out = (a0 + sum_s a_s / (sigma_s + lambda(p))) b for a plane wave b (unit links)."""
+    L = (8, 8, 8, 8)
+    c1, c3 = 0.9, -1.0 / 24.0
+    fat, lng = synth.unit_links(L, c1, c3)
+    a0, a, beta = synth.inverse_sqrt_rational(9, 0.01, 64.0)
+    m = 0.05
+    shifts = 4 * m * m + beta
+    k = (1, 2, 0, 3)
+    b = synth.plane_wave(L, k, 0, (1.0, -0.5j, 0.25))
+    got = oracle.rational_apply(L, fat, lng, shifts, a, 0.3, b, tol=1e-13, max_iter=5000)
+    lam = free_lambda(L, k, c1, c3, True)
+    want = (0.3 + np.sum(a / (shifts + lam))) * b
+    assert rel(got, want) < 1e-11
+
+
+def test_inverse_sqrt_rational_approximates_the_function():
+    """The quadrature rational function approximates x^(-1/2) on the interval it was built for."""
+    a0, a, beta = synth.inverse_sqrt_rational(9, 0.01, 64.0)
+    x = np.logspace(-2, np.log10(64.0), 50)
+    r = a0 + np.sum(a[None, :] / (x[:, None] + beta[None, :]), axis=1)
+    assert np.max(np.abs(r * np.sqrt(x) - 1.0)) < 2e-2
+    assert np.all(a > 0) and np.all(beta > 0)
