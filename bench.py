@@ -21,6 +21,7 @@ the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -56,7 +57,7 @@ NCU_TRAFFIC = {"sources_sha256": "b327f0b141b85bfff29ea9420e2938b9768f8ebd6edcb4
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
@@ -121,21 +122,37 @@ def whole_job_rate(flops_per_rank: float, seconds_per_rank: float, ranks: Ranks)
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms, started before the warm-up (so that the tool is
+    running when the timed region begins) and filtered to the timed region by their
+    timestamps (host clock of the same machine)."""
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, uuid: str | None):
         self.uuid = (uuid or "").replace("GPU-", "")
         self.proc = None
-        self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_stop(self):
+        self.t1 = datetime.datetime.now()
+
+    @staticmethod
+    def _when(ts: str):
+        try:
+            return datetime.datetime.strptime(ts, "%Y/%m/%d %H:%M:%S.%f")
+        except ValueError:
+            return None
 
     def stop(self):
         if not self.proc:
@@ -146,8 +163,12 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        rows = [[c.strip() for c in ln.split(",")] for ln in out.strip().splitlines() if ln.count(",") >= 8]
-        mine = [r for r in rows if self.uuid and self.uuid in r[0]] or rows
+        rows = [[c.strip() for c in ln.split(",")] for ln in out.strip().splitlines() if ln.count(",") >= 9]
+        mine = [r for r in rows if self.uuid and self.uuid in r[1]] or rows
+        if self.t0 and self.t1:
+            inside = [r for r in mine if (w := self._when(r[0])) is not None and self.t0 <= w <= self.t1]
+            mine = inside or mine
+        mine = [r[1:] for r in mine]
         if not mine:
             return None
         sm = [float(r[1]) for r in mine if r[1].replace(".", "").isdigit()]
@@ -315,25 +336,27 @@ def run_ours(args, ranks: Ranks):
         x.zero_()
         return lat.cg_solve(MASS, b, x, tol=TOL, max_iter=20000, mode=mode)
 
-    for _ in range(max(args.warmup, 0)):
-        solve(sq.MODE_MIXED)
-    torch.cuda.synchronize()
-
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(ranks.local).uuid)
     except Exception:
         pass
     clocks = ClockSampler(uuid)
+    clocks.start()
+    for _ in range(max(args.warmup, 0)):
+        solve(sq.MODE_MIXED)
+    torch.cuda.synchronize()
+
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ranks.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_start()
     e0.record(s)
     infos = [solve(sq.MODE_MIXED) for _ in range(args.steps)]
     e1.record(s)
     torch.cuda.synchronize()
+    clocks.mark_stop()
     ranks.barrier()
     clk = clocks.stop()
     t_step = e0.elapsed_time(e1) / 1e3 / args.steps

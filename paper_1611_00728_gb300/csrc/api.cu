@@ -53,6 +53,9 @@ void free_workspace(sqcg_ctx* ctx) {
   ctx->ms_nalloc = 0;
   for (int j = 0; j < ctx->rat_n; ++j) cudaFree(ctx->rat_x[j]);
   for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) ctx->rat_x[j] = nullptr;
+  cudaFree(ctx->ms_stack);
+  ctx->ms_stack = nullptr;
+  ctx->ms_stack_n = 0;
   ctx->rat_n = 0;
 }
 

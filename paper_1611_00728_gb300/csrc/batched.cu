@@ -57,6 +57,7 @@ struct LatDev {
   double2* x;
   double2* tmp64;
   const double2* b;
+  size_t b_stride;  // elements between the sources of consecutive RHS: 3 Vh, or 0 when all share one source
 };
 
 template <typename R> struct V2;
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
       }
     } else {  // M_TRUE_RESID (FP64): r = b - sigma x + D tmp64, |r|^2; r (FP32) and optionally p
       const double2* xb = L.x + (size_t)w0 * 3 * Vh;
-      const double2* bb = L.b + (size_t)w0 * 3 * Vh;
+      const double2* bb = L.b + (size_t)w0 * L.b_stride;
       float2* rb32 = L.r + (size_t)w0 * 3 * Vh;
       float2* pb32 = L.p + (size_t)w0 * 3 * Vh;
 #pragma unroll
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const size_t o = ((size_t)w * 3 + c) * Vh + i;
-            const double2 xc = __ldg(xb + o), bc = __ldg(bb + o);
+            const double2 xc = __ldg(xb + o), bc = __ldg(bb + (size_t)w * L.b_stride + (size_t)c * Vh + i);
             const double re = bc.x - sig * xc.x + (double)acc[w][c].x;
             const double im = bc.y - sig * xc.y + (double)acc[w][c].y;
             const float2 f = make_float2((float)re, (float)im);
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
         double n2 = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double2 v = L.b[base + (size_t)c * Vh + i];
+          const double2 v = L.b[(size_t)(wbase + w) * L.b_stride + (size_t)c * Vh + i];
           n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
         }
         part[w] = n2;
@@ -713,6 +714,7 @@ struct BatchPlan {
   int nrhs[SQCG_MAX_LATTICES];
   const void* b[SQCG_MAX_LATTICES];
   void* x[SQCG_MAX_LATTICES];
+  int b_shared;          // every RHS of a lattice reads the same source b[k]
   int W, T;              // tuned RHS block width and site block (threads along x)
   int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
   int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
@@ -953,11 +955,12 @@ void destroy_plan(BatchPlan* P) {
   free(P);
 }
 
-int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b, void* const* x,
+int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b, int b_shared, void* const* x,
                BatchPlan** out, cudaStream_t s) {
   BatchPlan* P = (BatchPlan*)calloc(1, sizeof(BatchPlan));
   if (!P) return SQCG_ERR_NO_MEMORY;
   P->nlat = nctx;
+  P->b_shared = b_shared;
   int total = 0, max_vh = 0;
   for (int k = 0; k < nctx; ++k) {
     sqcg_ctx* c = ctx[k];
@@ -983,6 +986,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     L.rhs0 = total;
     L.nrhs = nrhs[k];
     L.b = (const double2*)b[k];
+    L.b_stride = b_shared ? 0 : 3 * Vh;
     L.x = (double2*)x[k];
     const size_t n = (size_t)nrhs[k] * 3 * Vh;
     if (cudaMalloc(&P->work[k], n * (4 * sizeof(float2) + sizeof(double2))) != cudaSuccess) {
@@ -1092,8 +1096,8 @@ int capture_plan(BatchPlan& P) {
 }
 
 bool plan_matches(const BatchPlan* P, int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b,
-                  void* const* x) {
-  if (!P || P->nlat != nctx) return false;
+                  int b_shared, void* const* x) {
+  if (!P || P->nlat != nctx || P->b_shared != b_shared) return false;
   for (int k = 0; k < nctx; ++k)
     if (P->ctx[k] != ctx[k] || P->gen[k] != sqcg_links_generation(ctx[k]) || P->nrhs[k] != nrhs[k] ||
         P->b[k] != b[k] || P->x[k] != x[k])
@@ -1108,28 +1112,31 @@ void free_batch_plan(sqcg_ctx* ctx) {
   ctx->batch = nullptr;
 }
 
-extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
-                                     const void* const* b, void* const* x, double tol, int max_iter,
-                                     sqcg_info* info) {
+// The batched loop over explicit per-RHS shifts and tolerances (RHS in lattice
+// order). b_shared: every RHS of a lattice solves for the same source b[k].
+int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* sigma, const double* tol,
+                  const void* const* b, int b_shared, void* const* x, int max_iter, sqcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (nctx < 1 || nctx > SQCG_MAX_LATTICES || !ctx || !nrhs || !mass || !b || !x || !(tol > 0) || max_iter <= 0)
+  if (nctx < 1 || nctx > SQCG_MAX_LATTICES || !ctx || !nrhs || !sigma || !tol || !b || !x || max_iter <= 0)
     return SQCG_ERR_INVALID_ARG;
   int total = 0;
   for (int k = 0; k < nctx; ++k) {
-    if (!ctx[k] || nrhs[k] < 1 || !isfinite(mass[k]) || !b[k] || !x[k] || b[k] == x[k]) return SQCG_ERR_INVALID_ARG;
+    if (!ctx[k] || nrhs[k] < 1 || !b[k] || !x[k] || b[k] == x[k]) return SQCG_ERR_INVALID_ARG;
     if (((uintptr_t)b[k] | (uintptr_t)x[k]) & 15) return SQCG_ERR_INVALID_ARG;
     if (!ctx[k]->have_links) return SQCG_ERR_NO_LINKS;
     for (int j = 0; j < k; ++j)
       if (ctx[j] == ctx[k] || x[j] == x[k]) return SQCG_ERR_INVALID_ARG;
     total += nrhs[k];
+    if (total > SQCG_MAX_BATCH_RHS) return SQCG_ERR_INVALID_ARG;
   }
-  if (total > SQCG_MAX_BATCH_RHS) return SQCG_ERR_INVALID_ARG;
+  for (int j = 0; j < total; ++j)
+    if (!isfinite(sigma[j]) || sigma[j] < 0 || !(tol[j] > 0)) return SQCG_ERR_INVALID_ARG;
   sqcg_ctx* c0 = ctx[0];
   cudaStream_t s = c0->stream;
-  if (!plan_matches(c0->batch, nctx, ctx, nrhs, b, x)) {
+  if (!plan_matches(c0->batch, nctx, ctx, nrhs, b, b_shared, x)) {
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
     free_batch_plan(c0);
-    SQCG_TRY(build_plan(nctx, ctx, nrhs, b, x, &c0->batch, s));
+    SQCG_TRY(build_plan(nctx, ctx, nrhs, b, b_shared, x, &c0->batch, s));
   }
   BatchPlan& P = *c0->batch;
 
@@ -1143,9 +1150,10 @@ extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* 
   h->delta2 = c0->ru_delta * c0->ru_delta;
   for (int k = 0; k < nctx; ++k)
     for (int j = 0; j < nrhs[k]; ++j) {
-      RhsScalars& r = h->r[P.host[k].rhs0 + j];
-      r.sigma = 4.0 * mass[k] * mass[k];
-      r.stop_rr = tol * tol;
+      const int g = P.host[k].rhs0 + j;
+      RhsScalars& r = h->r[g];
+      r.sigma = sigma[g];
+      r.stop_rr = tol[g] * tol[g];
       r.active = 1;
       r.status = SQCG_OK;
     }
@@ -1211,6 +1219,22 @@ extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* 
     if (st != SQCG_OK && worst == SQCG_OK) worst = st;
   }
   return worst;
+}
+
+extern "C" int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
+                                     const void* const* b, void* const* x, double tol, int max_iter,
+                                     sqcg_info* info) {
+  if (nctx < 1 || nctx > SQCG_MAX_LATTICES || !ctx || !nrhs || !mass || !(tol > 0)) return SQCG_ERR_INVALID_ARG;
+  double sig[SQCG_MAX_BATCH_RHS], tols[SQCG_MAX_BATCH_RHS];
+  int total = 0;
+  for (int k = 0; k < nctx; ++k) {
+    if (nrhs[k] < 1 || !isfinite(mass[k]) || total + nrhs[k] > SQCG_MAX_BATCH_RHS) return SQCG_ERR_INVALID_ARG;
+    for (int j = 0; j < nrhs[k]; ++j, ++total) {
+      sig[total] = 4.0 * mass[k] * mass[k];
+      tols[total] = tol;
+    }
+  }
+  return batched_solve(nctx, ctx, nrhs, sig, tols, b, 0, x, max_iter, info);
 }
 
 extern "C" int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T) {

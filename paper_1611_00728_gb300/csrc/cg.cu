@@ -281,20 +281,6 @@ int run_eager(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x,
   return SQCG_OK;
 }
 
-// |b - (sigma - D_eo D_oe) x|^2 in FP64 (r64 as scratch); result in *rr
-int true_residual2(sqcg_ctx* ctx, double sigma, const void* b, const void* x, double* rr, cudaStream_t s) {
-  DslashLaunch L = {};
-  L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
-  SQCG_TRY(launch_dslash(ctx, L, s));
-  L = DslashLaunch{};
-  L.out_parity = 0; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_TRUE_RESID; L.in = ctx->tmp64; L.out = ctx->r64;
-  L.y = x; L.b = b; L.sigma = sigma; L.fin = FIN_STORE;
-  SQCG_TRY(launch_dslash(ctx, L, s));
-  SQCG_TRY(read_state(ctx, s));
-  *rr = ctx->st_host->pAp;
-  return SQCG_OK;
-}
-
 int validate_vec(const void* p, int prec) {
   if (!p) return SQCG_ERR_INVALID_ARG;
   const uintptr_t a = (uintptr_t)p;
@@ -483,34 +469,68 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];
   for (int j = 0; j < nshift; ++j) iters_s[j] = h->iters_s[j];
-  const double bb = h->bb;
 
-  // per-shift FP64 true residual, refinement where needed
+  // Per-shift FP64 true residual and refinement. Each refinement CG starts by
+  // computing r = b - (sigma_s - D_eo D_oe) x_s in FP64 and stops there when
+  // x_s already meets its tolerance. Mixed mode refines all shifts together as
+  // one batched mixed-precision CG (one RHS per shift, per-RHS sigma, shared
+  // source), so the links are read once per block of shifts.
+  int left = 1;
+  for (int j = 0; j < nshift; ++j)
+    if (max_iter - iters_s[j] > left) left = max_iter - iters_s[j];
   int worst = SQCG_OK;
+  sqcg_info ri[SQCG_MAX_SHIFTS] = {};
+  if (loop_status == SQCG_ERR_BREAKDOWN) {  // no refinement from a broken-down Krylov space
+    for (int j = 0; j < nshift; ++j) {
+      ri[j].status = SQCG_ERR_BREAKDOWN;
+      ri[j].true_rel_resid = NAN;
+    }
+  } else if (mixed) {
+    if (ctx->ms_stack_n < nshift) {
+      SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+      cudaFree(ctx->ms_stack);
+      ctx->ms_stack = nullptr;
+      ctx->ms_stack_n = 0;
+      if (cudaMalloc(&ctx->ms_stack, (size_t)nshift * n * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return SQCG_ERR_NO_MEMORY;
+      }
+      ctx->ms_stack_n = nshift;
+    }
+    double sig[SQCG_MAX_SHIFTS], tl[SQCG_MAX_SHIFTS];
+    for (int j = 0; j < nshift; ++j) {
+      sig[j] = shifts[perm[j]];
+      tl[j] = tol[perm[j]];
+      SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->ms_stack + (size_t)j * n, xs[j], n * sizeof(double2),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    sqcg_ctx* cl[1] = {ctx};
+    const int nr[1] = {nshift};
+    const void* bl[1] = {b};
+    void* xl[1] = {ctx->ms_stack};
+    const int st = batched_solve(1, cl, nr, sig, tl, bl, 1, xl, left, ri);
+    if (st == SQCG_ERR_CUDA || st == SQCG_ERR_INVALID_ARG || st == SQCG_ERR_NO_MEMORY) return st;
+    for (int j = 0; j < nshift; ++j)
+      SQCG_CUDA_TRY(cudaMemcpyAsync(xs[j], ctx->ms_stack + (size_t)j * n, n * sizeof(double2),
+                                    cudaMemcpyDeviceToDevice, s));
+    SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+    launches += ri[0].launches + 2 * nshift;
+  } else {
+    for (int j = 0; j < nshift; ++j) {
+      const int st = cg_solve_sigma(ctx, shifts[perm[j]], b, xs[j], tol[perm[j]], left, mode, &ri[j]);
+      if (st == SQCG_ERR_CUDA || st == SQCG_ERR_INVALID_ARG || st == SQCG_ERR_NO_MEMORY) return st;
+      ri[j].status = st;
+      launches += ri[j].launches;
+    }
+  }
   for (int j = 0; j < nshift; ++j) {
     const int u = perm[j];
-    const double sig = shifts[u];
-    double rr = 0.0;
-    int st = (loop_status == SQCG_ERR_BREAKDOWN) ? SQCG_ERR_BREAKDOWN : SQCG_OK;
-    SQCG_TRY(true_residual2(ctx, sig, b, xs[j], &rr, s));
-    launches += 3;
-    double rel = sqrt(rr / bb);
-    int extra = 0, updates = 0;
-    if (st == SQCG_OK && !(rel <= tol[u])) {
-      sqcg_info ri;
-      const int left = max_iter - iters_s[j] > 0 ? max_iter - iters_s[j] : 1;
-      st = cg_solve_sigma(ctx, sig, b, xs[j], tol[u], left, mode, &ri);
-      if (st == SQCG_ERR_CUDA || st == SQCG_ERR_INVALID_ARG || st == SQCG_ERR_NO_MEMORY) return st;
-      extra = ri.iters;
-      updates = ri.reliable_updates;
-      launches += ri.launches;
-      rel = ri.true_rel_resid;
-    }
+    const int st = ri[j].status;
     if (info) {
-      info[u].iters = iters_s[j] + extra;
-      info[u].reliable_updates = updates;
+      info[u].iters = iters_s[j] + ri[j].iters;
+      info[u].reliable_updates = ri[j].reliable_updates;
       info[u].status = st;
-      info[u].true_rel_resid = rel;
+      info[u].true_rel_resid = ri[j].true_rel_resid;
     }
     if (st != SQCG_OK && worst == SQCG_OK) worst = st;
   }

@@ -182,6 +182,8 @@ struct sqcg_ctx {
   void* ms_p[SQCG_MAX_SHIFTS];  // per-shift search directions (working precision)
   void* rat_x[SQCG_MAX_SHIFTS];  // per-shift solutions of sqcg_rational_apply (FP64)
   int rat_n;
+  double2* ms_stack;  // per-shift solutions stacked [nshift][3][Vh] for the batched refinement (FP64)
+  int ms_stack_n;
   int ms_nalloc;
   int ms_prec;
 
@@ -192,6 +194,10 @@ struct sqcg_ctx {
 };
 
 void free_batch_plan(sqcg_ctx* ctx);
+// batched mixed-precision CG with per-RHS shifts sigma[] and tolerances tol[] (RHS in lattice order);
+// b_shared: all RHS of lattice k solve for the one source b[k] (batched.cu)
+int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* sigma, const double* tol,
+                  const void* const* b, int b_shared, void* const* x, int max_iter, sqcg_info* info);
 
 // ---------------------------------------------------------------------------
 // launchers (defined in dslash.cu / blas.cu / layout.cu)

@@ -69,3 +69,35 @@ def test_single_rank_needs_no_process_group(monkeypatch):
     assert ranks.dist is None
     rate, tmax = bench.whole_job_rate(2e9, 0.5, ranks)
     assert rate == pytest.approx(4.0) and tmax == 0.5
+
+
+def test_clock_sampler_keeps_only_the_timed_region():
+    """Samples are filtered to [mark_start, mark_stop] by timestamp; throttle reasons are read per field."""
+    import datetime
+
+    import bench
+
+    rows = [
+        "2026/01/01 10:00:00.000, GPU-abc, 1200, 2070, 300, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/01/01 10:00:01.000, GPU-abc, 2070, 2070, 900, 0x4, Not Active, Not Active, Not Active, Active",
+        "2026/01/01 10:00:01.050, GPU-abc, 2055, 2070, 910, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/01/01 10:00:01.100, GPU-zzz, 900, 2070, 100, 0x0, Active, Not Active, Not Active, Not Active",
+        "2026/01/01 10:00:05.000, GPU-abc, 800, 2070, 200, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return "\n".join(rows) + "\n", ""
+
+    c = bench.ClockSampler("GPU-abc")
+    c.proc = FakeProc()
+    c.t0 = datetime.datetime(2026, 1, 1, 10, 0, 0, 500000)
+    c.t1 = datetime.datetime(2026, 1, 1, 10, 0, 2)
+    out = c.stop()
+    assert out["samples"] == 2
+    assert out["sm_mhz"] == (2070 + 2055) / 2
+    assert out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"]

@@ -283,3 +283,45 @@ def test_rational_apply_free_field_on_gpu(sqcg):
         out = lat.new_spinor()
         lat.rational_apply(shifts, a, 0.0, lat.pack(b), out, tol=1e-10, mode=0)
         assert rel(lat.unpack(out), want) <= 1e-8
+
+
+def test_multishift_mixed_refinement_alternates_with_batched_plans(sqcg, links_cache):
+    """Mixed multi-shift refines every shift in one batched solve (per-shift sigma and tol, one
+    shared source) held in the context's batched workspace; a user's batched solve on the same
+    context in between must not disturb either result."""
+    import torch
+
+    L = (8, 10, 12, 14)
+    fat, lng = links_cache(L, 88)
+    shifts = [0.3, 0.0004, 0.02, 0.0004 * 3]
+    tols = [1e-9, 1e-8, 1e-10, 1e-8]
+    b = synth.gaussian_source(L, 4100)
+    srcs = [synth.gaussian_source(L, 4200 + j) for j in range(3)]
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        db = lat.pack(b)
+        for rep in range(2):
+            xs = [lat.new_spinor() for _ in shifts]
+            infos = lat.multishift_cg_solve(shifts, db, xs, tol=tols, max_iter=20000, mode=1)
+            for s, t, info, x in zip(shifts, tols, infos, xs):
+                assert info.status == 0 and info.true_rel_resid <= t
+                assert oracle.true_rel_residual(L, fat, lng, s, b, lat.unpack(x)) <= t
+            bb = torch.stack([lat.pack(v) for v in srcs]).contiguous()
+            xb = torch.zeros_like(bb)
+            binf = sqcg.cg_solve_batched([lat], [0.05], [bb], [xb], tol=1e-8)[0]
+            for j, v in enumerate(srcs):
+                assert binf[j].status == 0
+                assert oracle.true_rel_residual(L, fat, lng, 0.01, v, lat.unpack(xb[j])) <= 1e-8
+
+
+def test_multishift_mixed_zero_source(sqcg, links_cache):
+    L = (8, 8, 8, 8)
+    fat, lng = links_cache(L, 1001)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        xs = [lat.new_spinor() for _ in range(3)]
+        for x in xs:
+            x.fill_(1.0)
+        infos = lat.multishift_cg_solve([0.01, 0.1, 1.0], lat.pack(np.zeros((lat.Vh, 3), complex)), xs, mode=1)
+        assert all(i.status == 0 and i.iters == 0 for i in infos)
+        assert all(not x.any() for x in xs)
