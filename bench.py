@@ -46,6 +46,7 @@ SOURCE_SEED = 2200  # 2000 + 100 * workload number + rhs
 # least bytes per output site (each link once, input once, output once): 16 links + 2 vectors
 BYTES_PER_SITE = {"f64": 16 * 144 + 2 * 48, "f32": 16 * 72 + 2 * 24, "f32_recon12": 8 * 72 + 8 * 48 + 2 * 24}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_FP64_GFLOPS = 1250.0  # GB300 FP64 rate (nominal figure of the hardware table)
 
 # DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
 # at 32^4, measured by ncu (profiles/dslash_f32_recon12_32x32x32x32.md), with the
@@ -62,7 +63,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
-    ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned"], default="single",
+    ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned", "hisq"], default="single",
                     help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
 
@@ -630,6 +631,74 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hisq(args):
+    """HISQ link construction at 32^4 (thin -> fat7 -> U(3) projection -> Lepage/Naik level), device entry
+    point timed with CUDA events; then mixed and FP64 CG on the HISQ links (m = 0.01, true residual 1e-8)."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    sq.build_if_needed()
+    V = int(np.prod(LATTICE))
+    thin = synth.thin_links(LATTICE, GAUGE_SEED)
+    d_thin = torch.from_numpy(thin.view(np.float64).reshape(-1)).cuda()
+    d_fat, d_lng = torch.empty_like(d_thin), torch.empty_like(d_thin)
+    ws = torch.empty(sq.hisq_workspace_bytes(LATTICE), dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        sq.hisq_smear(LATTICE, d_thin, d_fat, d_lng, ws)
+    times = []
+    for _ in range(args.steps):
+        _, ms = _timed(torch, lambda: sq.hisq_smear(LATTICE, d_thin, d_fat, d_lng, ws))
+        times.append(ms)
+    t = statistics.median(times) / 1e3
+    flops = V * 4 * sq.HISQ_FLOPS_PER_LINK
+    gflops = flops / t / 1e9
+    # the CG on the HISQ links (the long links are U(3): full 18-real storage)
+    lat = sq.Lattice(LATTICE)
+    lat.hisq_load_links(thin)
+    b = lat.pack(synth.gaussian_source(LATTICE, SOURCE_SEED))
+    x = lat.new_spinor()
+    cg = {}
+    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+        def solve(mode=mode):
+            x.zero_()
+            return lat.cg_solve(MASS, b, x, tol=TOL, max_iter=20000, mode=mode)
+        solve()
+        ts, info = [], None
+        for _ in range(args.steps):
+            info, ms = _timed(torch, solve)
+            ts.append(ms)
+        cg[name] = {"ms": statistics.median(ts), "iters": info.iters, "true_rel_resid": info.true_rel_resid}
+    lat.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle.hisq as oh
+
+        Ls = (8, 8, 8, 8)
+        th = synth.thin_links(Ls, GAUGE_SEED)
+        t0 = time.perf_counter()
+        oh.hisq_links(Ls, th)
+        dt = time.perf_counter() - t0
+        Vs = int(np.prod(Ls))
+        cpu = {"value": Vs * 4 * sq.HISQ_FLOPS_PER_LINK / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "seconds": dt, "sample": "oracle (numpy path sums, FP64) HISQ links of an 8^4 lattice, same counted "
+                                        "flops per link"}
+    line = {"metric": "HISQ link construction time (thin -> fat, long; FP64) and CG time on the HISQ links",
+            "unit": "ms", "value": t * 1e3, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "32^4 HISQ smearing of random SU(3) thin links (width 0.3, seed 1002); CG m=0.01 "
+                                   "to true rel. residual 1e-8 on the result", "sites": V,
+                       "l2": "inputs larger than L2 (thin links 0.6 GB, workspace 6.6 GB)"},
+            "roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, FP64 3x3 products)",
+                         "achieved": gflops, "peak": NOMINAL_FP64_GFLOPS, "unit": "GFLOP/s",
+                         "frac": gflops / NOMINAL_FP64_GFLOPS, "peak_kind": "nominal FP64 rate",
+                         "counted_flops_per_link": sq.HISQ_FLOPS_PER_LINK, "traffic": None},
+            "cpu_baseline": cpu, "cg_on_hisq_links": cg,
+            "cg_speedup_mixed_vs_fp64": cg["fp64"]["ms"] / cg["mixed"]["ms"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Learned preconditioner: train at 16^4 on CG pairs, flexible CG on held-out seeds at 16^4 and 32^4."""
     import torch
@@ -740,7 +809,8 @@ def main():
     if args.steps < 1:
         raise SystemExit("--steps must be >= 1")
     if args.workload != "single":
-        {"multishift": run_multishift, "rational": run_rational, "batched": run_batched, "learned": run_learned}[args.workload](args)
+        {"multishift": run_multishift, "rational": run_rational, "batched": run_batched, "learned": run_learned,
+         "hisq": run_hisq}[args.workload](args)
         return
     ranks = Ranks()
     try:

@@ -186,7 +186,9 @@ int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol
  * tolerance on the FP64 true relative residual. A shift stops when its
  * iterated residual |zeta_s| |r| / |b| <= tol[s]. Each x_s is then checked on
  * its FP64 true residual; where that is above tol[s] (expected with FP32
- * vectors) it is refined by CG of the same mode started from x_s.
+ * vectors) it is refined from x_s: in mixed mode all shifts together as one
+ * batched mixed-precision CG (one right-hand side per shift, held in the
+ * context's batched workspace), in FP64 mode by one CG per shift.
  * info: NULL or an array of nshift (per-shift iterations including refinement,
  * status, true residual; seconds = whole call). Returns SQCG_OK when every
  * shift converged, else the first failing status. Synchronises the stream. */
@@ -285,6 +287,52 @@ int sqcg_make_training_pair(sqcg_ctx* ctx, double sigma, const void* b, const vo
  * FP64 true residual. nn must be bound to ctx. Synchronises. */
 int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const void* b, void* x, double tol, int max_iter,
                       sqcg_info* info);
+
+/* ---- HISQ link construction (the action of the paper's benchmark application, Sec. 4:
+ * su3_rhmc_hisq; construction of Follana et al., hep-lat/0610092). Thin links U
+ * -> V = smear(U, level1) -> W = V (V^+ V)^(-1/2) (U(3) projection) ->
+ * fat = smear(W, level2), long = naik W_mu(n) W_mu(n+mu) W_mu(n+2mu).
+ * smear(X)_mu(n) = one_link X_mu(n) + three_staple (sum of the 6 3-link staples)
+ *   + five_staple (24 5-link) + seven_staple (48 7-link) + lepage (6 5-link
+ *   staples that step twice in the same direction and sign), every staple
+ *   running from n to n+mu through the other directions.
+ * Coefficients are for unphased links (periodic in every direction); the
+ * staggered phases and the time-boundary sign are applied when the result is
+ * loaded. Everything in FP64. */
+typedef struct {
+  double one_link, three_staple, five_staple, seven_staple, lepage;
+} sqcg_smear_level;
+typedef struct {
+  sqcg_smear_level level1, level2;
+  double naik;
+} sqcg_hisq_coeffs;
+/* NULL coefficients mean the HISQ values: level1 = fat7 (1/8, 1/16, 1/64,
+ * 1/384, 0), level2 = (1, 1/16, 1/64, 1/384, -1/8), naik = -1/24. The level-2
+ * one-link value follows from tree-level improvement of the free dispersion
+ * (fat + 3 naik = 1 and fat + 27 naik = 0 for unit thin links). */
+
+/* Device workspace sqcg_hisq_smear needs for this lattice (0 for bad dims). */
+size_t sqcg_hisq_workspace_bytes(const int dims[4]);
+
+/* Thin -> fat, long on the device. thin, fat, lng: device arrays in the host
+ * link order [V][4][3][3] complex double (lex sites, directions x, y, z, t);
+ * fat may alias thin (thin is consumed first), lng must not alias either.
+ * workspace: device memory of at least sqcg_hisq_workspace_bytes (caller
+ * owned, 16-byte aligned). Work goes on `stream` (a cudaStream_t, NULL =
+ * default); the call synchronises it. Returns SQCG_ERR_BREAKDOWN when a
+ * level-1 link is singular or non-finite (the U(3) projection is undefined);
+ * the outputs are then not meaningful. */
+int sqcg_hisq_smear(const int dims[4], const void* thin, void* fat, void* lng, const sqcg_hisq_coeffs* coeffs,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* HISQ links from host thin links, installed as the context's links as by
+ * sqcg_load_links (opts: SQCG_EIGHT_WAY; SQCG_RECON12_LONG is checked as
+ * usual and fails for HISQ long links, which are U(3), not SU(3) up to a real
+ * scale). The context must not have SQCG_PHASES_FOLDED. fat_out, lng_out:
+ * NULL or host arrays [V][4][3][3] complex double that receive the unphased
+ * links. Allocates and frees its own device memory; synchronises the stream. */
+int sqcg_hisq_load_links(sqcg_ctx* ctx, const double* thin, const sqcg_hisq_coeffs* coeffs, int opts,
+                         double* fat_out, double* lng_out);
 
 /* RHS block width W and site-block size T chosen by the autotuner for the
  * batched solve cached with ctx (the ctx passed first to the last batched call). */

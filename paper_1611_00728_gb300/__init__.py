@@ -21,7 +21,8 @@ import numpy as np
 __all__ = [
     "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
-    "batched_tuning", "Network", "NN_NPARAMS",
+    "batched_tuning", "Network", "NN_NPARAMS", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
+    "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK",
 ]
 
 F64, F32 = 0, 1
@@ -54,6 +55,29 @@ class SqcgError(RuntimeError):
         self.name = ERR_NAMES.get(code, str(code))
         msg = library().sqcg_strerror(code).decode()
         super().__init__(f"{what}: {self.name} ({msg})")
+
+
+#: counted flops of one HISQ link (3x3 complex products only, 198 flops each): 48 products per
+#: smearing level (12 in the 3-staples, 24 in the 5/7-staple fields, 12 in the final wraps), two
+#: levels, plus 2 for the Naik link; the U(3) projection and the additions are not counted
+HISQ_FLOPS_PER_LINK = (2 * 48 + 2) * 198
+
+
+class SmearLevel(ctypes.Structure):
+    _fields_ = [("one_link", ctypes.c_double), ("three_staple", ctypes.c_double), ("five_staple", ctypes.c_double),
+                ("seven_staple", ctypes.c_double), ("lepage", ctypes.c_double)]
+
+
+class HisqCoeffs(ctypes.Structure):
+    _fields_ = [("level1", SmearLevel), ("level2", SmearLevel), ("naik", ctypes.c_double)]
+
+
+def hisq_coeffs(level1: dict, level2: dict, naik: float) -> HisqCoeffs:
+    """Coefficient struct from dicts with keys one_link, three_staple, five_staple, seven_staple, lepage."""
+    def lv(d):
+        return SmearLevel(*[float(d.get(k, 0.0)) for k, _ in SmearLevel._fields_])
+
+    return HisqCoeffs(lv(level1), lv(level2), float(naik))
 
 
 class Info(ctypes.Structure):
@@ -110,6 +134,10 @@ def library():
                                       ctypes.POINTER(D)]
         lib.sqcg_make_training_pair.argtypes = [P, D, P, P, P, P, P]
         lib.sqcg_fcg_solve_nn.argtypes = [P, P, D, P, P, D, I, ctypes.POINTER(Info)]
+        lib.sqcg_hisq_workspace_bytes.argtypes = [P]
+        lib.sqcg_hisq_workspace_bytes.restype = ctypes.c_size_t
+        lib.sqcg_hisq_smear.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
+        lib.sqcg_hisq_load_links.argtypes = [P, P, P, I, P, P]
         lib.sqcg_strerror.argtypes = [I]
         lib.sqcg_strerror.restype = ctypes.c_char_p
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_set_reliable_update", "sqcg_spinor_bytes",
@@ -118,7 +146,8 @@ def library():
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
                      "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
-                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply"):
+                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply",
+                     "sqcg_hisq_smear", "sqcg_hisq_load_links"):
             getattr(lib, name).restype = I
         _lib = lib
     return _lib
@@ -194,6 +223,23 @@ class Lattice:
         opts = (RECON12_LONG if recon12 else 0) | (EIGHT_WAY if eight_way else 0)
         _check(library().sqcg_load_links(self._h, fat.ctypes.data, lng.ctypes.data, opts), "sqcg_load_links")
         self.recon12 = recon12
+
+    def hisq_load_links(self, thin: np.ndarray, coeffs: HisqCoeffs | None = None, recon12: bool = False,
+                        eight_way: bool = False, return_links: bool = False):
+        """HISQ fat and long links built on the GPU from host thin links (complex128 [V][4][3][3], unphased)
+        and installed as this lattice's links. return_links: also return the (fat, long) host arrays."""
+        thin = np.ascontiguousarray(thin, dtype=np.complex128)
+        if thin.shape != (self.V, 4, 3, 3):
+            raise ValueError(f"thin links must have shape ({self.V}, 4, 3, 3)")
+        fat = np.empty_like(thin) if return_links else None
+        lng = np.empty_like(thin) if return_links else None
+        self._sync_stream()
+        opts = (RECON12_LONG if recon12 else 0) | (EIGHT_WAY if eight_way else 0)
+        _check(library().sqcg_hisq_load_links(self._h, thin.ctypes.data, ctypes.byref(coeffs) if coeffs else None,
+                                              opts, fat.ctypes.data if return_links else None,
+                                              lng.ctypes.data if return_links else None), "sqcg_hisq_load_links")
+        self.recon12 = recon12
+        return (fat, lng) if return_links else None
 
     def new_spinor(self, prec: int = F64, count: int | None = None):
         """Zeroed device colour vector(s) in the library layout: (3, Vh, 2)."""
@@ -440,3 +486,25 @@ class Network:
         if raise_on_error:
             _check(rc, "sqcg_fcg_solve_nn")
         return info
+
+
+def hisq_workspace_bytes(dims) -> int:
+    return int(library().sqcg_hisq_workspace_bytes((ctypes.c_int * 4)(*[int(v) for v in dims])))
+
+
+def hisq_smear(dims, thin, fat, lng, workspace, coeffs: HisqCoeffs | None = None):
+    """Device HISQ smearing: thin, fat, lng are contiguous CUDA float64 tensors of V*4*9*2 values in the host
+    link order [V][4][3][3][re, im]; workspace a CUDA tensor of at least hisq_workspace_bytes(dims) bytes.
+    Runs on the current stream and synchronises it."""
+    torch = _torch()
+    V = int(np.prod(dims))
+    for t in (thin, fat, lng):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != V * 72:
+            raise ValueError("links must be contiguous CUDA float64 tensors of V*4*9*2 values")
+    if not workspace.is_cuda or not workspace.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(library().sqcg_hisq_smear((ctypes.c_int * 4)(*[int(v) for v in dims]), thin.data_ptr(), fat.data_ptr(),
+                                     lng.data_ptr(), ctypes.byref(coeffs) if coeffs else None, workspace.data_ptr(),
+                                     nbytes, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "sqcg_hisq_smear")

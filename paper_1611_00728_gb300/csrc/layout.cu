@@ -193,13 +193,24 @@ int ensure_stage(sqcg_ctx* ctx, size_t bytes) {
 
 }  // namespace
 
-int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts) {
+namespace {
+
+// fat, lng: host order [V][4][3][3] complex, in host memory or (on_device) in device memory
+int load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts, bool on_device) {
   if (!fat || !lng) return SQCG_ERR_INVALID_ARG;
   if (opts & ~(SQCG_RECON12_LONG | SQCG_EIGHT_WAY)) return SQCG_ERR_INVALID_ARG;
   const bool recon = (opts & SQCG_RECON12_LONG) != 0;
   const bool eightway = (opts & SQCG_EIGHT_WAY) != 0;
   double s0 = 1.0;
-  if (recon && !recon_check(ctx, lng, &s0)) return SQCG_ERR_RECON_REJECTED;
+  if (recon) {
+    if (on_device) {  // the eligibility test runs on the host
+      std::vector<double> h((size_t)2 * ctx->g.Vh * 4 * 18);
+      SQCG_CUDA_TRY(cudaMemcpy(h.data(), lng, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      if (!recon_check(ctx, h.data(), &s0)) return SQCG_ERR_RECON_REJECTED;
+    } else if (!recon_check(ctx, lng, &s0)) {
+      return SQCG_ERR_RECON_REJECTED;
+    }
+  }
 
   const size_t Vh = ctx->g.Vh, V = 2 * Vh;
   // the 12-real form is used for the FP32 copy only: on this GPU the FP64 Dslash is
@@ -225,7 +236,7 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
             cudaMalloc((void**)&ctx->lng64, nlng64 * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->fat32, nfat * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->lng32, nlng32 * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc(&raw, V * 4 * 9 * sizeof(double2)) == cudaSuccess;
+            (on_device || cudaMalloc(&raw, V * 4 * 9 * sizeof(double2)) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     cudaFree(raw);
@@ -239,11 +250,20 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   const int grid = (int)((nthreads + kThreads - 1) / kThreads);
   int rc = SQCG_OK;
   do {
-    if (cudaMemcpyAsync(raw, fat, V * 4 * 9 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-    k_pack_links<<<grid, kThreads, 0, s>>>((const double2*)raw, ctx->g, fold, 1, 9, ctx->fat64, ctx->fat32);
+    const double2* src = (const double2*)fat;
+    if (!on_device) {
+      if (cudaMemcpyAsync(raw, fat, V * 4 * 9 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+      src = (const double2*)raw;
+    }
+    k_pack_links<<<grid, kThreads, 0, s>>>(src, ctx->g, fold, 1, 9, ctx->fat64, ctx->fat32);
     if (cudaGetLastError() != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-    if (cudaMemcpyAsync(raw, lng, V * 4 * 9 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-    k_pack_links<<<grid, kThreads, 0, s>>>((const double2*)raw, ctx->g, fold, 3, nl32, ctx->lng64, ctx->lng32);
+    src = (const double2*)lng;
+    if (!on_device) {
+      // the fat pass must finish reading the staging buffer before it is overwritten (same stream)
+      if (cudaMemcpyAsync(raw, lng, V * 4 * 9 * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+      src = (const double2*)raw;
+    }
+    k_pack_links<<<grid, kThreads, 0, s>>>(src, ctx->g, fold, 3, nl32, ctx->lng64, ctx->lng32);
     if (cudaGetLastError() != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
   } while (0);
@@ -271,6 +291,16 @@ int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int o
   static unsigned long long generation = 0;
   ctx->links_gen = __atomic_add_fetch(&generation, 1ULL, __ATOMIC_RELAXED);
   return SQCG_OK;
+}
+
+}  // namespace
+
+int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts) {
+  return load_links(ctx, fat, lng, opts, false);
+}
+
+int layout_load_links_device(sqcg_ctx* ctx, const double* fat, const double* lng, int opts) {
+  return load_links(ctx, fat, lng, opts, true);
 }
 
 int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev) {

@@ -239,6 +239,8 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 
 int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
+// the same from links already in device memory (host order [V][4][3][3] complex)
+int layout_load_links_device(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
 int layout_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host);
 int layout_convert(sqcg_ctx* ctx, int from_prec, const void* src, int to_prec, void* dst, cudaStream_t s);
