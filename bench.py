@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
+    ap.add_argument("--lattice", default=None,
+                    help="hisq workload only: extents as Lx,Ly,Lz,Lt (default 32,32,32,32; smaller for profiling)")
     ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned", "hisq"], default="single",
                     help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
@@ -640,24 +642,25 @@ def run_hisq(args):
     import synth
 
     sq.build_if_needed()
-    V = int(np.prod(LATTICE))
-    thin = synth.thin_links(LATTICE, GAUGE_SEED)
+    lattice = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else LATTICE
+    V = int(np.prod(lattice))
+    thin = synth.thin_links(lattice, GAUGE_SEED)
     d_thin = torch.from_numpy(thin.view(np.float64).reshape(-1)).cuda()
     d_fat, d_lng = torch.empty_like(d_thin), torch.empty_like(d_thin)
-    ws = torch.empty(sq.hisq_workspace_bytes(LATTICE), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sq.hisq_workspace_bytes(lattice), dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 1)):
-        sq.hisq_smear(LATTICE, d_thin, d_fat, d_lng, ws)
+        sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws)
     times = []
     for _ in range(args.steps):
-        _, ms = _timed(torch, lambda: sq.hisq_smear(LATTICE, d_thin, d_fat, d_lng, ws))
+        _, ms = _timed(torch, lambda: sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws))
         times.append(ms)
     t = statistics.median(times) / 1e3
     flops = V * 4 * sq.HISQ_FLOPS_PER_LINK
     gflops = flops / t / 1e9
     # the CG on the HISQ links (the long links are U(3): full 18-real storage)
-    lat = sq.Lattice(LATTICE)
+    lat = sq.Lattice(lattice)
     lat.hisq_load_links(thin)
-    b = lat.pack(synth.gaussian_source(LATTICE, SOURCE_SEED))
+    b = lat.pack(synth.gaussian_source(lattice, SOURCE_SEED))
     x = lat.new_spinor()
     cg = {}
     for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
@@ -687,9 +690,9 @@ def run_hisq(args):
     line = {"metric": "HISQ link construction time (thin -> fat, long; FP64) and CG time on the HISQ links",
             "unit": "ms", "value": t * 1e3, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
-            "config": {"workload": "32^4 HISQ smearing of random SU(3) thin links (width 0.3, seed 1002); CG m=0.01 "
-                                   "to true rel. residual 1e-8 on the result", "sites": V,
-                       "l2": "inputs larger than L2 (thin links 0.6 GB, workspace 6.6 GB)"},
+            "config": {"workload": "x".join(map(str, lattice)) + " HISQ smearing of random SU(3) thin links (width 0.3, "
+                                   "seed 1002); CG m=0.01 to true rel. residual 1e-8 on the result", "sites": V,
+                       "l2": f"thin links {V * 576 / 1e9:.2f} GB, workspace {V * 56 * 144 / 1e9:.2f} GB (L2 129 MB)"},
             "roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, FP64 3x3 products)",
                          "achieved": gflops, "peak": NOMINAL_FP64_GFLOPS, "unit": "GFLOP/s",
                          "frac": gflops / NOMINAL_FP64_GFLOPS, "peak_kind": "nominal FP64 rate",

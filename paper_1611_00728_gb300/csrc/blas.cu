@@ -259,12 +259,7 @@ int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, doubl
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
   if (grid > ctx->max_blocks || nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
-  MSPtrs P;
-  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
-    P.x[j] = (j < nshift) ? x[j] : nullptr;
-    P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
-  }
-  (void)P;
+  (void)x;  // the x_s updates run in k_ms_xpay
   if (mixed)
     k_ms_update<float><<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, Vh, ctx->st, ctx->partials);
   else

@@ -12,7 +12,8 @@
 //
 // One smearing level is three kernels over full-lattice structure-of-arrays
 // fields [field][element][V] (site fastest, coalesced):
-//   A: S^s_{mu nu}(n), the single-sign 3-staples (24 fields);
+//   A: S^s_{mu nu}(n), the single-sign 3-staples (24 fields), and their sums
+//      S3_{mu nu} = S^+ + S^- (12 fields);
 //   B: Z_{mu nu}(n) = c5 (S3_{mu rho} + S3_{mu sig})(n)
 //                    + c7 (wrap_rho S3_{mu sig} + wrap_sig S3_{mu rho})(n),
 //      with S3 = S^+ + S^- and {rho, sig} the two directions other than mu, nu;
@@ -94,6 +95,23 @@ __device__ __forceinline__ M3 mm_dn(const M3& A, const M3& B) {  // A^+ B
     }
   return C;
 }
+// C += A B and C += A B^+ (the product accumulated into C directly)
+__device__ __forceinline__ void mm_acc(M3& C, const M3& A, const M3& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cfma(C.e[i * 3 + j], A.e[i * 3 + k], B.e[k * 3 + j]);
+}
+__device__ __forceinline__ void mm_nd_acc(M3& C, const M3& A, const M3& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cfma_cb(C.e[i * 3 + j], A.e[i * 3 + k], B.e[j * 3 + k]);
+}
 __device__ __forceinline__ void axpy(M3& Y, double a, const M3& X) {
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
@@ -122,11 +140,6 @@ __device__ __forceinline__ void st(double2* __restrict__ f, int k, long V, long 
 #pragma unroll
   for (int e = 0; e < 9; ++e) p[(size_t)e * V] = m.e[e];
 }
-__device__ __forceinline__ M3 ld_s3(const double2* __restrict__ S, int f0, long V, long n) {  // S^+ + S^-
-  M3 a = ld(S, f0, V, n);
-  addto(a, ld(S, f0 + 1, V, n));
-  return a;
-}
 
 __device__ __forceinline__ void coords(const Lat& g, long n, int c[4]) {
   c[0] = (int)(n % g.L[0]);
@@ -151,7 +164,9 @@ __device__ __forceinline__ long nb(const Lat& g, const int c[4], int d1, int k1,
 // the i-th direction other than mu (increasing order), and the inverse
 __device__ __forceinline__ int other(int mu, int i) { return i + (i >= mu ? 1 : 0); }
 __device__ __forceinline__ int other_index(int mu, int d) { return d - (d > mu ? 1 : 0); }
-__device__ __forceinline__ int s_field(int mu, int d, int s) { return (mu * 3 + other_index(mu, d)) * 2 + s; }
+// staple fields: single-sign S^s_{mu d} at (mu*3 + index of d)*2 + s, their sum S3_{mu d} at 24 + mu*3 + index
+constexpr int kNumS = 36;
+__device__ __forceinline__ int s3_field(int mu, int d) { return 24 + mu * 3 + other_index(mu, d); }
 
 // wrap^s_d X (n) for the direction-mu field X given at the displaced site
 __device__ __forceinline__ M3 wrap(const Lat& g, const double2* __restrict__ U, const int c[4], long n, int mu,
@@ -166,6 +181,20 @@ __device__ __forceinline__ M3 wrap(const Lat& g, const double2* __restrict__ U, 
   return mm(mm_dn(a, Xd), b);
 }
 
+// acc += wrap^s_d X (n)
+__device__ __forceinline__ void wrap_acc(M3& acc, const Lat& g, const double2* __restrict__ U, const int c[4], long n,
+                                         int mu, int d, int s, const M3& Xd) {
+  if (s == 0) {
+    const M3 a = ld(U, d, g.V, n);
+    const M3 b = ld(U, d, g.V, nb(g, c, mu, 1));
+    mm_nd_acc(acc, mm(a, Xd), b);
+    return;
+  }
+  const M3 a = ld(U, d, g.V, nb(g, c, d, -1));
+  const M3 b = ld(U, d, g.V, nb(g, c, d, -1, mu, 1));
+  mm_acc(acc, mm_dn(a, Xd), b);
+}
+
 // host AoS [V][4][9] -> [mu][e][V]
 __global__ void __launch_bounds__(kThreads) k_links_to_fields(Lat g, const double2* __restrict__ aos,
                                                               double2* __restrict__ U) {
@@ -176,16 +205,20 @@ __global__ void __launch_bounds__(kThreads) k_links_to_fields(Lat g, const doubl
   for (int e = 0; e < 9; ++e) U[((size_t)mu * 9 + e) * g.V + n] = aos[((size_t)n * 4 + mu) * 9 + e];
 }
 
-// A: single-sign 3-staples S^s_{mu nu}, field (mu*3 + nu index)*2 + s (s = 0 forward, 1 backward)
+// A: 3-staples S^+_{mu nu}, S^-_{mu nu} (s = 0 forward, 1 backward) and S3_{mu nu} = S^+ + S^-
 __global__ void __launch_bounds__(kThreads) k_staple3(Lat g, const double2* __restrict__ U, double2* __restrict__ S) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
-  const int f = blockIdx.y;
-  const int s = f & 1, mu = (f >> 1) / 3, nu = other(mu, (f >> 1) % 3);
+  const int f = blockIdx.y;  // mu*3 + nu index
+  const int mu = f / 3, nu = other(mu, f % 3);
   int c[4];
   coords(g, n, c);
-  const M3 x = ld(U, mu, g.V, nb(g, c, nu, s == 0 ? 1 : -1));
-  st(S, f, g.V, n, wrap(g, U, c, n, mu, nu, s, x));
+  const M3 sp = wrap(g, U, c, n, mu, nu, 0, ld(U, mu, g.V, nb(g, c, nu, 1)));
+  st(S, 2 * f, g.V, n, sp);
+  M3 sm = wrap(g, U, c, n, mu, nu, 1, ld(U, mu, g.V, nb(g, c, nu, -1)));
+  st(S, 2 * f + 1, g.V, n, sm);
+  addto(sm, sp);
+  st(S, 24 + f, g.V, n, sm);
 }
 
 // B: Z_{mu nu} = c5 (S3_{mu rho} + S3_{mu sig}) + c7 (wrap_rho S3_{mu sig} + wrap_sig S3_{mu rho})
@@ -205,17 +238,22 @@ __global__ void __launch_bounds__(kThreads) k_staple57(Lat g, const double2* __r
 #pragma unroll
   for (int e = 0; e < 9; ++e) z.e[e] = make_double2(0.0, 0.0);
   if (c5 != 0.0) {
-    axpy(z, c5, ld_s3(S, s_field(mu, rs[0], 0), g.V, n));
-    axpy(z, c5, ld_s3(S, s_field(mu, rs[1], 0), g.V, n));
+    M3 t = ld(S, s3_field(mu, rs[0]), g.V, n);
+    addto(t, ld(S, s3_field(mu, rs[1]), g.V, n));
+    axpy(z, c5, t);
   }
   if (c7 != 0.0) {
+    M3 w;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) w.e[e] = make_double2(0.0, 0.0);
     for (int q = 0; q < 2; ++q) {
       const int d = rs[q], inner = rs[1 - q];
       for (int s = 0; s < 2; ++s) {
-        const M3 x = ld_s3(S, s_field(mu, inner, 0), g.V, nb(g, c, d, s == 0 ? 1 : -1));
-        axpy(z, c7, wrap(g, U, c, n, mu, d, s, x));
+        const M3 x = ld(S, s3_field(mu, inner), g.V, nb(g, c, d, s == 0 ? 1 : -1));
+        wrap_acc(w, g, U, c, n, mu, d, s, x);
       }
     }
+    axpy(z, c7, w);
   }
   st(Z, f, g.V, n, z);
 }
@@ -239,9 +277,9 @@ __global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const double2* 
   }
   for (int i = 0; i < 3; ++i) {
     const int nu = other(mu, i);
+    if (c3 != 0.0) axpy(F, c3, ld(S, 24 + mu * 3 + i, g.V, n));  // both signs: S3_{mu nu}
     for (int s = 0; s < 2; ++s) {
       const int fs = (mu * 3 + i) * 2 + s;
-      if (c3 != 0.0) axpy(F, c3, ld(S, fs, g.V, n));
       if (!use_z && cL == 0.0) continue;
       const long y = nb(g, c, nu, s == 0 ? 1 : -1);
       M3 x;
@@ -256,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const double2* 
           x.e[e].y *= cL;
         }
       }
-      addto(F, wrap(g, U, c, n, mu, nu, s, x));
+      wrap_acc(F, g, U, c, n, mu, nu, s, x);
     }
   }
   if (aos) {
@@ -274,12 +312,6 @@ __global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const double2* 
 // conjugated cofactor matrix over conj(det X). At most kMaxPolar steps; a singular or
 // non-finite link, or no convergence, sets *err and leaves the link as it is.
 constexpr int kMaxPolar = 40;
-
-__device__ __forceinline__ double2 cdiv_conj(double2 a, double2 d) {  // conj(a / d)
-  const double den = d.x * d.x + d.y * d.y;
-  const double re = (a.x * d.x + a.y * d.y) / den, im = (a.y * d.x - a.x * d.y) / den;
-  return make_double2(re, -im);
-}
 
 __global__ void __launch_bounds__(kThreads) k_u3_project(Lat g, double2* __restrict__ F, int* __restrict__ err) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,27 +339,32 @@ __global__ void __launch_bounds__(kThreads) k_u3_project(Lat g, double2* __restr
     for (int j = 0; j < 3; ++j) cfma(det, X.e[j], C.e[j]);
     const double dn = det.x * det.x + det.y * det.y;
     if (!(dn > 0.0) || !isfinite(dn)) break;
+    const double inv_dn = 1.0 / dn;
     double nx = 0.0, nc = 0.0;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       nx += X.e[e].x * X.e[e].x + X.e[e].y * X.e[e].y;
       nc += C.e[e].x * C.e[e].x + C.e[e].y * C.e[e].y;
     }
-    // Frobenius scaling gamma = sqrt(|X^-1|_F / |X|_F), |X^-1|_F = |C|_F / |det|
-    const double gam = sqrt(sqrt(nc / dn) / sqrt(nx));
+    // Frobenius scaling gamma = sqrt(|X^-1|_F / |X|_F) = (|C|_F^2 / (|det|^2 |X|_F^2))^(1/4)
+    const double gam = sqrt(sqrt(nc * inv_dn / nx));
     const bool scale = fabs(gam - 1.0) > 1e-3;
-    const double g1 = scale ? gam : 1.0, g2 = scale ? 1.0 / gam : 1.0;
+    const double g1 = scale ? 0.5 * gam : 0.5, g2 = scale ? 0.5 / gam : 0.5;
+    // X^{-+} = conj(C) det / |det|^2, elementwise; q = g2 det / |det|^2
+    const double2 q = make_double2(g2 * det.x * inv_dn, g2 * det.y * inv_dn);
     double diff = 0.0;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-      const double2 xi = cdiv_conj(C.e[e], det);  // (X^{-+})_e
-      const double2 xn = make_double2(0.5 * (g1 * X.e[e].x + g2 * xi.x), 0.5 * (g1 * X.e[e].y + g2 * xi.y));
+      const double2 cc = C.e[e];
+      const double2 xn = make_double2(fma(g1, X.e[e].x, cc.x * q.x + cc.y * q.y),
+                                      fma(g1, X.e[e].y, cc.x * q.y - cc.y * q.x));
       const double dx = xn.x - X.e[e].x, dy = xn.y - X.e[e].y;
       diff += dx * dx + dy * dy;
       X.e[e] = xn;
     }
     if (!isfinite(diff)) break;
-    if (!scale && diff < 1e-30) {  // quadratic convergence: the next step would change X by ~diff
+    // unscaled and the step below 1e-9: Newton's quadratic convergence leaves an error ~1e-18
+    if (!scale && diff < 1e-18) {
       ok = true;
       break;
     }
@@ -387,7 +424,7 @@ int smear_level(const Lat& g, const double2* U, double2* S, double2* Z, const sq
   const unsigned gx = (unsigned)((g.V + kThreads - 1) / kThreads);
   const bool need_s = c.three_staple != 0.0 || c.five_staple != 0.0 || c.seven_staple != 0.0 || c.lepage != 0.0;
   const bool use_z = c.five_staple != 0.0 || c.seven_staple != 0.0;
-  if (need_s) k_staple3<<<dim3(gx, 24), blk, 0, s>>>(g, U, S);
+  if (need_s) k_staple3<<<dim3(gx, 12), blk, 0, s>>>(g, U, S);
   if (use_z) k_staple57<<<dim3(gx, 12), blk, 0, s>>>(g, U, S, c.five_staple, c.seven_staple, Z);
   k_smear_links<<<dim3(gx, 4), blk, 0, s>>>(g, U, S, Z, c.one_link, c.three_staple, c.lepage, use_z ? 1 : 0, aos,
                                              out);
@@ -399,8 +436,8 @@ int smear_level(const Lat& g, const double2* U, double2* S, double2* Z, const sq
 extern "C" size_t sqcg_hisq_workspace_bytes(const int dims[4]) {
   Lat g;
   if (check_dims(dims, &g) != SQCG_OK) return 0;
-  // thin fields (4) + staples (24) + Z (12) + level-1 result / projected links (4), then an error flag
-  return (size_t)(4 + 24 + 12 + 4) * 9 * g.V * sizeof(double2) + 256;
+  // thin fields (4) + staples (kNumS) + Z (12) + level-1 result / projected links (4), then an error flag
+  return (size_t)(4 + kNumS + 12 + 4) * 9 * g.V * sizeof(double2) + 256;
 }
 
 extern "C" int sqcg_hisq_smear(const int dims[4], const void* thin, void* fat, void* lng, const sqcg_hisq_coeffs* coeffs,
@@ -417,7 +454,7 @@ extern "C" int sqcg_hisq_smear(const int dims[4], const void* thin, void* fat, v
   const size_t nf = 9 * (size_t)g.V;
   double2* U = (double2*)workspace;
   double2* S = U + 4 * nf;
-  double2* Z = S + 24 * nf;
+  double2* Z = S + kNumS * nf;
   double2* W = Z + 12 * nf;
   int* err = (int*)(W + 4 * nf);
   const unsigned gx = (unsigned)((g.V + kThreads - 1) / kThreads);
