@@ -64,7 +64,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
     ap.add_argument("--lattice", default=None,
-                    help="hisq workload only: extents as Lx,Ly,Lz,Lt (default 32,32,32,32; smaller for profiling)")
+                    help="hisq and batched workloads: extents as Lx,Ly,Lz,Lt (hisq default 32^4; batched: one "
+                         "lattice with 16 sources instead of the three; for profiling)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="batched workload: skip the one-source-at-a-time comparison solves (profiling runs)")
     ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned", "hisq"], default="single",
                     help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
@@ -575,6 +578,8 @@ def run_batched(args):
 
     sq.build_if_needed()
     specs = [(16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 64)]
+    if args.lattice:
+        specs = [tuple(int(v) for v in args.lattice.split(","))]
     m, nr = 0.02, 16
     lats, bs, xs = [], [], []
     for n, L in enumerate(specs):
@@ -588,7 +593,7 @@ def run_batched(args):
     def solve():
         for x in xs:
             x.zero_()
-        return sq.cg_solve_batched(lats, [m] * 3, bs, xs, tol=TOL, max_iter=20000)
+        return sq.cg_solve_batched(lats, [m] * len(lats), bs, xs, tol=TOL, max_iter=20000)
 
     for _ in range(max(args.warmup, 1)):
         solve()
@@ -599,35 +604,40 @@ def run_batched(args):
     t_batched = statistics.median(times)
     W, T = sq.batched_tuning(lats[0])
     # plain FP64 CG and single-RHS mixed CG, one source at a time
-    t64, tmix, it64 = 0.0, 0.0, []
-    for lat, b in zip(lats, bs):
-        x = lat.new_spinor()
-        for j in range(nr):
-            def f64():
-                x.zero_()
-                return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
-            def fmx():
-                x.zero_()
-                return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_MIXED)
-            i64, ms = _timed(torch, f64)
-            t64 += ms
-            it64.append(i64.iters)
-            _, ms = _timed(torch, fmx)
-            tmix += ms
+    t64 = tmix = None
+    if not args.no_compare:
+        t64, tmix = 0.0, 0.0
+        for lat, b in zip(lats, bs):
+            x = lat.new_spinor()
+            for j in range(nr):
+                def f64():
+                    x.zero_()
+                    return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
+
+                def fmx():
+                    x.zero_()
+                    return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_MIXED)
+
+                _, ms = _timed(torch, f64)
+                t64 += ms
+                _, ms = _timed(torch, fmx)
+                tmix += ms
     site_rhs = sum(nr * int(np.prod(L)) // 2 for L in specs)
     apps = sum(2 * (i.iters + i.reliable_updates + 1) * int(np.prod(L)) // 2
                for L, lst in zip(specs, infos) for i in lst)
-    line = {"metric": "batched CG time to true residual 1e-8 (48 sources, 3 lattices) vs plain FP64 CG", "unit": "ms",
+    line = {"metric": f"batched CG time to true residual 1e-8 ({nr * len(specs)} sources, {len(specs)} lattices) "
+                      "vs plain FP64 CG", "unit": "ms",
             "value": t_batched, "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "16 Gaussian sources each on 16^4, 24^4, 32^3x64, m=0.02 (gauge seeds 1004-1006)",
-                       "site_rhs": site_rhs},
+            "config": {"workload": "16 Gaussian sources each on " + ", ".join("x".join(map(str, L)) for L in specs)
+                                   + ", m=0.02 (gauge seeds from 1004)", "site_rhs": site_rhs},
             "batched_ms": t_batched, "tuned_W": W, "tuned_T": T,
             "dslash_gflops_in_solve": FLOPS_PER_SITE * apps / (t_batched / 1e3) / 1e9,
             "max_iters": max(i.iters for lst in infos for i in lst),
             "max_true_rel_resid": max(i.true_rel_resid for lst in infos for i in lst),
             "fp64_cg_one_per_source_ms": t64, "mixed_cg_one_per_source_ms": tmix,
-            "speedup_vs_fp64_cg": t64 / t_batched, "speedup_vs_mixed_cg_sequential": tmix / t_batched}
+            "speedup_vs_fp64_cg": t64 / t_batched if t64 else None,
+            "speedup_vs_mixed_cg_sequential": tmix / t_batched if tmix else None}
     for lat in lats:
         lat.close()
     print(json.dumps(line), flush=True)

@@ -716,6 +716,7 @@ struct BatchPlan {
   void* x[SQCG_MAX_LATTICES];
   int b_shared;          // every RHS of a lattice reads the same source b[k]
   int W, T;              // tuned RHS block width and site block (threads along x)
+  int carve;             // tuned shared-memory carveout of the FP32 Dslash (percent; -1 = driver default)
   int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
   int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
   int ntiles_b;          // BLAS tiles over all lattices
@@ -737,7 +738,7 @@ extern unsigned long long sqcg_links_generation(const sqcg_ctx* ctx);
 namespace {
 
 struct TuneChoice {
-  int W, WT, T;
+  int W, WT, T, carve;
 };
 
 std::map<std::string, TuneChoice>& tune_cache() {
@@ -754,9 +755,12 @@ void tune_file_load() {
   if (!path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char key[512];
-  int W, WT, T;
-  while (fscanf(f, "%511s %d %d %d", key, &W, &WT, &T) == 4) tune_cache()[key] = {W, WT, T};
+  char line[768], key[512];
+  while (fgets(line, sizeof(line), f)) {
+    int W, WT, T, carve = -1;
+    const int got = sscanf(line, "%511s %d %d %d %d", key, &W, &WT, &T, &carve);
+    if (got >= 4) tune_cache()[key] = {W, WT, T, got == 5 ? carve : -1};
+  }
   fclose(f);
 }
 
@@ -765,7 +769,7 @@ void tune_file_store(const std::string& key, const TuneChoice& c) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d\n", key.c_str(), c.W, c.WT, c.T);
+  fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.W, c.WT, c.T, c.carve);
   fclose(f);
 }
 
@@ -852,6 +856,21 @@ int launch_finish_b(const BatchPlan& P, int fin, int blas, cudaStream_t s) {
   return SQCG_OK;
 }
 
+// The shared-memory carveout of each FP32 Dslash instantiation: a smaller carveout leaves
+// more of the SM's 256 KB to L1, which serves the neighbour gathers, at fewer resident blocks.
+// Set outside graph capture (by the tuner, before the plan's graph is captured).
+int set_carve(int WT, int carve) {
+  static int cur[3] = {-2, -2, -2};
+  const int k = WT == 1 ? 0 : WT == 2 ? 1 : WT == 4 ? 2 : -1;
+  if (k < 0) return SQCG_ERR_INVALID_ARG;
+  if (cur[k] == carve) return SQCG_OK;
+  const void* fn = k == 0 ? (const void*)k_mrhs_dslash_smem<1> : k == 1 ? (const void*)k_mrhs_dslash_smem<2>
+                                                                          : (const void*)k_mrhs_dslash_smem<4>;
+  SQCG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  cur[k] = carve;
+  return SQCG_OK;
+}
+
 int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
   const int G = P.W / P.WT, T = P.T;
   if (T * G > kMaxThreads || T % 32) return SQCG_ERR_INVALID_ARG;
@@ -898,17 +917,39 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   for (int k = 0; k < P.nlat; ++k) maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
   if (it != tune_cache().end()) {
     layout_tiles(P, it->second.W, it->second.WT, it->second.T);
+    P.carve = it->second.carve;
+    SQCG_TRY(set_carve(P.WT, P.carve));
     return upload_lats(P, s);
   }
   cudaEvent_t e0, e1;
   SQCG_CUDA_TRY(cudaEventCreate(&e0));
   SQCG_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  TuneChoice bestc = {1, 1, 128};
+  TuneChoice bestc = {1, 1, 128, -1};
   const int Ws[] = {1, 2, 4, 8, 16};
   const int WTs[] = {1, 2, 4};
   const int Ts[] = {32, 64, 128, 256};
   int rc = SQCG_OK;
+  // time one configuration (5 launches after 2 warm-up launches); keep it if fastest
+  auto trial = [&](int W, int WT, int T, int carve) {
+    layout_tiles(P, W, WT, T);
+    P.carve = carve;
+    if ((rc = set_carve(WT, carve)) != SQCG_OK) return;
+    if ((rc = upload_lats(P, s)) != SQCG_OK) return;
+    for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+    if (rc != SQCG_OK) return;
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+    cudaEventRecord(e1, s);
+    if (rc != SQCG_OK) return;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; return; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (getenv("SQCG_TUNE_VERBOSE"))
+      fprintf(stderr, "sqcg tune %s W=%d WT=%d T=%d carve=%d %.4f ms\n", key.c_str(), W, WT, T, carve, ms / 5);
+    if (ms < best) { best = ms; bestc = {W, WT, T, carve}; }
+  };
+  // 1: block shapes at the driver's default carveout
   for (int W : Ws) {
     if (W > 1 && W / 2 >= maxr) break;  // wider blocks than any lattice's RHS count only add idle lanes
     for (int WT : WTs) {
@@ -916,24 +957,25 @@ int autotune(BatchPlan& P, cudaStream_t s) {
       const int G = W / WT;
       for (int T : Ts) {
         if (T * G > kMaxThreads || T > kMaxTSmem) break;
-        layout_tiles(P, W, WT, T);
-        if ((rc = upload_lats(P, s)) != SQCG_OK) break;
-        for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
+        trial(W, WT, T, -1);
         if (rc != SQCG_OK) break;
-        cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 5 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
-        cudaEventRecord(e1, s);
-        if (rc != SQCG_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (getenv("SQCG_TUNE_VERBOSE"))
-          fprintf(stderr, "sqcg tune %s W=%d WT=%d T=%d %.4f ms\n", key.c_str(), W, WT, T, ms / 5);
-        if (ms < best) { best = ms; bestc = {W, WT, T}; }
       }
       if (rc != SQCG_OK) break;
     }
     if (rc != SQCG_OK) break;
+  }
+  // 2: the best W and WT again with smaller shared-memory carveouts (more L1 for the gathers)
+  if (rc == SQCG_OK) {
+    const int W = bestc.W, WT = bestc.WT, G = W / WT;
+    const int carves[] = {25, 50, 75};
+    for (int T : Ts) {
+      if (T * G > kMaxThreads || T > kMaxTSmem) break;
+      for (int cv : carves) {
+        trial(W, WT, T, cv);
+        if (rc != SQCG_OK) break;
+      }
+      if (rc != SQCG_OK) break;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -941,6 +983,8 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   tune_cache()[key] = bestc;
   tune_file_store(key, bestc);
   layout_tiles(P, bestc.W, bestc.WT, bestc.T);
+  P.carve = bestc.carve;
+  SQCG_TRY(set_carve(P.WT, P.carve));
   return upload_lats(P, s);
 }
 
