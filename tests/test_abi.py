@@ -76,3 +76,29 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(pkg, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU path"):
         pkg.library()
+
+
+def test_host_side_argument_checks(libpath):
+    """Checks that return before any CUDA call: lattice extents, the 2^28-site index limit, flags,
+    null handles, and the HISQ workspace size (host arithmetic only)."""
+    lib = ctypes.CDLL(libpath)
+    lib.sqcg_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    lib.sqcg_hisq_workspace_bytes.argtypes = [ctypes.c_void_p]
+    lib.sqcg_hisq_workspace_bytes.restype = ctypes.c_size_t
+    lib.sqcg_destroy.argtypes = [ctypes.c_void_p]
+    h = ctypes.c_void_p()
+
+    def create(dims, flags=1):
+        return lib.sqcg_create((ctypes.c_int * 4)(*dims), flags, None, ctypes.byref(h))
+
+    for dims in ((8, 8, 8, 5), (2, 8, 8, 8), (8, 8, 0, 8), (8, -8, 8, 8), (128, 128, 128, 130)):
+        assert create(dims) == -1, dims
+        assert not h.value
+    assert create((8, 8, 8, 8), flags=4) == -1  # unknown flag
+    assert lib.sqcg_create(None, 1, None, ctypes.byref(h)) == -1
+    assert lib.sqcg_destroy(None) == 0
+    # 32^4: (4 thin + 36 staple + 12 Z + 4 projected) fields of V 3x3 complex doubles, plus a flag
+    V = 32 ** 4
+    assert lib.sqcg_hisq_workspace_bytes((ctypes.c_int * 4)(32, 32, 32, 32)) == 56 * 9 * V * 16 + 256
+    assert lib.sqcg_hisq_workspace_bytes((ctypes.c_int * 4)(4, 4, 4, 3)) == 0
+    assert lib.sqcg_hisq_workspace_bytes(None) == 0
