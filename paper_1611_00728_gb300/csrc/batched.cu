@@ -536,15 +536,52 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
     for (int w = 0; w < WT; ++w)
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[w][c] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int h = 0; h < kHops; ++h) {
+    // one-hop software pipeline: the next hop's neighbour vectors are in flight while
+    // this hop's products run (the gathers, not the FMAs, set the pace of this kernel)
+    float2 vin[WT][3], vnx[WT][3];
+    auto gather = [&](int h, float2 (&v)[WT][3]) {
       const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
       const int j = nbr(mu, bwd ? (lng ? -3 : -1) : (lng ? 3 : 1));
+#pragma unroll
+      for (int w = 0; w < WT; ++w)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          v[w][c] = (w < nw) ? __ldg(in + ((size_t)w * 3 + c) * Vh + j) : make_float2(0.f, 0.f);
+    };
+    gather(0, vin);
+#pragma unroll
+    for (int h = 0; h < kHops; ++h) {
+      if (h + 1 < kHops) gather(h + 1, vnx);
+      const bool bwd = h & 1;
       float2 U[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) U[e] = sU[(h * 9 + e) * TX + threadIdx.x];
-      if (bwd) apply_w<float, WT, true>(acc, U, in, Vh, j, nw);
-      else apply_w<float, WT, false>(acc, U, in, Vh, j, nw);
+#pragma unroll
+      for (int w = 0; w < WT; ++w)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const float2 v = vin[w][b];
+            if (!bwd) {
+              const float2 u = U[a * 3 + b];
+              acc[w][a].x = fmaf(u.x, v.x, acc[w][a].x);
+              acc[w][a].x = fmaf(-u.y, v.y, acc[w][a].x);
+              acc[w][a].y = fmaf(u.x, v.y, acc[w][a].y);
+              acc[w][a].y = fmaf(u.y, v.x, acc[w][a].y);
+            } else {
+              const float2 u = U[b * 3 + a];
+              acc[w][a].x = fmaf(-u.x, v.x, acc[w][a].x);
+              acc[w][a].x = fmaf(-u.y, v.y, acc[w][a].x);
+              acc[w][a].y = fmaf(-u.x, v.y, acc[w][a].y);
+              acc[w][a].y = fmaf(u.y, v.x, acc[w][a].y);
+            }
+          }
+      if (h + 1 < kHops)
+#pragma unroll
+        for (int w = 0; w < WT; ++w)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) vin[w][c] = vnx[w][c];
     }
     if (a.epi == M_PLAIN) {
       float2* out = L.tmp + (size_t)w0 * 3 * Vh;

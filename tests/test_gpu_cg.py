@@ -325,3 +325,66 @@ def test_multishift_mixed_zero_source(sqcg, links_cache):
         infos = lat.multishift_cg_solve([0.01, 0.1, 1.0], lat.pack(np.zeros((lat.Vh, 3), complex)), xs, mode=1)
         assert all(i.status == 0 and i.iters == 0 for i in infos)
         assert all(not x.any() for x in xs)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_multishift_degenerate_and_maximum_shift_counts(sqcg, links_cache, mode):
+    """One shift is plain CG; 32 shifts (the maximum) with duplicates all converge; bad arguments are refused."""
+    L, tol = (6, 8, 10, 12), 1e-8
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 4300)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db = lat.pack(b)
+        x1 = [lat.new_spinor()]
+        info = lat.multishift_cg_solve([0.04], db, x1, tol=tol, mode=mode)[0]
+        xc = lat.new_spinor()
+        ic = lat.cg_solve(0.1, db, xc, tol=tol, mode=mode)
+        assert info.status == 0 and info.true_rel_resid <= tol
+        if mode == 0:  # FP64: the same Krylov space as the single-mass CG (kernels round differently)
+            assert abs(info.iters - ic.iters) <= 1
+        # both within tol of the same solution; kappa(sigma = 0.04) <~ 1.5e3
+        assert rel(lat.unpack(x1[0]), lat.unpack(xc)) <= 2e3 * tol
+        shifts = list(np.logspace(-3, 1, 30)) + [0.01, 0.01]
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, db, xs, tol=tol, mode=mode)
+        for s, i, x in zip(shifts, infos, xs):
+            assert i.status == 0
+            assert oracle.true_rel_residual(L, fat, lng, s, b, lat.unpack(x)) <= tol
+        assert rel(lat.unpack(xs[-1]), lat.unpack(xs[-2])) <= 1e-10  # duplicate shifts: identical arithmetic
+        for bad in ([0.1] * 33, [-0.1], [float("nan")]):
+            with pytest.raises(sqcg.SqcgError) as e:
+                lat.multishift_cg_solve(bad, db, [lat.new_spinor() for _ in bad], mode=mode)
+            assert e.value.name == "INVALID_ARG"
+        x_same = lat.new_spinor()
+        with pytest.raises(sqcg.SqcgError):  # the same output buffer twice
+            lat.multishift_cg_solve([0.1, 0.2], db, [x_same, x_same], mode=mode)
+
+
+def test_rational_apply_constant_term_and_one_pole(sqcg, links_cache):
+    L = (8, 8, 8, 8)
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 4400)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        db, out = lat.pack(b), lat.new_spinor()
+        lat.rational_apply([0.5], [0.0], 2.5, db, out, tol=1e-10, mode=1)  # zero residue: out = a0 b
+        assert rel(lat.unpack(out), 2.5 * b) <= 1e-15
+        lat.rational_apply([0.5], [3.0], 0.0, db, out, tol=1e-11, mode=1)  # one pole: 3 (0.5 - DD)^-1 b
+        x, _, _ = oracle.cg(L, fat, lng, 0.5, b, tol=1e-13)
+        assert rel(lat.unpack(out), 3.0 * x) <= 1e-8  # kappa(0.5 - DD) <~ 120
+        with pytest.raises(sqcg.SqcgError):
+            lat.rational_apply([0.5], [1.0], 0.0, db, db)  # out aliases b
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pack_unpack_round_trip(sqcg, prec):
+    L = (6, 4, 10, 8)
+    psi = synth.gaussian_source(L, 4500)
+    with sqcg.Lattice(L) as lat:
+        got = lat.unpack(lat.pack(psi, prec), prec)
+    if prec == 0:
+        assert np.array_equal(got, psi)
+    else:  # round to nearest FP32, component by component
+        want = psi.real.astype(np.float32).astype(np.float64) + 1j * psi.imag.astype(np.float32).astype(np.float64)
+        assert np.array_equal(got, want)
