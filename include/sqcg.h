@@ -103,7 +103,7 @@ int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
 /* Reliable-update trigger of the mixed-precision solvers on this context: the
  * FP64 true residual is recomputed when the iterated |r| falls below
  * delta * (max |r| since the last update), or after `interval` iterations,
- * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.01 and 100).
+ * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.001 and 100).
  * The batched solve uses the settings of its first context. */
 int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval);
 

@@ -203,7 +203,7 @@ class Lattice:
     def __exit__(self, *exc):
         self.close()
 
-    def set_reliable_update(self, delta: float = 0.01, interval: int = 100):
+    def set_reliable_update(self, delta: float = 0.001, interval: int = 100):
         """Mixed-precision trigger: FP64 true residual when |r| < delta * max|r| since the last one, or every
         `interval` iterations."""
         _check(library().sqcg_set_reliable_update(self._h, float(delta), int(interval)), "sqcg_set_reliable_update")

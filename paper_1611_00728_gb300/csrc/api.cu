@@ -88,7 +88,7 @@ int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out)
   g.st = g.Lxh * g.Ly * g.Lz;
   g.apbc = (flags & SQCG_ANTIPERIODIC_T) ? 1 : 0;
   c->stream = (cudaStream_t)cuda_stream;
-  c->ru_delta = 0.01;
+  c->ru_delta = 0.001;
   c->ru_interval = 100;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     sqcg_set_last_cuda_error(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);

@@ -226,7 +226,7 @@ def test_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch)
     assert all(np.array_equal(a, c) for a, c in zip(g[4], e[4]))
 
 
-@pytest.mark.parametrize("delta,interval", [(0.01, 100), (0.5, 5), (0.1, 1000)])
+@pytest.mark.parametrize("delta,interval", [(0.001, 100), (0.01, 100), (0.5, 5), (0.1, 1000), (1e-5, 100)])
 def test_reliable_update_settings(sqcg, links_cache, delta, interval):
     """Any trigger setting still ends on the FP64 true residual; the count follows the setting."""
     L, m, tol = (8, 10, 12, 14), 0.01, 1e-9
