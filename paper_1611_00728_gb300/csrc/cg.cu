@@ -486,12 +486,14 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
       ri[j].true_rel_resid = NAN;
     }
   } else if (mixed) {
-    if (ctx->ms_stack_n < nshift) {
+    // library-owned copies (solutions stacked, then the source) keep the cached batched plan
+    // valid across calls whatever buffers the caller passes
+    if (ctx->ms_stack_n != nshift) {
       SQCG_CUDA_TRY(cudaStreamSynchronize(s));
       cudaFree(ctx->ms_stack);
       ctx->ms_stack = nullptr;
       ctx->ms_stack_n = 0;
-      if (cudaMalloc(&ctx->ms_stack, (size_t)nshift * n * sizeof(double2)) != cudaSuccess) {
+      if (cudaMalloc(&ctx->ms_stack, (size_t)(nshift + 1) * n * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
         return SQCG_ERR_NO_MEMORY;
       }
@@ -504,9 +506,11 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
       SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->ms_stack + (size_t)j * n, xs[j], n * sizeof(double2),
                                     cudaMemcpyDeviceToDevice, s));
     }
+    double2* bcopy = ctx->ms_stack + (size_t)nshift * n;
+    SQCG_CUDA_TRY(cudaMemcpyAsync(bcopy, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     sqcg_ctx* cl[1] = {ctx};
     const int nr[1] = {nshift};
-    const void* bl[1] = {b};
+    const void* bl[1] = {bcopy};
     void* xl[1] = {ctx->ms_stack};
     const int st = batched_solve(1, cl, nr, sig, tl, bl, 1, xl, left, ri);
     if (st == SQCG_ERR_CUDA || st == SQCG_ERR_INVALID_ARG || st == SQCG_ERR_NO_MEMORY) return st;

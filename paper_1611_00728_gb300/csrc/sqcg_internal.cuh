@@ -182,7 +182,7 @@ struct sqcg_ctx {
   void* ms_p[SQCG_MAX_SHIFTS];  // per-shift search directions (working precision)
   void* rat_x[SQCG_MAX_SHIFTS];  // per-shift solutions of sqcg_rational_apply (FP64)
   int rat_n;
-  double2* ms_stack;  // per-shift solutions stacked [nshift][3][Vh] for the batched refinement (FP64)
+  double2* ms_stack;  // batched refinement (FP64): per-shift solutions [nshift][3][Vh], then a copy of b
   int ms_stack_n;
   int ms_nalloc;
   int ms_prec;

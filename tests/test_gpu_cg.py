@@ -295,12 +295,12 @@ def test_multishift_mixed_refinement_alternates_with_batched_plans(sqcg, links_c
     fat, lng = links_cache(L, 88)
     shifts = [0.3, 0.0004, 0.02, 0.0004 * 3]
     tols = [1e-9, 1e-8, 1e-10, 1e-8]
-    b = synth.gaussian_source(L, 4100)
     srcs = [synth.gaussian_source(L, 4200 + j) for j in range(3)]
     with sqcg.Lattice(L) as lat:
         lat.load_links(fat, lng, recon12=True)
-        db = lat.pack(b)
-        for rep in range(2):
+        for rep in range(3):  # a new source buffer each call
+            b = synth.gaussian_source(L, 4100 + rep)
+            db = lat.pack(b)
             xs = [lat.new_spinor() for _ in shifts]
             infos = lat.multishift_cg_solve(shifts, db, xs, tol=tols, max_iter=20000, mode=1)
             for s, t, info, x in zip(shifts, tols, infos, xs):
