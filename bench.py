@@ -46,6 +46,10 @@ SOURCE_SEED = 2200  # 2000 + 100 * workload number + rhs
 # least bytes per output site (each link once, input once, output once): 16 links + 2 vectors
 BYTES_PER_SITE = {"f64": 16 * 144 + 2 * 48, "f32": 16 * 72 + 2 * 24, "f32_recon12": 8 * 72 + 8 * 48 + 2 * 24}
 FALLBACK_HBM_GBS = 6800.0
+# the paper's own figures (Sec. 4), other hardware and FP64 multi-mass CG: context, not targets
+PAPER_CONTEXT = {"milc_multimass_cg_one_knl7250_gflops": 65, "qphix_speedup_one_knl": 1.5,
+                 "qphix_multimass_cg_16_knl7210_gflops": 900,
+                 "qphix_dslash_fraction_of_knl_read_bandwidth": 0.8, "precision": "FP64"}
 NOMINAL_FP64_GFLOPS = 1250.0  # GB300 FP64 rate (nominal figure of the hardware table)
 
 # DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
@@ -236,7 +240,34 @@ def oracle_sample(fat, lng, b, budget_s: float = 15.0):
     return {"value": FLOPS_PER_SITE * Vh * apps / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle", "seconds": dt,
             "sample": f"oracle CG on the 32^4 workload, {iters} iterations + initial and final residual "
-                      f"({apps} Dslash applications), OpenMP over sites"}
+                      f"({apps} Dslash applications), OpenMP over sites",
+            "dslash": oracle_dslash_rates(fat, lng)}
+
+
+def oracle_dslash_rates(fat32, lng32, reps: int = 3):
+    """The oracle Dslash alone, single-threaded and on all host cores, at 8^4 and at 32^4 (median of reps)."""
+    import oracle
+    import synth
+
+    out = {}
+    for L in ((8, 8, 8, 8), LATTICE):
+        if L == LATTICE:
+            fat, lng = fat32, lng32
+        else:
+            fat, lng = synth.fat_long_links(L, 1001)
+        psi = synth.gaussian_source(L, 2001)
+        Vh = int(np.prod(L)) // 2
+        row = {}
+        for name, nt in (("single_thread", 1), ("all_cores", oracle.max_threads())):
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                oracle.dslash(L, fat, lng, psi, 1, nthreads=nt)
+                ts.append(time.perf_counter() - t0)
+            row[name + "_gflops"] = FLOPS_PER_SITE * Vh / statistics.median(ts) / 1e9
+        row["cores"] = oracle.max_threads()
+        out["x".join(map(str, L))] = row
+    return out
 
 
 def cpu_info():
@@ -456,6 +487,13 @@ def run_ours(args, ranks: Ranks):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "cg_mixed": mixed_info, "cg_fp64": fp64_info,
                 "speedup_vs_fp64_cg": t64 / t_step, "dslash": dslash, "cpu": cpu_info(),
+                "dslash_gpu_vs_oracle": None if cpu is None else {
+                    "gpu_f32_recon12_gflops": dslash["f32_recon12"]["gflops"], "gpu_f64_gflops": dslash["f64"]["gflops"],
+                    "vs_single_thread_32^4": dslash["f32_recon12"]["gflops"]
+                    / cpu["dslash"]["x".join(map(str, LATTICE))]["single_thread_gflops"],
+                    "vs_all_cores_32^4": dslash["f32_recon12"]["gflops"]
+                    / cpu["dslash"]["x".join(map(str, LATTICE))]["all_cores_gflops"]},
+                "paper_context": PAPER_CONTEXT,
                 "notes": "dtype f32: FP32 Dslash and Krylov vectors; FP64 x, reductions, scalar recurrences and "
                          "reliable updates. Roofline: Dslash-only loop timed with CUDA events in this run."}
         print(json.dumps(line), flush=True)
