@@ -2,8 +2,9 @@
 // reductions around the Dslash; paper Sec. 4 notes that multi-mass CG is even
 // more bandwidth bound than CG because of them). Each kernel streams its
 // vectors once; norms and dot products are accumulated in FP64 and reduced
-// deterministically (warp shuffle -> block -> last block in index order),
-// and the scalar CG step runs in the last block.
+// deterministically (warp shuffle -> block partial -> one finisher block that
+// adds the partials in index order), and the scalar CG step runs in that
+// finisher.
 #include "solver_device.cuh"
 #include "sqcg_internal.cuh"
 

@@ -1,7 +1,8 @@
 // Device-side solver control: gates, deterministic grid reductions and the
-// scalar steps of CG and multi-shift CG that run in the last block of a
-// reduction. All scalars live in SolverState in device memory, so a captured
-// solver iteration needs no host round trip.
+// scalar steps of CG and multi-shift CG, which one thread of the finisher
+// kernel (the second stage of a reduction) runs. All scalars live in
+// SolverState in device memory, so a captured solver iteration needs no host
+// round trip.
 #pragma once
 
 #include <math.h>
@@ -36,7 +37,7 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// scalar steps (run by one thread, in the last block of a reduction)
+// scalar steps (run by thread 0 of the finisher, after the partials are summed)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void finish_breakdown(SolverState* s) {
   s->status = SQCG_ERR_BREAKDOWN;

@@ -122,7 +122,7 @@ struct BatchPlan;  // defined in batched.cu
 // gates: which kernels of a captured iteration actually run
 enum Gate { GATE_NONE = 0, GATE_ITER = 1, GATE_UPDATE = 2 };
 
-// what the last block of a grid reduction does with the total
+// what the finisher of a grid reduction does with the total
 enum Finisher {
   FIN_NONE = 0,
   FIN_STORE = 1,       // store the total in state->pAp (generic scalar result slot)
