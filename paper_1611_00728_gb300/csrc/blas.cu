@@ -25,9 +25,8 @@ k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const ty
   if (!gate_open(st, GATE_ITER)) return;
   const double alpha = st->alpha;
   const R ra = (R)alpha;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     R part = R(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -44,7 +43,7 @@ k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const ty
       r[k] = rc;
       part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
     }
-    nrm = (double)part;
+    nrm += (double)part;
   }
   block_partial(nrm, partials);
 }
@@ -56,24 +55,23 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
   typedef typename V2<R>::T R2;
   if (!gate_open(st, GATE_ITER)) return;
   const R beta = (R)st->beta;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Vh) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const size_t k = (size_t)c * Vh + i;
-    const R2 rc = r[k];
-    R2 pc = p[k];
-    pc.x = fma(beta, pc.x, rc.x);
-    pc.y = fma(beta, pc.y, rc.y);
-    p[k] = pc;
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      const R2 rc = r[k];
+      R2 pc = p[k];
+      pc.x = fma(beta, pc.x, rc.x);
+      pc.y = fma(beta, pc.y, rc.y);
+      p[k] = pc;
+    }
   }
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_norm2_f64(const double2* __restrict__ v, int Vh, SolverState* st, double* partials, int fin) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double2 a = v[(size_t)c * Vh + i];
@@ -107,10 +105,9 @@ k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restri
             double* partials) {
   typedef typename V2<R>::T R2;
   if (!gate_open(st, GATE_ITER)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const R ra = (R)st->alpha;
   double nrm = 0.0;
-  if (i < Vh) {
-    const R ra = (R)st->alpha;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     R part = R(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -122,7 +119,7 @@ k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restri
       r[k] = rc;
       part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
     }
-    nrm = (double)part;
+    nrm += (double)part;
   }
   block_partial(nrm, partials);
 }
@@ -140,35 +137,35 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
   const volatile SolverState* vs = st;
   const int done = vs->done;
   if (done && !vs->ms_final) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Vh) return;
   const int ns = st->nshift;
-  R2 rc[3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    R2 rc[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) rc[c] = r[(size_t)c * Vh + i];
-  for (int j = 0; j < ns; ++j) {
-    const int act = st->active[j];
-    const bool upd_p = !done && (j == 0 || act == 1);  // the base direction moves while the loop runs
-    if (!act && !upd_p) continue;
-    R2* ps = (j == 0) ? p : static_cast<R2*>(P.p[j]);
-    const double as = st->alpha_s[j];
-    const R z = (j == 0) ? R(1) : (R)st->zeta[j];
-    const R bs = (j == 0) ? (R)st->beta : (R)st->beta_s[j];
-    double2* xs = P.x[j];
+    for (int c = 0; c < 3; ++c) rc[c] = r[(size_t)c * Vh + i];
+    for (int j = 0; j < ns; ++j) {
+      const int act = st->active[j];
+      const bool upd_p = !done && (j == 0 || act == 1);  // the base direction moves while the loop runs
+      if (!act && !upd_p) continue;
+      R2* ps = (j == 0) ? p : static_cast<R2*>(P.p[j]);
+      const double as = st->alpha_s[j];
+      const R z = (j == 0) ? R(1) : (R)st->zeta[j];
+      const R bs = (j == 0) ? (R)st->beta : (R)st->beta_s[j];
+      double2* xs = P.x[j];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const size_t k = (size_t)c * Vh + i;
-      R2 pc = ps[k];
-      if (act) {
-        double2 xc = xs[k];
-        xc.x = fma(as, (double)pc.x, xc.x);
-        xc.y = fma(as, (double)pc.y, xc.y);
-        xs[k] = xc;
-      }
-      if (upd_p) {
-        pc.x = fma(bs, pc.x, z * rc[c].x);
-        pc.y = fma(bs, pc.y, z * rc[c].y);
-        ps[k] = pc;
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * Vh + i;
+        R2 pc = ps[k];
+        if (act) {
+          double2 xc = xs[k];
+          xc.x = fma(as, (double)pc.x, xc.x);
+          xc.y = fma(as, (double)pc.y, xc.y);
+          xs[k] = xc;
+        }
+        if (upd_p) {
+          pc.x = fma(bs, pc.x, z * rc[c].x);
+          pc.y = fma(bs, pc.y, z * rc[c].y);
+          ps[k] = pc;
+        }
       }
     }
   }
@@ -202,6 +199,26 @@ __global__ void k_loop_control(SolverState* st) {
 
 }  // namespace
 
+// Grid of the streaming BLAS kernels: one wave of resident blocks on every SM, each
+// thread looping over sites (no partially filled last wave). Fixed per context, so
+// the reductions stay deterministic.
+int blas_grid(sqcg_ctx* ctx) {
+  if (ctx->blas_grid > 0) return ctx->blas_grid;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_update<float>, kThreads, 0) != cudaSuccess ||
+      nsm < 1 || per_sm < 1) {
+    cudaGetLastError();
+    nsm = 1;
+    per_sm = 1 << 20;  // fall back to one thread per site
+  }
+  const long g = (long)nsm * per_sm;
+  const int full = grid_for(ctx->g.Vh, kThreads);
+  ctx->blas_grid = g < full ? (int)g : full;
+  return ctx->blas_grid;
+}
+
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
   k_finish<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -222,7 +239,7 @@ int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s) {
 
 // variant with an explicit x (the solver's output vector)
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s) {
-  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
   if (mixed)
     k_cg_update<float><<<grid, kThreads, 0, s>>>(x, ctx->r32, ctx->p32, ctx->Ap32, Vh, ctx->st, ctx->partials);
@@ -233,7 +250,7 @@ int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s) {
 }
 
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
-  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   if (mixed)
     k_cg_xpay<float><<<grid, kThreads, 0, s>>>(ctx->r32, ctx->p32, Vh, ctx->st);
   else
@@ -243,7 +260,7 @@ int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
 }
 
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s) {
-  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
   k_norm2_f64<<<grid, kThreads, 0, s>>>(v, Vh, ctx->st, ctx->partials, fin);
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -258,6 +275,7 @@ int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, doubl
 }
 
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
+  // one thread per site: measured faster here than the one-wave grid of the CG kernels
   const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
   if (grid > ctx->max_blocks || nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
   (void)x;  // the x_s updates run in k_ms_xpay

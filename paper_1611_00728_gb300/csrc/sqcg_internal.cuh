@@ -175,6 +175,7 @@ struct sqcg_ctx {
   float2 *r32, *p32, *Ap32, *tmp32;
   double* partials;
   int max_blocks;
+  int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   SolverState* st;       // device
   SolverState* st_host;  // pinned host mirror
 
