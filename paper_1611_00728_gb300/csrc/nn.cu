@@ -200,12 +200,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
         float2 u[9];
         if (dir == 0) load_link9(a.fat[par] + (size_t)mu * 9 * Vh, Vh, i, u);  // F_mu(n)
         else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);             // F_mu(n - mu)
+        const int tap = 1 + 2 * mu + dir;
+        if constexpr (COUT == 1 && CIN > 1) {
+          // one output channel: the weights mix channels and the link acts on colour, so
+          // sum_ci w_ci (U v_ci) = U (sum_ci w_ci v_ci): mix first, transport once
+          float2 m[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll 2
-        for (int ci = 0; ci < CIN; ++ci) {
-          float2 v[3], t[3];
-          load_in(ci, q, j, v);
-          apply_link(u, dir == 1, v, t);
-          mix(1 + 2 * mu + dir, t, ci);
+          for (int ci = 0; ci < CIN; ++ci) {
+            float2 v[3];
+            load_in(ci, q, j, v);
+            const float2 w = W[tap * CIN + ci];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cmac(m[c], w, v[c]);
+          }
+          float2 t[3];
+          apply_link(u, dir == 1, m, t);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            acc[0][c].x += t[c].x;
+            acc[0][c].y += t[c].y;
+          }
+        } else {
+#pragma unroll 2
+          for (int ci = 0; ci < CIN; ++ci) {
+            float2 v[3], t[3];
+            load_in(ci, q, j, v);
+            apply_link(u, dir == 1, v, t);
+            mix(tap, t, ci);
+          }
         }
       }
     }
