@@ -84,13 +84,16 @@ __device__ __forceinline__ int find_lat(const LatDev* lats, int nlat, int tile, 
 // ---------------------------------------------------------------------------
 // per-RHS CG scalar steps (same rules as the single-mass solver)
 // ---------------------------------------------------------------------------
-enum BFin { BFIN_BB = 1, BFIN_INIT = 2, BFIN_PAP = 3, BFIN_UPDATE = 4, BFIN_TRUE = 5 };
+enum BFin { BFIN_BB = 1, BFIN_INIT = 2, BFIN_PAP = 3, BFIN_UPDATE = 4, BFIN_TRUE = 5, BFIN_XX = 6 };
 
 __device__ void rhs_finish(RhsScalars& s, const BatchState* st, int fin, double v) {
   switch (fin) {
     case BFIN_BB:
       s.bb = v;
       s.stop_rr *= v;
+      break;
+    case BFIN_XX:  // |x0|^2, parked in pAp until the first iteration overwrites it
+      s.pAp = v;
       break;
     case BFIN_INIT:
       if (!isfinite(v)) { s.status = SQCG_ERR_BREAKDOWN; s.active = 0; break; }
@@ -618,7 +621,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
 // ---------------------------------------------------------------------------
 // multi-RHS BLAS: x += alpha p, r -= alpha Ap (|r|^2); p = r + beta p; |b|^2
 // ---------------------------------------------------------------------------
-enum MBlas { B_UPDATE = 0, B_XPAY = 1, B_NORM_B = 2 };
+// B_NORM_X: |x0|^2; B_INIT_B: r = p = b (FP32) with |b|^2, the exact initial residual for x0 = 0
+enum MBlas { B_UPDATE = 0, B_XPAY = 1, B_NORM_B = 2, B_NORM_X = 3, B_INIT_B = 4 };
 
 struct BArgs {
   const LatDev* lats;
@@ -642,7 +646,7 @@ __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
   const int wbase = rb * W;
   const int nw = min(W, L.nrhs - wbase);
   const int blk = L.rb0 + rb;
-  if (a.op != B_NORM_B && !a.st->blk_active[blk]) return;
+  if (a.op != B_NORM_B && a.op != B_NORM_X && a.op != B_INIT_B && !a.st->blk_active[blk]) return;
   const int Vh = L.g.Vh;
   const int i = sb * blockDim.x + threadIdx.x;
   double part[W];
@@ -659,6 +663,25 @@ __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const double2 v = L.b[(size_t)(wbase + w) * L.b_stride + (size_t)c * Vh + i];
+          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
+        }
+        part[w] = n2;
+      } else if (a.op == B_NORM_X) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 v = L.x[base + (size_t)c * Vh + i];
+          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
+        }
+        part[w] = n2;
+      } else if (a.op == B_INIT_B) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 v = L.b[(size_t)(wbase + w) * L.b_stride + (size_t)c * Vh + i];
+          const float2 f = make_float2((float)v.x, (float)v.y);
+          L.r[base + (size_t)c * Vh + i] = f;
+          L.p[base + (size_t)c * Vh + i] = f;
           n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
         }
         part[w] = n2;
@@ -1243,14 +1266,29 @@ int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double*
   // |b|^2 per RHS; r = b - A x0 in FP64 (x holds the initial guess), p = r
   SQCG_TRY(launch_mrhs_blas(P, B_NORM_B, s));
   SQCG_TRY(launch_finish_b(P, BFIN_BB, 1, s));
-  for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 1;
-  SQCG_CUDA_TRY(cudaMemcpyAsync(P.st->blk_update, h->blk_update, sizeof(int) * P.nblk, cudaMemcpyHostToDevice, s));
-  SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_NONE, 0, s));
-  SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_NONE, 1, s));
-  SQCG_TRY(launch_finish_b(P, BFIN_INIT, 0, s));
+  // |x0|^2 per RHS: when every initial guess is zero (the usual start) the initial residual
+  // is exactly b, and the FP64 passes of b - A x0 are skipped
+  SQCG_TRY(launch_mrhs_blas(P, B_NORM_X, s));
+  SQCG_TRY(launch_finish_b(P, BFIN_XX, 1, s));
   SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
   SQCG_CUDA_TRY(cudaStreamSynchronize(s));
-  int launches = 6;
+  bool x0_zero = true;
+  for (int j = 0; j < total; ++j) x0_zero = x0_zero && h->r[j].pAp == 0.0;
+  int launches = 4;
+  if (x0_zero) {
+    SQCG_TRY(launch_mrhs_blas(P, B_INIT_B, s));
+    SQCG_TRY(launch_finish_b(P, BFIN_INIT, 1, s));
+    launches += 2;
+  } else {
+    for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 1;
+    SQCG_CUDA_TRY(cudaMemcpyAsync(P.st->blk_update, h->blk_update, sizeof(int) * P.nblk, cudaMemcpyHostToDevice, s));
+    SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_NONE, 0, s));
+    SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_NONE, 1, s));
+    SQCG_TRY(launch_finish_b(P, BFIN_INIT, 0, s));
+    launches += 3;
+  }
+  SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+  SQCG_CUDA_TRY(cudaStreamSynchronize(s));
   int any = 0;
   for (int j = 0; j < total; ++j) {
     if (h->r[j].bb == 0.0 && h->r[j].active) {  // b = 0: x = 0 is the solution

@@ -315,20 +315,46 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   h->status = SQCG_OK;
   SQCG_TRY(write_state(ctx, s));
   SQCG_TRY(launch_norm2_f64(ctx, (const double2*)b, FIN_BB, s));
-  // r = b - A x0 (FP64), p = r, both in the working precision
-  DslashLaunch L = {};
-  L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
-  SQCG_TRY(launch_dslash(ctx, L, s));
-  L = DslashLaunch{};
-  L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = mixed ? SQCG_F32 : SQCG_F64; L.epi = EPI_TRUE_RESID;
-  L.in = ctx->tmp64; L.out = mixed ? (void*)ctx->r32 : (void*)ctx->r64;
-  L.out2 = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
-  L.y = x; L.b = b; L.sigma = sigma; L.fin = FIN_INIT;
-  SQCG_TRY(launch_dslash(ctx, L, s));
+  // |x0|^2: for a zero initial guess (the usual start) the initial residual is exactly b,
+  // and the two FP64 Dslash passes of b - A x0 are skipped
+  SQCG_TRY(launch_norm2_f64(ctx, (const double2*)x, FIN_STORE, s));
   SQCG_TRY(read_state(ctx, s));
+  void* r0 = mixed ? (void*)ctx->r32 : (void*)ctx->r64;
+  void* p0 = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
+  int launches = 4;
+  if (h->pAp == 0.0) {
+    const int wp = mixed ? SQCG_F32 : SQCG_F64;
+    SQCG_TRY(layout_convert(ctx, SQCG_F64, b, wp, r0, s));
+    SQCG_TRY(layout_convert(ctx, SQCG_F64, b, wp, p0, s));
+    // the initial-residual step of the device state, with |r|^2 = |b|^2
+    const double v = h->bb;
+    if (!isfinite(v)) {
+      h->status = SQCG_ERR_BREAKDOWN;
+      h->done = 1;
+      h->need_update = 0;
+    } else {
+      h->rr = h->rr_true = h->rr_max = h->rr_prev = v;
+      h->iter_last_update = 0;
+      if (v <= h->stop_rr) h->done = 1;
+    }
+    SQCG_TRY(write_state(ctx, s));
+    launches += 2;
+  } else {
+    // r = b - A x0 (FP64), p = r, both in the working precision
+    DslashLaunch L = {};
+    L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    L = DslashLaunch{};
+    L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = mixed ? SQCG_F32 : SQCG_F64; L.epi = EPI_TRUE_RESID;
+    L.in = ctx->tmp64; L.out = r0; L.out2 = p0;
+    L.y = x; L.b = b; L.sigma = sigma; L.fin = FIN_INIT;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    SQCG_TRY(read_state(ctx, s));
+    launches += 3;
+  }
 
   int status = SQCG_OK;
-  int launches = 5, loops = 0;
+  int loops = 0;
   if (h->bb == 0.0) {  // b = 0: the solution is x = 0
     SQCG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)ctx->g.Vh * 3 * sizeof(double2), s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));

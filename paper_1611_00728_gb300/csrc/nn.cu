@@ -551,6 +551,12 @@ struct sqcg_nn {
   float2* T;               // training taps [9][CH][2][3][Vh]
   float2 *d, *Ad, *tmp, *zbuf;  // even FP32 vectors (training) / odd temp
   float2 *r_old, *z;       // flexible CG vectors
+  // the captured flexible-CG loop, reused while b, x and the links stay the same
+  cudaGraphExec_t fcg_exec;
+  cudaGraphConditionalHandle fcg_hw, fcg_hif;
+  const void* fcg_b;
+  void* fcg_x;
+  unsigned long long fcg_gen;
   bool train_ready;
   int loss_norm;           // 1: A-norm of the error, 2: A^2-norm (preconditioned residual)
 };
@@ -779,6 +785,7 @@ int sqcg_nn_create(sqcg_ctx* ctx, sqcg_nn** out) {
 int sqcg_nn_destroy(sqcg_nn* nn) {
   if (!nn) return SQCG_OK;
   cudaStreamSynchronize(nn->ctx->stream);
+  if (nn->fcg_exec) cudaGraphExecDestroy(nn->fcg_exec);
   void* bufs[] = {nn->master, nn->wfwd, nn->wadj, nn->grad, nn->adam_m, nn->adam_v, nn->scal, nn->partials,
                   nn->h1, nn->h2, nn->a1, nn->a2, nn->g1, nn->g2, nn->g3, nn->T, nn->d, nn->Ad, nn->tmp,
                   nn->zbuf, nn->r_old, nn->z};
@@ -1130,15 +1137,36 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
   h->status = SQCG_OK;
   SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, s));
   SQCG_TRY(launch_norm2_f64(ctx, (const double2*)b, FIN_BB, s));
-  // r = b - A x0 (FP64) into r32; z = N(r); p = z; rz = <z, r>
-  DslashLaunch L = {};
-  L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
-  SQCG_TRY(launch_dslash(ctx, L, s));
-  L = DslashLaunch{};
-  L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = SQCG_F32; L.epi = EPI_TRUE_RESID; L.in = ctx->tmp64;
-  L.out = ctx->r32; L.y = x; L.b = b; L.sigma = sigma; L.fin = FIN_INIT;
-  SQCG_TRY(launch_dslash(ctx, L, s));
-  int launches = 5;
+  // |x0|^2: a zero initial guess has the exact initial residual r = b (no FP64 Dslash)
+  SQCG_TRY(launch_norm2_f64(ctx, (const double2*)x, FIN_STORE, s));
+  SQCG_CUDA_TRY(cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+  int launches = 4;
+  if (h->pAp == 0.0) {
+    SQCG_TRY(layout_convert(ctx, SQCG_F64, b, SQCG_F32, ctx->r32, s));
+    const double v = h->bb;  // the initial-residual step of the device state, |r|^2 = |b|^2
+    if (!isfinite(v)) {
+      h->status = SQCG_ERR_BREAKDOWN;
+      h->done = 1;
+    } else {
+      h->rr = h->rr_true = h->rr_max = h->rr_prev = v;
+      h->iter_last_update = 0;
+      if (v <= h->stop_rr) h->done = 1;
+    }
+    SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, s));
+    launches += 1;
+  } else {
+    // r = b - A x0 (FP64) into r32
+    DslashLaunch L = {};
+    L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    L = DslashLaunch{};
+    L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = SQCG_F32; L.epi = EPI_TRUE_RESID; L.in = ctx->tmp64;
+    L.out = ctx->r32; L.y = x; L.b = b; L.sigma = sigma; L.fin = FIN_INIT;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    launches += 3;
+  }
+  // then z = N(r); p = z; rz = <z, r>
   SQCG_CUDA_TRY(cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
   SQCG_CUDA_TRY(cudaStreamSynchronize(s));
   int status = SQCG_OK, fallback = 0, iters = 0, updates = 0;
@@ -1159,17 +1187,21 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
     k_copy2<<<nn_grid(3 * Vh), kThreads, 0, s>>>(nn->z, ctx->p32, 3 * Vh);
     SQCG_CUDA_TRY(cudaGetLastError());
     launches += 8;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle hw = 0, hif = 0;
-    SQCG_TRY(fcg_graph(nn, b, x, &exec, &hw, &hif));
+    if (!nn->fcg_exec || nn->fcg_b != b || nn->fcg_x != x || nn->fcg_gen != ctx->links_gen) {
+      SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+      if (nn->fcg_exec) cudaGraphExecDestroy(nn->fcg_exec);
+      nn->fcg_exec = nullptr;
+      SQCG_TRY(fcg_graph(nn, b, x, &nn->fcg_exec, &nn->fcg_hw, &nn->fcg_hif));
+      nn->fcg_b = b;
+      nn->fcg_x = x;
+      nn->fcg_gen = ctx->links_gen;
+    }
     SQCG_CUDA_TRY(cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h->done) {  // breakdown of the network output on the first residual
-      cudaGraphExecDestroy(exec);
-      exec = nullptr;
-    }
-    h->h_while = hw;
-    h->h_if = hif;
+    // no launch after a breakdown of the network output on the first residual
+    cudaGraphExec_t exec = h->done ? nullptr : nn->fcg_exec;
+    h->h_while = nn->fcg_hw;
+    h->h_if = nn->fcg_hif;
     h->use_if = 1;
     h->loop_count = 0;
     h->loop_limit = max_iter + 4;
@@ -1177,7 +1209,6 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
     cudaError_t e = exec ? cudaGraphLaunch(exec, s) : cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (exec) cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "flexible CG", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
     launches += h->loop_count * 14 + h->updates * 3;
     iters = h->iter;

@@ -167,3 +167,35 @@ def test_fcg_falls_back_to_plain_cg(sqcg, links_cache):
         assert info.fallback == 1 and info.status == 0
         assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
         net.close()
+
+
+def test_fcg_reuses_its_graph_and_follows_new_links(sqcg, links_cache):
+    """The captured flexible-CG loop is reused for the same buffers (identical iterates), starts from a
+    nonzero guess through the FP64 residual, and is recaptured when the links change."""
+    L, m, tol = (8, 8, 8, 8), 0.05, 1e-8
+    fat, lng = links_cache(L, 62)
+    fat2, lng2 = links_cache(L, 64)
+    b = synth.gaussian_source(L, 92)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(8, scale=0.3)))
+        db, x = lat.pack(b), lat.new_spinor()
+        i1 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
+        x1 = lat.unpack(x)
+        x.zero_()
+        i2 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
+        assert i1.status == i2.status == 0 and i1.iters == i2.iters
+        assert np.array_equal(x1, lat.unpack(x))
+        # nonzero initial guess: half the solution
+        x.copy_(lat.pack(0.5 * x1))
+        i3 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
+        assert i3.status == 0
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
+        # new links on the same context
+        lat.load_links(fat2, lng2)
+        x.zero_()
+        i4 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
+        assert i4.status == 0
+        assert oracle.true_rel_residual(L, fat2, lng2, 4 * m * m, b, lat.unpack(x)) <= tol
+        net.close()
