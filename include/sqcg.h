@@ -168,7 +168,10 @@ int sqcg_normal_op_noalloc(sqcg_ctx* ctx, double sigma, int prec, const void* x,
 
 /* Solve (4 mass^2 - D_eo D_oe) x = b on the even sites by CG (paper Sec. 3,
  * single-mass CG). b, x: FP64 device vectors; x holds the initial guess on
- * entry (zero it for x0 = 0) and the solution on return. Stops when the FP64
+ * entry (zero it for x0 = 0) and the solution on return. A zero guess is
+ * detected (|x0| = 0) and its initial residual is b itself, with no FP64
+ * operator application; any other guess starts from r = b - A x0 in FP64.
+ * Stops when the FP64
  * true relative residual |b - A x|/|b| <= tol, or after max_iter iterations
  * (SQCG_ERR_NOT_CONVERGED, x = last iterate). mode: SQCG_MODE_F64 or
  * SQCG_MODE_MIXED (FP32 Krylov vectors with FP64 reliable updates). info may
@@ -222,7 +225,9 @@ int sqcg_rational_apply(sqcg_ctx* ctx, int nshift, const double* shifts, const d
  * ctx[k]: distinct contexts with links loaded, all on the current device; the
  * work runs on ctx[0]'s stream. b[k], x[k]: device arrays of nrhs[k]
  * consecutive FP64 device vectors ([nrhs][3][Vh] complex double); x[k] holds
- * the initial guesses and receives the solutions. tol: FP64 true relative
+ * the initial guesses and receives the solutions (when every guess is zero the
+ * initial residuals are the b[k] themselves; otherwise r = b - A x0 in FP64 for
+ * all). tol: FP64 true relative
  * residual target for every RHS. info: NULL or sum(nrhs) entries, lattice-major.
  * Workspace (about 48 bytes per site and RHS) is cached with ctx[0] for
  * repeated calls with the same arguments. Returns SQCG_OK when every RHS
@@ -284,7 +289,10 @@ int sqcg_make_training_pair(sqcg_ctx* ctx, double sigma, const void* b, const vo
  * solution out). On breakdown (<p,Ap> <= 0, <z,r> <= 0, non-finite) or
  * without convergence it hands over to the mixed-precision CG from the
  * current iterate (info->fallback = 1), which also confirms the answer on the
- * FP64 true residual. nn must be bound to ctx. Synchronises. */
+ * FP64 true residual. nn must be bound to ctx. The captured solver loop is
+ * kept with nn and reused while b, x and the context's links stay the same
+ * (the weights and the mass are read on the device, so they may change).
+ * A zero initial guess starts from r = b. Synchronises. */
 int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const void* b, void* x, double tol, int max_iter,
                       sqcg_info* info);
 
