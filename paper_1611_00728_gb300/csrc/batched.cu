@@ -21,6 +21,7 @@
 #include <chrono>
 #include <map>
 #include <math.h>
+#include <mutex>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -801,6 +802,13 @@ struct TuneChoice {
   int W, WT, T, carve;
 };
 
+// Guards the process-wide tuning state (the cache and file, and the per-kernel shared-memory
+// attributes) when several host threads run batched solves on their own contexts.
+std::recursive_mutex& tune_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
+
 std::map<std::string, TuneChoice>& tune_cache() {
   static std::map<std::string, TuneChoice> m;
   return m;
@@ -920,6 +928,7 @@ int launch_finish_b(const BatchPlan& P, int fin, int blas, cudaStream_t s) {
 // more of the SM's 256 KB to L1, which serves the neighbour gathers, at fewer resident blocks.
 // Set outside graph capture (by the tuner, before the plan's graph is captured).
 int set_carve(int WT, int carve) {
+  std::lock_guard<std::recursive_mutex> lock(tune_mutex());
   static int cur[3] = {-2, -2, -2};
   const int k = WT == 1 ? 0 : WT == 2 ? 1 : WT == 4 ? 2 : -1;
   if (k < 0) return SQCG_ERR_INVALID_ARG;
@@ -935,6 +944,7 @@ int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaS
   const int G = P.W / P.WT, T = P.T;
   if (T * G > kMaxThreads || T % 32) return SQCG_ERR_INVALID_ARG;
   const size_t smem = (size_t)kHops * 9 * T * sizeof(float2);
+  std::lock_guard<std::recursive_mutex> lock(tune_mutex());
   static bool attr_set[3] = {false, false, false};  // per WT instantiation
   const MArgs a = margs(P, par, in_vec, epi, gate, 0);
   const dim3 block(T, G);
@@ -970,6 +980,7 @@ int upload_lats(BatchPlan& P, cudaStream_t s) {
 
 // time the FP32 multi-RHS Dslash over the batch for each (W, WT, T); keep the fastest
 int autotune(BatchPlan& P, cudaStream_t s) {
+  std::lock_guard<std::recursive_mutex> lock(tune_mutex());
   tune_file_load();
   const std::string key = tune_key(P);
   auto it = tune_cache().find(key);

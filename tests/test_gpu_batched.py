@@ -112,3 +112,37 @@ def test_batched_full_workload(sqcg, links_cache):
             assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], x) <= tol
     for lat in lats:
         lat.close()
+
+
+def test_batched_from_two_host_threads(sqcg, links_cache):
+    """Two host threads, each with its own contexts, tune and solve at the same time (the tuning state is
+    process-wide and guarded); both answers are checked against the oracle."""
+    import threading
+
+    specs = [((8, 8, 8, 8), 2, 0.1, 300), ((6, 8, 10, 12), 3, 0.08, 301)]
+    results, errors = {}, []
+
+    def work(k, L, nr, m, seed):
+        try:
+            fat, lng = links_cache(L, seed)
+            with sqcg.Lattice(L) as lat:
+                lat.load_links(fat, lng)
+                srcs = [synth.gaussian_source(L, 7100 + 10 * k + j) for j in range(nr)]
+                b, x = make_batch(sqcg, lat, srcs)
+                infos = sqcg.cg_solve_batched([lat], [m], [b], [x], tol=1e-9)[0]
+                results[k] = [(i.status, oracle.true_rel_residual(L, fat, lng, 4 * m * m, s, lat.unpack(x[j])))
+                              for j, (i, s) in enumerate(zip(infos, srcs))]
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    # links first (the fixture caches them), then the threads
+    for k, (L, nr, m, seed) in enumerate(specs):
+        links_cache(L, seed)
+    threads = [threading.Thread(target=work, args=(k, *spec)) for k, spec in enumerate(specs)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for k in range(len(specs)):
+        assert all(st == 0 and res <= 1e-9 for st, res in results[k]), results[k]
