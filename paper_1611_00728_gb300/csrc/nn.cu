@@ -138,8 +138,15 @@ struct ConvArgs {
   int npar;
 };
 
+// the 8 -> 8 layer holds 8 x 3 complex accumulators: it gets the registers of 3 resident
+// blocks per SM (no spills) instead of 4
+template <int CIN, int COUT>
+struct ConvOcc {
+  static constexpr int blocks = (CIN > 1 && COUT > 1) ? 3 : 4;
+};
+
 template <int CIN, int COUT, int IN, int OUT>
-__global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
+__global__ void __launch_bounds__(kThreads, ConvOcc<CIN, COUT>::blocks) k_conv(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
   __shared__ float2 W[NT * COUT * CIN];
   for (int j = threadIdx.x; j < NT * COUT * CIN; j += blockDim.x) W[j] = a.W[j];
