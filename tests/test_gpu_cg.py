@@ -388,3 +388,37 @@ def test_pack_unpack_round_trip(sqcg, prec):
     else:  # round to nearest FP32, component by component
         want = psi.real.astype(np.float32).astype(np.float64) + 1j * psi.imag.astype(np.float32).astype(np.float64)
         assert np.array_equal(got, want)
+
+
+def test_everything_on_a_side_stream(sqcg, links_cache):
+    """All work on a non-default torch stream: the binding hands the current stream to the context before
+    each call, graphs launch on it, and the results match the oracle."""
+    import torch
+
+    L, m, tol = (6, 8, 10, 12), 0.05, 1e-9
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 4600)
+    psi = synth.gaussian_source(L, 4601)
+    side = torch.cuda.Stream()
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        with torch.cuda.stream(side):
+            db = lat.pack(b)
+            out = lat.new_spinor()
+            lat.dslash(1, lat.pack(psi), out)
+            x = lat.new_spinor()
+            info = lat.cg_solve(m, db, x, tol=tol, mode=sqcg.MODE_MIXED)
+            xs = [lat.new_spinor() for _ in range(3)]
+            ms = lat.multishift_cg_solve([0.01, 0.1, 1.0], db, xs, tol=tol, mode=sqcg.MODE_MIXED)
+            bb = torch.stack([lat.pack(synth.gaussian_source(L, 4610 + j)) for j in range(2)]).contiguous()
+            xb = torch.zeros_like(bb)
+            bi = sqcg.cg_solve_batched([lat], [m], [bb], [xb], tol=tol)[0]
+        side.synchronize()
+        assert rel(lat.unpack(out), oracle.dslash(L, fat, lng, psi, 1)) <= 1e-12
+        assert info.status == 0 and oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
+        for s, i, xx in zip([0.01, 0.1, 1.0], ms, xs):
+            assert i.status == 0 and oracle.true_rel_residual(L, fat, lng, s, b, lat.unpack(xx)) <= tol
+        for j in range(2):
+            src = synth.gaussian_source(L, 4610 + j)
+            assert bi[j].status == 0
+            assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, src, lat.unpack(xb[j])) <= tol
