@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
+    ap.add_argument("--links", choices=["recon12", "full", "8way", "8way-recon12"], default="recon12",
+                    help="--dslash-only: the FP32 link storage to time (default: 12-real long links, as the solvers)")
     ap.add_argument("--lattice", default=None,
                     help="hisq and batched workloads: extents as Lx,Ly,Lz,Lt (hisq default 32^4; batched: one "
                          "lattice with 16 sources instead of the three; for profiling)")
@@ -363,8 +365,12 @@ def run_ours(args, ranks: Ranks):
     peak, peak_kind = hbm_peak()
 
     if args.dslash_only:
+        if args.links != "recon12":
+            lat.close()
+            lat = sq.Lattice(LATTICE)
+            lat.load_links(fat, lng, recon12=args.links.endswith("recon12"), eight_way=args.links.startswith("8way"))
         t = time_dslash(torch, lat, sq, sq.F32, 20)
-        print(json.dumps({"dslash_f32_recon12_ms": t * 1e3}), flush=True)
+        print(json.dumps({f"dslash_f32_{args.links}_ms": t * 1e3}), flush=True)
         return
 
     b = lat.pack(b_host)
