@@ -54,6 +54,7 @@ struct LatDev {
   int nrb64, rb640;  // FP64 RHS blocks of width min(W, kW64)
   int tile0, tile640;  // first FP32 / FP64 tile
   int nsb_b, tile0_b;  // BLAS tiling: site blocks of kTB sites, first BLAS tile
+  int sbt0;            // first BLAS site block of this lattice over all lattices
   float2 *r, *p, *Ap, *tmp;  // [nrhs][3][Vh]
   double2* x;
   double2* tmp64;
@@ -635,93 +636,91 @@ struct BArgs {
   int W;
 };
 
-template <int W>
+// One thread per (site, RHS): blockIdx.x runs over the kTB-site blocks of all lattices,
+// blockIdx.y over the RHS of a lattice. Every thread streams its own three colour
+// components, so all loads of a block are independent and in flight together. Per-RHS
+// sums go to partials[rhs][site block] for k_batch_finish.
 __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
-  const int tile = blockIdx.x;
   int k = 0;
   for (int j = 1; j < a.nlat; ++j)
-    if (tile >= a.lats[j].tile0_b) k = j;
+    if ((int)blockIdx.x >= a.lats[j].sbt0) k = j;
   const LatDev& L = a.lats[k];
-  const int local = tile - L.tile0_b;
-  const int rb = local % L.nrb, sb = local / L.nrb;
-  const int wbase = rb * W;
-  const int nw = min(W, L.nrhs - wbase);
-  const int blk = L.rb0 + rb;
-  if (a.op != B_NORM_B && a.op != B_NORM_X && a.op != B_INIT_B && !a.st->blk_active[blk]) return;
+  const int w = blockIdx.y;
+  if (w >= L.nrhs) return;
+  const int sb = blockIdx.x - L.sbt0;
+  const int rhs = L.rhs0 + w;
+  const bool all = (a.op == B_NORM_B || a.op == B_NORM_X || a.op == B_INIT_B);
+  if (!all && (!a.st->blk_active[L.rb0 + w / a.W] || !a.st->r[rhs].active)) return;
   const int Vh = L.g.Vh;
+  const size_t base = (size_t)w * 3 * Vh;
+  const double2* __restrict__ b = L.b + (size_t)w * L.b_stride;
+  double2* __restrict__ x = L.x + base;
+  float2* __restrict__ r = L.r + base;
+  float2* __restrict__ p = L.p + base;
+  const float2* __restrict__ Ap = L.Ap + base;
+  const double alpha = a.st->r[rhs].alpha, beta = a.st->r[rhs].beta;
   const int i = sb * blockDim.x + threadIdx.x;
-  double part[W];
-#pragma unroll
-  for (int w = 0; w < W; ++w) part[w] = 0.0;
+  double part = 0.0;
   if (i < Vh) {
+    if (a.op == B_NORM_B || a.op == B_NORM_X || a.op == B_INIT_B) {
+      const double2* v = (a.op == B_NORM_X) ? x : b;
+      double2 vc[3];
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      if (w >= nw) continue;
-      const RhsScalars& s = a.st->r[L.rhs0 + wbase + w];
-      const size_t base = (size_t)(wbase + w) * 3 * Vh;
-      if (a.op == B_NORM_B) {
-        double n2 = 0.0;
+      for (int c = 0; c < 3; ++c) vc[c] = v[(size_t)c * Vh + i];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double2 v = L.b[(size_t)(wbase + w) * L.b_stride + (size_t)c * Vh + i];
-          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
+      for (int c = 0; c < 3; ++c) {
+        part = fma(vc[c].x, vc[c].x, fma(vc[c].y, vc[c].y, part));
+        if (a.op == B_INIT_B) {
+          const float2 f = make_float2((float)vc[c].x, (float)vc[c].y);
+          r[(size_t)c * Vh + i] = f;
+          p[(size_t)c * Vh + i] = f;
         }
-        part[w] = n2;
-      } else if (a.op == B_NORM_X) {
-        double n2 = 0.0;
+      }
+    } else if (a.op == B_UPDATE) {
+      const float fa = (float)alpha;
+      float2 pc[3], apc[3], rc[3];
+      double2 xc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double2 v = L.x[base + (size_t)c * Vh + i];
-          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
-        }
-        part[w] = n2;
-      } else if (a.op == B_INIT_B) {
-        double n2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = (size_t)c * Vh + i;
+        pc[c] = p[o];
+        apc[c] = Ap[o];
+        rc[c] = r[o];
+        xc[c] = x[o];
+      }
+      float n2 = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double2 v = L.b[(size_t)(wbase + w) * L.b_stride + (size_t)c * Vh + i];
-          const float2 f = make_float2((float)v.x, (float)v.y);
-          L.r[base + (size_t)c * Vh + i] = f;
-          L.p[base + (size_t)c * Vh + i] = f;
-          n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
-        }
-        part[w] = n2;
-      } else if (!s.active) {
-        continue;
-      } else if (a.op == B_UPDATE) {
-        const double al = s.alpha;
-        const float fa = (float)al;
-        float n2 = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = (size_t)c * Vh + i;
+        xc[c].x = fma(alpha, (double)pc[c].x, xc[c].x);
+        xc[c].y = fma(alpha, (double)pc[c].y, xc[c].y);
+        x[o] = xc[c];
+        rc[c].x = fmaf(-fa, apc[c].x, rc[c].x);
+        rc[c].y = fmaf(-fa, apc[c].y, rc[c].y);
+        r[o] = rc[c];
+        n2 = fmaf(rc[c].x, rc[c].x, fmaf(rc[c].y, rc[c].y, n2));
+      }
+      part = (double)n2;
+    } else {  // B_XPAY
+      const float be = (float)beta;
+      float2 rc[3], pc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const size_t o = base + (size_t)c * Vh + i;
-          const float2 pc = L.p[o], apc = L.Ap[o];
-          float2 rc = L.r[o];
-          double2 xc = L.x[o];
-          xc.x = fma(al, (double)pc.x, xc.x);
-          xc.y = fma(al, (double)pc.y, xc.y);
-          L.x[o] = xc;
-          rc.x = fmaf(-fa, apc.x, rc.x);
-          rc.y = fmaf(-fa, apc.y, rc.y);
-          L.r[o] = rc;
-          n2 = fmaf(rc.x, rc.x, fmaf(rc.y, rc.y, n2));
-        }
-        part[w] = (double)n2;
-      } else {  // B_XPAY
-        const float be = (float)s.beta;
+      for (int c = 0; c < 3; ++c) {
+        rc[c] = r[(size_t)c * Vh + i];
+        pc[c] = p[(size_t)c * Vh + i];
+      }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const size_t o = base + (size_t)c * Vh + i;
-          const float2 rc = L.r[o];
-          float2 pc = L.p[o];
-          pc.x = fmaf(be, pc.x, rc.x);
-          pc.y = fmaf(be, pc.y, rc.y);
-          L.p[o] = pc;
-        }
+      for (int c = 0; c < 3; ++c) {
+        pc[c].x = fmaf(be, pc[c].x, rc[c].x);
+        pc[c].y = fmaf(be, pc[c].y, rc[c].y);
+        p[(size_t)c * Vh + i] = pc[c];
       }
     }
   }
-  if (a.op != B_XPAY) rhs_block_partial<W>(part, L, wbase, nw, sb, a.partials, a.max_nsb);
+  if (a.op != B_XPAY) {
+    const double t = block_sum(part);
+    if (threadIdx.x == 0) a.partials[(size_t)rhs * a.max_nsb + sb] = t;
+  }
 }
 
 // One thread: which RHS blocks need the FP64 reliable update -> IF condition
@@ -854,7 +853,7 @@ std::string tune_key(const BatchPlan& P) {
 
 // tiles, blocks and first indices for a given W and T
 void layout_tiles(BatchPlan& P, int W, int WT, int T) {
-  int tile = 0, tile64 = 0, tileb = 0, rb0 = 0, rb640 = 0;
+  int tile = 0, tile64 = 0, tileb = 0, rb0 = 0, rb640 = 0, sbt = 0;
   const int W64 = W < kW64 ? W : kW64;
   for (int k = 0; k < P.nlat; ++k) {
     LatDev& L = P.host[k];
@@ -867,6 +866,8 @@ void layout_tiles(BatchPlan& P, int W, int WT, int T) {
     L.tile640 = tile64;
     L.nsb_b = grid_for(L.g.Vh, kTB);
     L.tile0_b = tileb;
+    L.sbt0 = sbt;
+    sbt += L.nsb_b;
     tileb += L.nsb_b * L.nrb;
     tile += L.nsb * L.nrb;
     tile64 += L.nsb * L.nrb64;
@@ -899,14 +900,12 @@ int launch_mrhs_dslash_w(int WT, int G, int grid, int T, cudaStream_t s, const M
 int launch_mrhs_blas(const BatchPlan& P, int op, cudaStream_t s) {
   BArgs a;
   a.lats = P.dev; a.nlat = P.nlat; a.op = op; a.st = P.st; a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W;
-  switch (P.W) {
-    case 1: k_mrhs_blas<1><<<P.ntiles_b, kTB, 0, s>>>(a); break;
-    case 2: k_mrhs_blas<2><<<P.ntiles_b, kTB, 0, s>>>(a); break;
-    case 4: k_mrhs_blas<4><<<P.ntiles_b, kTB, 0, s>>>(a); break;
-    case 8: k_mrhs_blas<8><<<P.ntiles_b, kTB, 0, s>>>(a); break;
-    case 16: k_mrhs_blas<16><<<P.ntiles_b, kTB, 0, s>>>(a); break;
-    default: return SQCG_ERR_INVALID_ARG;
+  int maxr = 0, nsb = 0;
+  for (int k = 0; k < P.nlat; ++k) {
+    maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
+    nsb += P.host[k].nsb_b;
   }
+  k_mrhs_blas<<<dim3(nsb, maxr), kTB, 0, s>>>(a);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }
