@@ -27,21 +27,29 @@ k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const ty
   const R ra = (R)alpha;
   double nrm = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    // all loads before any store: the colour offsets of one array are not provably distinct,
+    // so interleaved stores would hold back the next colour's loads
+    R2 pc[3], apc[3], rc[3];
+    double2 xc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      pc[c] = p[k];
+      apc[c] = Ap[k];
+      rc[c] = r[k];
+      xc[c] = x[k];
+    }
     R part = R(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * Vh + i;
-      const R2 pc = p[k];
-      const R2 apc = Ap[k];
-      R2 rc = r[k];
-      double2 xc = x[k];
-      xc.x = fma(alpha, (double)pc.x, xc.x);
-      xc.y = fma(alpha, (double)pc.y, xc.y);
-      x[k] = xc;
-      rc.x = fma(-ra, apc.x, rc.x);
-      rc.y = fma(-ra, apc.y, rc.y);
-      r[k] = rc;
-      part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
+      xc[c].x = fma(alpha, (double)pc[c].x, xc[c].x);
+      xc[c].y = fma(alpha, (double)pc[c].y, xc[c].y);
+      x[k] = xc[c];
+      rc[c].x = fma(-ra, apc[c].x, rc[c].x);
+      rc[c].y = fma(-ra, apc[c].y, rc[c].y);
+      r[k] = rc[c];
+      part = fma(rc[c].x, rc[c].x, fma(rc[c].y, rc[c].y, part));
     }
     nrm += (double)part;
   }
@@ -56,14 +64,17 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
   if (!gate_open(st, GATE_ITER)) return;
   const R beta = (R)st->beta;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    R2 rc[3], pc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const size_t k = (size_t)c * Vh + i;
-      const R2 rc = r[k];
-      R2 pc = p[k];
-      pc.x = fma(beta, pc.x, rc.x);
-      pc.y = fma(beta, pc.y, rc.y);
-      p[k] = pc;
+      rc[c] = r[(size_t)c * Vh + i];
+      pc[c] = p[(size_t)c * Vh + i];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pc[c].x = fma(beta, pc[c].x, rc[c].x);
+      pc[c].y = fma(beta, pc[c].y, rc[c].y);
+      p[(size_t)c * Vh + i] = pc[c];
     }
   }
 }
@@ -108,16 +119,19 @@ k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restri
   const R ra = (R)st->alpha;
   double nrm = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    R2 rc[3], apc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rc[c] = r[(size_t)c * Vh + i];
+      apc[c] = Ap[(size_t)c * Vh + i];
+    }
     R part = R(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const size_t k = (size_t)c * Vh + i;
-      R2 rc = r[k];
-      const R2 apc = Ap[k];
-      rc.x = fma(-ra, apc.x, rc.x);
-      rc.y = fma(-ra, apc.y, rc.y);
-      r[k] = rc;
-      part = fma(rc.x, rc.x, fma(rc.y, rc.y, part));
+      rc[c].x = fma(-ra, apc[c].x, rc[c].x);
+      rc[c].y = fma(-ra, apc[c].y, rc[c].y);
+      r[(size_t)c * Vh + i] = rc[c];
+      part = fma(rc[c].x, rc[c].x, fma(rc[c].y, rc[c].y, part));
     }
     nrm += (double)part;
   }
@@ -151,20 +165,26 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
       const R z = (j == 0) ? R(1) : (R)st->zeta[j];
       const R bs = (j == 0) ? (R)st->beta : (R)st->beta_s[j];
       double2* xs = P.x[j];
+      R2 pc[3];
+      double2 xc[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {  // loads before stores (see k_cg_update)
+        pc[c] = ps[(size_t)c * Vh + i];
+        if (act) xc[c] = xs[(size_t)c * Vh + i];
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t k = (size_t)c * Vh + i;
-        R2 pc = ps[k];
         if (act) {
-          double2 xc = xs[k];
-          xc.x = fma(as, (double)pc.x, xc.x);
-          xc.y = fma(as, (double)pc.y, xc.y);
-          xs[k] = xc;
+          xc[c].x = fma(as, (double)pc[c].x, xc[c].x);
+          xc[c].y = fma(as, (double)pc[c].y, xc[c].y);
+          xs[k] = xc[c];
         }
         if (upd_p) {
-          pc.x = fma(bs, pc.x, z * rc[c].x);
-          pc.y = fma(bs, pc.y, z * rc[c].y);
-          ps[k] = pc;
+          R2 pn;
+          pn.x = fma(bs, pc[c].x, z * rc[c].x);
+          pn.y = fma(bs, pc[c].y, z * rc[c].y);
+          ps[k] = pn;
         }
       }
     }
