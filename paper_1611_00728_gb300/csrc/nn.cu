@@ -908,21 +908,29 @@ __global__ void __launch_bounds__(kRedThreads) k_fcg_update(double2* __restrict_
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0.0;
   if (i < Vh) {
+    // every colour component is loaded before any store, so the loads overlap
+    float2 pc[3], qc[3], rc[3];
+    double2 xc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      pc[c] = p[k];
+      qc[c] = q[k];
+      rc[c] = r[k];
+      xc[c] = x[k];
+    }
     float part = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * Vh + i;
-      const float2 pc = p[k], qc = q[k];
-      float2 rc = r[k];
-      r_old[k] = rc;
-      double2 xc = x[k];
-      xc.x = fma(alpha, (double)pc.x, xc.x);
-      xc.y = fma(alpha, (double)pc.y, xc.y);
-      x[k] = xc;
-      rc.x = fmaf(-fa, qc.x, rc.x);
-      rc.y = fmaf(-fa, qc.y, rc.y);
-      r[k] = rc;
-      part = fmaf(rc.x, rc.x, fmaf(rc.y, rc.y, part));
+      r_old[k] = rc[c];
+      xc[c].x = fma(alpha, (double)pc[c].x, xc[c].x);
+      xc[c].y = fma(alpha, (double)pc[c].y, xc[c].y);
+      x[k] = xc[c];
+      rc[c].x = fmaf(-fa, qc[c].x, rc[c].x);
+      rc[c].y = fmaf(-fa, qc[c].y, rc[c].y);
+      r[k] = rc[c];
+      part = fmaf(rc[c].x, rc[c].x, fmaf(rc[c].y, rc[c].y, part));
     }
     nrm = (double)part;
   }
