@@ -138,15 +138,10 @@ struct ConvArgs {
   int npar;
 };
 
-// the 8 -> 8 layer holds 8 x 3 complex accumulators: it gets the registers of 3 resident
-// blocks per SM (no spills) instead of 4
-template <int CIN, int COUT>
-struct ConvOcc {
-  static constexpr int blocks = (CIN > 1 && COUT > 1) ? 3 : 4;
-};
-
+// one lane per site: the layers with one input or one output channel (the 8 -> 8 layer is
+// k_conv88 below)
 template <int CIN, int COUT, int IN, int OUT>
-__global__ void __launch_bounds__(kThreads, ConvOcc<CIN, COUT>::blocks) k_conv(ConvArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
   __shared__ float2 W[NT * COUT * CIN];
   for (int j = threadIdx.x; j < NT * COUT * CIN; j += blockDim.x) W[j] = a.W[j];
@@ -260,6 +255,106 @@ __global__ void __launch_bounds__(kThreads, ConvOcc<CIN, COUT>::blocks) k_conv(C
         if (OUT == OUT_GATE_TRAIN) a.pre[k] = acc[o][c];
         a.out[k] = make_float2(acc[o][c].x * gf, acc[o][c].y * gf);
       }
+    }
+  }
+}
+
+// The 8 -> 8 layer with two lanes per site. Each lane accumulates 4 of the 8 output
+// channels and transports 4 of the 8 input channels per hop; the two lanes swap their
+// transported vectors with a warp shuffle, so no product is done twice and a lane holds half
+// the accumulators of the one-lane form (more resident warps to hide the neighbour loads).
+// Lanes past the end compute on a clamped site and store nothing, so every lane of a warp
+// takes part in the shuffles.
+template <int OUT>
+__global__ void __launch_bounds__(kThreads) k_conv88(ConvArgs a) {
+  if (a.st && !gate_open(a.st, a.gate)) return;
+  __shared__ float2 W[NT * CH * CH];
+  for (int j = threadIdx.x; j < NT * CH * CH; j += blockDim.x) W[j] = a.W[j];
+  __syncthreads();
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = gid & 1;  // this lane's half of the channels
+  const int site = gid >> 1;
+  const bool valid = site < a.npar * Vh;
+  const int sv = valid ? site : 0;
+  const int par = a.par0 + sv / Vh;
+  const int i = sv % Vh;
+  const int q = 1 - par;
+  const Site s = site_of(g, i, par);
+
+  float2 acc[4][3];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[o][c] = make_float2(0.f, 0.f);
+  auto load_in = [&](int ci, int pp, int j, float2 (&v)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)ci * 2 + pp) * 3 + c) * Vh + j);
+  };
+  auto mix1 = [&](int tap, int ci, const float2 (&t)[3]) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float2 w = W[(tap * CH + 4 * h + o) * CH + ci];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cmac(acc[o][c], w, t[c]);
+    }
+  };
+  // self tap: every input channel at the site (the partner lane reads the same values, from L1)
+#pragma unroll 2
+  for (int ci = 0; ci < CH; ++ci) {
+    float2 v[3];
+    load_in(ci, par, i, v);
+    mix1(0, ci, v);
+  }
+  // hops
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      const int j = nbr(g, s, mu, dir == 0 ? +1 : -1);
+      const int tap = 1 + 2 * mu + dir;
+      float2 t[4][3];
+      {
+        float2 u[9];
+        if (dir == 0) load_link9(a.fat[par] + (size_t)mu * 9 * Vh, Vh, i, u);  // F_mu(n)
+        else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);             // F_mu(n - mu)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float2 v[3];
+          load_in(4 * h + k, q, j, v);
+          apply_link(u, dir == 1, v, t[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 pt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pt[c].x = __shfl_xor_sync(0xffffffffu, t[k][c].x, 1);
+          pt[c].y = __shfl_xor_sync(0xffffffffu, t[k][c].y, 1);
+        }
+        mix1(tap, 4 * h + k, t[k]);
+        mix1(tap, 4 * (1 - h) + k, pt);
+      }
+    }
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int o4 = 0; o4 < 4; ++o4) {
+    const int o = 4 * h + o4;
+    float gf = 1.f;
+    if (OUT == OUT_GATE_TRAIN || OUT == OUT_GATE_INFER) {
+      float n2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) n2 = fmaf(acc[o4][c].x, acc[o4][c].x, fmaf(acc[o4][c].y, acc[o4][c].y, n2));
+      gf = 1.f / (1.f + __expf(-(a.gate_a[o] * n2 + a.gate_b[o])));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t kk = (((size_t)o * 2 + par) * 3 + c) * Vh + i;
+      if (OUT == OUT_GATE_TRAIN) a.pre[kk] = acc[o4][c];
+      a.out[kk] = make_float2(acc[o4][c].x * gf, acc[o4][c].y * gf);
     }
   }
 }
@@ -593,6 +688,7 @@ int conv_launch(sqcg_nn* nn, int layer, bool adjoint, int in_mode, int out_mode,
   a.par0 = par0;
   a.npar = npar;
   const int grid = nn_grid(npar * (int)Vh);
+  const int grid2 = nn_grid(2 * npar * (int)Vh);  // the two-lane 8 -> 8 kernel
   // channel counts of the (possibly adjoint) layer
   int cin = (layer == 0) ? 1 : CH, cout = (layer == 2) ? 1 : CH;
   if (adjoint) { const int t = cin; cin = cout; cout = t; }
@@ -601,11 +697,11 @@ int conv_launch(sqcg_nn* nn, int layer, bool adjoint, int in_mode, int out_mode,
   else if (cin == 1 && cout == CH && in_mode == IN_EVEN_SCALED && out_mode == OUT_GATE_TRAIN)
     k_conv<1, CH, IN_EVEN_SCALED, OUT_GATE_TRAIN><<<grid, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_INFER)
-    k_conv<CH, CH, IN_FULL, OUT_GATE_INFER><<<grid, kThreads, 0, s>>>(a);
+    k_conv88<OUT_GATE_INFER><<<grid2, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_TRAIN)
-    k_conv<CH, CH, IN_FULL, OUT_GATE_TRAIN><<<grid, kThreads, 0, s>>>(a);
+    k_conv88<OUT_GATE_TRAIN><<<grid2, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_FULL)
-    k_conv<CH, CH, IN_FULL, OUT_FULL><<<grid, kThreads, 0, s>>>(a);
+    k_conv88<OUT_FULL><<<grid2, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == 1 && in_mode == IN_FULL && out_mode == OUT_EVEN_SCALED)
     k_conv<CH, 1, IN_FULL, OUT_EVEN_SCALED><<<grid, kThreads, 0, s>>>(a);
   else if (cin == 1 && cout == CH && in_mode == IN_FULL && out_mode == OUT_FULL)
