@@ -346,6 +346,20 @@ int sqcg_hisq_load_links(sqcg_ctx* ctx, const double* thin, const sqcg_hisq_coef
  * batched solve cached with ctx (the ctx passed first to the last batched call). */
 int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T);
 
+/* The full FP32 Dslash configuration of that batched solve: RHS block width W,
+ * right-hand sides per thread WT (W / WT thread groups per site block), site
+ * block T and shared-memory carveout in percent (-1 = the driver's default).
+ * Any output pointer may be NULL. */
+int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve);
+
+/* Pin the FP32 Dslash configuration of batched solves planned from now on in
+ * this process instead of autotuning it (plans already cached with a context
+ * keep theirs); W = 0 returns to autotuning. Requirements: W in {1, 2, 4, 8,
+ * 16}; WT in {1, 2, 4}, WT <= W; T a multiple of 32 in [32, 128] with
+ * T * W / WT <= 512; carve -1 or 0..100. SQCG_ERR_INVALID_ARG otherwise
+ * (nothing changes). Thread-safe. */
+int sqcg_batched_pin_tuning(int W, int WT, int T, int carve);
+
 const char* sqcg_strerror(int status);
 
 #ifdef __cplusplus

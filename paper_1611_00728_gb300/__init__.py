@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
-    "batched_tuning", "Network", "NN_NPARAMS", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
+    "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
     "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK",
 ]
 
@@ -122,6 +122,8 @@ def library():
         lib.sqcg_rational_apply.argtypes = [P, I, P, P, D, P, P, D, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
         lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.sqcg_batched_tuning_ex.argtypes = [P] + [ctypes.POINTER(I)] * 4
+        lib.sqcg_batched_pin_tuning.argtypes = [I] * 4
         lib.sqcg_nn_create.argtypes = [P, ctypes.POINTER(P)]
         lib.sqcg_nn_destroy.argtypes = [P]
         lib.sqcg_nn_nparams.argtypes = []
@@ -147,6 +149,7 @@ def library():
                      "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
                      "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply",
+                     "sqcg_batched_tuning_ex", "sqcg_batched_pin_tuning",
                      "sqcg_hisq_smear", "sqcg_hisq_load_links"):
             getattr(lib, name).restype = I
         _lib = lib
@@ -389,6 +392,20 @@ def batched_tuning(lattice) -> tuple[int, int]:
     W, T = ctypes.c_int(), ctypes.c_int()
     _check(library().sqcg_batched_tuning(lattice._h, ctypes.byref(W), ctypes.byref(T)), "sqcg_batched_tuning")
     return W.value, T.value
+
+
+def batched_tuning_ex(lattice) -> dict:
+    """The full FP32 Dslash configuration of the last batched solve led by lattice:
+    W, WT (RHS per thread), T and carve (shared-memory carveout in percent, -1 = default)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(library().sqcg_batched_tuning_ex(lattice._h, *[ctypes.byref(c) for c in v]), "sqcg_batched_tuning_ex")
+    return dict(zip(("W", "WT", "T", "carve"), (c.value for c in v)))
+
+
+def pin_batched_tuning(W: int, WT: int = 1, T: int = 64, carve: int = -1):
+    """Pin the FP32 Dslash configuration of batched solves planned from now on (W = 0: autotune again)."""
+    _check(library().sqcg_batched_pin_tuning(int(W), int(WT), int(T), int(carve)),
+           "sqcg_batched_pin_tuning")
 
 
 class Network:

@@ -808,6 +808,11 @@ std::recursive_mutex& tune_mutex() {
   return m;
 }
 
+TuneChoice& tune_pin() {  // W = 0: autotune
+  static TuneChoice c = {0, 0, 0, -1};
+  return c;
+}
+
 std::map<std::string, TuneChoice>& tune_cache() {
   static std::map<std::string, TuneChoice> m;
   return m;
@@ -985,6 +990,13 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   auto it = tune_cache().find(key);
   int maxr = 0;
   for (int k = 0; k < P.nlat; ++k) maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
+  if (tune_pin().W > 0) {
+    const TuneChoice& c = tune_pin();
+    layout_tiles(P, c.W, c.WT, c.T);
+    P.carve = c.carve;
+    SQCG_TRY(set_carve(P.WT, P.carve));
+    return upload_lats(P, s);
+  }
   if (it != tune_cache().end()) {
     layout_tiles(P, it->second.W, it->second.WT, it->second.T);
     P.carve = it->second.carve;
@@ -1370,5 +1382,29 @@ extern "C" int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T) {
   if (!ctx || !ctx->batch || !W || !T) return SQCG_ERR_INVALID_ARG;
   *W = ctx->batch->W;
   *T = ctx->batch->T;
+  return SQCG_OK;
+}
+
+extern "C" int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve) {
+  if (!ctx || !ctx->batch) return SQCG_ERR_INVALID_ARG;
+  const BatchPlan& P = *ctx->batch;
+  if (W) *W = P.W;
+  if (WT) *WT = P.WT;
+  if (T) *T = P.T;
+  if (carve) *carve = P.carve;
+  return SQCG_OK;
+}
+
+extern "C" int sqcg_batched_pin_tuning(int W, int WT, int T, int carve) {
+  std::lock_guard<std::recursive_mutex> lock(tune_mutex());
+  if (W == 0) {
+    tune_pin() = {0, 0, 0, -1};
+    return SQCG_OK;
+  }
+  if ((W != 1 && W != 2 && W != 4 && W != 8 && W != 16) || (WT != 1 && WT != 2 && WT != 4) || WT > W)
+    return SQCG_ERR_INVALID_ARG;
+  if (T < 32 || T > kMaxTSmem || T % 32 || T * (W / WT) > kMaxThreads) return SQCG_ERR_INVALID_ARG;
+  if (carve < -1 || carve > 100) return SQCG_ERR_INVALID_ARG;
+  tune_pin() = {W, WT, T, carve};
   return SQCG_OK;
 }

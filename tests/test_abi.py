@@ -102,3 +102,18 @@ def test_host_side_argument_checks(libpath):
     assert lib.sqcg_hisq_workspace_bytes((ctypes.c_int * 4)(32, 32, 32, 32)) == 56 * 9 * V * 16 + 256
     assert lib.sqcg_hisq_workspace_bytes((ctypes.c_int * 4)(4, 4, 4, 3)) == 0
     assert lib.sqcg_hisq_workspace_bytes(None) == 0
+
+
+def test_batched_pin_tuning_checks(libpath):
+    """The pinned batched Dslash configuration is validated on the host (no CUDA call)."""
+    lib = ctypes.CDLL(libpath)
+    pin = lib.sqcg_batched_pin_tuning
+    pin.argtypes = [ctypes.c_int] * 4
+    bad = [(3, 1, 64, -1), (4, 8, 64, -1), (2, 4, 64, -1), (4, 3, 64, -1),  # W, WT
+           (4, 1, 48, -1), (4, 1, 256, -1), (16, 1, 64, -1),  # T: multiple of 32, <= 128, T * W / WT <= 512
+           (4, 1, 64, 101), (4, 1, 64, -2)]  # carveout
+    for args in bad:
+        assert pin(*args) == -1, args
+    for args in [(1, 1, 32, -1), (16, 4, 128, 50), (8, 4, 128, -1), (16, 2, 64, 25)]:
+        assert pin(*args) == 0, args
+    assert pin(0, 0, 0, 0) == 0  # back to autotuning

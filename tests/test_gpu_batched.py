@@ -146,3 +146,34 @@ def test_batched_from_two_host_threads(sqcg, links_cache):
     assert not errors, errors
     for k in range(len(specs)):
         assert all(st == 0 and res <= 1e-9 for st, res in results[k]), results[k]
+
+
+@pytest.mark.parametrize("cfg", [dict(W=4, WT=1, T=64, carve=-1), dict(W=8, WT=2, T=128, carve=-1),
+                                 dict(W=16, WT=4, T=64, carve=50), dict(W=2, WT=2, T=32, carve=25),
+                                 dict(W=4, WT=4, T=32, carve=-1)])
+def test_batched_pinned_configurations(sqcg, links_cache, cfg):
+    """Every FP32 Dslash instantiation (1, 2 or 4 RHS per thread), pinned instead of tuned, on an uneven batch
+    with a ragged RHS block and a 12-real long-link lattice: each RHS reaches tol on the oracle."""
+    specs = [((8, 8, 8, 8), 5, 0.1), ((6, 8, 10, 12), 3, 0.05), ((4, 4, 4, 8), 1, 0.2)]
+    tol = 1e-9
+    sqcg.pin_batched_tuning(**cfg)
+    try:
+        lats, bs, xs, srcs, links = [], [], [], [], []
+        for n, (L, nr, m) in enumerate(specs):
+            fat, lng = links_cache(L, 410 + n)
+            lat = sqcg.Lattice(L)
+            lat.load_links(fat, lng, recon12=n == 1)
+            s = [synth.gaussian_source(L, 5200 + 10 * n + j) for j in range(nr)]
+            b, x = make_batch(sqcg, lat, s)
+            lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
+        infos = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=tol, max_iter=5000)
+        assert sqcg.batched_tuning_ex(lats[0]) == cfg
+    finally:
+        sqcg.pin_batched_tuning(0)
+    for n, (L, nr, m) in enumerate(specs):
+        fat, lng = links[n]
+        for j in range(nr):
+            assert infos[n][j].status == 0 and infos[n][j].true_rel_resid <= tol
+            assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], lats[n].unpack(xs[n][j])) <= tol
+    for lat in lats:
+        lat.close()
