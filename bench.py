@@ -73,8 +73,10 @@ def parse():
     ap.add_argument("--lattice", default=None,
                     help="hisq and batched workloads: extents as Lx,Ly,Lz,Lt (hisq default 32^4; batched: one "
                          "lattice with 16 sources instead of the three; for profiling)")
+    ap.add_argument("--save-params", default=None, help="learned: write the trained network parameters (.npy)")
+    ap.add_argument("--load-params", default=None, help="learned: skip training, use these parameters (.npy)")
     ap.add_argument("--no-compare", action="store_true",
-                    help="batched workload: skip the one-source-at-a-time comparison solves (profiling runs)")
+                    help="batched, multishift, learned: skip the FP64 and mixed comparison solves (profiling runs)")
     ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned", "hisq"], default="single",
                     help="single (default): the 32^4 single-mass solve; the others print their own line")
     return ap.parse_args()
@@ -537,8 +539,9 @@ def run_multishift(args):
     lat.load_links(fat, lng, recon12=True)
     b = lat.pack(b_host)
     xs = [lat.new_spinor() for _ in shifts]
-    res = {}
-    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+    res = {"fp64": None, "fp64_cg_per_shift": None}
+    modes = (("mixed", sq.MODE_MIXED),) if args.no_compare else (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64))
+    for name, mode in modes:
         for _ in range(max(args.warmup, 1)):
             lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode)
         times, infos = [], None
@@ -548,13 +551,14 @@ def run_multishift(args):
         res[name] = {"ms": statistics.median(times), "iters": [i.iters for i in infos],
                      "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
     # plain FP64 CG, one solve per shift
-    x = lat.new_spinor()
-    total, iters = 0.0, []
-    for sg in shifts:
-        info, ms = _timed(torch, lambda sg=sg: _solve_sigma(lat, sg, b, x, sq))
-        total += ms
-        iters.append(info.iters)
-    res["fp64_cg_per_shift"] = {"ms": total, "iters": iters}
+    if not args.no_compare:
+        x = lat.new_spinor()
+        total, iters = 0.0, []
+        for sg in shifts:
+            info, ms = _timed(torch, lambda sg=sg: _solve_sigma(lat, sg, b, x, sq))
+            total += ms
+            iters.append(info.iters)
+        res["fp64_cg_per_shift"] = {"ms": total, "iters": iters}
     lat.close()
     Vh = int(np.prod(LATTICE)) // 2
     line = {"metric": "multi-shift CG time to per-shift true residual 1e-8 vs plain FP64 CG", "unit": "ms",
@@ -564,8 +568,9 @@ def run_multishift(args):
                        "vh": Vh, "shifts": shifts},
             "multishift_mixed": res["mixed"], "multishift_fp64": res["fp64"],
             "fp64_cg_one_per_shift": res["fp64_cg_per_shift"],
-            "speedup_vs_fp64_cg_per_shift": res["fp64_cg_per_shift"]["ms"] / res["mixed"]["ms"],
-            "speedup_vs_fp64_multishift": res["fp64"]["ms"] / res["mixed"]["ms"]}
+            "speedup_vs_fp64_cg_per_shift": (res["fp64_cg_per_shift"]["ms"] / res["mixed"]["ms"]
+                                             if res["fp64_cg_per_shift"] else None),
+            "speedup_vs_fp64_multishift": res["fp64"]["ms"] / res["mixed"]["ms"] if res["fp64"] else None}
     print(json.dumps(line), flush=True)
 
 
@@ -769,6 +774,8 @@ def run_learned(args):
     sq.build_if_needed()
     m, sigma = 0.005, 4 * 0.005 ** 2
     Ltr = (16, 16, 16, 16)
+    if args.load_params:
+        return _learned_eval(args, np.load(args.load_params).astype(np.float32), None)
     t0 = time.perf_counter()
     # training pairs: CG iterates x_k (CG from 0 truncated at k) against an FP64 x* solved to 1e-13,
     # 8 gauge seeds x 4 sources. Only iterates well before convergence (about 120 iterations here):
@@ -822,6 +829,22 @@ def run_learned(args):
     for lat, net in nets:
         net.close()
         lat.close()
+    if args.save_params:
+        np.save(args.save_params, np.asarray(params, dtype=np.float32))
+    return _learned_eval(args, params, {"ks": ks, "pairs": len(R), "lrs": lrs, "losses": losses, "t_data": t_data,
+                                        "t_train": t_train})
+
+
+def _learned_eval(args, params, tr):
+    """Flexible CG with the trained parameters on the held-out gauge field at 16^4 and 32^4, next to plain FP64
+    and mixed CG (skipped with --no-compare); tr describes the training run (None: parameters loaded)."""
+    import torch
+
+    import paper_1611_00728_gb300 as sq
+    import synth
+
+    m = 0.005
+    Ltr = (16, 16, 16, 16)
     results = {}
     for L in (Ltr, (32, 32, 32, 32)):
         fat, lng = synth.fat_long_links(L, 9000)
@@ -832,9 +855,10 @@ def run_learned(args):
         b = lat.pack(synth.gaussian_source(L, 9100))
         x = lat.new_spinor()
         out = {}
-        for name, fn in (("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64)),
-                         ("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
-                         ("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))):
+        solvers = [("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64)),
+                   ("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
+                   ("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))]
+        for name, fn in solvers[2:] if args.no_compare else solvers:
             x.zero_()
             fn()
             x.zero_()
@@ -847,12 +871,15 @@ def run_learned(args):
     line = {"metric": "learned-preconditioned flexible CG time to true residual 1e-8 vs plain FP64 CG", "unit": "ms",
             "value": results["32x32x32x32"]["fcg_nn"]["ms"], "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "f32/bf16",
-            "config": {"workload": "train 16^4 (gauge seeds 0-7, 4 sources each, CG iterates k in "
-                                   f"{ks}), held-out gauge seed 9000 at 16^4 and 32^4, m=0.005",
-                       "pairs": len(R), "training": f"{len(lrs)} epochs x 8 gauge fields x 60 Adam steps "
-                                                     f"(batch 8), step size {lrs}"},
-            "train_loss_first_last": [losses[0][0], losses[-1][1]], "seconds_data": t_data,
-            "seconds_train": t_train, "results": results}
+            "config": {"workload": ("train 16^4 (gauge seeds 0-7, 4 sources each, CG iterates k in "
+                                    f"{tr['ks']}), " if tr else f"parameters from {args.load_params}, ")
+                                   + "held-out gauge seed 9000 at 16^4 and 32^4, m=0.005"},
+            "results": results}
+    if tr:
+        line["config"].update({"pairs": tr["pairs"], "training": f"{len(tr['lrs'])} epochs x 8 gauge fields x 60 "
+                                                                   f"Adam steps (batch 8), step size {tr['lrs']}"})
+        line.update({"train_loss_first_last": [tr["losses"][0][0], tr["losses"][-1][1]],
+                     "seconds_data": tr["t_data"], "seconds_train": tr["t_train"]})
     print(json.dumps(line), flush=True)
 
 

@@ -255,7 +255,10 @@ int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const
 typedef struct sqcg_nn sqcg_nn;
 #define SQCG_NN_NPARAMS 1472
 
-/* Network bound to ctx (its links and geometry); parameters start at zero. */
+/* Network bound to ctx (its links and geometry); parameters start at zero.
+ * After sqcg_destroy(ctx) the only valid call on its networks is
+ * sqcg_nn_destroy, which does not touch the context (it waits for the whole
+ * device before freeing the network's buffers). */
 int sqcg_nn_create(sqcg_ctx* ctx, sqcg_nn** out);
 int sqcg_nn_destroy(sqcg_nn* nn);
 int sqcg_nn_nparams(void);

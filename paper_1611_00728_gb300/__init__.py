@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -187,9 +188,12 @@ class Lattice:
         _check(library().sqcg_create(d, flags, ctypes.c_void_p(stream), ctypes.byref(h)), "sqcg_create")
         self._h = h
         self.recon12 = False
+        self._networks = weakref.WeakSet()  # networks bound to this lattice: closed with it
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
+        for net in list(getattr(self, "_networks", ())):
+            net.close()
         if getattr(self, "_h", None) is not None and self._h.value:
             library().sqcg_destroy(self._h)
             self._h = None
@@ -418,6 +422,7 @@ class Network:
         h = ctypes.c_void_p()
         _check(library().sqcg_nn_create(lattice._h, ctypes.byref(h)), "sqcg_nn_create")
         self._h = h
+        lattice._networks.add(self)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

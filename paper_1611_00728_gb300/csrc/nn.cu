@@ -887,7 +887,8 @@ int sqcg_nn_create(sqcg_ctx* ctx, sqcg_nn** out) {
 
 int sqcg_nn_destroy(sqcg_nn* nn) {
   if (!nn) return SQCG_OK;
-  cudaStreamSynchronize(nn->ctx->stream);
+  // the context may already be gone: wait for the device, not for the context's stream
+  cudaDeviceSynchronize();
   if (nn->fcg_exec) cudaGraphExecDestroy(nn->fcg_exec);
   void* bufs[] = {nn->master, nn->wfwd, nn->wadj, nn->grad, nn->adam_m, nn->adam_v, nn->scal, nn->partials,
                   nn->h1, nn->h2, nn->a1, nn->a2, nn->g1, nn->g2, nn->g3, nn->T, nn->d, nn->Ad, nn->tmp,
@@ -1001,9 +1002,8 @@ __global__ void __launch_bounds__(kRedThreads) k_fcg_update(double2* __restrict_
   if (!gate_open(st, GATE_ITER)) return;
   const double alpha = st->alpha;
   const float fa = (float)alpha;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     // every colour component is loaded before any store, so the loads overlap
     float2 pc[3], qc[3], rc[3];
     double2 xc[3];
@@ -1028,26 +1028,34 @@ __global__ void __launch_bounds__(kRedThreads) k_fcg_update(double2* __restrict_
       r[k] = rc[c];
       part = fmaf(rc[c].x, rc[c].x, fmaf(rc[c].y, rc[c].y, part));
     }
-    nrm = (double)part;
+    nrm += (double)part;
   }
   block_partial(nrm, partials);
 }
 
-// <z, r> and <z, r_old> partials
+// <z, r> and <z, r_old> partials: each site's sum in FP32, the sums over sites in FP64
 __global__ void __launch_bounds__(kRedThreads) k_fcg_dots(const float2* __restrict__ z, const float2* __restrict__ r,
                                                           const float2* __restrict__ r_old, int Vh,
                                                           const SolverState* st, double* partials) {
   if (!gate_open(st, GATE_ITER)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, b = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    float2 zc[3], rc[3], oc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * Vh + i;
-      const float2 zc = z[k], rc = r[k], oc = r_old[k];
-      a += (double)zc.x * rc.x + (double)zc.y * rc.y;
-      b += (double)zc.x * oc.x + (double)zc.y * oc.y;
+      zc[c] = z[k];
+      rc[c] = r[k];
+      oc[c] = r_old[k];
     }
+    float pa = 0.f, pb = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pa = fmaf(zc[c].x, rc[c].x, fmaf(zc[c].y, rc[c].y, pa));
+      pb = fmaf(zc[c].x, oc[c].x, fmaf(zc[c].y, oc[c].y, pb));
+    }
+    a += (double)pa;
+    b += (double)pb;
   }
   block_partial2(a, b, partials);
 }
@@ -1056,29 +1064,31 @@ __global__ void __launch_bounds__(kRedThreads) k_fcg_dots(const float2* __restri
 __global__ void __launch_bounds__(kRedThreads) k_norm_gated(const float2* __restrict__ r, int Vh, const SolverState* st,
                                                             double* partials) {
   if (!gate_open(st, GATE_ITER)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0;
-  if (i < Vh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    float2 v[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2 v = r[(size_t)c * Vh + i];
-      a += (double)v.x * v.x + (double)v.y * v.y;
-    }
+    for (int c = 0; c < 3; ++c) v[c] = r[(size_t)c * Vh + i];
+    float part = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) part = fmaf(v[c].x, v[c].x, fmaf(v[c].y, v[c].y, part));
+    a += (double)part;
   }
   block_partial(a, partials);
 }
 
-// p = z + beta p
-__global__ void k_fcg_xpay(const float2* __restrict__ z, float2* __restrict__ p, int n, const SolverState* st) {
+// p = z + beta p over the 3 Vh colour components
+__global__ void __launch_bounds__(kRedThreads) k_fcg_xpay(const float2* __restrict__ z, float2* __restrict__ p, int n,
+                                                          const SolverState* st) {
   if (!gate_open(st, GATE_ITER)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const float b = (float)st->beta;
-  const float2 zc = z[i];
-  float2 pc = p[i];
-  pc.x = fmaf(b, pc.x, zc.x);
-  pc.y = fmaf(b, pc.y, zc.y);
-  p[i] = pc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 zc = z[i];
+    float2 pc = p[i];
+    pc.x = fmaf(b, pc.x, zc.x);
+    pc.y = fmaf(b, pc.y, zc.y);
+    p[i] = pc;
+  }
 }
 
 __global__ void k_copy2(const float2* __restrict__ a, float2* __restrict__ b, int n) {
@@ -1089,17 +1099,18 @@ __global__ void k_copy2(const float2* __restrict__ a, float2* __restrict__ b, in
 // z = N(r) with the input scale taken from the solver state
 int fcg_precondition(sqcg_nn* nn, int gate, cudaStream_t s) {
   sqcg_ctx* ctx = nn->ctx;
-  const int Vh = ctx->g.Vh, grid = (Vh + kRedThreads - 1) / kRedThreads;
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   k_norm_gated<<<grid, kRedThreads, 0, s>>>(ctx->r32, Vh, ctx->st, ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
   SQCG_TRY(launch_finish(ctx, grid, FIN_NN_SCALE, gate, s));
   return nn_forward_infer(nn, ctx->r32, nn->z, &ctx->st->nn_s, ctx->st, gate, s);
 }
 
-int fcg_body(sqcg_nn* nn, const void* b, void* x, cudaStream_t cs, cudaGraph_t* ifbody,
-             cudaGraphConditionalHandle* hif_out) {
+// One flexible-CG iteration in three parts: head (A p, <p,Ap>, alpha; x, r update, |r|^2), the
+// FP64 reliable update (fcg_reliable), tail (z = N(r), beta, p = z + beta p).
+int fcg_head(sqcg_nn* nn, void* x, cudaStream_t cs) {
   sqcg_ctx* ctx = nn->ctx;
-  const int Vh = ctx->g.Vh, grid = (Vh + kRedThreads - 1) / kRedThreads;
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->p32; L.out = ctx->tmp32;
   L.gate = GATE_ITER;
@@ -1111,7 +1122,23 @@ int fcg_body(sqcg_nn* nn, const void* b, void* x, cudaStream_t cs, cudaGraph_t* 
   k_fcg_update<<<grid, kRedThreads, 0, cs>>>((double2*)x, ctx->r32, nn->r_old, ctx->p32, ctx->Ap32, Vh, ctx->st,
                                              ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
-  SQCG_TRY(launch_finish(ctx, grid, FIN_UPDATE, GATE_ITER, cs));
+  return launch_finish(ctx, grid, FIN_UPDATE, GATE_ITER, cs);
+}
+
+int fcg_tail(sqcg_nn* nn, cudaStream_t cs) {
+  sqcg_ctx* ctx = nn->ctx;
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
+  SQCG_TRY(fcg_precondition(nn, GATE_ITER, cs));
+  k_fcg_dots<<<grid, kRedThreads, 0, cs>>>(nn->z, ctx->r32, nn->r_old, Vh, ctx->st, ctx->partials);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  SQCG_TRY(launch_finish2(ctx, grid, FIN_FCG_BETA, GATE_ITER, cs));
+  k_fcg_xpay<<<grid, kRedThreads, 0, cs>>>(nn->z, ctx->p32, 3 * Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int fcg_body(sqcg_nn* nn, void* x, cudaStream_t cs, cudaGraph_t* ifbody, cudaGraphConditionalHandle* hif_out) {
+  SQCG_TRY(fcg_head(nn, x, cs));
   // IF node: reliable update r = b - A x (FP64)
   cudaStreamCaptureStatus status;
   cudaGraph_t capg = nullptr;
@@ -1130,15 +1157,8 @@ int fcg_body(sqcg_nn* nn, const void* b, void* x, cudaStream_t cs, cudaGraph_t* 
   SQCG_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
   *ifbody = ip.conditional.phGraph_out[0];
   *hif_out = hif;
-  // z = N(r); beta; p = z + beta p
-  SQCG_TRY(fcg_precondition(nn, GATE_ITER, cs));
-  k_fcg_dots<<<grid, kRedThreads, 0, cs>>>(nn->z, ctx->r32, nn->r_old, Vh, ctx->st, ctx->partials);
-  SQCG_CUDA_TRY(cudaGetLastError());
-  SQCG_TRY(launch_finish2(ctx, grid, FIN_FCG_BETA, GATE_ITER, cs));
-  k_fcg_xpay<<<nn_grid(3 * Vh), kThreads, 0, cs>>>(nn->z, ctx->p32, 3 * Vh, ctx->st);
-  SQCG_CUDA_TRY(cudaGetLastError());
-  SQCG_TRY(launch_loop_control(ctx, cs));
-  return SQCG_OK;
+  SQCG_TRY(fcg_tail(nn, cs));
+  return launch_loop_control(nn->ctx, cs);
 }
 
 int fcg_reliable(sqcg_nn* nn, const void* b, void* x, cudaStream_t cs) {
@@ -1172,7 +1192,7 @@ int fcg_graph(sqcg_nn* nn, const void* b, void* x, cudaGraphExec_t* exec, cudaGr
     if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
     if (cudaStreamBeginCaptureToGraph(cs, wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
-    rc = fcg_body(nn, b, x, cs, &ifbody, hif);
+    rc = fcg_body(nn, x, cs, &ifbody, hif);
     cudaGraph_t got = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &got);
     if (rc != SQCG_OK) break;
@@ -1187,6 +1207,39 @@ int fcg_graph(sqcg_nn* nn, const void* b, void* x, cudaGraphExec_t* exec, cudaGr
   if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "flexible CG graph", __FILE__, __LINE__);
   cudaGraphDestroy(top);
   return rc;
+}
+
+// The same iterations launched one kernel at a time (SQCG_LAUNCH_MODE=eager), the host reading
+// the state where the graph's conditional nodes branch, for kernel-level profilers.
+int fcg_eager(sqcg_nn* nn, const void* b, void* x, cudaStream_t s) {
+  sqcg_ctx* ctx = nn->ctx;
+  SolverState* h = ctx->st_host;
+  auto read = [&]() -> int {
+    SQCG_CUDA_TRY(cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+    return SQCG_OK;
+  };
+  SQCG_TRY(read());
+  const int limit = h->loop_limit;
+  int it = 0;
+  while (!h->done) {
+    SQCG_TRY(fcg_head(nn, x, s));
+    SQCG_TRY(read());
+    if (!h->done && h->need_update) {
+      SQCG_TRY(fcg_reliable(nn, b, x, s));
+      SQCG_TRY(read());
+    }
+    if (!h->done) {
+      SQCG_TRY(fcg_tail(nn, s));
+      SQCG_TRY(read());
+    }
+    if (++it >= limit && !h->done) {  // the loop-control kernel's bound
+      h->done = 1;
+      h->status = SQCG_ERR_NOT_CONVERGED;
+    }
+  }
+  h->loop_count = it;
+  return SQCG_OK;
 }
 
 }  // namespace
@@ -1290,7 +1343,7 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
     rel = sqrt(h->rr_true / h->bb);
   } else {
     // z0 = N(r0); p0 = z0; <z0, r0> (first of the two sums of k_fcg_dots)
-    const int grid = (Vh + kRedThreads - 1) / kRedThreads;
+    const int grid = blas_grid(ctx);
     SQCG_TRY(fcg_precondition(nn, GATE_ITER, s));
     k_fcg_dots<<<grid, kRedThreads, 0, s>>>(nn->z, ctx->r32, ctx->r32, Vh, ctx->st, ctx->partials);
     SQCG_CUDA_TRY(cudaGetLastError());
@@ -1298,7 +1351,9 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
     k_copy2<<<nn_grid(3 * Vh), kThreads, 0, s>>>(nn->z, ctx->p32, 3 * Vh);
     SQCG_CUDA_TRY(cudaGetLastError());
     launches += 8;
-    if (!nn->fcg_exec || nn->fcg_b != b || nn->fcg_x != x || nn->fcg_gen != ctx->links_gen) {
+    const char* mode = getenv("SQCG_LAUNCH_MODE");
+    const bool eager = mode && strcmp(mode, "eager") == 0;
+    if (!eager && (!nn->fcg_exec || nn->fcg_b != b || nn->fcg_x != x || nn->fcg_gen != ctx->links_gen)) {
       SQCG_CUDA_TRY(cudaStreamSynchronize(s));
       if (nn->fcg_exec) cudaGraphExecDestroy(nn->fcg_exec);
       nn->fcg_exec = nullptr;
@@ -1310,17 +1365,21 @@ extern "C" int sqcg_fcg_solve_nn(sqcg_ctx* ctx, sqcg_nn* nn, double mass, const 
     SQCG_CUDA_TRY(cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
     // no launch after a breakdown of the network output on the first residual
-    cudaGraphExec_t exec = h->done ? nullptr : nn->fcg_exec;
+    cudaGraphExec_t exec = (h->done || eager) ? nullptr : nn->fcg_exec;
     h->h_while = nn->fcg_hw;
     h->h_if = nn->fcg_hif;
-    h->use_if = 1;
+    h->use_if = eager ? 0 : 1;  // eager: the kernels must not touch conditional handles
     h->loop_count = 0;
     h->loop_limit = max_iter + 4;
     SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, s));
-    cudaError_t e = exec ? cudaGraphLaunch(exec, s) : cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "flexible CG", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+    if (eager) {
+      SQCG_TRY(fcg_eager(nn, b, x, s));
+    } else {
+      cudaError_t e = exec ? cudaGraphLaunch(exec, s) : cudaSuccess;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "flexible CG", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
+    }
     launches += h->loop_count * 14 + h->updates * 3;
     iters = h->iter;
     updates = h->updates;

@@ -37,7 +37,8 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// scalar steps (run by thread 0 of the finisher, after the partials are summed)
+// scalar steps (run by thread 0 of the finisher, after the partials are summed;
+// the multi-shift steps run on the whole block, see solver_finish_ms)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void finish_breakdown(SolverState* s) {
   s->status = SQCG_ERR_BREAKDOWN;
@@ -103,48 +104,6 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       }
       break;
     }
-    case FIN_MS_PAP: {  // base alpha_k, then zeta_{k+1} and alpha^s_k for every shift
-      s->pAp = v;
-      for (int j = 0; j < s->nshift; ++j)
-        if (s->active[j] == 2) s->active[j] = 0;  // its final x update was applied last iteration
-      if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); break; }
-      const double a = s->rr / v;
-      s->alpha = a;
-      for (int j = 0; j < s->nshift; ++j) {
-        if (!s->active[j]) { s->alpha_s[j] = 0.0; continue; }
-        const double zk = s->zeta[j], zkm = s->zeta_prev[j];
-        const double den = a * s->beta_prev * (zkm - zk) + zkm * s->alpha_prev * (1.0 + s->dsig[j] * a);
-        const double znext = zk * zkm * s->alpha_prev / den;
-        s->alpha_s[j] = a * znext / zk;
-        s->beta_s[j] = znext;  // holds zeta_{k+1} until the update step
-      }
-      break;
-    }
-    case FIN_MS_UPDATE: {  // |r_{k+1}|^2, beta_k, beta^s_k, per-shift convergence
-      if (!isfinite(v)) { finish_breakdown(s); break; }
-      s->iter += 1;
-      const double b = v / s->rr;
-      int any = 0;
-      for (int j = 0; j < s->nshift; ++j) {
-        if (s->active[j] != 1) continue;
-        const double zk = s->zeta[j], znext = s->beta_s[j];
-        s->zeta_prev[j] = zk;
-        s->zeta[j] = znext;
-        s->beta_s[j] = b * (znext / zk) * (znext / zk);
-        s->iters_s[j] = s->iter;
-        // shift residual = zeta * r; a converged shift still takes this iteration's x update (state 2)
-        if (znext * znext * v <= s->stop_rr_s[j]) s->active[j] = 2;
-        else any = 1;
-      }
-      s->rr_prev = s->rr;
-      s->rr = v;
-      s->beta = b;
-      s->alpha_prev = s->alpha;
-      s->beta_prev = b;
-      if (!any) { s->done = 1; s->status = SQCG_OK; s->ms_final = 1; }
-      else if (s->iter >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; s->ms_final = 1; }
-      break;
-    }
     case FIN_NN_SCALE:  // |r|^2 of the network input
       if (!(v > 0.0) || !isfinite(v)) { finish_breakdown(s); s->nn_s = s->nn_inv_s = 0.0; break; }
       s->nn_s = sqrt(3.0 * (double)s->vh / v);
@@ -161,6 +120,69 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       break;
     default:
       break;
+  }
+}
+
+// The multi-shift scalar steps, run by the whole finisher block: thread j < nshift
+// advances shift j's recurrences, thread 0 the base system's scalars. v is the
+// block's total (the same in every thread).
+__device__ inline void solver_finish_ms(SolverState* s, int fin, double v) {
+  const int j = threadIdx.x;
+  const bool own = j < s->nshift;
+  if (fin == FIN_MS_PAP) {  // base alpha_k, then zeta_{k+1} and alpha^s_k for every shift
+    const bool bad = !(v > 0.0) || !isfinite(v);
+    const double a = s->rr / v;
+    if (own) {
+      int act = s->active[j];
+      if (act == 2) s->active[j] = act = 0;  // its final x update was applied last iteration
+      if (!bad) {
+        if (!act) {
+          s->alpha_s[j] = 0.0;
+        } else {
+          const double zk = s->zeta[j], zkm = s->zeta_prev[j];
+          const double den = a * s->beta_prev * (zkm - zk) + zkm * s->alpha_prev * (1.0 + s->dsig[j] * a);
+          const double znext = zk * zkm * s->alpha_prev / den;
+          s->alpha_s[j] = a * znext / zk;
+          s->beta_s[j] = znext;  // holds zeta_{k+1} until the update step
+        }
+      }
+    }
+    __syncthreads();  // every thread has read the base scalars before thread 0 writes them
+    if (j == 0) {
+      s->pAp = v;
+      if (bad) finish_breakdown(s);
+      else s->alpha = a;
+    }
+  } else if (fin == FIN_MS_UPDATE) {  // |r_{k+1}|^2, beta_k, beta^s_k, per-shift convergence
+    const bool bad = !isfinite(v);
+    const double b = v / s->rr;
+    const int it = s->iter + 1;
+    int any = 0;
+    if (own && !bad && s->active[j] == 1) {
+      const double zk = s->zeta[j], znext = s->beta_s[j];
+      s->zeta_prev[j] = zk;
+      s->zeta[j] = znext;
+      s->beta_s[j] = b * (znext / zk) * (znext / zk);
+      s->iters_s[j] = it;
+      // shift residual = zeta * r; a converged shift still takes this iteration's x update (state 2)
+      if (znext * znext * v <= s->stop_rr_s[j]) s->active[j] = 2;
+      else any = 1;
+    }
+    any = __syncthreads_or(any);  // also: every thread has read the base scalars
+    if (j == 0) {
+      if (bad) {
+        finish_breakdown(s);
+      } else {
+        s->iter = it;
+        s->rr_prev = s->rr;
+        s->rr = v;
+        s->beta = b;
+        s->alpha_prev = s->alpha;
+        s->beta_prev = b;
+        if (!any) { s->done = 1; s->status = SQCG_OK; s->ms_final = 1; }
+        else if (it >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; s->ms_final = 1; }
+      }
+    }
   }
 }
 
@@ -191,7 +213,14 @@ __device__ __forceinline__ void finish_partials(SolverState* st, const double* p
 #pragma unroll 4
   for (int j = threadIdx.x; j < n; j += blockDim.x) s += partials[j];
   s = block_sum(s);
-  if (threadIdx.x == 0) solver_finish(st, fin, s);
+  if (fin == FIN_MS_PAP || fin == FIN_MS_UPDATE) {
+    __shared__ double total;
+    if (threadIdx.x == 0) total = s;
+    __syncthreads();
+    solver_finish_ms(st, fin, total);
+  } else if (threadIdx.x == 0) {
+    solver_finish(st, fin, s);
+  }
 }
 
 // two sums at once: block partials of the second sum follow those of the first (offset n)

@@ -70,7 +70,6 @@ struct SolverState {
   int mixed;        // working vectors are FP32
   int vh;           // sites per parity (network input scale)
   int use_if;       // the reliable-update pass is an IF node whose condition FIN_UPDATE sets
-  unsigned int counter;  // last-block counter of the grid reductions
   int loop_count;        // iterations of the device-side WHILE loop so far
   int loop_limit;        // hard bound on loop_count (the loop always ends)
   unsigned long long h_while;  // conditional handle of the WHILE node (cudaGraphConditionalHandle)
@@ -109,8 +108,8 @@ struct BatchState {
   int max_iter, update_interval;
   double delta2;
   int loop_count, loop_limit;
-  int if_runs;  // executions of the reliable-update IF body
-  int pad;
+  int if_runs;    // executions of the reliable-update IF body
+  int use_graph;  // the control kernels set the graph's conditional handles (0: eager launches)
   unsigned long long h_while, h_if;
   RhsScalars r[SQCG_MAX_BATCH_RHS];
   int blk_active[SQCG_MAX_BATCH_RHS];  // RHS block has an active RHS
@@ -230,6 +229,8 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
 
 int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
 int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
+// blocks of the streaming BLAS kernels (one wave on every SM; each thread loops over sites)
+int blas_grid(sqcg_ctx* ctx);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);

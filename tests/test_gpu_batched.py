@@ -177,3 +177,32 @@ def test_batched_pinned_configurations(sqcg, links_cache, cfg):
             assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], lats[n].unpack(xs[n][j])) <= tol
     for lat in lats:
         lat.close()
+
+
+@pytest.mark.parametrize("max_iter", [5000, 9])
+def test_batched_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch, max_iter):
+    """The captured batched loop and the eager profiling mode (one launch per kernel, the host branching where
+    the graph's conditional nodes do) give identical iterates; max_iter = 9 ends every RHS on the bound."""
+    specs = [((8, 8, 8, 8), 5, 0.1), ((6, 8, 10, 12), 3, 0.05)]
+    out = {}
+    for mode in ("graph", "eager"):
+        if mode == "eager":
+            monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
+        else:
+            monkeypatch.delenv("SQCG_LAUNCH_MODE", raising=False)
+        lats, bs, xs = [], [], []
+        for n, (L, nr, m) in enumerate(specs):
+            fat, lng = links_cache(L, 420 + n)
+            lat = sqcg.Lattice(L)
+            lat.load_links(fat, lng, recon12=n == 1)
+            b, x = make_batch(sqcg, lat, [synth.gaussian_source(L, 5300 + 10 * n + j) for j in range(nr)])
+            lats.append(lat); bs.append(b); xs.append(x)
+        infos = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=1e-9, max_iter=max_iter,
+                                      raise_on_error=False)
+        out[mode] = ([x.cpu().numpy() for x in xs], [(i.status, i.iters, i.reliable_updates) for r in infos for i in r])
+        for lat in lats:
+            lat.close()
+    g, e = out["graph"], out["eager"]
+    assert g[1] == e[1]
+    assert all(np.array_equal(a, c) for a, c in zip(g[0], e[0]))
+    assert all(st == (0 if max_iter == 5000 else -3) for st, _, _ in g[1])

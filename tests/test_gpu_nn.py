@@ -199,3 +199,54 @@ def test_fcg_reuses_its_graph_and_follows_new_links(sqcg, links_cache):
         assert i4.status == 0
         assert oracle.true_rel_residual(L, fat2, lng2, 4 * m * m, b, lat.unpack(x)) <= tol
         net.close()
+
+
+@pytest.mark.parametrize("max_iter", [2000, 7])
+def test_fcg_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch, max_iter):
+    """The captured flexible-CG loop and the eager profiling mode (one launch per kernel, the host branching
+    where the graph's conditional nodes do) give identical iterates; max_iter = 7 ends on the iteration bound
+    and hands over to plain CG."""
+    L, m, tol = (8, 8, 8, 8), 0.05, 1e-8
+    fat, lng = links_cache(L, 62)
+    b = synth.gaussian_source(L, 93)
+    out = {}
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        # a near-identity network (self taps 1, open gates) with small random taps: a preconditioner that keeps
+        # the flexible CG converging, so the loop runs to the FP64 confirmation without falling back
+        d = onn.init_params(8, scale=0.02)
+        for w in d["W"]:
+            w[0, 0, 0] += 1.0
+        d["gates"] = [(np.zeros(8), np.full(8, 10.0)), (np.zeros(8), np.full(8, 10.0))]
+        net.set_params(params_to_flat(d))
+        db = lat.pack(b)
+        for mode in ("graph", "eager"):
+            if mode == "eager":
+                monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
+            else:
+                monkeypatch.delenv("SQCG_LAUNCH_MODE", raising=False)
+            x = lat.new_spinor()
+            info = net.fcg_solve(m, db, x, tol=tol, max_iter=max_iter, raise_on_error=False)
+            out[mode] = (info.status, info.iters, info.reliable_updates, info.fallback, lat.unpack(x))
+        net.close()
+    g, e = out["graph"], out["eager"]
+    assert g[:4] == e[:4] and np.array_equal(g[4], e[4])
+    if max_iter == 7:  # the loop ends on the bound, plain CG takes over with what is left and stops too
+        assert g[3] == 1 and g[0] == -3
+    else:
+        assert g[3] == 0 and g[0] == 0
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, g[4]) <= tol
+
+
+def test_network_closes_with_its_lattice(sqcg, links_cache):
+    """A network left open is closed with its lattice (before the context it uses is destroyed)."""
+    L = (4, 4, 4, 6)
+    fat, lng = links_cache(L, 65)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(8, scale=0.3)))
+    assert net._h is None
+    with pytest.raises(sqcg.SqcgError):
+        net.set_params(params_to_flat(onn.init_params(8, scale=0.3)))
