@@ -266,10 +266,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
 // Lanes past the end compute on a clamped site and store nothing, so every lane of a warp
 // takes part in the shuffles.
 template <int OUT>
-__global__ void __launch_bounds__(kThreads) k_conv88(ConvArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) k_conv88(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
-  __shared__ float2 W[NT * CH * CH];
-  for (int j = threadIdx.x; j < NT * CH * CH; j += blockDim.x) W[j] = a.W[j];
+  // weights as [tap][c_in][c_out]: a lane's 4 output channels of one (tap, c_in) are two 16-byte loads
+  __shared__ __align__(16) float2 W[NT * CH * CH];
+  for (int j = threadIdx.x; j < NT * CH * CH; j += blockDim.x) {
+    const int tap = j / (CH * CH), o = (j / CH) % CH, ci = j % CH;
+    W[(tap * CH + ci) * CH + o] = a.W[j];
+  }
   __syncthreads();
   const Geom& g = a.g;
   const int Vh = g.Vh;
@@ -293,12 +297,14 @@ __global__ void __launch_bounds__(kThreads) k_conv88(ConvArgs a) {
     for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)ci * 2 + pp) * 3 + c) * Vh + j);
   };
   auto mix1 = [&](int tap, int ci, const float2 (&t)[3]) {
+    const float4* w4 = reinterpret_cast<const float4*>(W + (tap * CH + ci) * CH + 4 * h);
+    const float4 wa = w4[0], wb = w4[1];
+    const float2 w[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                         make_float2(wb.z, wb.w)};
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      const float2 w = W[(tap * CH + 4 * h + o) * CH + ci];
+    for (int o = 0; o < 4; ++o)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cmac(acc[o][c], w, t[c]);
-    }
+      for (int c = 0; c < 3; ++c) cmac(acc[o][c], w[o], t[c]);
   };
   // self tap: every input channel at the site (the partner lane reads the same values, from L1)
 #pragma unroll 2
