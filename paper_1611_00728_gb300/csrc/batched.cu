@@ -55,12 +55,56 @@ struct LatDev {
   int tile0, tile640;  // first FP32 / FP64 tile
   int nsb_b, tile0_b;  // BLAS tiling: site blocks of kTB sites, first BLAS tile
   int sbt0;            // first BLAS site block of this lattice over all lattices
-  float2 *r, *p, *Ap, *tmp;  // [nrhs][3][Vh]
+  float2 *r, *p, *Ap, *tmp;  // RHS pairs: element (w, c, i) at pv(w, c, i, Vh)
   double2* x;
   double2* tmp64;
   const double2* b;
   size_t b_stride;  // elements between the sources of consecutive RHS: 3 Vh, or 0 when all share one source
 };
+
+// The FP32 work vectors r, p, Ap and tmp hold the right-hand sides of a lattice in pairs:
+// element (RHS w, colour c, site i) is float2 number ((w/2)*3 + c)*2Vh + 2i + w%2, so the two
+// RHS of a pair at one site and colour form one 16-byte word (one gather for a thread that
+// holds both). An odd RHS count leaves the second half of the last pair zero. The FP64
+// vectors (x, b, tmp64) keep the caller's [w][c][Vh] order.
+__host__ __device__ __forceinline__ size_t pv(int w, int c, int i, int Vh) {
+  return (((size_t)(w >> 1) * 3 + c) * Vh + i) * 2 + (w & 1);
+}
+
+// v[w] = element (w0 + w, c, i) for w < WT; zero where w >= nw. WT = 1, or WT even with w0 even.
+template <int WT>
+__device__ __forceinline__ void pv_load(const float2* __restrict__ base, int w0, int nw, int c, int i, int Vh,
+                                        float2 (&v)[WT]) {
+  if constexpr (WT == 1) {
+    v[0] = nw > 0 ? __ldg(base + pv(w0, c, i, Vh)) : make_float2(0.f, 0.f);
+  } else {
+#pragma unroll
+    for (int q = 0; q < WT / 2; ++q) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (2 * q < nw) t = __ldg(reinterpret_cast<const float4*>(base) + ((size_t)((w0 >> 1) + q) * 3 + c) * Vh + i);
+      v[2 * q] = make_float2(t.x, t.y);
+      v[2 * q + 1] = make_float2(t.z, t.w);
+    }
+  }
+}
+
+// element (w0 + w, c, i) = v[w] for w < nw (the same layouts as pv_load)
+template <int WT>
+__device__ __forceinline__ void pv_store(float2* __restrict__ base, int w0, int nw, int c, int i, int Vh,
+                                         const float2 (&v)[WT]) {
+  if constexpr (WT == 1) {
+    if (nw > 0) base[pv(w0, c, i, Vh)] = v[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < WT / 2; ++q) {
+      if (2 * q + 1 < nw)
+        reinterpret_cast<float4*>(base)[((size_t)((w0 >> 1) + q) * 3 + c) * Vh + i] =
+            make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+      else if (2 * q < nw)
+        base[pv(w0 + 2 * q, c, i, Vh)] = v[2 * q];
+    }
+  }
+}
 
 template <typename R> struct V2;
 template <> struct V2<double> { typedef double2 T; };
@@ -355,6 +399,7 @@ template <typename R, int WT>
 __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   typedef typename V2<R>::T R2;
   constexpr bool F64 = sizeof(R) == 8;
+  static_assert(F64, "the FP32 batched Dslash is k_mrhs_dslash_smem");
   const int tile = blockIdx.x;
   const int k = find_lat(a.lats, a.nlat, tile, F64);
   const LatDev& L = a.lats[k];
@@ -374,10 +419,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
   double part[WT];
 #pragma unroll
   for (int w = 0; w < WT; ++w) part[w] = 0.0;
-  const R2* in;
-  if constexpr (F64) in = (a.in_vec == V_X ? (const R2*)L.x : (const R2*)L.tmp64);
-  else in = (a.in_vec == V_P ? (const R2*)L.p : (const R2*)L.tmp);
-  in += (size_t)w0 * 3 * Vh;
+  const R2* in = (a.in_vec == V_X ? (const R2*)L.x : (const R2*)L.tmp64) + (size_t)w0 * 3 * Vh;
   // in a reliable-update pass only the RHS that asked for one are computed (FP64 work is the cost here)
   unsigned mask = 0xffffffffu;
   if (a.gate == GATE_UPDATE) {
@@ -390,36 +432,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
     R2 acc[WT][3];
     dslash_mrhs_site<R, WT>(L, a.par, i, in, nw, acc, mask);
     if (a.epi == M_PLAIN) {
-      R2* out = (F64 ? (R2*)L.tmp64 : (R2*)L.tmp) + (size_t)w0 * 3 * Vh;
+      R2* out = (R2*)L.tmp64 + (size_t)w0 * 3 * Vh;
 #pragma unroll
       for (int w = 0; w < WT; ++w)
         if (w < nw && ((mask >> w) & 1u))
 #pragma unroll
           for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
-    } else if constexpr (!F64) {  // M_NORMAL_DOT (FP32): Ap = sigma p - D tmp, <p, Ap>
-      const R2* y = (const R2*)L.p + (size_t)w0 * 3 * Vh;
-      R2* out = (R2*)L.Ap + (size_t)w0 * 3 * Vh;
-#pragma unroll
-      for (int w = 0; w < WT; ++w) {
-        if (w < nw) {
-          const R sig = (R)a.st->r[L.rhs0 + w0 + w].sigma;
-          R dot = R(0);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const size_t o = ((size_t)w * 3 + c) * Vh + i;
-            const R2 yc = __ldg(y + o);
-            const R2 v = mk2<R2>(sig * yc.x - acc[w][c].x, sig * yc.y - acc[w][c].y);
-            out[o] = v;
-            dot = fma(yc.x, v.x, fma(yc.y, v.y, dot));
-          }
-          part[w] = (double)dot;
-        }
-      }
-    } else {  // M_TRUE_RESID (FP64): r = b - sigma x + D tmp64, |r|^2; r (FP32) and optionally p
+    } else {  // M_TRUE_RESID: r = b - sigma x + D tmp64, |r|^2; r (FP32) and optionally p
       const double2* xb = L.x + (size_t)w0 * 3 * Vh;
       const double2* bb = L.b + (size_t)w0 * L.b_stride;
-      float2* rb32 = L.r + (size_t)w0 * 3 * Vh;
-      float2* pb32 = L.p + (size_t)w0 * 3 * Vh;
 #pragma unroll
       for (int w = 0; w < WT; ++w) {
         if (w < nw && ((mask >> w) & 1u)) {
@@ -432,8 +453,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
             const double re = bc.x - sig * xc.x + (double)acc[w][c].x;
             const double im = bc.y - sig * xc.y + (double)acc[w][c].y;
             const float2 f = make_float2((float)re, (float)im);
-            rb32[o] = f;
-            if (a.write_p) pb32[o] = f;
+            L.r[pv(w0 + w, c, i, Vh)] = f;
+            if (a.write_p) L.p[pv(w0 + w, c, i, Vh)] = f;
             n2 += re * re + im * im;
           }
           part[w] = n2;
@@ -548,7 +569,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
   double part[WT];
 #pragma unroll
   for (int w = 0; w < WT; ++w) part[w] = 0.0;
-  const float2* in = (a.in_vec == V_P ? (const float2*)L.p : (const float2*)L.tmp) + (size_t)w0 * 3 * Vh;
+  const float2* in = (a.in_vec == V_P ? (const float2*)L.p : (const float2*)L.tmp);
   if (valid && nw > 0) {
     float2 acc[WT][3];
 #pragma unroll
@@ -562,10 +583,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
       const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
       const int j = nbr(mu, bwd ? (lng ? -3 : -1) : (lng ? 3 : 1));
 #pragma unroll
-      for (int w = 0; w < WT; ++w)
+      for (int c = 0; c < 3; ++c) {
+        float2 t[WT];
+        pv_load<WT>(in, w0, nw, c, j, Vh, t);  // one 16-byte gather per RHS pair
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          v[w][c] = (w < nw) ? __ldg(in + ((size_t)w * 3 + c) * Vh + j) : make_float2(0.f, 0.f);
+        for (int w = 0; w < WT; ++w) v[w][c] = t[w];
+      }
     };
     gather(0, vin);
 #pragma unroll
@@ -603,31 +626,34 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
           for (int c = 0; c < 3; ++c) vin[w][c] = vnx[w][c];
     }
     if (a.epi == M_PLAIN) {
-      float2* out = L.tmp + (size_t)w0 * 3 * Vh;
 #pragma unroll
-      for (int w = 0; w < WT; ++w)
-        if (w < nw)
+      for (int c = 0; c < 3; ++c) {
+        float2 t[WT];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
+        for (int w = 0; w < WT; ++w) t[w] = acc[w][c];
+        pv_store<WT>(L.tmp, w0, nw, c, i, Vh, t);
+      }
     } else {  // M_NORMAL_DOT: Ap = sigma p - D tmp, <p, Ap>
-      const float2* yv = L.p + (size_t)w0 * 3 * Vh;
-      float2* out = L.Ap + (size_t)w0 * 3 * Vh;
+      float sig[WT], dot[WT];
 #pragma unroll
       for (int w = 0; w < WT; ++w) {
-        if (w < nw) {
-          const float sig = (float)a.st->r[L.rhs0 + w0 + w].sigma;
-          float dot = 0.f;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const size_t o = ((size_t)w * 3 + c) * Vh + i;
-            const float2 yc = __ldg(yv + o);
-            const float2 v = make_float2(sig * yc.x - acc[w][c].x, sig * yc.y - acc[w][c].y);
-            out[o] = v;
-            dot = fmaf(yc.x, v.x, fmaf(yc.y, v.y, dot));
-          }
-          part[w] = (double)dot;
-        }
+        sig[w] = w < nw ? (float)a.st->r[L.rhs0 + w0 + w].sigma : 0.f;
+        dot[w] = 0.f;
       }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 yc[WT], v[WT];
+        pv_load<WT>(L.p, w0, nw, c, i, Vh, yc);
+#pragma unroll
+        for (int w = 0; w < WT; ++w) {
+          v[w] = make_float2(sig[w] * yc[w].x - acc[w][c].x, sig[w] * yc[w].y - acc[w][c].y);
+          dot[w] = fmaf(yc[w].x, v[w].x, fmaf(yc[w].y, v[w].y, dot[w]));
+        }
+        pv_store<WT>(L.Ap, w0, nw, c, i, Vh, v);
+      }
+#pragma unroll
+      for (int w = 0; w < WT; ++w)
+        if (w < nw) part[w] = (double)dot[w];
     }
   }
   if (a.epi != M_PLAIN)
@@ -650,90 +676,113 @@ struct BArgs {
   int W;
 };
 
-// One thread per (site, RHS): blockIdx.x runs over the kTB-site blocks of all lattices,
-// blockIdx.y over the RHS of a lattice. Every thread streams its own three colour
-// components, so all loads of a block are independent and in flight together. Per-RHS
+// One thread per (site, RHS pair): blockIdx.x runs over the kTB-site blocks of all lattices,
+// blockIdx.y over the RHS pairs of a lattice. A thread streams the three colour components
+// of both RHS (16-byte words of the paired FP32 vectors), so all loads of a block are
+// independent and in flight together. An RHS that is not running keeps its values. Per-RHS
 // sums go to partials[rhs][site block] for k_batch_finish.
 __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
   int k = 0;
   for (int j = 1; j < a.nlat; ++j)
     if ((int)blockIdx.x >= a.lats[j].sbt0) k = j;
   const LatDev& L = a.lats[k];
-  const int w = blockIdx.y;
-  if (w >= L.nrhs) return;
+  const int w0 = 2 * blockIdx.y;
+  if (w0 >= L.nrhs) return;
+  const int nw = min(2, L.nrhs - w0);
   const int sb = blockIdx.x - L.sbt0;
-  const int rhs = L.rhs0 + w;
   const bool all = (a.op == B_NORM_B || a.op == B_NORM_X || a.op == B_INIT_B);
-  if (!all && (!a.st->blk_active[L.rb0 + w / a.W] || !a.st->r[rhs].active)) return;
+  bool act[2];
+  double alpha[2], beta[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int rhs = L.rhs0 + w0 + u;
+    act[u] = u < nw && (all || (a.st->blk_active[L.rb0 + (w0 + u) / a.W] && a.st->r[rhs].active));
+    alpha[u] = act[u] ? a.st->r[rhs].alpha : 0.0;
+    beta[u] = act[u] ? a.st->r[rhs].beta : 0.0;
+  }
+  if (!act[0] && !act[1]) return;
   const int Vh = L.g.Vh;
-  const size_t base = (size_t)w * 3 * Vh;
-  const double2* __restrict__ b = L.b + (size_t)w * L.b_stride;
-  double2* __restrict__ x = L.x + base;
-  float2* __restrict__ r = L.r + base;
-  float2* __restrict__ p = L.p + base;
-  const float2* __restrict__ Ap = L.Ap + base;
-  const double alpha = a.st->r[rhs].alpha, beta = a.st->r[rhs].beta;
   const int i = sb * blockDim.x + threadIdx.x;
-  double part = 0.0;
+  double part[2] = {0.0, 0.0};
   if (i < Vh) {
-    if (a.op == B_NORM_B || a.op == B_NORM_X || a.op == B_INIT_B) {
-      const double2* v = (a.op == B_NORM_X) ? x : b;
-      double2 vc[3];
+    if (all) {
+      float2 f[3][2];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) vc[c] = v[(size_t)c * Vh + i];
+      for (int u = 0; u < 2; ++u) {
+        if (!act[u]) continue;
+        const double2* v = (a.op == B_NORM_X) ? L.x + (size_t)(w0 + u) * 3 * Vh : L.b + (size_t)(w0 + u) * L.b_stride;
+        double2 vc[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        part = fma(vc[c].x, vc[c].x, fma(vc[c].y, vc[c].y, part));
-        if (a.op == B_INIT_B) {
-          const float2 f = make_float2((float)vc[c].x, (float)vc[c].y);
-          r[(size_t)c * Vh + i] = f;
-          p[(size_t)c * Vh + i] = f;
+        for (int c = 0; c < 3; ++c) vc[c] = v[(size_t)c * Vh + i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          part[u] = fma(vc[c].x, vc[c].x, fma(vc[c].y, vc[c].y, part[u]));
+          f[c][u] = make_float2((float)vc[c].x, (float)vc[c].y);
         }
       }
+      if (a.op == B_INIT_B)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pv_store<2>(L.r, w0, nw, c, i, Vh, f[c]);
+          pv_store<2>(L.p, w0, nw, c, i, Vh, f[c]);
+        }
     } else if (a.op == B_UPDATE) {
-      const float fa = (float)alpha;
-      float2 pc[3], apc[3], rc[3];
-      double2 xc[3];
+      float2 pc[3][2], apc[3][2], rc[3][2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const size_t o = (size_t)c * Vh + i;
-        pc[c] = p[o];
-        apc[c] = Ap[o];
-        rc[c] = r[o];
-        xc[c] = x[o];
+        pv_load<2>(L.p, w0, nw, c, i, Vh, pc[c]);
+        pv_load<2>(L.Ap, w0, nw, c, i, Vh, apc[c]);
+        pv_load<2>(L.r, w0, nw, c, i, Vh, rc[c]);
       }
-      float n2 = 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t o = (size_t)c * Vh + i;
-        xc[c].x = fma(alpha, (double)pc[c].x, xc[c].x);
-        xc[c].y = fma(alpha, (double)pc[c].y, xc[c].y);
-        x[o] = xc[c];
-        rc[c].x = fmaf(-fa, apc[c].x, rc[c].x);
-        rc[c].y = fmaf(-fa, apc[c].y, rc[c].y);
-        r[o] = rc[c];
-        n2 = fmaf(rc[c].x, rc[c].x, fmaf(rc[c].y, rc[c].y, n2));
+      for (int u = 0; u < 2; ++u) {
+        if (!act[u]) continue;
+        double2* x = L.x + (size_t)(w0 + u) * 3 * Vh;
+        double2 xc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xc[c] = x[(size_t)c * Vh + i];
+        const float fa = (float)alpha[u];
+        float n2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xc[c].x = fma(alpha[u], (double)pc[c][u].x, xc[c].x);
+          xc[c].y = fma(alpha[u], (double)pc[c][u].y, xc[c].y);
+          x[(size_t)c * Vh + i] = xc[c];
+          rc[c][u].x = fmaf(-fa, apc[c][u].x, rc[c][u].x);
+          rc[c][u].y = fmaf(-fa, apc[c][u].y, rc[c][u].y);
+          n2 = fmaf(rc[c][u].x, rc[c][u].x, fmaf(rc[c][u].y, rc[c][u].y, n2));
+        }
+        part[u] = (double)n2;
       }
-      part = (double)n2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv_store<2>(L.r, w0, nw, c, i, Vh, rc[c]);
     } else {  // B_XPAY
-      const float be = (float)beta;
-      float2 rc[3], pc[3];
+      float2 rc[3][2], pc[3][2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        rc[c] = r[(size_t)c * Vh + i];
-        pc[c] = p[(size_t)c * Vh + i];
+        pv_load<2>(L.r, w0, nw, c, i, Vh, rc[c]);
+        pv_load<2>(L.p, w0, nw, c, i, Vh, pc[c]);
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        pc[c].x = fmaf(be, pc[c].x, rc[c].x);
-        pc[c].y = fmaf(be, pc[c].y, rc[c].y);
-        p[(size_t)c * Vh + i] = pc[c];
+      for (int u = 0; u < 2; ++u) {
+        if (!act[u]) continue;
+        const float be = (float)beta[u];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pc[c][u].x = fmaf(be, pc[c][u].x, rc[c][u].x);
+          pc[c][u].y = fmaf(be, pc[c][u].y, rc[c][u].y);
+        }
       }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv_store<2>(L.p, w0, nw, c, i, Vh, pc[c]);
     }
   }
   if (a.op != B_XPAY) {
-    const double t = block_sum(part);
-    if (threadIdx.x == 0) a.partials[(size_t)rhs * a.max_nsb + sb] = t;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const double t = block_sum(part[u]);
+      if (threadIdx.x == 0 && act[u]) a.partials[(size_t)(L.rhs0 + w0 + u) * a.max_nsb + sb] = t;
+    }
   }
 }
 
@@ -924,7 +973,7 @@ int launch_mrhs_blas(const BatchPlan& P, int op, cudaStream_t s) {
     maxr = P.nrhs[k] > maxr ? P.nrhs[k] : maxr;
     nsb += P.host[k].nsb_b;
   }
-  k_mrhs_blas<<<dim3(nsb, maxr), kTB, 0, s>>>(a);
+  k_mrhs_blas<<<dim3(nsb, (maxr + 1) / 2), kTB, 0, s>>>(a);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }
@@ -1084,6 +1133,12 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   return upload_lats(P, s);
 }
 
+// per lattice: r, p, Ap, tmp in RHS pairs (FP32) and tmp64 (FP64)
+size_t work_bytes(int nrhs, size_t Vh) {
+  const size_t nf = (size_t)((nrhs + 1) / 2) * 2 * 3 * Vh;
+  return 4 * nf * sizeof(float2) + (size_t)nrhs * 3 * Vh * sizeof(double2);
+}
+
 void destroy_plan(BatchPlan* P) {
   if (!P) return;
   if (P->exec) cudaGraphExecDestroy(P->exec);
@@ -1128,15 +1183,16 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     L.b = (const double2*)b[k];
     L.b_stride = b_shared ? 0 : 3 * Vh;
     L.x = (double2*)x[k];
-    const size_t n = (size_t)nrhs[k] * 3 * Vh;
-    if (cudaMalloc(&P->work[k], n * (4 * sizeof(float2) + sizeof(double2))) != cudaSuccess) {
+    // FP32 vectors: (nrhs + 1) / 2 RHS pairs each (see pv); FP64 tmp64: nrhs vectors
+    if (cudaMalloc(&P->work[k], work_bytes(nrhs[k], Vh)) != cudaSuccess) {
       cudaGetLastError();
       destroy_plan(P);
       return SQCG_ERR_NO_MEMORY;
     }
+    const size_t nf = (size_t)((nrhs[k] + 1) / 2) * 2 * 3 * Vh;
     float2* w = (float2*)P->work[k];
-    L.r = w; L.p = w + n; L.Ap = w + 2 * n; L.tmp = w + 3 * n;
-    L.tmp64 = (double2*)(w + 4 * n);
+    L.r = w; L.p = w + nf; L.Ap = w + 2 * nf; L.tmp = w + 3 * nf;
+    L.tmp64 = (double2*)(w + 4 * nf);
     total += nrhs[k];
     if ((int)Vh > max_vh) max_vh = (int)Vh;
   }
@@ -1152,8 +1208,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     return SQCG_ERR_NO_MEMORY;
   }
   SQCG_CUDA_TRY(cudaMemsetAsync(P->st, 0, sizeof(BatchState), s));
-  for (int k = 0; k < nctx; ++k)
-    SQCG_CUDA_TRY(cudaMemsetAsync(P->work[k], 0, (size_t)nrhs[k] * 3 * ctx[k]->g.Vh * (4 * sizeof(float2) + sizeof(double2)), s));
+  for (int k = 0; k < nctx; ++k) SQCG_CUDA_TRY(cudaMemsetAsync(P->work[k], 0, work_bytes(nrhs[k], ctx[k]->g.Vh), s));
   int rc = autotune(*P, s);
   if (rc != SQCG_OK) { destroy_plan(P); return rc; }
   *out = P;
