@@ -56,8 +56,8 @@ NOMINAL_FP64_GFLOPS = 1250.0  # GB300 FP64 rate (nominal figure of the hardware 
 # DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
 # at 32^4, measured by ncu (profiles/dslash_f32_recon12_32x32x32x32.md), with the
 # hash of the kernel sources they were taken on (reported as null once those change).
-NCU_TRAFFIC = {"sources_sha256": "555c392f5e0c94950128d17cc60e6646364f527bf8fcc002451b1c39e813d706",
-               "bytes_per_launch": 525996288 + 11997696, "lattice": [32, 32, 32, 32]}
+NCU_TRAFFIC = {"sources_sha256": "c1caf973742dd60118b1bb18f38c5ef32a9645ab3b4244860590f95ca062d4f0",
+               "bytes_per_launch": 525955328 + 11930112, "lattice": [32, 32, 32, 32]}
 
 
 def parse():
