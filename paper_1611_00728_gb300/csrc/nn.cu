@@ -93,6 +93,18 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
+// (a.x b.x + c.x, a.y b.y + c.y) as one packed two-lane FP32 FMA (sm_100 and later); each
+// lane is an ordinary round-to-nearest FMA, so the results equal two fmaf calls
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 __device__ __forceinline__ void load_link9(const float2* __restrict__ U, int Vh, int idx, float2 (&u)[9]) {
 #pragma unroll
   for (int e = 0; e < 9; ++e) u[e] = __ldg(U + (size_t)e * Vh + idx);
@@ -268,11 +280,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv(ConvArgs a) {
 template <int OUT>
 __global__ void __launch_bounds__(kThreads, 5) k_conv88(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
-  // weights as [tap][c_in][c_out]: a lane's 4 output channels of one (tap, c_in) are two 16-byte loads
-  __shared__ __align__(16) float2 W[NT * CH * CH];
+  // weights as [tap][c_in][c_out], each complex w stored as (w.x, w.x, -w.y, w.y): the two packed
+  // operands of acc += w t in two-lane FMAs, acc = (w.x, w.x) (t.x, t.y) + (-w.y, w.y) (t.y, t.x) + acc,
+  // which rounds exactly as the scalar complex multiply-add (same products, same order per lane)
+  __shared__ float4 W[NT * CH * CH];
   for (int j = threadIdx.x; j < NT * CH * CH; j += blockDim.x) {
     const int tap = j / (CH * CH), o = (j / CH) % CH, ci = j % CH;
-    W[(tap * CH + ci) * CH + o] = a.W[j];
+    const float2 w = a.W[j];
+    W[(tap * CH + ci) * CH + o] = make_float4(w.x, w.x, -w.y, w.y);
   }
   __syncthreads();
   const Geom& g = a.g;
@@ -297,14 +312,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_conv88(ConvArgs a) {
     for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)ci * 2 + pp) * 3 + c) * Vh + j);
   };
   auto mix1 = [&](int tap, int ci, const float2 (&t)[3]) {
-    const float4* w4 = reinterpret_cast<const float4*>(W + (tap * CH + ci) * CH + 4 * h);
-    const float4 wa = w4[0], wb = w4[1];
-    const float2 w[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
-                         make_float2(wb.z, wb.w)};
+    const float4* wq = W + (tap * CH + ci) * CH + 4 * h;
+    float2 ts[3];
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
+    for (int c = 0; c < 3; ++c) ts[c] = make_float2(t[c].y, t[c].x);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cmac(acc[o][c], w[o], t[c]);
+    for (int o = 0; o < 4; ++o) {
+      const float4 w = wq[o];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[o][c] = ffma2(make_float2(w.x, w.y), t[c], acc[o][c]);
+        acc[o][c] = ffma2(make_float2(w.z, w.w), ts[c], acc[o][c]);
+      }
+    }
   };
   // self tap: every input channel at the site (the partner lane reads the same values, from L1)
 #pragma unroll 2
