@@ -5,19 +5,23 @@
 // Work decomposition: a tile is (lattice, RHS block of width W, block of T
 // sites). One launch per phase covers the tiles of every lattice, so the small
 // lattices ride along with the large one instead of paying their own launch
-// and tail. Within a tile each thread owns one site and applies every link it
-// loads to the W right-hand sides of the block, so the link stream (96% of the
-// single-RHS bytes) is paid once per W sources: 1152/W + 48 bytes per
-// site-RHS in FP32. Tiles are ordered with the RHS blocks of one site block
-// adjacent, so when W < nrhs the other blocks find the links in L2.
+// and tail. The FP32 Dslash block first stages the 16 links of each of its
+// sites in shared memory, then its W / WT thread groups apply them to WT
+// right-hand sides each, so the link stream (96% of the single-RHS bytes) is
+// read from HBM once per W sources: 1152/W + 48 bytes per site-RHS. The FP32
+// work vectors hold the RHS in pairs (see pv), so a thread's two RHS of one
+// site and colour are one 16-byte gather.
 //
 // Every RHS has its own CG scalars in BatchState; the per-RHS dot products are
 // reduced deterministically in two stages (warp shuffle -> block partial per
 // tile, then one block per RHS adds the partials in site-block order). The
-// BLAS kernels use their own 256-site tiles, independent of the Dslash tile. The loop is one CUDA graph: a WHILE node
-// around [D_oe p, A p with <p,Ap>, x/r update, IF(reliable update in FP64),
-// p update, loop control]. W and T are chosen by a small autotuner that times
-// the FP32 multi-RHS Dslash over the whole batch and caches the choice.
+// BLAS kernels use their own 256-site tiles, independent of the Dslash tile.
+// The loop is one CUDA graph: a WHILE node around [D_oe p, A p with <p,Ap>,
+// x/r update, IF(reliable update in FP64), p update, loop control], or the
+// same kernels launched one at a time (SQCG_LAUNCH_MODE=eager). W, WT, T and
+// the shared-memory carveout are chosen by a small autotuner that times the
+// FP32 multi-RHS Dslash over the whole batch and caches the choice (or are
+// pinned by sqcg_batched_pin_tuning).
 #include <chrono>
 #include <map>
 #include <math.h>

@@ -21,8 +21,9 @@
 //   q = A p; alpha = <z,r>/<p,q>; x += alpha p; r_old = r; r -= alpha q;
 //   z = N(r); beta = (<z,r> - <z,r_old>) / <z_old,r_old>; p = z + beta p,
 // with FP32 vectors, FP64 x and reliable updates as in the mixed CG, run as
-// one CUDA graph (WHILE node). On breakdown or no convergence it falls back
-// to the mixed-precision CG from the current iterate.
+// one CUDA graph (WHILE node; SQCG_LAUNCH_MODE=eager launches the same kernels
+// one at a time). On breakdown or no convergence it falls back to the
+// mixed-precision CG from the current iterate.
 #include <chrono>
 #include <cuda_bf16.h>
 #include <math.h>
