@@ -1255,7 +1255,8 @@ int run_eager(BatchPlan& P, cudaStream_t s) {
     SQCG_CUDA_TRY(cudaStreamSynchronize(s));
     return SQCG_OK;
   };
-  for (;;) {
+  const int limit = h->loop_limit;  // the host bounds the loop too, whatever the device state says
+  for (int it = 0; it < limit; ++it) {
     SQCG_TRY(enqueue_head(P, s));
     SQCG_TRY(read());
     int upd = 0;
