@@ -117,3 +117,14 @@ def test_batched_pin_tuning_checks(libpath):
     for args in [(1, 1, 32, -1), (16, 4, 128, 50), (8, 4, 128, -1), (16, 2, 64, 25)]:
         assert pin(*args) == 0, args
     assert pin(0, 0, 0, 0) == 0  # back to autotuning
+
+
+def test_binding_pin_batched_tuning(libpath):
+    """The binding's pin call reaches the host-side checks (no GPU needed) and raises on a bad shape."""
+    import paper_1611_00728_gb300 as sq
+
+    sq.pin_batched_tuning(16, WT=2, T=32, carve=-1)
+    with pytest.raises(sq.SqcgError) as e:
+        sq.pin_batched_tuning(16, WT=1, T=64)  # 64 x 16 threads > 512
+    assert e.value.name == "INVALID_ARG"
+    sq.pin_batched_tuning(0)
