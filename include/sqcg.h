@@ -35,10 +35,11 @@
  *    gives a message. Nothing aborts the process and no kernel traps.
  *  - A context is not thread-safe: one host thread at a time per context.
  *  - Solver loops run on the device as one CUDA graph launch (conditional
- *    WHILE/IF nodes). With the environment variable SQCG_LAUNCH_MODE=eager the
- *    single-mass and multi-shift solvers launch the same kernels one at a time
- *    with a host round trip per iteration instead (kernel-level profilers do
- *    not list kernels inside conditional graph nodes); results are identical.
+ *    WHILE/IF nodes). With the environment variable SQCG_LAUNCH_MODE=eager
+ *    every solver (single-mass, multi-shift with its refinement, batched,
+ *    flexible CG) launches the same kernels one at a time with a host round
+ *    trip per iteration instead (kernel-level profilers do not list kernels
+ *    inside conditional graph nodes); results are identical.
  */
 #ifndef SQCG_H
 #define SQCG_H
@@ -217,21 +218,23 @@ int sqcg_rational_apply(sqcg_ctx* ctx, int nshift, const double* shifts, const d
  * device-side loop, mixed precision (FP32 Dslash and Krylov vectors, FP64 x,
  * reductions and reliable updates). This applies the paper's single-mass CG
  * (Sec. 3) to many sources at once; batching is not in the paper. Each link is
- * loaded once per block of W right-hand sides. W (1..16) and the site-block
- * size are picked on the first call for a given set of lattices by timing the
- * multi-RHS Dslash (cached per process, and in the file named by the
- * environment variable SQCG_TUNE_CACHE if set; SQCG_TUNE_VERBOSE=1 prints each
- * timed candidate to stderr).
+ * loaded once per block of W right-hand sides. W (1..16), the RHS per thread,
+ * the site-block size and the shared-memory carveout are picked on the first
+ * call for a given set of lattices by timing the multi-RHS Dslash (cached per
+ * process, and in the file named by the environment variable SQCG_TUNE_CACHE
+ * if set; SQCG_TUNE_VERBOSE=1 prints each timed candidate to stderr), unless
+ * sqcg_batched_pin_tuning has fixed them.
  * ctx[k]: distinct contexts with links loaded, all on the current device; the
  * work runs on ctx[0]'s stream. b[k], x[k]: device arrays of nrhs[k]
  * consecutive FP64 device vectors ([nrhs][3][Vh] complex double); x[k] holds
  * the initial guesses and receives the solutions (when every guess is zero the
  * initial residuals are the b[k] themselves; otherwise r = b - A x0 in FP64 for
- * all). tol: FP64 true relative
- * residual target for every RHS. info: NULL or sum(nrhs) entries, lattice-major.
- * Workspace (about 48 bytes per site and RHS) is cached with ctx[0] for
- * repeated calls with the same arguments. Returns SQCG_OK when every RHS
- * converged, else the first failing status. Synchronises the stream. */
+ * all). tol: FP64 true relative residual target for every RHS. info: NULL or
+ * sum(nrhs) entries, lattice-major. Workspace (per site and RHS: 96 bytes of
+ * FP32 vectors, for an RHS count rounded up to even, and 48 bytes of FP64) is
+ * cached with ctx[0] for repeated calls with the same arguments. Returns
+ * SQCG_OK when every RHS converged, else the first failing status.
+ * Synchronises the stream. */
 int sqcg_cg_solve_batched(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double* mass,
                           const void* const* b, void* const* x, double tol, int max_iter,
                           sqcg_info* info);
