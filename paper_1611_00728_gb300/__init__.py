@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
-    "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
+    "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "NN_LAYERS", "NN_GATES", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
     "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK",
 ]
 
@@ -33,6 +33,12 @@ RECON12_LONG = 1
 EIGHT_WAY = 2
 #: parameters of the preconditioner network (see include/sqcg.h for the layout)
 NN_NPARAMS = 1472
+#: host parameter layout of the network, as include/sqcg.h states it: per layer the slice of
+#: interleaved (re, im) weights and the complex weight shape (tap, out, in); per gate the slices
+#: of its a[8] and b[8]
+NN_LAYERS = ((slice(0, 144), (9, 8, 1)), (slice(144, 1296), (9, 8, 8)), (slice(1296, 1440), (9, 1, 8)))
+NN_GATES = ((slice(1440, 1448), slice(1448, 1456)), (slice(1456, 1464), slice(1464, 1472)))
+assert NN_LAYERS[-1][0].stop == NN_GATES[0][0].start and NN_GATES[-1][1].stop == NN_NPARAMS
 #: MILC's flop count of one Dslash output site: 16 x 66 (3x3 complex mat-vec) + 15 x 6 (adds)
 FLOPS_PER_SITE = 1146
 

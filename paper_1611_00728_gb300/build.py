@@ -44,6 +44,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def _compile_cmd(src: str, extra=()) -> list:
+    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    return [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+
+
+def _link_cmd(objs, out: str) -> list:
+    return [nvcc()] + ARCH + ["-shared", "-o", out] + list(objs)
+
+
+def commands() -> list:
+    """The nvcc command lines of a full build (every translation unit, then the link)."""
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    cmds = [_compile_cmd(src) for src in sources]
+    return cmds + [_link_cmd([c[-1] for c in cmds], LIB)]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     if not force and up_to_date():
         return LIB
@@ -52,8 +68,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc()] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+        cmd = _compile_cmd(src, extra)
+        obj = cmd[-1]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,7 +83,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for obj, err in results:
             print(f"== {os.path.basename(obj)}\n{err}")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = _link_cmd([o for o, _ in results], tmp)
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
