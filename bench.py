@@ -22,6 +22,7 @@ the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import datetime
 import hashlib
 import json
@@ -75,6 +76,8 @@ def parse():
                          "lattice with 16 sources instead of the three; for profiling)")
     ap.add_argument("--save-params", default=None, help="learned: write the trained network parameters (.npy)")
     ap.add_argument("--load-params", default=None, help="learned: skip training, use these parameters (.npy)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the forms block (multi-shift, rational, batched, learned, HISQ)")
     ap.add_argument("--no-compare", action="store_true",
                     help="batched, multishift, learned: skip the FP64 and mixed comparison solves (profiling runs)")
     ap.add_argument("--workload", choices=["single", "multishift", "rational", "batched", "learned", "hisq"], default="single",
@@ -138,16 +141,19 @@ def whole_job_rate(flops_per_rank: float, seconds_per_rank: float, ranks: Ranks)
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi samples every 50 ms, started before the warm-up (so that the tool is
-    running when the timed region begins) and filtered to the timed region by their
-    timestamps (host clock of the same machine)."""
+    running when a timed region begins) and filtered to the timed regions by their
+    timestamps (host clock of the same machine). Timed regions are tagged, so one
+    sampler serves the main solve and each form of the `forms` block."""
     FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, uuid: str | None):
         self.uuid = (uuid or "").replace("GPU-", "")
         self.proc = None
-        self.t0 = self.t1 = None
+        self.windows = []  # (tag, t0, t1)
+        self.rows = None
 
     def start(self):
         try:
@@ -155,12 +161,15 @@ class ClockSampler:
                                           "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
+        return self
 
-    def mark_start(self):
-        self.t0 = datetime.datetime.now()
-
-    def mark_stop(self):
-        self.t1 = datetime.datetime.now()
+    @contextlib.contextmanager
+    def timed(self, tag: str):
+        t0 = datetime.datetime.now()
+        try:
+            yield
+        finally:
+            self.windows.append((tag, t0, datetime.datetime.now()))
 
     @staticmethod
     def _when(ts: str):
@@ -171,7 +180,8 @@ class ClockSampler:
 
     def stop(self):
         if not self.proc:
-            return None
+            self.rows = []
+            return self
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
@@ -180,18 +190,30 @@ class ClockSampler:
             out, _ = self.proc.communicate()
         rows = [[c.strip() for c in ln.split(",")] for ln in out.strip().splitlines() if ln.count(",") >= 9]
         mine = [r for r in rows if self.uuid and self.uuid in r[1]] or rows
-        if self.t0 and self.t1:
-            inside = [r for r in mine if (w := self._when(r[0])) is not None and self.t0 <= w <= self.t1]
-            mine = inside or mine
-        mine = [r[1:] for r in mine]
-        if not mine:
+        self.rows = [(self._when(r[0]), r[1:]) for r in mine]
+        return self
+
+    def summary(self, prefix: str = ""):
+        """Clock record of the timed regions whose tag starts with prefix (median SM clock under load,
+        maximum clock, throttle reasons seen, sample count); None without samples."""
+        if self.rows is None:
+            self.stop()
+        wins = [(a, b) for tag, a, b in self.windows if tag.startswith(prefix)]
+        inside = [r for w, r in self.rows if w is not None and any(a <= w <= b for a, b in wins)]
+        if not inside:
             return None
-        sm = [float(r[1]) for r in mine if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in mine for k in range(4) if r[5 + k].lower() == "active"})
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        reasons = sorted({self.REASONS[k] for r in inside for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(mine)}
+                "reasons": reasons, "samples": len(inside)}
+
+
+def gpu_uuid(torch, dev: int):
+    try:
+        return str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
 
 
 def hbm_peak():
@@ -382,13 +404,7 @@ def run_ours(args, ranks: Ranks):
         x.zero_()
         return lat.cg_solve(MASS, b, x, tol=TOL, max_iter=20000, mode=mode)
 
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(ranks.local).uuid)
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
-    clocks.start()
+    clocks = ClockSampler(gpu_uuid(torch, ranks.local)).start()
     for _ in range(max(args.warmup, 0)):
         solve(sq.MODE_MIXED)
     torch.cuda.synchronize()
@@ -397,14 +413,12 @@ def run_ours(args, ranks: Ranks):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ranks.barrier()
     torch.cuda.synchronize()
-    clocks.mark_start()
-    e0.record(s)
-    infos = [solve(sq.MODE_MIXED) for _ in range(args.steps)]
-    e1.record(s)
-    torch.cuda.synchronize()
-    clocks.mark_stop()
+    with clocks.timed("main"):
+        e0.record(s)
+        infos = [solve(sq.MODE_MIXED) for _ in range(args.steps)]
+        e1.record(s)
+        torch.cuda.synchronize()
     ranks.barrier()
-    clk = clocks.stop()
     t_step = e0.elapsed_time(e1) / 1e3 / args.steps
     # Dslash applications: 2 per iteration and 2 per FP64 reliable update (the last one is the convergence
     # check); from x0 = 0 the initial residual is b itself, with no operator application
@@ -487,16 +501,26 @@ def run_ours(args, ranks: Ranks):
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.nbytes),
            "d2h_bytes_per_step": int(b_host.nbytes), "ms_per_step": t_e2e * 1e3}
 
+    lat.close()
+    del lat, b, x, lat_f
+    forms = None
+    if ranks.world == 1 and not args.no_forms:
+        forms = run_forms(torch, sq, clocks)
+    clocks.stop()
+    clk = clocks.summary("main")
+    if forms:
+        for name, rec in forms.items():
+            if "unavailable" not in rec:
+                rec["clocks"] = clocks.summary(name)
     cpu = None
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(fat, lng, b_host)
-    lat.close()
     if ranks.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "cg_mixed": mixed_info, "cg_fp64": fp64_info,
+                "clocks": clk, "cg_mixed": mixed_info, "cg_fp64": fp64_info, "forms": forms,
                 "speedup_vs_fp64_cg": t64 / t_step, "dslash": dslash, "cpu": cpu_info(),
                 "dslash_gpu_vs_oracle": None if cpu is None else {
                     "gpu_f32_recon12_gflops": dslash["f32_recon12"]["gflops"], "gpu_f64_gflops": dslash["f64"]["gflops"],
@@ -524,6 +548,270 @@ def _timed(torch, fn):
     return out, e0.elapsed_time(e1)
 
 
+def _repeat(torch, clk, tag, fn, steps):
+    """steps timed calls of fn inside one clock window; (median ms, last result)."""
+    times, out = [], None
+    with clk.timed(tag):
+        for _ in range(steps):
+            out, ms = _timed(torch, fn)
+            times.append(ms)
+    return statistics.median(times), out
+
+
+def _solve_sigma(lat, sigma, b, x, sq, mode=None):
+    """CG of (sigma - D_eo D_oe) x = b (mass = sqrt(sigma) / 2), plain FP64 unless mode says otherwise."""
+    x.zero_()
+    return lat.cg_solve(float(np.sqrt(sigma) / 2), b, x, tol=TOL, max_iter=20000,
+                        mode=sq.MODE_F64 if mode is None else mode)
+
+
+MS_SEEDS = (1003, 2300)  # gauge, source of the multi-shift workload (third configuration)
+MS_SHIFTS = tuple(float(v) for v in np.logspace(-4, 0, 11))
+
+
+def measure_multishift(torch, sq, clk, lat, b, steps, compare=True, tag="multishift"):
+    """Mixed multi-shift (11 shifts) against the FP64 multi-shift and plain FP64 CG one shift at a time."""
+    shifts = list(MS_SHIFTS)
+    xs = [lat.new_spinor() for _ in shifts]
+    res = {}
+    modes = (("mixed", sq.MODE_MIXED),) + ((("fp64_multishift", sq.MODE_F64),) if compare else ())
+    for name, mode in modes:
+        def run(mode=mode):
+            return lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode)
+        run()
+        ms, infos = _repeat(torch, clk, f"{tag}.{name}", run, steps if name == "mixed" else 1)
+        res[name] = {"ms": ms, "iters": [i.iters for i in infos],
+                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+    if compare:  # plain FP64 CG, one solve per shift (the same buffers: one captured graph)
+        x = lat.new_spinor()
+        _solve_sigma(lat, shifts[0], b, x, sq)
+        total, iters = 0.0, []
+        with clk.timed(f"{tag}.fp64_cg"):
+            for sg in shifts:
+                info, ms = _timed(torch, lambda sg=sg: _solve_sigma(lat, sg, b, x, sq))
+                total += ms
+                iters.append(info.iters)
+        res["fp64_cg_one_per_shift"] = {"ms": total, "iters": iters}
+        res["speedup_vs_fp64_cg_one_per_shift"] = total / res["mixed"]["ms"]
+        res["speedup_vs_fp64_multishift"] = res["fp64_multishift"]["ms"] / res["mixed"]["ms"]
+    return res
+
+
+def measure_rational(torch, sq, clk, lat, b, steps, tag="rational"):
+    """12-pole rational approximation of (4m^2 - D_eo D_oe)^(-1/2) applied to b (m = 0.01), mixed vs FP64."""
+    m = 0.01
+    a0, a, beta = synth_rational(m)
+    shifts = 4 * m * m + beta
+    out = lat.new_spinor()
+    res = {"shifts": [float(v) for v in shifts]}
+    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+        def run(mode=mode):
+            return lat.rational_apply(shifts, a, a0, b, out, tol=TOL, max_iter=20000, mode=mode)
+        run()
+        ms, infos = _repeat(torch, clk, f"{tag}.{name}", run, steps if name == "mixed" else 1)
+        res[name] = {"ms": ms, "iters": max(i.iters for i in infos),
+                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+    res["speedup_vs_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    return res
+
+
+def synth_rational(m):
+    import synth
+
+    return synth.inverse_sqrt_rational(12, 4 * m * m, 16.0)
+
+
+BATCHED_SPECS = ((16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 64))
+
+
+def make_batched(sq, torch, specs, nr=16):
+    import synth
+
+    lats, bs, xs = [], [], []
+    for n, L in enumerate(specs):
+        fat, lng = synth.fat_long_links(L, 1004 + n)
+        lat = sq.Lattice(L)
+        lat.load_links(fat, lng, recon12=True)
+        src = synth.gaussian_source(L, 2400 + 10 * n, nrhs=nr)
+        b = torch.stack([lat.pack(v) for v in src]).contiguous()
+        lats.append(lat); bs.append(b); xs.append(torch.zeros_like(b))
+    return lats, bs, xs
+
+
+def measure_batched(torch, sq, clk, lats, bs, xs, steps, compare=True, fp64_per_lattice=None, tag="batched"):
+    """All RHS of all lattices in one batched solve (m = 0.02), against mixed CG and plain FP64 CG one source
+    at a time. fp64_per_lattice: time plain FP64 CG on only the first sources of each lattice and scale the
+    sum by nrhs / that count (None: every source)."""
+    m = 0.02
+    specs = [lat.dims for lat in lats]
+
+    def solve():
+        for x in xs:
+            x.zero_()
+        return sq.cg_solve_batched(lats, [m] * len(lats), bs, xs, tol=TOL, max_iter=20000)
+
+    solve()  # tunes the batched Dslash on the first call
+    t_batched, infos = _repeat(torch, clk, f"{tag}.batched", solve, steps)
+    cfg = sq.batched_tuning_ex(lats[0])
+    nr = int(bs[0].shape[0])
+    res = {"ms": t_batched, "tuned": cfg, "nrhs_per_lattice": nr, "lattices": ["x".join(map(str, L)) for L in specs],
+           "max_iters": max(i.iters for lst in infos for i in lst),
+           "max_true_rel_resid": max(i.true_rel_resid for lst in infos for i in lst)}
+    apps = sum(2 * (i.iters + i.reliable_updates) * int(np.prod(L)) // 2 for L, lst in zip(specs, infos) for i in lst)
+    res["dslash_gflops_in_solve"] = FLOPS_PER_SITE * apps / (t_batched / 1e3) / 1e9
+    if compare:
+        t64, tmix, n64 = 0.0, 0.0, 0
+        k64 = nr if fp64_per_lattice is None else min(nr, fp64_per_lattice)
+        for lat, b in zip(lats, bs):
+            x = lat.new_spinor()
+            for mode in (sq.MODE_MIXED, sq.MODE_F64):  # capture each mode's graph once
+                x.zero_()
+                lat.cg_solve(m, b[0], x, tol=TOL, max_iter=20000, mode=mode)
+            with clk.timed(f"{tag}.sequential"):
+                for j in range(nr):
+                    def run(mode, j=j):
+                        x.zero_()
+                        return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=mode)
+
+                    tmix += _timed(torch, lambda: run(sq.MODE_MIXED))[1]
+                    if j < k64:
+                        t64 += _timed(torch, lambda: run(sq.MODE_F64))[1]
+                        n64 += 1
+        scale = len(lats) * nr / n64
+        res.update({"mixed_cg_one_per_source_ms": tmix, "fp64_cg_one_per_source_ms": t64 * scale,
+                    "fp64_cg_sources_timed": n64, "fp64_cg_scaled_by": scale,
+                    "speedup_vs_fp64_cg": t64 * scale / t_batched, "speedup_vs_mixed_cg_sequential": tmix / t_batched})
+    return res
+
+
+LEARNED_MASS = 0.005
+LEARNED_HELD_OUT = (9000, 9100)  # gauge, source of the held-out evaluation
+PARAMS_DIR = os.path.join(ROOT, "paper_1611_00728_gb300", "trained")
+PARAMS_FILE = os.path.join(PARAMS_DIR, "fcg_network_16x16x16x16.npy")
+
+
+def measure_learned(torch, sq, clk, L, params, steps, compare=True, tag="learned"):
+    """Flexible CG with the network on the held-out gauge field, against plain FP64 and mixed CG at 1e-8."""
+    import synth
+
+    m = LEARNED_MASS
+    fat, lng = synth.fat_long_links(L, LEARNED_HELD_OUT[0])
+    lat = sq.Lattice(L)
+    lat.load_links(fat, lng, recon12=True)
+    net = sq.Network(lat)
+    net.set_params(params)
+    b = lat.pack(synth.gaussian_source(L, LEARNED_HELD_OUT[1]))
+    x = lat.new_spinor()
+    out = {}
+    solvers = [("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))]
+    if compare:
+        solvers += [("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
+                    ("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64))]
+    for name, fn in solvers:
+        def run(fn=fn):
+            x.zero_()
+            return fn()
+        run()
+        ms, info = _repeat(torch, clk, f"{tag}.{name}", run, steps if name != "fp64_cg" else 1)
+        out[name] = {"ms": ms, "iters": info.iters, "true_rel_resid": info.true_rel_resid,
+                     "fallback": getattr(info, "fallback", 0)}
+    if compare:
+        out["speedup_vs_fp64_cg"] = out["fp64_cg"]["ms"] / out["fcg_nn"]["ms"]
+        out["speedup_vs_mixed_cg"] = out["mixed_cg"]["ms"] / out["fcg_nn"]["ms"]
+    net.close()
+    lat.close()
+    return out
+
+
+def measure_hisq(torch, sq, clk, lattice, steps, tag="hisq"):
+    """HISQ link construction (device entry point), then mixed and FP64 CG on the HISQ links."""
+    import synth
+
+    V = int(np.prod(lattice))
+    thin = synth.thin_links(lattice, GAUGE_SEED)
+    d_thin = torch.from_numpy(thin.view(np.float64).reshape(-1)).cuda()
+    d_fat, d_lng = torch.empty_like(d_thin), torch.empty_like(d_thin)
+    ws = torch.empty(sq.hisq_workspace_bytes(lattice), dtype=torch.uint8, device="cuda")
+    sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws)
+    t_ms, _ = _repeat(torch, clk, f"{tag}.smear", lambda: sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws), steps)
+    del d_fat, d_lng, ws
+    gflops = V * 4 * sq.HISQ_FLOPS_PER_LINK / (t_ms / 1e3) / 1e9
+    lat = sq.Lattice(lattice)
+    lat.hisq_load_links(thin)
+    b = lat.pack(synth.gaussian_source(lattice, SOURCE_SEED))
+    x = lat.new_spinor()
+    cg = {}
+    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
+        def solve(mode=mode):
+            x.zero_()
+            return lat.cg_solve(MASS, b, x, tol=TOL, max_iter=20000, mode=mode)
+        solve()
+        ms, info = _repeat(torch, clk, f"{tag}.cg_{name}", solve, steps if name == "mixed" else 1)
+        cg[name] = {"ms": ms, "iters": info.iters, "true_rel_resid": info.true_rel_resid}
+    lat.close()
+    return {"smear_ms": t_ms, "smear_gflops": gflops, "smear_frac_of_nominal_fp64": gflops / NOMINAL_FP64_GFLOPS,
+            "cg_on_hisq_links": cg, "cg_speedup_mixed_vs_fp64": cg["fp64"]["ms"] / cg["mixed"]["ms"]}
+
+
+def load_trained_params():
+    """The committed network parameters and their training record (None, reason when absent)."""
+    if not os.path.exists(PARAMS_FILE):
+        return None, f"no trained parameters at {os.path.relpath(PARAMS_FILE, ROOT)}"
+    rec = None
+    side = PARAMS_FILE[:-4] + ".json"
+    if os.path.exists(side):
+        with open(side) as f:
+            rec = json.load(f)
+    return np.load(PARAMS_FILE).astype(np.float32), rec
+
+
+def run_forms(torch, sq, clk):
+    """The other forms of the solve, each against plain FP64 GPU CG at the same true residual 1e-8, in the
+    default line (one GPU): mixed multi-shift, rational application, the batched 48-source solve, the learned
+    flexible CG (committed parameters) and the CG on GPU-built HISQ links."""
+    import synth
+
+    forms = {}
+    fat, lng = synth.fat_long_links(LATTICE, MS_SEEDS[0])
+    lat = sq.Lattice(LATTICE)
+    lat.load_links(fat, lng, recon12=True)
+    b = lat.pack(synth.gaussian_source(LATTICE, MS_SEEDS[1]))
+    del fat, lng
+    forms["multishift"] = measure_multishift(torch, sq, clk, lat, b, 3)
+    forms["multishift"]["config"] = "32^4, 11 shifts logspace(-4,0), seeds 1003/2300"
+    forms["rational"] = measure_rational(torch, sq, clk, lat, b, 3)
+    forms["rational"]["config"] = "32^4, m=0.01, 12 poles of x^(-1/2) on [4m^2, 16], seeds 1003/2300"
+    lat.close()
+    lats, bs, xs = make_batched(sq, torch, BATCHED_SPECS)
+    forms["batched"] = measure_batched(torch, sq, clk, lats, bs, xs, 2, fp64_per_lattice=4)
+    forms["batched"]["config"] = "16 sources each on 16^4, 24^4, 32^3x64, m=0.02 (gauge seeds 1004-1006)"
+    for lat_ in lats:
+        lat_.close()
+    del lats, bs, xs
+    params, rec = load_trained_params()
+    if params is None:
+        forms["learned"] = {"unavailable": rec}
+    else:
+        forms["learned"] = measure_learned(torch, sq, clk, LATTICE, params, 3)
+        forms["learned"]["config"] = ("32^4, m=0.005, held-out gauge seed 9000, source 9100; network parameters "
+                                      f"from {os.path.relpath(PARAMS_FILE, ROOT)}")
+        if rec:
+            forms["learned"]["training"] = {k: rec.get(k) for k in ("pairs", "schedule", "seconds_data",
+                                                                     "seconds_train", "command")}
+    forms["hisq"] = measure_hisq(torch, sq, clk, LATTICE, 3)
+    forms["hisq"]["config"] = "32^4 thin links seed 1002 -> HISQ fat/long (FP64); CG m=0.01 on the result"
+    torch.cuda.synchronize()
+    return forms
+
+
+def _workload_line(metric, value, args, config, clk, extra, dtype="f32", unit="ms", hib=False):
+    line = {"metric": metric, "unit": unit, "value": value, "higher_is_better": hib, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": dtype, "config": config,
+            "clocks": clk.summary("")}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
 def run_multishift(args):
     """32^4, 11 shifts logspace(-4, 0), one Gaussian source, per-shift tol 1e-8."""
     import torch
@@ -532,46 +820,18 @@ def run_multishift(args):
     import synth
 
     sq.build_if_needed()
-    fat, lng = synth.fat_long_links(LATTICE, 1003)
-    b_host = synth.gaussian_source(LATTICE, 2300)
-    shifts = list(np.logspace(-4, 0, 11))
+    fat, lng = synth.fat_long_links(LATTICE, MS_SEEDS[0])
     lat = sq.Lattice(LATTICE)
     lat.load_links(fat, lng, recon12=True)
-    b = lat.pack(b_host)
-    xs = [lat.new_spinor() for _ in shifts]
-    res = {"fp64": None, "fp64_cg_per_shift": None}
-    modes = (("mixed", sq.MODE_MIXED),) if args.no_compare else (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64))
-    for name, mode in modes:
-        for _ in range(max(args.warmup, 1)):
-            lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode)
-        times, infos = [], None
-        for _ in range(args.steps):
-            infos, ms = _timed(torch, lambda: lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=mode))
-            times.append(ms)
-        res[name] = {"ms": statistics.median(times), "iters": [i.iters for i in infos],
-                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
-    # plain FP64 CG, one solve per shift
-    if not args.no_compare:
-        x = lat.new_spinor()
-        total, iters = 0.0, []
-        for sg in shifts:
-            info, ms = _timed(torch, lambda sg=sg: _solve_sigma(lat, sg, b, x, sq))
-            total += ms
-            iters.append(info.iters)
-        res["fp64_cg_per_shift"] = {"ms": total, "iters": iters}
+    b = lat.pack(synth.gaussian_source(LATTICE, MS_SEEDS[1]))
+    clk = ClockSampler(gpu_uuid(torch, 0)).start()
+    res = measure_multishift(torch, sq, clk, lat, b, args.steps, compare=not args.no_compare)
+    clk.stop()
+    res["clocks"] = clk.summary("multishift")
     lat.close()
-    Vh = int(np.prod(LATTICE)) // 2
-    line = {"metric": "multi-shift CG time to per-shift true residual 1e-8 vs plain FP64 CG", "unit": "ms",
-            "value": res["mixed"]["ms"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "32^4 multi-shift CG, 11 shifts logspace(-4,0), 1 source (seeds 1003/2300)",
-                       "vh": Vh, "shifts": shifts},
-            "multishift_mixed": res["mixed"], "multishift_fp64": res["fp64"],
-            "fp64_cg_one_per_shift": res["fp64_cg_per_shift"],
-            "speedup_vs_fp64_cg_per_shift": (res["fp64_cg_per_shift"]["ms"] / res["mixed"]["ms"]
-                                             if res["fp64_cg_per_shift"] else None),
-            "speedup_vs_fp64_multishift": res["fp64"]["ms"] / res["mixed"]["ms"] if res["fp64"] else None}
-    print(json.dumps(line), flush=True)
+    _workload_line("multi-shift CG time to per-shift true residual 1e-8 vs plain FP64 CG", res["mixed"]["ms"], args,
+                   {"workload": "32^4 multi-shift CG, 11 shifts logspace(-4,0), 1 source (seeds 1003/2300)",
+                    "vh": int(np.prod(LATTICE)) // 2, "shifts": list(MS_SHIFTS)}, clk, {"multishift": res})
 
 
 def run_rational(args):
@@ -583,42 +843,19 @@ def run_rational(args):
     import synth
 
     sq.build_if_needed()
-    m = 0.01
-    fat, lng = synth.fat_long_links(LATTICE, 1003)
-    b_host = synth.gaussian_source(LATTICE, 2300)
-    a0, a, beta = synth.inverse_sqrt_rational(12, 4 * m * m, 16.0)
-    shifts = 4 * m * m + beta
+    fat, lng = synth.fat_long_links(LATTICE, MS_SEEDS[0])
     lat = sq.Lattice(LATTICE)
     lat.load_links(fat, lng, recon12=True)
-    b = lat.pack(b_host)
-    out = lat.new_spinor()
-    res = {}
-    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
-        for _ in range(max(args.warmup, 1)):
-            lat.rational_apply(shifts, a, a0, b, out, tol=TOL, max_iter=20000, mode=mode)
-        times, infos = [], None
-        for _ in range(args.steps):
-            infos, ms = _timed(torch, lambda: lat.rational_apply(shifts, a, a0, b, out, tol=TOL, max_iter=20000,
-                                                                 mode=mode))
-            times.append(ms)
-        res[name] = {"ms": statistics.median(times), "iters": max(i.iters for i in infos),
-                     "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+    b = lat.pack(synth.gaussian_source(LATTICE, MS_SEEDS[1]))
+    clk = ClockSampler(gpu_uuid(torch, 0)).start()
+    res = measure_rational(torch, sq, clk, lat, b, args.steps)
+    clk.stop()
     lat.close()
-    line = {"metric": "rational-function application r(A) b (12 poles) time, every pole to true residual 1e-8",
-            "unit": "ms", "value": res["mixed"]["ms"], "higher_is_better": False, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "32^4, m=0.01, 12-pole Gauss-Legendre approximation of x^(-1/2) on [4m^2, 16], "
-                                   "1 source (seeds 1003/2300)", "vh": int(np.prod(LATTICE)) // 2,
-                       "shifts": [float(v) for v in shifts]},
-            "rational_mixed": res["mixed"], "rational_fp64": res["fp64"],
-            "speedup_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"]}
-    print(json.dumps(line), flush=True)
-
-
-def _solve_sigma(lat, sigma, b, x, sq):
-    """Plain FP64 CG of (sigma - D_eo D_oe) x = b (mass = sqrt(sigma) / 2)."""
-    x.zero_()
-    return lat.cg_solve(float(np.sqrt(sigma) / 2), b, x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
+    _workload_line("rational-function application r(A) b (12 poles) time, every pole to true residual 1e-8",
+                   res["mixed"]["ms"], args,
+                   {"workload": "32^4, m=0.01, 12-pole Gauss-Legendre approximation of x^(-1/2) on [4m^2, 16], "
+                                "1 source (seeds 1003/2300)", "vh": int(np.prod(LATTICE)) // 2}, clk,
+                   {"rational": res})
 
 
 def run_batched(args):
@@ -626,73 +863,25 @@ def run_batched(args):
     import torch
 
     import paper_1611_00728_gb300 as sq
-    import synth
 
     sq.build_if_needed()
-    specs = [(16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 64)]
+    specs = BATCHED_SPECS
     if args.lattice:
-        specs = [tuple(int(v) for v in args.lattice.split(","))]
-    m, nr = 0.02, 16
-    lats, bs, xs = [], [], []
-    for n, L in enumerate(specs):
-        fat, lng = synth.fat_long_links(L, 1004 + n)
-        lat = sq.Lattice(L)
-        lat.load_links(fat, lng, recon12=True)
-        src = synth.gaussian_source(L, 2400 + 10 * n, nrhs=nr)
-        b = torch.stack([lat.pack(s) for s in src]).contiguous()
-        lats.append(lat); bs.append(b); xs.append(torch.zeros_like(b))
-
-    def solve():
-        for x in xs:
-            x.zero_()
-        return sq.cg_solve_batched(lats, [m] * len(lats), bs, xs, tol=TOL, max_iter=20000)
-
-    for _ in range(max(args.warmup, 1)):
-        solve()
-    times, infos = [], None
-    for _ in range(args.steps):
-        infos, ms = _timed(torch, solve)
-        times.append(ms)
-    t_batched = statistics.median(times)
-    W, T = sq.batched_tuning(lats[0])
-    # plain FP64 CG and single-RHS mixed CG, one source at a time
-    t64 = tmix = None
-    if not args.no_compare:
-        t64, tmix = 0.0, 0.0
-        for lat, b in zip(lats, bs):
-            x = lat.new_spinor()
-            for j in range(nr):
-                def f64():
-                    x.zero_()
-                    return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_F64)
-
-                def fmx():
-                    x.zero_()
-                    return lat.cg_solve(m, b[j], x, tol=TOL, max_iter=20000, mode=sq.MODE_MIXED)
-
-                _, ms = _timed(torch, f64)
-                t64 += ms
-                _, ms = _timed(torch, fmx)
-                tmix += ms
-    site_rhs = sum(nr * int(np.prod(L)) // 2 for L in specs)
-    apps = sum(2 * (i.iters + i.reliable_updates) * int(np.prod(L)) // 2
-               for L, lst in zip(specs, infos) for i in lst)
-    line = {"metric": f"batched CG time to true residual 1e-8 ({nr * len(specs)} sources, {len(specs)} lattices) "
-                      "vs plain FP64 CG", "unit": "ms",
-            "value": t_batched, "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "16 Gaussian sources each on " + ", ".join("x".join(map(str, L)) for L in specs)
-                                   + ", m=0.02 (gauge seeds from 1004)", "site_rhs": site_rhs},
-            "batched_ms": t_batched, "tuned_W": W, "tuned_T": T,
-            "dslash_gflops_in_solve": FLOPS_PER_SITE * apps / (t_batched / 1e3) / 1e9,
-            "max_iters": max(i.iters for lst in infos for i in lst),
-            "max_true_rel_resid": max(i.true_rel_resid for lst in infos for i in lst),
-            "fp64_cg_one_per_source_ms": t64, "mixed_cg_one_per_source_ms": tmix,
-            "speedup_vs_fp64_cg": t64 / t_batched if t64 else None,
-            "speedup_vs_mixed_cg_sequential": tmix / t_batched if tmix else None}
+        specs = (tuple(int(v) for v in args.lattice.split(",")),)
+    lats, bs, xs = make_batched(sq, torch, specs)
+    clk = ClockSampler(gpu_uuid(torch, 0)).start()
+    res = measure_batched(torch, sq, clk, lats, bs, xs, args.steps, compare=not args.no_compare)
+    clk.stop()
+    res["clocks"] = clk.summary("batched")
     for lat in lats:
         lat.close()
-    print(json.dumps(line), flush=True)
+    n = int(bs[0].shape[0]) * len(specs)
+    _workload_line(f"batched CG time to true residual 1e-8 ({n} sources, {len(specs)} lattices) vs plain FP64 CG",
+                   res["ms"], args, {"workload": "16 Gaussian sources each on " + ", ".join("x".join(map(str, L))
+                                                                                        for L in specs)
+                                     + ", m=0.02 (gauge seeds from 1004)",
+                                     "site_rhs": sum(16 * int(np.prod(L)) // 2 for L in specs)}, clk,
+                   {"batched": res})
 
 
 def run_hisq(args):
@@ -706,36 +895,9 @@ def run_hisq(args):
     sq.build_if_needed()
     lattice = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else LATTICE
     V = int(np.prod(lattice))
-    thin = synth.thin_links(lattice, GAUGE_SEED)
-    d_thin = torch.from_numpy(thin.view(np.float64).reshape(-1)).cuda()
-    d_fat, d_lng = torch.empty_like(d_thin), torch.empty_like(d_thin)
-    ws = torch.empty(sq.hisq_workspace_bytes(lattice), dtype=torch.uint8, device="cuda")
-    for _ in range(max(args.warmup, 1)):
-        sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws)
-    times = []
-    for _ in range(args.steps):
-        _, ms = _timed(torch, lambda: sq.hisq_smear(lattice, d_thin, d_fat, d_lng, ws))
-        times.append(ms)
-    t = statistics.median(times) / 1e3
-    flops = V * 4 * sq.HISQ_FLOPS_PER_LINK
-    gflops = flops / t / 1e9
-    # the CG on the HISQ links (the long links are U(3): full 18-real storage)
-    lat = sq.Lattice(lattice)
-    lat.hisq_load_links(thin)
-    b = lat.pack(synth.gaussian_source(lattice, SOURCE_SEED))
-    x = lat.new_spinor()
-    cg = {}
-    for name, mode in (("mixed", sq.MODE_MIXED), ("fp64", sq.MODE_F64)):
-        def solve(mode=mode):
-            x.zero_()
-            return lat.cg_solve(MASS, b, x, tol=TOL, max_iter=20000, mode=mode)
-        solve()
-        ts, info = [], None
-        for _ in range(args.steps):
-            info, ms = _timed(torch, solve)
-            ts.append(ms)
-        cg[name] = {"ms": statistics.median(ts), "iters": info.iters, "true_rel_resid": info.true_rel_resid}
-    lat.close()
+    clk = ClockSampler(gpu_uuid(torch, 0)).start()
+    res = measure_hisq(torch, sq, clk, lattice, args.steps)
+    clk.stop()
     cpu = None
     if not args.no_cpu_baseline:
         import oracle.hisq as oh
@@ -749,150 +911,133 @@ def run_hisq(args):
         cpu = {"value": Vs * 4 * sq.HISQ_FLOPS_PER_LINK / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "seconds": dt, "sample": "oracle (numpy path sums, FP64) HISQ links of an 8^4 lattice, same counted "
                                         "flops per link"}
-    line = {"metric": "HISQ link construction time (thin -> fat, long; FP64) and CG time on the HISQ links",
-            "unit": "ms", "value": t * 1e3, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
-            "config": {"workload": "x".join(map(str, lattice)) + " HISQ smearing of random SU(3) thin links (width 0.3, "
-                                   "seed 1002); CG m=0.01 to true rel. residual 1e-8 on the result", "sites": V,
-                       "l2": f"thin links {V * 576 / 1e9:.2f} GB, workspace {V * 56 * 144 / 1e9:.2f} GB (L2 129 MB)"},
-            "roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, FP64 3x3 products)",
-                         "achieved": gflops, "peak": NOMINAL_FP64_GFLOPS, "unit": "GFLOP/s",
-                         "frac": gflops / NOMINAL_FP64_GFLOPS, "peak_kind": "nominal FP64 rate",
-                         "counted_flops_per_link": sq.HISQ_FLOPS_PER_LINK, "traffic": None},
-            "cpu_baseline": cpu, "cg_on_hisq_links": cg,
-            "cg_speedup_mixed_vs_fp64": cg["fp64"]["ms"] / cg["mixed"]["ms"]}
-    print(json.dumps(line), flush=True)
+    gflops = res["smear_gflops"]
+    _workload_line("HISQ link construction time (thin -> fat, long; FP64) and CG time on the HISQ links",
+                   res["smear_ms"], args,
+                   {"workload": "x".join(map(str, lattice)) + " HISQ smearing of random SU(3) thin links (width 0.3, "
+                                "seed 1002); CG m=0.01 to true rel. residual 1e-8 on the result", "sites": V,
+                    "l2": f"thin links {V * 576 / 1e9:.2f} GB, workspace {V * 56 * 144 / 1e9:.2f} GB (L2 129 MB)"},
+                   clk, {"roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, FP64 3x3 products)",
+                                      "achieved": gflops, "peak": NOMINAL_FP64_GFLOPS, "unit": "GFLOP/s",
+                                      "frac": gflops / NOMINAL_FP64_GFLOPS, "peak_kind": "nominal FP64 rate",
+                                      "counted_flops_per_link": sq.HISQ_FLOPS_PER_LINK, "traffic": None},
+                         "cpu_baseline": cpu, "hisq": res}, dtype="f64")
 
 
-def run_learned(args):
-    """Learned preconditioner: train at 16^4 on CG pairs, flexible CG on held-out seeds at 16^4 and 32^4."""
-    import torch
+# The learned preconditioner's training set: (residual, error) pairs from plain FP64 CG on seeded 16^4 gauge
+# fields (seeds 0..TRAIN_FIELDS-1), TRAIN_SOURCES Gaussian sources each, at the CG iterates TRAIN_KS.
+TRAIN_FIELDS = 32
+TRAIN_SOURCES = 8
+TRAIN_KS = tuple(range(0, 24)) + tuple(range(24, 64, 3)) + (64, 70, 76, 82, 90)
+TRAIN_LRS = (1e-2, 1e-2, 5e-3, 2.5e-3, 1.25e-3, 6e-4)
+TRAIN_STEPS_PER_FIELD = 60
 
-    import paper_1611_00728_gb300 as sq
+
+def train_network(torch, sq, log=None):
+    """Train the network at 16^4 on about 10^4 CG pairs (R13 of the design notes: iterates well before
+    convergence against an FP64 x* solved to 1e-13, A^2-norm loss). Returns (params, record)."""
     import synth
 
-    sq.build_if_needed()
-    m, sigma = 0.005, 4 * 0.005 ** 2
+    m, sigma = LEARNED_MASS, 4 * LEARNED_MASS ** 2
     Ltr = (16, 16, 16, 16)
-    if args.load_params:
-        return _learned_eval(args, np.load(args.load_params).astype(np.float32), None)
     t0 = time.perf_counter()
-    # training pairs: CG iterates x_k (CG from 0 truncated at k) against an FP64 x* solved to 1e-13,
-    # 8 gauge seeds x 4 sources. Only iterates well before convergence (about 120 iterations here):
-    # near convergence e = x* - x_k is dominated by the error of x* itself.
-    ks = [0, 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 80]
-    R, E = [], []
-    nets = []
-    for gseed in range(8):
+    per = len(TRAIN_KS) * TRAIN_SOURCES
+    fields = []
+    for gseed in range(TRAIN_FIELDS):
         fat, lng = synth.fat_long_links(Ltr, gseed)
         lat = sq.Lattice(Ltr)
         lat.load_links(fat, lng, recon12=True)
         net = sq.Network(lat)
         net.set_loss(2)
-        for src in range(4):
-            b = lat.pack(synth.gaussian_source(Ltr, 5000 + 10 * gseed + src))
-            xs = lat.new_spinor()
+        R = lat.new_spinor(sq.F32, count=per)
+        E = lat.new_spinor(sq.F32, count=per)
+        xs, xk = lat.new_spinor(), lat.new_spinor()
+        n = 0
+        for src in range(TRAIN_SOURCES):
+            b = lat.pack(synth.gaussian_source(Ltr, 5000 + 100 * gseed + src))
+            xs.zero_()
             lat.cg_solve(m, b, xs, tol=1e-13, max_iter=50000, mode=sq.MODE_F64)
-            for k in ks:
-                xk = lat.new_spinor()
-                if k > 0:
+            for k in TRAIN_KS:
+                xk.zero_()
+                if k > 0:  # CG from 0 truncated at k iterations: exactly the k-th iterate of the long run
                     lat.cg_solve(m, b, xk, tol=1e-30, max_iter=k, mode=sq.MODE_F64, raise_on_error=False)
-                r32, e32 = lat.new_spinor(sq.F32), lat.new_spinor(sq.F32)
-                net.make_pair(sigma, b, xk, xs, r32, e32)
-                R.append(r32); E.append(e32)
-        nets.append((lat, net))
+                net.make_pair(sigma, b, xk, xs, R[n], E[n])
+                n += 1
+        fields.append((lat, net, R, E))
+        if log:
+            log(f"pairs: field {gseed + 1}/{TRAIN_FIELDS} ({time.perf_counter() - t0:.0f} s)")
+    torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    # train on the first lattice's network (weights are lattice independent) against all pairs: the pairs'
-    # A-norm needs their own links, so train per gauge field in turn and share the parameters
     rng = np.random.default_rng(0)
     params = None
-    t0 = time.perf_counter()
-    per = len(ks) * 4
     losses = []
-    # 8 epochs with a decaying step size: with 3 epochs at a constant 1e-2 the held-out 32^4 FCG took
-    # anywhere from 118 to 207 iterations across changes of the permutation or the initial weights;
-    # this schedule gave 112-114 in the same tests
-    lrs = [1e-2, 1e-2, 1e-2, 5e-3, 5e-3, 2.5e-3, 1.25e-3, 6e-4]
-    for epoch, lr in enumerate(lrs):
-        for g in rng.permutation(8):
-            lat, net = nets[g]
-            if params is not None:
-                net.set_params(params)
-            Rg = torch.stack(R[g * per:(g + 1) * per]).contiguous()
-            Eg = torch.stack(E[g * per:(g + 1) * per]).contiguous()
-            if params is None:
-                net.set_params(_init_net_params())
-            first, last = net.train(sigma, Rg, Eg, steps=60, batch=8, lr=lr, seed=int(g) + 1 + 100 * epoch)
+    t0 = time.perf_counter()
+    for epoch, lr in enumerate(TRAIN_LRS):
+        for g in rng.permutation(TRAIN_FIELDS):
+            lat, net, R, E = fields[g]
+            net.set_params(params if params is not None else init_net_params(sq))
+            first, last = net.train(sigma, R, E, steps=TRAIN_STEPS_PER_FIELD, batch=8, lr=lr,
+                                    seed=int(g) + 1 + 100 * epoch)
             losses.append((first, last))
             params = net.get_params()
+        if log:
+            log(f"epoch {epoch + 1}/{len(TRAIN_LRS)}: last batch loss {losses[-1][1]:.4f}")
     t_train = time.perf_counter() - t0
-    for lat, net in nets:
+    for lat, net, R, E in fields:
         net.close()
         lat.close()
-    if args.save_params:
-        np.save(args.save_params, np.asarray(params, dtype=np.float32))
-    return _learned_eval(args, params, {"ks": ks, "pairs": len(R), "lrs": lrs, "losses": losses, "t_data": t_data,
-                                        "t_train": t_train})
+    rec = {"pairs": TRAIN_FIELDS * per, "lattice": list(Ltr), "mass": m,
+           "schedule": f"{len(TRAIN_LRS)} epochs x {TRAIN_FIELDS} gauge fields x {TRAIN_STEPS_PER_FIELD} Adam steps "
+                       f"(batch 8), step size {list(TRAIN_LRS)}, A^2-norm loss",
+           "data": f"gauge seeds 0-{TRAIN_FIELDS - 1}, {TRAIN_SOURCES} sources each (seeds 5000 + 100 field + "
+                   f"source), CG iterates k in {list(TRAIN_KS)}",
+           "train_loss_first_last": [losses[0][0], losses[-1][1]], "seconds_data": t_data, "seconds_train": t_train}
+    return params, rec
 
 
-def _learned_eval(args, params, tr):
-    """Flexible CG with the trained parameters on the held-out gauge field at 16^4 and 32^4, next to plain FP64
-    and mixed CG (skipped with --no-compare); tr describes the training run (None: parameters loaded)."""
+def run_learned(args):
+    """Learned preconditioner: train at 16^4 on ~10^4 CG pairs (or load parameters), flexible CG on the held-out
+    gauge field at 16^4 and 32^4 against plain FP64 and mixed CG."""
     import torch
 
     import paper_1611_00728_gb300 as sq
-    import synth
 
-    m = 0.005
-    Ltr = (16, 16, 16, 16)
+    sq.build_if_needed()
+    if args.load_params:
+        params, rec = np.load(args.load_params).astype(np.float32), None
+    else:
+        params, rec = train_network(torch, sq, log=lambda msg: print(msg, file=sys.stderr, flush=True))
+        rec["command"] = "python bench.py --workload learned --save-params " + (args.save_params or "<path>")
+    clk = ClockSampler(gpu_uuid(torch, 0)).start()
     results = {}
-    for L in (Ltr, (32, 32, 32, 32)):
-        fat, lng = synth.fat_long_links(L, 9000)
-        lat = sq.Lattice(L)
-        lat.load_links(fat, lng, recon12=True)
-        net = sq.Network(lat)
-        net.set_params(params)
-        b = lat.pack(synth.gaussian_source(L, 9100))
-        x = lat.new_spinor()
-        out = {}
-        solvers = [("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64)),
-                   ("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
-                   ("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))]
-        for name, fn in solvers[2:] if args.no_compare else solvers:
-            x.zero_()
-            fn()
-            x.zero_()
-            info, ms = _timed(torch, fn)
-            out[name] = {"ms": ms, "iters": info.iters, "true_rel_resid": info.true_rel_resid,
-                         "fallback": getattr(info, "fallback", 0)}
-        results["x".join(map(str, L))] = out
-        net.close()
-        lat.close()
-    line = {"metric": "learned-preconditioned flexible CG time to true residual 1e-8 vs plain FP64 CG", "unit": "ms",
-            "value": results["32x32x32x32"]["fcg_nn"]["ms"], "higher_is_better": False, "n_gpus": 1,
-            "data": "synthetic", "dtype": "f32/bf16",
-            "config": {"workload": ("train 16^4 (gauge seeds 0-7, 4 sources each, CG iterates k in "
-                                    f"{tr['ks']}), " if tr else f"parameters from {args.load_params}, ")
-                                   + "held-out gauge seed 9000 at 16^4 and 32^4, m=0.005"},
-            "results": results}
-    if tr:
-        line["config"].update({"pairs": tr["pairs"], "training": f"{len(tr['lrs'])} epochs x 8 gauge fields x 60 "
-                                                                   f"Adam steps (batch 8), step size {tr['lrs']}"})
-        line.update({"train_loss_first_last": [tr["losses"][0][0], tr["losses"][-1][1]],
-                     "seconds_data": tr["t_data"], "seconds_train": tr["t_train"]})
-    print(json.dumps(line), flush=True)
+    for L in ((16, 16, 16, 16), LATTICE):
+        results["x".join(map(str, L))] = measure_learned(torch, sq, clk, L, params, args.steps,
+                                                         compare=not args.no_compare, tag="learned" + str(L[0]))
+    clk.stop()
+    if rec is not None:
+        rec["held_out"] = {k: {n: v for n, v in r.items() if isinstance(v, dict)} for k, r in results.items()}
+    if args.save_params:
+        np.save(args.save_params, np.asarray(params, dtype=np.float32))
+        if rec is not None:
+            with open(args.save_params[:-4] + ".json" if args.save_params.endswith(".npy")
+                      else args.save_params + ".json", "w") as f:
+                json.dump(rec, f, indent=1)
+    _workload_line("learned-preconditioned flexible CG time to true residual 1e-8 vs plain FP64 CG",
+                   results["32x32x32x32"]["fcg_nn"]["ms"], args,
+                   {"workload": "held-out gauge seed 9000 (source 9100) at 16^4 and 32^4, m=0.005; network "
+                                + (f"parameters from {args.load_params}" if args.load_params else
+                                   "trained in this run at 16^4")}, clk,
+                   {"results": results, "training": rec}, dtype="f32/bf16")
 
 
-def _init_net_params():
-    """Small seeded initial weights (numpy; layout as in include/sqcg.h)."""
+def init_net_params(sq):
+    """Small seeded initial weights (numpy; the binding's parameter layout)."""
     rng = np.random.default_rng(12345)
-    p = np.zeros(1472, dtype=np.float32)
-    for lo, hi, cin in ((0, 144, 1), (144, 1296, 8), (1296, 1440, 8)):
-        p[lo:hi] = rng.standard_normal(hi - lo) * 0.3 / np.sqrt(9 * cin)
-    p[1440:1448] = -0.5
-    p[1448:1456] = 1.0
-    p[1456:1464] = -0.5
-    p[1464:1472] = 1.0
+    p = np.zeros(sq.NN_NPARAMS, dtype=np.float32)
+    for sl, shape in sq.NN_LAYERS:
+        p[sl] = rng.standard_normal(sl.stop - sl.start) * 0.3 / np.sqrt(9 * shape[2])
+    for ga, gb in sq.NN_GATES:
+        p[ga], p[gb] = -0.5, 1.0
     return p
 
 

@@ -21,6 +21,8 @@ Seeds (fixed by convention for the benchmark workloads): gauge field
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 __all__ = [
@@ -83,16 +85,39 @@ def _reunitarise(U: np.ndarray) -> np.ndarray:
     return np.stack([a, b, c], axis=-2)
 
 
-def random_su3(rng: np.random.Generator, n: int, width: float = 0.3) -> np.ndarray:
-    """n random SU(3) matrices U = exp(i*width*H), H = sum_a g_a lambda_a / 2, g_a ~ N(0,1).
-
-    The exponential is taken through the Hermitian eigendecomposition of H, then
-    the result is re-unitarised so that U is SU(3) to rounding."""
-    g = rng.standard_normal((n, 8))
+def _su3_from_gaussians(g: np.ndarray, width: float) -> np.ndarray:
+    """exp(i*width*H) for H = sum_a g_a lambda_a / 2, one matrix per row of g, re-unitarised."""
     H = np.einsum("na,aij->nij", g, _GELL_MANN) * 0.5
     w, v = np.linalg.eigh(H)
     U = np.einsum("nij,nj,nkj->nik", v, np.exp(1j * width * w), np.conj(v))
     return _reunitarise(U)
+
+
+# above this many matrices the per-matrix work runs in a process pool (numpy's batched eigh holds
+# the GIL); every matrix is computed on its own, so the result is the same bit for bit
+_PARALLEL_MIN = 1 << 20
+
+
+def random_su3(rng: np.random.Generator, n: int, width: float = 0.3, workers: int | None = None) -> np.ndarray:
+    """n random SU(3) matrices U = exp(i*width*H), H = sum_a g_a lambda_a / 2, g_a ~ N(0,1).
+
+    The exponential is taken through the Hermitian eigendecomposition of H, then
+    the result is re-unitarised so that U is SU(3) to rounding. All random numbers
+    are drawn first, in one stream; large batches are then split over `workers`
+    spawned processes (default: all host cores)."""
+    g = rng.standard_normal((n, 8))
+    if workers is None:
+        workers = (os.cpu_count() or 1) if n >= _PARALLEL_MIN else 1
+    if workers <= 1:
+        return _su3_from_gaussians(g, width)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    chunks = np.array_split(g, 4 * workers)
+    # spawn, not fork: callers may already hold a CUDA context
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_su3_from_gaussians, chunks, [width] * len(chunks)))
+    return np.concatenate(parts)
 
 
 def thin_links(L, seed: int, width: float = 0.3) -> np.ndarray:

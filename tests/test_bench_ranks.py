@@ -71,8 +71,9 @@ def test_single_rank_needs_no_process_group(monkeypatch):
     assert rate == pytest.approx(4.0) and tmax == 0.5
 
 
-def test_clock_sampler_keeps_only_the_timed_region():
-    """Samples are filtered to [mark_start, mark_stop] by timestamp; throttle reasons are read per field."""
+def test_clock_sampler_keeps_only_the_timed_regions():
+    """Samples are filtered by timestamp to the tagged timed regions (one record per tag prefix, or over all
+    regions); samples of other GPUs are dropped; throttle reasons are read per field."""
     import datetime
 
     import bench
@@ -83,6 +84,7 @@ def test_clock_sampler_keeps_only_the_timed_region():
         "2026/01/01 10:00:01.050, GPU-abc, 2055, 2070, 910, 0x0, Not Active, Not Active, Not Active, Not Active",
         "2026/01/01 10:00:01.100, GPU-zzz, 900, 2070, 100, 0x0, Active, Not Active, Not Active, Not Active",
         "2026/01/01 10:00:05.000, GPU-abc, 800, 2070, 200, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/01/01 10:00:07.000, GPU-abc, 1980, 2070, 950, 0x0, Not Active, Active, Not Active, Not Active",
     ]
 
     class FakeProc:
@@ -94,13 +96,18 @@ def test_clock_sampler_keeps_only_the_timed_region():
 
     c = bench.ClockSampler("GPU-abc")
     c.proc = FakeProc()
-    c.t0 = datetime.datetime(2026, 1, 1, 10, 0, 0, 500000)
-    c.t1 = datetime.datetime(2026, 1, 1, 10, 0, 2)
-    out = c.stop()
+    T = lambda s_, us=0: datetime.datetime(2026, 1, 1, 10, 0, s_, us)  # noqa: E731
+    c.windows = [("main", T(0, 500000), T(2)), ("forms.batched", T(6), T(8))]
+    c.stop()
+    out = c.summary("main")
     assert out["samples"] == 2
     assert out["sm_mhz"] == (2070 + 2055) / 2
     assert out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["sw_power_cap"]
+    f = c.summary("forms")
+    assert f["samples"] == 1 and f["sm_mhz"] == 1980 and f["reasons"] == ["hw_thermal_slowdown"]
+    assert c.summary("")["samples"] == 3
+    assert c.summary("nothing") is None
 
 
 def test_reference_arm_prints_its_contract_line():
