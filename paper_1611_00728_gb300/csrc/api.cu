@@ -26,7 +26,9 @@ int ensure_workspace(sqcg_ctx* ctx) {
             cudaMalloc((void**)&ctx->p32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->Ap32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->tmp32, n * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&ctx->partials, (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->q32, n * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->xh32, n * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->partials, 2 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->st, sizeof(SolverState)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) == cudaSuccess;
   if (!ok) {
@@ -41,10 +43,12 @@ int ensure_workspace(sqcg_ctx* ctx) {
 void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->r64); cudaFree(ctx->p64); cudaFree(ctx->Ap64); cudaFree(ctx->tmp64);
   cudaFree(ctx->r32); cudaFree(ctx->p32); cudaFree(ctx->Ap32); cudaFree(ctx->tmp32);
+  cudaFree(ctx->q32); cudaFree(ctx->xh32);
   cudaFree(ctx->partials); cudaFree(ctx->st);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   ctx->r64 = ctx->p64 = ctx->Ap64 = ctx->tmp64 = nullptr;
   ctx->r32 = ctx->p32 = ctx->Ap32 = ctx->tmp32 = nullptr;
+  ctx->q32 = ctx->xh32 = nullptr;
   ctx->partials = nullptr;
   ctx->st = nullptr;
   ctx->st_host = nullptr;

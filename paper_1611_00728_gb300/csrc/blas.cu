@@ -79,6 +79,70 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
   }
 }
 
+// Single-reduction CG update, one pass over five FP32 vectors (s = A r, written by the Dslash epilogue):
+//   p = r + beta p,  q = s + beta q  (= A p),  xh += alpha p,  r -= alpha q.
+// xh is the FP32 partial solution, flushed into the FP64 x at every reliable update. Thread 0 of block 0
+// also runs the control step of the captured WHILE loop (count, hard bound, condition), so no separate
+// loop-control kernel follows it.
+__global__ void __launch_bounds__(kThreads)
+k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __restrict__ p, float2* __restrict__ q,
+            float2* __restrict__ xh, int Vh, SolverState* st) {
+  const volatile SolverState* vs = st;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->h_while) {
+    // the loop continues while the solve is not done and the hard bound is not reached; on the bound,
+    // the status says so and the host sees done == 0 (done itself is not written here: other blocks read it)
+    const int n = st->loop_count + 1;
+    st->loop_count = n;
+    const int go = !vs->done && n < st->loop_limit;
+    if (!go && !vs->done) st->status = SQCG_ERR_NOT_CONVERGED;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, go ? 1u : 0u);
+  }
+  if (vs->done) return;
+  const float alpha = (float)st->alpha, beta = (float)st->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    float2 rc[3], sc[3], pc[3], qc[3], xc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {  // all loads before any store (see k_cg_update)
+      const size_t k = (size_t)c * Vh + i;
+      rc[c] = r[k];
+      sc[c] = sv[k];
+      pc[c] = p[k];
+      qc[c] = q[k];
+      xc[c] = xh[k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      pc[c].x = fmaf(beta, pc[c].x, rc[c].x);
+      pc[c].y = fmaf(beta, pc[c].y, rc[c].y);
+      qc[c].x = fmaf(beta, qc[c].x, sc[c].x);
+      qc[c].y = fmaf(beta, qc[c].y, sc[c].y);
+      xc[c].x = fmaf(alpha, pc[c].x, xc[c].x);
+      xc[c].y = fmaf(alpha, pc[c].y, xc[c].y);
+      rc[c].x = fmaf(-alpha, qc[c].x, rc[c].x);
+      rc[c].y = fmaf(-alpha, qc[c].y, rc[c].y);
+      p[k] = pc[c];
+      q[k] = qc[c];
+      xh[k] = xc[c];
+      r[k] = rc[c];
+    }
+  }
+}
+
+// x += xh (the FP32 partial solution, added in FP64), xh = 0
+__global__ void __launch_bounds__(kThreads)
+k_flush_partial_x(double2* __restrict__ x, float2* __restrict__ xh, int n, const SolverState* st, int gate) {
+  if (!gate_open(st, gate)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 h = xh[i];
+    double2 v = x[i];
+    v.x += (double)h.x;
+    v.y += (double)h.y;
+    x[i] = v;
+    xh[i] = make_float2(0.f, 0.f);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_norm2_f64(const double2* __restrict__ v, int Vh, SolverState* st, double* partials, int fin) {
   double nrm = 0.0;
@@ -275,6 +339,20 @@ int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
     k_cg_xpay<float><<<grid, kThreads, 0, s>>>(ctx->r32, ctx->p32, Vh, ctx->st);
   else
     k_cg_xpay<double><<<grid, kThreads, 0, s>>>(ctx->r64, ctx->p64, Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
+  k_sr_update<<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, ctx->p32, ctx->q32, ctx->xh32, Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_flush_partial_x(sqcg_ctx* ctx, double2* x, int gate, cudaStream_t s) {
+  const int n = ctx->g.Vh * 3;
+  k_flush_partial_x<<<blas_grid(ctx), kThreads, 0, s>>>(x, ctx->xh32, n, ctx->st, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

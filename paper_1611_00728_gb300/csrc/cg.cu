@@ -19,8 +19,11 @@ namespace {
 constexpr int kCGKernelsPerIter = 7;  // enqueue_cg_head (3 + 2 finishers) + xpay + loop control
 constexpr int kCGKernelsPerUpdate = 3;  // enqueue_cg_reliable (2 + finisher)
 constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control
+constexpr int kSRKernelsPerIter = 4;  // enqueue_sr_head (2 + finisher) + the update (with loop control)
+constexpr int kSRKernelsPerUpdate = 7;  // enqueue_sr_reliable: flush, 2 FP64 + finisher, 2 FP32 + finisher
 
-enum { KIND_CG = 0, KIND_MS = 1 };
+// KIND_CG: Hestenes-Stiefel CG (FP64 mode); KIND_MS: multi-shift; KIND_SR: single-reduction mixed CG
+enum { KIND_CG = 0, KIND_MS = 1, KIND_SR = 2 };
 
 }  // namespace
 
@@ -109,6 +112,36 @@ int enqueue_cg_reliable(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaSt
   return SQCG_OK;
 }
 
+// Single-reduction mixed CG, head of one iteration: tmp = D_oe r; s = sigma r - D_eo tmp (into Ap32)
+// with <r, s> and |r|^2 from one reduction; the finisher decides on convergence and the reliable update
+// and, without one, computes alpha and beta.
+int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s) {
+  DslashLaunch L = {};
+  L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->r32; L.out = ctx->tmp32;
+  L.gate = GATE_ITER;
+  SQCG_TRY(launch_dslash(ctx, L, s));
+  L = DslashLaunch{};
+  L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_NORMAL_DOT2; L.in = ctx->tmp32; L.out = ctx->Ap32;
+  L.y = ctx->r32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_SR_STEP;
+  return launch_dslash(ctx, L, s);
+}
+
+// Single-reduction mixed CG, reliable update (IF-node body): x += xh, then r = b - A x in FP64 (also
+// the convergence check), then A r and the step's scalars again from the true residual.
+int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
+  SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_UPDATE, s));
+  DslashLaunch L = {};
+  L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
+  L.gate = GATE_UPDATE;
+  SQCG_TRY(launch_dslash(ctx, L, s));
+  L = DslashLaunch{};
+  L.out_parity = 0; L.prec = SQCG_F64; L.out_prec = SQCG_F32; L.epi = EPI_TRUE_RESID;
+  L.in = ctx->tmp64; L.out = ctx->r32; L.y = x; L.b = b; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_UPDATE;
+  L.fin = FIN_TRUE_RESID;
+  SQCG_TRY(launch_dslash(ctx, L, s));
+  return enqueue_sr_head(ctx, s);  // gated on the loop going on (GATE_ITER)
+}
+
 int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
   const int wp = mixed ? SQCG_F32 : SQCG_F64;
   void* p = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
@@ -136,8 +169,8 @@ int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const*
   cudaStream_t cs = ctx->cap_stream;
   SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int rc = SQCG_OK;
-  if (kind == KIND_CG) {
-    rc = enqueue_cg_head(ctx, mixed, x[0], cs);
+  if (kind == KIND_CG || kind == KIND_SR) {
+    rc = (kind == KIND_CG) ? enqueue_cg_head(ctx, mixed, x[0], cs) : enqueue_sr_head(ctx, cs);
     if (rc == SQCG_OK) {
       cudaStreamCaptureStatus status;
       cudaGraph_t capg = nullptr;
@@ -161,19 +194,19 @@ int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const*
           *ifbody = ip.conditional.phGraph_out[0];
       }
     }
-    if (rc == SQCG_OK) rc = launch_cg_xpay(ctx, mixed, cs);
+    if (rc == SQCG_OK) rc = (kind == KIND_CG) ? launch_cg_xpay(ctx, mixed, cs) : launch_sr_update(ctx, cs);
   } else {
     rc = enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, cs);
   }
-  if (rc == SQCG_OK) rc = launch_loop_control(ctx, cs);
+  if (rc == SQCG_OK && kind != KIND_SR) rc = launch_loop_control(ctx, cs);  // KIND_SR: inside the update
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &out);
   if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "conditional node", __FILE__, __LINE__);
   if (rc != SQCG_OK) return rc;
   if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
-  if (kind == KIND_CG) {
+  if (kind == KIND_CG || kind == KIND_SR) {
     SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, *ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_cg_reliable(ctx, mixed, b, x[0], cs);
+    rc = (kind == KIND_CG) ? enqueue_cg_reliable(ctx, mixed, b, x[0], cs) : enqueue_sr_reliable(ctx, b, x[0], cs);
     e = cudaStreamEndCapture(cs, &out);
     if (rc != SQCG_OK) return rc;
     if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
@@ -236,7 +269,7 @@ int run_loop(sqcg_ctx* ctx, CGGraph* g, int max_iter, cudaStream_t s, int* iters
   SolverState* h = ctx->st_host;
   h->h_while = g->h_while;
   h->h_if = g->h_if;
-  h->use_if = (g->kind == KIND_CG) ? 1 : 0;
+  h->use_if = (g->kind == KIND_CG || g->kind == KIND_SR) ? 1 : 0;
   h->loop_count = 0;
   h->loop_limit = max_iter + 4;
   SQCG_TRY(write_state(ctx, s));
@@ -271,6 +304,15 @@ int run_eager(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x,
       }
       if (h->done) break;
       SQCG_TRY(launch_cg_xpay(ctx, mixed, s));
+    } else if (kind == KIND_SR) {
+      SQCG_TRY(enqueue_sr_head(ctx, s));
+      SQCG_TRY(read_state(ctx, s));
+      if (!h->done && h->need_update) {
+        SQCG_TRY(enqueue_sr_reliable(ctx, b, x[0], s));
+        SQCG_TRY(read_state(ctx, s));
+      }
+      if (h->done) break;
+      SQCG_TRY(launch_sr_update(ctx, s));
     } else {
       SQCG_TRY(enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, s));
       SQCG_TRY(read_state(ctx, s));
@@ -312,6 +354,7 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   h->max_iter = max_iter;
   h->update_interval = mixed ? ctx->ru_interval : (1 << 30);
   h->mixed = mixed;
+  h->sr = mixed;  // mixed mode runs the single-reduction loop; FP64 mode the Hestenes-Stiefel loop
   h->status = SQCG_OK;
   SQCG_TRY(write_state(ctx, s));
   SQCG_TRY(launch_norm2_f64(ctx, (const double2*)b, FIN_BB, s));
@@ -367,14 +410,27 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   }
   if (!h->done) {
     void* xs[1] = {x};
+    const int kind = mixed ? KIND_SR : KIND_CG;
+    if (mixed) {  // p, q and the FP32 partial solution start at zero
+      const size_t wb = (size_t)ctx->g.Vh * 3 * sizeof(float2);
+      SQCG_CUDA_TRY(cudaMemsetAsync(ctx->p32, 0, wb, s));
+      SQCG_CUDA_TRY(cudaMemsetAsync(ctx->q32, 0, wb, s));
+      SQCG_CUDA_TRY(cudaMemsetAsync(ctx->xh32, 0, wb, s));
+    }
     if (eager_mode()) {
-      SQCG_TRY(run_eager(ctx, KIND_CG, mixed, b, xs, 1, max_iter, s, &loops));
+      SQCG_TRY(run_eager(ctx, kind, mixed, b, xs, 1, max_iter, s, &loops));
     } else {
       CGGraph* g = nullptr;
-      SQCG_TRY(capture(ctx, KIND_CG, mixed, b, xs, 1, &g));
+      SQCG_TRY(capture(ctx, kind, mixed, b, xs, 1, &g));
       SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
     }
-    launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
+    if (mixed) {  // whatever the partial solution still holds (nothing after a converged update)
+      SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_NONE, s));
+      SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+      launches += loops * kSRKernelsPerIter + h->updates * kSRKernelsPerUpdate + 1;
+    } else {
+      launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
+    }
     status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   } else {
     status = h->status;  // x0 already solves the system (or breakdown on a non-finite residual)

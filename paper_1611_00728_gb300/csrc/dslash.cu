@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0;
+  double part = 0.0, part2 = 0.0;
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -210,18 +210,20 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
     if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = mk<O2>((RO)acc[c].x, (RO)acc[c].y);
-    } else if constexpr (EPI == EPI_NORMAL || EPI == EPI_NORMAL_DOT) {
+    } else if constexpr (EPI == EPI_NORMAL || EPI == EPI_NORMAL_DOT || EPI == EPI_NORMAL_DOT2) {
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* yv = static_cast<const R2*>(a.y);
-      R dot = R(0);
+      R dot = R(0), yy = R(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const R2 yc = ldg2(yv + (size_t)c * Vh + i);
         O2 o = mk<O2>((RO)(sig * yc.x - acc[c].x), (RO)(sig * yc.y - acc[c].y));
         out[(size_t)c * Vh + i] = o;
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
+        if constexpr (EPI == EPI_NORMAL_DOT2) yy = fma(yc.x, yc.x, fma(yc.y, yc.y, yy));
       }
       part = (double)dot;
+      part2 = (double)yy;
     } else {  // EPI_TRUE_RESID: out = b - sigma*x + D in, in FP64
       const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
       const double2* xv = static_cast<const double2*>(a.y);
@@ -244,6 +246,10 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
+  if constexpr (EPI == EPI_NORMAL_DOT2) {
+    if (a.fin != FIN_NONE) block_partial2(part, part2, a.partials);
+  }
+  (void)part2;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -279,18 +285,21 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
     return SQCG_ERR_INVALID_ARG;
   const int grid = grid_for(ctx->g.Vh, kThreads);
-  if ((L.epi == EPI_NORMAL_DOT || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE && grid > ctx->max_blocks)
-    return SQCG_ERR_INVALID_ARG;
+  const bool reduces = (L.epi == EPI_NORMAL_DOT || L.epi == EPI_NORMAL_DOT2 || L.epi == EPI_TRUE_RESID) &&
+                       L.fin != FIN_NONE;
+  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 2 * max_blocks
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_NORMAL_DOT2: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT2><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
-  if ((L.epi == EPI_NORMAL_DOT || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE)
-    return launch_finish(ctx, grid, L.fin, L.gate, s);
+  if (reduces)
+    return L.epi == EPI_NORMAL_DOT2 ? launch_finish2(ctx, grid, L.fin, L.gate, s)
+                                    : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
 }
 
@@ -314,7 +323,8 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
-  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT) && !L.y) return SQCG_ERR_INVALID_ARG;
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_NORMAL_DOT2) && !L.y)
+    return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);
   return SQCG_ERR_INVALID_ARG;

@@ -98,6 +98,8 @@ __device__ inline void solver_finish(SolverState* s, int fin, double v) {
       } else if (s->iter >= s->max_iter) {
         s->done = 1;
         s->status = SQCG_ERR_NOT_CONVERGED;
+      } else if (s->sr) {
+        s->after_update = 1;  // the single-reduction step recomputes alpha and beta from A r_true
       } else {
         s->beta = v / s->rr_prev;  // continue from the true residual
         s->rr = v;
@@ -186,12 +188,52 @@ __device__ inline void solver_finish_ms(SolverState* s, int fin, double v) {
   }
 }
 
+// Single-reduction CG step (Chronopoulos and Gear's form of CG): with gamma_k = |r_k|^2 and
+// delta_k = <r_k, A r_k> from one reduction,
+//   beta_k = gamma_k / gamma_{k-1},  <p_k, A p_k> = delta_k - beta_k gamma_k / alpha_{k-1},
+//   alpha_k = gamma_k / <p_k, A p_k>   (beta_0 = 0, alpha_0 = gamma_0 / delta_0),
+// which is the same CG as alpha = |r|^2/<p,Ap>, beta = |r_new|^2/|r|^2 when p_k = r_k + beta_k p_{k-1}
+// and A p_k is carried as q_k = A r_k + beta_k q_{k-1}. Before that, gamma_k decides convergence and
+// the reliable update (an FP64 true residual, after which the step runs again on r_true).
+__device__ inline void sr_step(SolverState* s, double d, double g) {
+  if (!isfinite(d) || !isfinite(g)) { finish_breakdown(s); return; }
+  if (s->after_update) {  // r was just replaced by the FP64 true residual (not converged)
+    s->after_update = 0;
+    s->rr = g;
+  } else {
+    s->rr_prev = s->rr;
+    s->rr = g;
+    if (g > s->rr_max) s->rr_max = g;
+    if (g <= s->stop_rr) {
+      s->need_update = 1;  // confirm on the FP64 true residual
+    } else if (g < s->delta2 * s->rr_max || s->iter - s->iter_last_update >= s->update_interval) {
+      s->need_update = 1;  // reliable update
+    }
+    if (s->iter >= s->max_iter) s->need_update = 1;  // final true residual, then stop
+    if (s->use_if) cudaGraphSetConditional((cudaGraphConditionalHandle)s->h_if, s->need_update ? 1u : 0u);
+    if (s->need_update) return;  // the step runs again after the update
+  }
+  double beta = 0.0, pAp = d;
+  if (s->iter > 0) {
+    beta = g / s->rr_prev;
+    pAp = d - beta * g / s->sr_alpha_prev;
+  }
+  if (!(pAp > 0.0) || !isfinite(pAp)) { finish_breakdown(s); return; }
+  s->beta = beta;
+  s->pAp = pAp;
+  s->alpha = g / pAp;
+  s->sr_alpha_prev = s->alpha;
+  s->iter += 1;  // the update kernel that follows makes iterate number iter
+}
+
 // scalar steps that take two sums (a = first, b = second)
 __device__ inline void solver_finish2(SolverState* s, int fin, double a, double b) {
   if (fin == FIN_FCG_BETA) {  // a = <z_{k+1}, r_{k+1}>, b = <z_{k+1}, r_k>
     if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) { finish_breakdown(s); return; }
     s->beta = (a - b) / s->rz;  // Polak-Ribiere (flexible) beta
     s->rz = a;
+  } else if (fin == FIN_SR_STEP) {  // a = <r, A r>, b = |r|^2
+    sr_step(s, a, b);
   }
 }
 

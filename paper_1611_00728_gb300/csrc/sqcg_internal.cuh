@@ -75,6 +75,11 @@ struct SolverState {
   unsigned long long h_while;  // conditional handle of the WHILE node (cudaGraphConditionalHandle)
   unsigned long long h_if;     // conditional handle of the reliable-update IF node
 
+  // single-reduction CG (mixed mode): one reduction per iteration, <r, A r> and |r|^2 together
+  int sr;            // the loop is the single-reduction form
+  int after_update;  // the next FIN_SR_STEP follows a reliable update (its residual is the true one)
+  double sr_alpha_prev;  // alpha of the previous iteration
+
   // flexible CG with the network preconditioner
   double rz;          // <z_k, r_k>
   double nn_s;        // network input scale sqrt(3 Vh) / |r|
@@ -136,6 +141,8 @@ enum Finisher {
   FIN_FCG_PAP = 10,    // flexible CG: alpha = <z,r> / <p,Ap>
   FIN_FCG_BETA = 11,   // flexible CG (two sums): beta = (<z,r> - <z,r_old>) / <z_old,r_old>
   FIN_FCG_INIT = 12,   // flexible CG: <z_0, r_0>
+  FIN_SR_STEP = 13,    // single-reduction CG (two sums <r, A r>, |r|^2): convergence / reliable-update
+                       // decision, then alpha and beta of the iteration
 };
 
 // ---------------------------------------------------------------------------
@@ -172,7 +179,8 @@ struct sqcg_ctx {
   // solver workspace (allocated on first solve)
   double2 *r64, *p64, *Ap64, *tmp64;
   float2 *r32, *p32, *Ap32, *tmp32;
-  double* partials;
+  float2 *q32, *xh32;  // single-reduction mixed CG: q = A p, and the FP32 partial solution
+  double* partials;    // two sums' worth: 2 * max_blocks
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   SolverState* st;       // device
@@ -207,6 +215,7 @@ enum DslashEpi {
   EPI_NORMAL = 1,         // out = sigma*y - D in
   EPI_NORMAL_DOT = 2,     // out = sigma*y - D in, reduce Re<y, out>
   EPI_TRUE_RESID = 3,     // out = b - sigma*y + D in (b, y FP64), reduce |out|^2
+  EPI_NORMAL_DOT2 = 4,    // out = sigma*y - D in, reduce Re<y, out> and |y|^2 (two sums)
 };
 
 struct DslashLaunch {
@@ -234,6 +243,11 @@ int blas_grid(sqcg_ctx* ctx);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
+// single-reduction mixed CG: p = r + beta p, q = s + beta q, xh += alpha p, r -= alpha q (s in Ap32), with
+// the WHILE-loop control of the captured loop in one thread
+int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s);
+// x += xh (FP64 += FP32), xh = 0
+int launch_flush_partial_x(sqcg_ctx* ctx, double2* x, int gate, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
 

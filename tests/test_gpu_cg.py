@@ -177,7 +177,7 @@ def test_cg_32_single_mass_fp64_and_mixed(sqcg, links_cache, recon12):
     L, m, tol = (32, 32, 32, 32), 0.01, 1e-8
     fat, lng = links_cache(L, 1002)
     b = synth.gaussian_source(L, 2200)
-    sols = {}
+    sols, iters = {}, {}
     with sqcg.Lattice(L) as lat:
         lat.load_links(fat, lng, recon12=recon12)
         assert lat.recon12 == recon12
@@ -187,6 +187,9 @@ def test_cg_32_single_mass_fp64_and_mixed(sqcg, links_cache, recon12):
             info = lat.cg_solve(m, db, dx, tol=tol, max_iter=20000, mode=mode)
             assert info.status == 0 and info.true_rel_resid <= tol
             sols[mode] = (lat.unpack(dx), info.true_rel_resid)
+            iters[mode] = info.iters
+    # the mixed solver (single-reduction form, FP32 vectors) keeps the FP64 CG's convergence rate
+    assert iters[1] <= iters[0] + 10, iters
     for mode, (x, lib_res) in sols.items():
         res = oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x)
         assert res <= tol, (mode, res)
