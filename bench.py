@@ -69,8 +69,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--dslash-only", action="store_true", help="only the Dslash roofline loop (profiling runs)")
-    ap.add_argument("--links", choices=["recon12", "full", "8way", "8way-recon12"], default="recon12",
-                    help="--dslash-only: the FP32 link storage to time (default: 12-real long links, as the solvers)")
+    ap.add_argument("--links", choices=["recon12", "full", "8way", "8way-recon12", "ff", "f64"], default="recon12",
+                    help="--dslash-only: the FP32 link storage to time (default: 12-real long links, as the solvers), "
+                         "or the float-float (ff) or FP64 (f64) Dslash")
     ap.add_argument("--lattice", default=None,
                     help="hisq and batched workloads: extents as Lx,Ly,Lz,Lt (hisq default 32^4; batched: one "
                          "lattice with 16 sources instead of the three; for profiling)")
@@ -389,6 +390,11 @@ def run_ours(args, ranks: Ranks):
     peak, peak_kind = hbm_peak()
 
     if args.dslash_only:
+        if args.links in ("ff", "f64"):
+            t = time_dslash(torch, lat, sq, sq.FF if args.links == "ff" else sq.F64, 20)
+            print(json.dumps({f"dslash_{args.links}_ms": t * 1e3,
+                              "gbs": BYTES_PER_SITE["f64"] * Vh / t / 1e9}), flush=True)
+            return
         if args.links != "recon12":
             lat.close()
             lat = sq.Lattice(LATTICE)
@@ -445,6 +451,7 @@ def run_ours(args, ranks: Ranks):
     # links, as the solve uses it) and the other variants
     t32r = time_dslash(torch, lat, sq, sq.F32, 50)
     t64d = time_dslash(torch, lat, sq, sq.F64, 20)
+    tffd = time_dslash(torch, lat, sq, sq.FF, 20)
     lat_f = sq.Lattice(LATTICE)
     lat_f.load_links(fat, lng)
     t32 = time_dslash(torch, lat_f, sq, sq.F32, 50)
@@ -478,7 +485,11 @@ def run_ours(args, ranks: Ranks):
                                    "frac_hbm": BYTES_PER_SITE["f32_recon12"] * Vh / t8[True] / 1e9 / peak},
               "f64": {"ms": t64d * 1e3, "gflops": FLOPS_PER_SITE * Vh / t64d / 1e9,
                       "gbs": BYTES_PER_SITE["f64"] * Vh / t64d / 1e9,
-                      "frac_hbm": BYTES_PER_SITE["f64"] * Vh / t64d / 1e9 / peak}}
+                      "frac_hbm": BYTES_PER_SITE["f64"] * Vh / t64d / 1e9 / peak},
+              "ff": {"ms": tffd * 1e3, "gflops": FLOPS_PER_SITE * Vh / tffd / 1e9,
+                     "gbs": BYTES_PER_SITE["f64"] * Vh / tffd / 1e9,
+                     "frac_hbm": BYTES_PER_SITE["f64"] * Vh / tffd / 1e9 / peak,
+                     "note": "float-float (hi + lo floats per real) Dslash of the reliable updates; FP64 bytes"}}
 
     # end to end through the C ABI with host buffers: H2D of b, solve, D2H of x
     b_pin = torch.from_numpy(b_host.view(np.float64)).pin_memory()

@@ -72,6 +72,16 @@ extern "C" {
 /* ---- precisions ---- */
 #define SQCG_F64 0
 #define SQCG_F32 1
+/* Float-float ("double-single"): each real is an unevaluated sum hi + lo of
+ * two floats (about 48 significand bits). A device colour vector is
+ * [3][Vh] of float4 (re_hi, re_lo, im_hi, im_lo), 16 bytes per complex like
+ * SQCG_F64, 16-byte aligned. The Dslash in this arithmetic runs on the FP32
+ * pipe with error-free products and sums (relative error of order 1e-14,
+ * tested against the FP64 oracle at 1e-12); on the GB300, whose FP64 FMA rate
+ * is 1/64 of FP32, it is bound by memory instead of FP64 arithmetic. Accepted
+ * by sqcg_dslash, sqcg_pack_spinor, sqcg_unpack_spinor, sqcg_spinor_bytes and
+ * sqcg_set_update_arithmetic. Not in the paper, whose kernels are FP64. */
+#define SQCG_FF 2
 
 /* ---- solver modes ---- */
 #define SQCG_MODE_F64 0   /* everything in FP64 */
@@ -108,14 +118,23 @@ int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
  * The batched solve uses the settings of its first context. */
 int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval);
 
-/* Bytes of one device colour vector on one parity in precision prec (Vh * 3 * 2 * sizeof(real)). */
+/* Arithmetic of the true-residual recomputations (reliable updates and the
+ * final convergence check) of the single-mass mixed-precision solve on this
+ * context: SQCG_FF (default; float-float Dslash from float-float copies of the
+ * FP64 links, the sum b - sigma x + D x and the norm in FP64) or SQCG_F64 (the
+ * FP64 Dslash). The FP64 solver mode always uses FP64. Not in the paper. */
+int sqcg_set_update_arithmetic(sqcg_ctx* ctx, int prec);
+
+/* Bytes of one device colour vector on one parity in precision prec (Vh * 3 * 2 * sizeof(real);
+ * SQCG_FF: Vh * 3 * 16). */
 int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
 
 /* Load fat (one-hop) and long (three-hop) links from host memory in the host
  * gauge format above. The library folds eta and the boundary sign into its
  * copies unless the context has SQCG_PHASES_FOLDED, converts them to its
- * parity-split structure-of-arrays layout and keeps an FP64 and an FP32 copy on
- * the device (owned by the context, replacing earlier links). The host arrays
+ * parity-split structure-of-arrays layout and keeps an FP64, an FP32 and a
+ * float-float (SQCG_FF) copy on the device (owned by the context, replacing
+ * earlier links). The host arrays
  * are only read during the call.
  * opts: SQCG_RECON12_LONG stores the FP32 copy of the long links as their
  * first two rows (the FP32 Dslash rebuilds the third); it is accepted only if
@@ -131,11 +150,12 @@ int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes);
 int sqcg_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 
 /* Copy one host colour vector (parity order, complex double [Vh][3]) into a
- * device vector of precision prec (rounded to nearest for SQCG_F32). */
+ * device vector of precision prec (rounded to nearest for SQCG_F32; for
+ * SQCG_FF hi = fl32(v), lo = fl32(v - hi)). */
 int sqcg_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev);
 
 /* Copy a device vector of precision prec back to host parity order (complex
- * double [Vh][3]). Synchronises the stream. */
+ * double [Vh][3]; SQCG_FF: hi + lo in FP64). Synchronises the stream. */
 int sqcg_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host);
 
 /* out = D in on the sites of parity out_parity, reading in on the other

@@ -20,13 +20,13 @@ import weakref
 import numpy as np
 
 __all__ = [
-    "F64", "F32", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
+    "F64", "F32", "FF", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
     "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "NN_LAYERS", "NN_GATES", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
     "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK",
 ]
 
-F64, F32 = 0, 1
+F64, F32, FF = 0, 1, 2  # FF: float-float (hi, lo floats per real), device vectors (3, Vh, 4) float32
 MODE_F64, MODE_MIXED = 0, 1
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
@@ -117,6 +117,7 @@ def library():
         lib.sqcg_destroy.argtypes = [P]
         lib.sqcg_set_stream.argtypes = [P, P]
         lib.sqcg_set_reliable_update.argtypes = [P, D, I]
+        lib.sqcg_set_update_arithmetic.argtypes = [P, I]
         lib.sqcg_spinor_bytes.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
         lib.sqcg_load_links.argtypes = [P, P, P, I]
         lib.sqcg_pack_spinor.argtypes = [P, I, P, P]
@@ -150,6 +151,7 @@ def library():
         lib.sqcg_strerror.argtypes = [I]
         lib.sqcg_strerror.restype = ctypes.c_char_p
         for name in ("sqcg_create", "sqcg_destroy", "sqcg_set_stream", "sqcg_set_reliable_update", "sqcg_spinor_bytes",
+                     "sqcg_set_update_arithmetic",
                      "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
@@ -221,6 +223,10 @@ class Lattice:
         `interval` iterations."""
         _check(library().sqcg_set_reliable_update(self._h, float(delta), int(interval)), "sqcg_set_reliable_update")
 
+    def set_update_arithmetic(self, prec: int):
+        """Arithmetic of the mixed solve's true-residual recomputations: FF (default) or F64."""
+        _check(library().sqcg_set_update_arithmetic(self._h, int(prec)), "sqcg_set_update_arithmetic")
+
     def _sync_stream(self):
         library().sqcg_set_stream(self._h, ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream))
 
@@ -255,18 +261,21 @@ class Lattice:
         return (fat, lng) if return_links else None
 
     def new_spinor(self, prec: int = F64, count: int | None = None):
-        """Zeroed device colour vector(s) in the library layout: (3, Vh, 2)."""
+        """Zeroed device colour vector(s) in the library layout: (3, Vh, 2), or (3, Vh, 4) for FF."""
         torch = _torch()
         dt = torch.float64 if prec == F64 else torch.float32
-        shape = (3, self.Vh, 2) if count is None else (count, 3, self.Vh, 2)
+        last = 4 if prec == FF else 2
+        shape = (3, self.Vh, last) if count is None else (count, 3, self.Vh, last)
         return torch.zeros(shape, dtype=dt, device="cuda")
 
     @staticmethod
     def _check_spinor(t, prec, Vh):
         torch = _torch()
         dt = torch.float64 if prec == F64 else torch.float32
-        if t.dtype != dt or tuple(t.shape) != (3, Vh, 2) or not t.is_cuda or not t.is_contiguous():
-            raise ValueError(f"expected a contiguous CUDA tensor (3, {Vh}, 2) of {dt}, got {t.dtype} {tuple(t.shape)}")
+        last = 4 if prec == FF else 2
+        if t.dtype != dt or tuple(t.shape) != (3, Vh, last) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA tensor (3, {Vh}, {last}) of {dt}, got {t.dtype} "
+                             f"{tuple(t.shape)}")
         return ctypes.c_void_p(t.data_ptr())
 
     def pack(self, host: np.ndarray, prec: int = F64, out=None):

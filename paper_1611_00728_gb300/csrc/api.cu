@@ -28,7 +28,8 @@ int ensure_workspace(sqcg_ctx* ctx) {
             cudaMalloc((void**)&ctx->tmp32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->q32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->xh32, n * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&ctx->partials, 2 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->xff, n * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->partials, 4 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->st, sizeof(SolverState)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) == cudaSuccess;
   if (!ok) {
@@ -43,12 +44,13 @@ int ensure_workspace(sqcg_ctx* ctx) {
 void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->r64); cudaFree(ctx->p64); cudaFree(ctx->Ap64); cudaFree(ctx->tmp64);
   cudaFree(ctx->r32); cudaFree(ctx->p32); cudaFree(ctx->Ap32); cudaFree(ctx->tmp32);
-  cudaFree(ctx->q32); cudaFree(ctx->xh32);
+  cudaFree(ctx->q32); cudaFree(ctx->xh32); cudaFree(ctx->xff);
   cudaFree(ctx->partials); cudaFree(ctx->st);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   ctx->r64 = ctx->p64 = ctx->Ap64 = ctx->tmp64 = nullptr;
   ctx->r32 = ctx->p32 = ctx->Ap32 = ctx->tmp32 = nullptr;
   ctx->q32 = ctx->xh32 = nullptr;
+  ctx->xff = nullptr;
   ctx->partials = nullptr;
   ctx->st = nullptr;
   ctx->st_host = nullptr;
@@ -92,6 +94,7 @@ int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out)
   g.st = g.Lxh * g.Ly * g.Lz;
   g.apbc = (flags & SQCG_ANTIPERIODIC_T) ? 1 : 0;
   c->stream = (cudaStream_t)cuda_stream;
+  c->ru_arith = SQCG_FF;
   c->ru_delta = 0.001;
   c->ru_interval = 100;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -111,6 +114,7 @@ int sqcg_destroy(sqcg_ctx* ctx) {
   free_workspace(ctx);
   cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
   cudaFree(ctx->fatb32); cudaFree(ctx->lngb32);
+  cudaFree(ctx->fatff); cudaFree(ctx->lngff);
   cudaFree(ctx->stage);
   cudaStreamDestroy(ctx->cap_stream);
   free(ctx);
@@ -130,9 +134,16 @@ int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval) {
   return SQCG_OK;
 }
 
+int sqcg_set_update_arithmetic(sqcg_ctx* ctx, int prec) {
+  if (!ctx || (prec != SQCG_F64 && prec != SQCG_FF)) return SQCG_ERR_INVALID_ARG;
+  if (prec != ctx->ru_arith) free_graphs(ctx);  // captured loops hold the old kernels
+  ctx->ru_arith = prec;
+  return SQCG_OK;
+}
+
 int sqcg_spinor_bytes(const sqcg_ctx* ctx, int prec, size_t* bytes) {
-  if (!ctx || !bytes || (prec != SQCG_F64 && prec != SQCG_F32)) return SQCG_ERR_INVALID_ARG;
-  *bytes = (size_t)ctx->g.Vh * 3 * (prec == SQCG_F64 ? sizeof(double2) : sizeof(float2));
+  if (!ctx || !bytes || (prec != SQCG_F64 && prec != SQCG_F32 && prec != SQCG_FF)) return SQCG_ERR_INVALID_ARG;
+  *bytes = (size_t)ctx->g.Vh * 3 * (prec == SQCG_F32 ? sizeof(float2) : sizeof(double2));
   return SQCG_OK;
 }
 
@@ -153,6 +164,14 @@ int sqcg_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host) {
 
 int sqcg_dslash(sqcg_ctx* ctx, int out_parity, int prec, const void* in, void* out) {
   if (!ctx || !in || !out || in == out) return SQCG_ERR_INVALID_ARG;
+  if (prec == SQCG_FF) {
+    if (((uintptr_t)in | (uintptr_t)out) % 16) return SQCG_ERR_INVALID_ARG;
+    FFLaunch F = {};
+    F.out_parity = out_parity;
+    F.in = in;
+    F.out_ff = out;
+    return launch_dslash_ff(ctx, F, ctx->stream);
+  }
   if (prec != SQCG_F64 && prec != SQCG_F32) return SQCG_ERR_INVALID_ARG;
   DslashLaunch L = {};
   L.out_parity = out_parity;

@@ -113,22 +113,36 @@ int enqueue_cg_reliable(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaSt
 }
 
 // Single-reduction mixed CG, head of one iteration: tmp = D_oe r; s = sigma r - D_eo tmp (into Ap32)
-// with <r, s> and |r|^2 from one reduction; the finisher decides on convergence and the reliable update
-// and, without one, computes alpha and beta.
+// with the four sums of the step (see EPI_SR_DOTS) from one reduction; the finisher decides on
+// convergence and the reliable update and, without one, computes alpha and beta.
 int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s) {
   DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->r32; L.out = ctx->tmp32;
   L.gate = GATE_ITER;
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
-  L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_NORMAL_DOT2; L.in = ctx->tmp32; L.out = ctx->Ap32;
-  L.y = ctx->r32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_SR_STEP;
+  L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_SR_DOTS; L.in = ctx->tmp32; L.out = ctx->Ap32;
+  L.y = ctx->r32; L.y2 = ctx->p32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
+  L.fin = FIN_SR_STEP;
   return launch_dslash(ctx, L, s);
 }
 
-// Single-reduction mixed CG, reliable update (IF-node body): x += xh, then r = b - A x in FP64 (also
-// the convergence check), then A r and the step's scalars again from the true residual.
+// Single-reduction mixed CG, reliable update (IF-node body): x += xh, then r = b - A x (also the
+// convergence check), then A r and the step's scalars again from the true residual. The true residual's
+// Dslash pair runs in float-float (default) or FP64 arithmetic (sqcg_set_update_arithmetic); the sum
+// b - sigma x + D x and its norm are FP64 either way.
 int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
+  if (ctx->ru_arith == SQCG_FF) {
+    SQCG_TRY(launch_flush_split(ctx, (double2*)x, ctx->xh32, ctx->xff, GATE_UPDATE, s));
+    FFLaunch F = {};
+    F.out_parity = 1; F.in = ctx->xff; F.out_ff = ctx->tmp64; F.gate = GATE_UPDATE;  // tmp64 holds float4 [3][Vh]
+    SQCG_TRY(launch_dslash_ff(ctx, F, s));
+    F = FFLaunch{};
+    F.out_parity = 0; F.true_resid = 1; F.in = ctx->tmp64; F.out32 = ctx->r32; F.x = x; F.b = b;
+    F.sigma_dev = &ctx->st->sigma; F.gate = GATE_UPDATE; F.fin = FIN_TRUE_RESID;
+    SQCG_TRY(launch_dslash_ff(ctx, F, s));
+    return enqueue_sr_head(ctx, s);
+  }
   SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_UPDATE, s));
   DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;

@@ -103,6 +103,8 @@ struct DArgs {
   void* out;
   void* out2;
   const void* y;
+  const void* y2;
+  const void* y3;
   const double2* b;
   double sigma;
   const double* sigma_dev;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0, part2 = 0.0;
+  double part = 0.0, part2 = 0.0, part3 = 0.0, part4 = 0.0;
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -210,20 +212,40 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
     if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = mk<O2>((RO)acc[c].x, (RO)acc[c].y);
-    } else if constexpr (EPI == EPI_NORMAL || EPI == EPI_NORMAL_DOT || EPI == EPI_NORMAL_DOT2) {
+    } else if constexpr (EPI == EPI_NORMAL || EPI == EPI_NORMAL_DOT) {
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* yv = static_cast<const R2*>(a.y);
-      R dot = R(0), yy = R(0);
+      R dot = R(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const R2 yc = ldg2(yv + (size_t)c * Vh + i);
         O2 o = mk<O2>((RO)(sig * yc.x - acc[c].x), (RO)(sig * yc.y - acc[c].y));
         out[(size_t)c * Vh + i] = o;
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
-        if constexpr (EPI == EPI_NORMAL_DOT2) yy = fma(yc.x, yc.x, fma(yc.y, yc.y, yy));
       }
       part = (double)dot;
-      part2 = (double)yy;
+    } else if constexpr (EPI == EPI_SR_DOTS) {  // s = sigma r - D in; <r,s>, <r,q> + <p,s>, <p,q>, |r|^2
+      const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
+      const R2* rv = static_cast<const R2*>(a.y);
+      const R2* pv = static_cast<const R2*>(a.y2);
+      const R2* qv = static_cast<const R2*>(a.y3);
+      R rs = R(0), cross = R(0), pq = R(0), rr = R(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * Vh + i;
+        const R2 rc = ldg2(rv + k), pc = ldg2(pv + k), qc = ldg2(qv + k);
+        O2 o = mk<O2>((RO)(sig * rc.x - acc[c].x), (RO)(sig * rc.y - acc[c].y));
+        out[k] = o;
+        rs = fma(rc.x, o.x, fma(rc.y, o.y, rs));
+        cross = fma(rc.x, qc.x, fma(rc.y, qc.y, cross));
+        cross = fma(pc.x, o.x, fma(pc.y, o.y, cross));
+        pq = fma(pc.x, qc.x, fma(pc.y, qc.y, pq));
+        rr = fma(rc.x, rc.x, fma(rc.y, rc.y, rr));
+      }
+      part = (double)rs;
+      part2 = (double)cross;
+      part3 = (double)pq;
+      part4 = (double)rr;
     } else {  // EPI_TRUE_RESID: out = b - sigma*x + D in, in FP64
       const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
       const double2* xv = static_cast<const double2*>(a.y);
@@ -246,10 +268,10 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
-  if constexpr (EPI == EPI_NORMAL_DOT2) {
-    if (a.fin != FIN_NONE) block_partial2(part, part2, a.partials);
+  if constexpr (EPI == EPI_SR_DOTS) {
+    if (a.fin != FIN_NONE) block_partial4(part, part2, part3, part4, a.partials);
   }
-  (void)part2;
+  (void)part2; (void)part3; (void)part4;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -275,6 +297,8 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   a.out = L.out;
   a.out2 = L.out2;
   a.y = L.y;
+  a.y2 = L.y2;
+  a.y3 = L.y3;
   a.b = static_cast<const double2*>(L.b);
   a.sigma = L.sigma;
   a.sigma_dev = L.sigma_dev;
@@ -285,21 +309,21 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
     return SQCG_ERR_INVALID_ARG;
   const int grid = grid_for(ctx->g.Vh, kThreads);
-  const bool reduces = (L.epi == EPI_NORMAL_DOT || L.epi == EPI_NORMAL_DOT2 || L.epi == EPI_TRUE_RESID) &&
+  const bool reduces = (L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_TRUE_RESID) &&
                        L.fin != FIN_NONE;
-  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 2 * max_blocks
+  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 4 * max_blocks
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
-    case EPI_NORMAL_DOT2: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT2><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_SR_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_NORMAL_DOT2 ? launch_finish2(ctx, grid, L.fin, L.gate, s)
-                                    : launch_finish(ctx, grid, L.fin, L.gate, s);
+    return L.epi == EPI_SR_DOTS ? launch_finish4(ctx, grid, L.fin, L.gate, s)
+                                : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
 }
 
@@ -323,8 +347,8 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
-  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_NORMAL_DOT2) && !L.y)
-    return SQCG_ERR_INVALID_ARG;
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS) && !L.y) return SQCG_ERR_INVALID_ARG;
+  if (L.epi == EPI_SR_DOTS && (!L.y2 || !L.y3)) return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);
   return SQCG_ERR_INVALID_ARG;

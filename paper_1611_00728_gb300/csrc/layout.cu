@@ -72,6 +72,29 @@ __global__ void k_aos_to_soa(const double2* __restrict__ aos, O2* __restrict__ s
   }
 }
 
+// host parity order [Vh][3] complex double -> device [3][Vh] float-float (hi = fl32(v), lo = fl32(v - hi))
+__global__ void k_aos_to_soa_ff(const double2* __restrict__ aos, float4* __restrict__ soa, int Vh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Vh) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double2 v = aos[(size_t)i * 3 + c];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    soa[(size_t)c * Vh + i] =
+        make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+  }
+}
+
+__global__ void k_soa_ff_to_aos(const float4* __restrict__ soa, double2* __restrict__ aos, int Vh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Vh) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float4 v = soa[(size_t)c * Vh + i];
+    aos[(size_t)i * 3 + c] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+
 template <typename I2>
 __global__ void k_soa_to_aos(const I2* __restrict__ soa, double2* __restrict__ aos, int Vh) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,9 +246,11 @@ int load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts, bo
   SQCG_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
   cudaFree(ctx->fatb32); cudaFree(ctx->lngb32);
+  cudaFree(ctx->fatff); cudaFree(ctx->lngff);
   ctx->fat64 = ctx->lng64 = nullptr;
   ctx->fat32 = ctx->lng32 = nullptr;
   ctx->fatb32 = ctx->lngb32 = nullptr;
+  ctx->fatff = ctx->lngff = nullptr;
   ctx->eightway = false;
   ctx->have_links = false;
   free_graphs(ctx);
@@ -236,13 +261,17 @@ int load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts, bo
             cudaMalloc((void**)&ctx->lng64, nlng64 * sizeof(double2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->fat32, nfat * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->lng32, nlng32 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->fatff, nfat * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->lngff, nlng64 * sizeof(float4)) == cudaSuccess &&
             (on_device || cudaMalloc(&raw, V * 4 * 9 * sizeof(double2)) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     cudaFree(raw);
     cudaFree(ctx->fat64); cudaFree(ctx->lng64); cudaFree(ctx->fat32); cudaFree(ctx->lng32);
+    cudaFree(ctx->fatff); cudaFree(ctx->lngff);
     ctx->fat64 = ctx->lng64 = nullptr;
     ctx->fat32 = ctx->lng32 = nullptr;
+    ctx->fatff = ctx->lngff = nullptr;
     return SQCG_ERR_NO_MEMORY;
   }
   const int fold = (ctx->flags & SQCG_PHASES_FOLDED) ? 0 : 1;
@@ -265,6 +294,9 @@ int load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts, bo
     }
     k_pack_links<<<grid, kThreads, 0, s>>>(src, ctx->g, fold, 3, nl32, ctx->lng64, ctx->lng32);
     if (cudaGetLastError() != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
+    // the float-float copy of the folded FP64 links (reliable-update arithmetic)
+    if (launch_split_ff(ctx->fat64, ctx->fatff, nfat, s) != SQCG_OK) { rc = SQCG_ERR_CUDA; break; }
+    if (launch_split_ff(ctx->lng64, ctx->lngff, nlng64, s) != SQCG_OK) { rc = SQCG_ERR_CUDA; break; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SQCG_ERR_CUDA; break; }
   } while (0);
   cudaFree(raw);
@@ -304,7 +336,7 @@ int layout_load_links_device(sqcg_ctx* ctx, const double* fat, const double* lng
 }
 
 int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev) {
-  if (!host || !dev || (prec != SQCG_F64 && prec != SQCG_F32)) return SQCG_ERR_INVALID_ARG;
+  if (!host || !dev || (prec != SQCG_F64 && prec != SQCG_F32 && prec != SQCG_FF)) return SQCG_ERR_INVALID_ARG;
   const int Vh = ctx->g.Vh;
   const size_t bytes = (size_t)Vh * 3 * sizeof(double2);
   SQCG_TRY(ensure_stage(ctx, bytes));
@@ -312,6 +344,8 @@ int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev) {
   SQCG_CUDA_TRY(cudaMemcpyAsync(ctx->stage, host, bytes, cudaMemcpyHostToDevice, s));
   if (prec == SQCG_F64)
     k_aos_to_soa<double2><<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const double2*)ctx->stage, (double2*)dev, Vh);
+  else if (prec == SQCG_FF)
+    k_aos_to_soa_ff<<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const double2*)ctx->stage, (float4*)dev, Vh);
   else
     k_aos_to_soa<float2><<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const double2*)ctx->stage, (float2*)dev, Vh);
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -319,13 +353,15 @@ int layout_pack_spinor(sqcg_ctx* ctx, int prec, const double* host, void* dev) {
 }
 
 int layout_unpack_spinor(sqcg_ctx* ctx, int prec, const void* dev, double* host) {
-  if (!host || !dev || (prec != SQCG_F64 && prec != SQCG_F32)) return SQCG_ERR_INVALID_ARG;
+  if (!host || !dev || (prec != SQCG_F64 && prec != SQCG_F32 && prec != SQCG_FF)) return SQCG_ERR_INVALID_ARG;
   const int Vh = ctx->g.Vh;
   const size_t bytes = (size_t)Vh * 3 * sizeof(double2);
   SQCG_TRY(ensure_stage(ctx, bytes));
   cudaStream_t s = ctx->stream;
   if (prec == SQCG_F64)
     k_soa_to_aos<double2><<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const double2*)dev, (double2*)ctx->stage, Vh);
+  else if (prec == SQCG_FF)
+    k_soa_ff_to_aos<<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const float4*)dev, (double2*)ctx->stage, Vh);
   else
     k_soa_to_aos<float2><<<grid_for(Vh, kThreads), kThreads, 0, s>>>((const float2*)dev, (double2*)ctx->stage, Vh);
   SQCG_CUDA_TRY(cudaGetLastError());

@@ -188,15 +188,17 @@ __device__ inline void solver_finish_ms(SolverState* s, int fin, double v) {
   }
 }
 
-// Single-reduction CG step (Chronopoulos and Gear's form of CG): with gamma_k = |r_k|^2 and
-// delta_k = <r_k, A r_k> from one reduction,
-//   beta_k = gamma_k / gamma_{k-1},  <p_k, A p_k> = delta_k - beta_k gamma_k / alpha_{k-1},
-//   alpha_k = gamma_k / <p_k, A p_k>   (beta_0 = 0, alpha_0 = gamma_0 / delta_0),
-// which is the same CG as alpha = |r|^2/<p,Ap>, beta = |r_new|^2/|r|^2 when p_k = r_k + beta_k p_{k-1}
-// and A p_k is carried as q_k = A r_k + beta_k q_{k-1}. Before that, gamma_k decides convergence and
-// the reliable update (an FP64 true residual, after which the step runs again on r_true).
-__device__ inline void sr_step(SolverState* s, double d, double g) {
-  if (!isfinite(d) || !isfinite(g)) { finish_breakdown(s); return; }
+// Single-reduction CG step (Chronopoulos and Gear's form of CG, one reduction per iteration). The
+// iteration carries p, q = A p (recursively) and r; one Dslash pass gives s = A r_k, and its epilogue
+// reduces gamma = |r_k|^2, d = Re<r_k, s>, c = Re<r_k, q_{k-1}> + Re<p_{k-1}, s>, e = Re<p_{k-1}, q_{k-1}>.
+// Then beta_k = gamma_k / gamma_{k-1} (beta_0 = 0), and the new p_k = r_k + beta p_{k-1},
+// q_k = s + beta q_{k-1} have <p_k, q_k> = d + beta c + beta^2 e exactly (a bilinear expansion of
+// measured dot products, no orthogonality assumed: with FP32 vectors the classical shortcut
+// d - beta gamma / alpha_{k-1} loses its sign after long stretches without a reliable update), and
+// alpha_k = gamma_k / <p_k, q_k>. Before that, gamma_k decides convergence and the reliable update (an
+// FP64 true residual, after which the step runs again on r_true).
+__device__ inline void sr_step(SolverState* s, double d, double c, double e, double g) {
+  if (!isfinite(d) || !isfinite(c) || !isfinite(e) || !isfinite(g)) { finish_breakdown(s); return; }
   if (s->after_update) {  // r was just replaced by the FP64 true residual (not converged)
     s->after_update = 0;
     s->rr = g;
@@ -213,11 +215,8 @@ __device__ inline void sr_step(SolverState* s, double d, double g) {
     if (s->use_if) cudaGraphSetConditional((cudaGraphConditionalHandle)s->h_if, s->need_update ? 1u : 0u);
     if (s->need_update) return;  // the step runs again after the update
   }
-  double beta = 0.0, pAp = d;
-  if (s->iter > 0) {
-    beta = g / s->rr_prev;
-    pAp = d - beta * g / s->sr_alpha_prev;
-  }
+  const double beta = (s->iter > 0) ? g / s->rr_prev : 0.0;
+  const double pAp = d + beta * (c + beta * e);
   if (!(pAp > 0.0) || !isfinite(pAp)) { finish_breakdown(s); return; }
   s->beta = beta;
   s->pAp = pAp;
@@ -232,8 +231,6 @@ __device__ inline void solver_finish2(SolverState* s, int fin, double a, double 
     if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) { finish_breakdown(s); return; }
     s->beta = (a - b) / s->rz;  // Polak-Ribiere (flexible) beta
     s->rz = a;
-  } else if (fin == FIN_SR_STEP) {  // a = <r, A r>, b = |r|^2
-    sr_step(s, a, b);
   }
 }
 
@@ -273,6 +270,31 @@ __device__ __forceinline__ void block_partial2(double v, double w, double* parti
     partials[blockIdx.x] = a;
     partials[gridDim.x + blockIdx.x] = b;
   }
+}
+
+// four sums at once: partials of sum k at offset k * gridDim.x
+__device__ __forceinline__ void block_partial4(double v0, double v1, double v2, double v3, double* partials) {
+  const double a = block_sum(v0);
+  const double b = block_sum(v1);
+  const double c = block_sum(v2);
+  const double d = block_sum(v3);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = b;
+    partials[2 * gridDim.x + blockIdx.x] = c;
+    partials[3 * gridDim.x + blockIdx.x] = d;
+  }
+}
+
+__device__ __forceinline__ void finish_partials4(SolverState* st, const double* partials, int n, int fin) {
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] += partials[(size_t)k * n + j];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[k] = block_sum(t[k]);
+  if (threadIdx.x == 0 && fin == FIN_SR_STEP) sr_step(st, t[0], t[1], t[2], t[3]);
 }
 
 __device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {

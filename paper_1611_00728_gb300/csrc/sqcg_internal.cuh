@@ -141,7 +141,7 @@ enum Finisher {
   FIN_FCG_PAP = 10,    // flexible CG: alpha = <z,r> / <p,Ap>
   FIN_FCG_BETA = 11,   // flexible CG (two sums): beta = (<z,r> - <z,r_old>) / <z_old,r_old>
   FIN_FCG_INIT = 12,   // flexible CG: <z_0, r_0>
-  FIN_SR_STEP = 13,    // single-reduction CG (two sums <r, A r>, |r|^2): convergence / reliable-update
+  FIN_SR_STEP = 13,    // single-reduction CG (four sums, see EPI_SR_DOTS): convergence / reliable-update
                        // decision, then alpha and beta of the iteration
 };
 
@@ -167,6 +167,9 @@ struct sqcg_ctx {
   double2* lng64;
   float2* fat32;
   float2* lng32;
+  // float-float copy of the FP64 links (hi, lo floats per real; float4 per complex), same layout
+  float4* fatff;
+  float4* lngff;
   // 8-way option (FP32 only): backward links -F_mu(n-mu)^+, -L_mu(n-3mu)^+ stored at n
   bool eightway;
   float2* fatb32;
@@ -180,7 +183,8 @@ struct sqcg_ctx {
   double2 *r64, *p64, *Ap64, *tmp64;
   float2 *r32, *p32, *Ap32, *tmp32;
   float2 *q32, *xh32;  // single-reduction mixed CG: q = A p, and the FP32 partial solution
-  double* partials;    // two sums' worth: 2 * max_blocks
+  float4* xff;         // float-float copy of x for the reliable update (its odd intermediate lives in tmp64)
+  double* partials;    // four sums' worth: 4 * max_blocks
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   SolverState* st;       // device
@@ -195,6 +199,7 @@ struct sqcg_ctx {
   int ms_nalloc;
   int ms_prec;
 
+  int ru_arith;        // arithmetic of the mixed solvers' true residuals: SQCG_F64 or SQCG_FF (default)
   double ru_delta;     // reliable update when |r| < ru_delta * max |r| since the last one
   int ru_interval;     // ... or after this many iterations
   CGGraph* graphs;  // cached captured solver loops
@@ -215,7 +220,8 @@ enum DslashEpi {
   EPI_NORMAL = 1,         // out = sigma*y - D in
   EPI_NORMAL_DOT = 2,     // out = sigma*y - D in, reduce Re<y, out>
   EPI_TRUE_RESID = 3,     // out = b - sigma*y + D in (b, y FP64), reduce |out|^2
-  EPI_NORMAL_DOT2 = 4,    // out = sigma*y - D in, reduce Re<y, out> and |y|^2 (two sums)
+  EPI_SR_DOTS = 4,        // single-reduction CG: s = sigma*r - D in (r = y, p = y2, q = y3 on the output
+                          // parity); four sums Re<r,s>, Re<r,q> + Re<p,s>, Re<p,q>, |r|^2
 };
 
 struct DslashLaunch {
@@ -227,6 +233,8 @@ struct DslashLaunch {
   void* out;
   void* out2;        // EPI_TRUE_RESID: optional second copy of out (same precision as out)
   const void* y;     // EPI_NORMAL*: vector on out_parity (precision prec); EPI_TRUE_RESID: FP64 x
+  const void* y2;    // EPI_SR_DOTS: p on out_parity
+  const void* y3;    // EPI_SR_DOTS: q on out_parity
   const void* b;     // EPI_TRUE_RESID: FP64 right-hand side
   double sigma;
   const double* sigma_dev;  // if non-null, sigma is read from here (solver state)
@@ -242,6 +250,7 @@ int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 int blas_grid(sqcg_ctx* ctx);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
+int launch_finish4(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 // single-reduction mixed CG: p = r + beta p, q = s + beta q, xh += alpha p, r -= alpha q (s in Ap32), with
 // the WHILE-loop control of the captured loop in one thread
@@ -253,6 +262,26 @@ int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, doubl
 
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
+
+// float-float Dslash (dslash_ff.cu): in and out_ff are float4 [3][Vh] (re_hi, re_lo, im_hi, im_lo);
+// true_resid: out32 (FP32) = b - sigma x + D in with |.|^2 reduced in FP64 (x, b FP64)
+struct FFLaunch {
+  int out_parity;
+  int true_resid;
+  const void* in;
+  void* out_ff;
+  void* out32;
+  const void* x;
+  const void* b;
+  double sigma;
+  const double* sigma_dev;
+  int gate;
+  int fin;
+};
+int launch_dslash_ff(sqcg_ctx* ctx, const FFLaunch& L, cudaStream_t s);
+int launch_split_ff(const double2* in, float4* out, size_t n, cudaStream_t s);
+// x += xh (if xh), xh = 0, xff = float-float copy of x
+int launch_flush_split(sqcg_ctx* ctx, double2* x, float2* xh, float4* xff, int gate, cudaStream_t s);
 
 int layout_load_links(sqcg_ctx* ctx, const double* fat, const double* lng, int opts);
 // the same from links already in device memory (host order [V][4][3][3] complex)

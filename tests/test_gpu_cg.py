@@ -436,3 +436,25 @@ def test_everything_on_a_side_stream(sqcg, links_cache):
             src = synth.gaussian_source(L, 4610 + j)
             assert bi[j].status == 0
             assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, src, lat.unpack(xb[j])) <= tol
+
+
+@pytest.mark.parametrize("arith", ["FF", "F64"])
+@pytest.mark.parametrize("L,m,tol", [((8, 8, 8, 8), 0.1, 1e-10), ((8, 10, 12, 14), 0.01, 1e-9)])
+def test_mixed_cg_update_arithmetic(sqcg, links_cache, arith, L, m, tol):
+    """The mixed solve's true residuals in float-float (default) or FP64 arithmetic: both reach the
+    oracle-recomputed residual, the library's reported residual agrees with the oracle's, and both take
+    the same iterations up to a few."""
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 4700)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        lat.set_update_arithmetic(getattr(sqcg, arith))
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, lat.pack(b), dx, tol=tol, max_iter=5000, mode=sqcg.MODE_MIXED)
+        x = lat.unpack(dx)
+        with pytest.raises(sqcg.SqcgError):
+            lat.set_update_arithmetic(sqcg.F32)
+    assert info.status == 0
+    res = oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x)
+    assert res <= tol
+    assert abs(res - info.true_rel_resid) <= 1e-3 * tol, (res, info.true_rel_resid)
