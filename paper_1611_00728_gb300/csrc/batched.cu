@@ -31,6 +31,7 @@
 #include <string.h>
 #include <string>
 
+#include "ff_arith.cuh"
 #include "solver_device.cuh"
 #include "sqcg_internal.cuh"
 
@@ -61,7 +62,10 @@ struct LatDev {
   int sbt0;            // first BLAS site block of this lattice over all lattices
   float2 *r, *p, *Ap, *tmp;  // RHS pairs: element (w, c, i) at pv(w, c, i, Vh)
   double2* x;
-  double2* tmp64;
+  double2* tmp64;       // FP64 intermediate, or the float-float one (float4 [w][c][Vh]) of the float-float passes
+  const float4* fatff[2];  // float-float links (reliable updates in float-float arithmetic)
+  const float4* lngff[2];
+  float4* xff;          // float-float copy of x for those passes ([w][c][Vh])
   const double2* b;
   size_t b_stride;  // elements between the sources of consecutive RHS: 3 Vh, or 0 when all share one source
 };
@@ -380,7 +384,7 @@ __device__ __forceinline__ void dslash_mrhs_site(const LatDev& L, int par, int i
 }
 
 enum MEpi { M_PLAIN = 0, M_NORMAL_DOT = 1, M_TRUE_RESID = 2 };
-enum MVec { V_P = 0, V_TMP = 1, V_X = 2, V_TMP64 = 3 };
+enum MVec { V_P = 0, V_TMP = 1, V_X = 2, V_TMP64 = 3, V_XFF = 4 };
 
 struct MArgs {
   const LatDev* lats;
@@ -471,6 +475,151 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
     (void)fin;
     rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
   }
+}
+
+// The reliable-update passes in float-float arithmetic (ff_arith.cuh): the same tiles, gates and
+// epilogues as k_mrhs_dslash<double, WT>, with links and vectors as float4 (hi, lo) pairs. On this GPU
+// the FP64 kernel is bound by the FP64 FMA rate (1/64 of FP32); this one runs on the FP32 pipe.
+template <int WT>
+__device__ __forceinline__ void apply_w_ff(float4 (&acc)[WT][3], const float4 (&U)[9], const float4* __restrict__ in,
+                                           int Vh, int idx, int nw, unsigned mask, bool dag) {
+#pragma unroll
+  for (int w = 0; w < WT; ++w) {
+    if (w < nw && ((mask >> w) & 1u)) {
+      float4 v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] = __ldg(in + ((size_t)w * 3 + c) * Vh + idx);
+      if (dag) ff_mdv_sub(acc[w], U, v);
+      else ff_mv(acc[w], U, v);
+    }
+  }
+}
+
+template <int WT>
+__global__ void __launch_bounds__(256) k_mrhs_dslash_ff(MArgs a) {
+  const int tile = blockIdx.x;
+  const int k = find_lat(a.lats, a.nlat, tile, true);
+  const LatDev& L = a.lats[k];
+  const int local = tile - L.tile640;
+  const int rb = local % L.nrb64, sb = local / L.nrb64;
+  const int wbase = rb * WT;  // one thread group per tile: the tile's RHS block is this thread's WT RHS
+  const int nw_tile = min(WT, L.nrhs - wbase);
+  const int w0 = wbase;
+  const int nw = max(0, min(WT, L.nrhs - w0));
+  const int blk = L.rb0 + wbase / a.W;
+  if (a.gate == GATE_UPDATE && !a.st->blk_update[blk]) return;
+  const Geom& g = L.g;
+  const int Vh = g.Vh;
+  const int i = sb * blockDim.x + threadIdx.x;
+  double part[WT];
+#pragma unroll
+  for (int w = 0; w < WT; ++w) part[w] = 0.0;
+  unsigned mask = 0xffffffffu;
+  if (a.gate == GATE_UPDATE) {
+    mask = 0u;
+#pragma unroll
+    for (int w = 0; w < WT; ++w)
+      if (w < nw && a.st->r[L.rhs0 + w0 + w].need_update && a.st->r[L.rhs0 + w0 + w].active) mask |= 1u << w;
+  }
+  const float4* in = (a.in_vec == V_XFF ? (const float4*)L.xff : (const float4*)L.tmp64) + (size_t)w0 * 3 * Vh;
+  if (i < Vh && nw > 0 && mask) {
+    const int xh = i % g.Lxh;
+    int rr = i / g.Lxh;
+    const int y = rr % g.Ly;
+    rr /= g.Ly;
+    const int z = rr % g.Lz;
+    const int t = rr / g.Lz;
+    const int x = 2 * xh + ((y + z + t + a.par) & 1);
+    const int row = i - xh;
+    float4 acc[WT][3];
+#pragma unroll
+    for (int w = 0; w < WT; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[w][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 U[9];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int cmu = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
+      const int Lmu = (mu == 0) ? g.Lx : (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+      const int smu = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const int d = (kk == 0) ? 1 : 3;
+        int fwd, bwd;
+        if (mu == 0) {
+          int xp = x + d; if (xp >= g.Lx) xp -= g.Lx;
+          int xm = x - d; if (xm < 0) xm += g.Lx;
+          fwd = row + (xp >> 1);
+          bwd = row + (xm >> 1);
+        } else {
+          fwd = i + d * smu; if (cmu + d >= Lmu) fwd -= Lmu * smu;
+          bwd = i - d * smu; if (cmu - d < 0) bwd += Lmu * smu;
+        }
+        const float4* fl = (kk == 0) ? L.fatff[a.par] : L.lngff[a.par];
+        const float4* bl = (kk == 0) ? L.fatff[1 - a.par] : L.lngff[1 - a.par];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) U[e] = __ldg(fl + ((size_t)mu * 9 + e) * Vh + i);
+        apply_w_ff<WT>(acc, U, in, Vh, fwd, nw, mask, false);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) U[e] = __ldg(bl + ((size_t)mu * 9 + e) * Vh + bwd);
+        apply_w_ff<WT>(acc, U, in, Vh, bwd, nw, mask, true);
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < WT; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        ff_norm(acc[w][c].x, acc[w][c].y);
+        ff_norm(acc[w][c].z, acc[w][c].w);
+      }
+    if (a.epi == M_PLAIN) {
+      float4* out = (float4*)L.tmp64 + (size_t)w0 * 3 * Vh;
+#pragma unroll
+      for (int w = 0; w < WT; ++w)
+        if (w < nw && ((mask >> w) & 1u))
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
+    } else {  // M_TRUE_RESID: r = b - sigma x + D tmp, the sum in FP64; r (FP32) and optionally p
+      const double2* xb = L.x + (size_t)w0 * 3 * Vh;
+      const double2* bb = L.b + (size_t)w0 * L.b_stride;
+#pragma unroll
+      for (int w = 0; w < WT; ++w) {
+        if (w < nw && ((mask >> w) & 1u)) {
+          const double sig = a.st->r[L.rhs0 + w0 + w].sigma;
+          double n2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const size_t o = ((size_t)w * 3 + c) * Vh + i;
+            const double2 xc = __ldg(xb + o), bc = __ldg(bb + (size_t)w * L.b_stride + (size_t)c * Vh + i);
+            const double2 dv = join_ff(acc[w][c]);
+            const double re = bc.x - sig * xc.x + dv.x;
+            const double im = bc.y - sig * xc.y + dv.y;
+            const float2 f = make_float2((float)re, (float)im);
+            L.r[pv(w0 + w, c, i, Vh)] = f;
+            if (a.write_p) L.p[pv(w0 + w, c, i, Vh)] = f;
+            n2 += re * re + im * im;
+          }
+          part[w] = n2;
+        }
+      }
+    }
+  }
+  if (a.epi != M_PLAIN) rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
+}
+
+// xff = float-float copy of x for every RHS that takes the reliable update (all RHS when not gated)
+__global__ void k_mrhs_split_x(const LatDev* lats, int nlat, const BatchState* st, int gated) {
+  const int g = blockIdx.y;
+  int k = 0;
+  for (int j = 1; j < nlat; ++j)
+    if (g >= lats[j].rhs0) k = j;
+  const LatDev& L = lats[k];
+  const int w = g - L.rhs0;
+  if (w >= L.nrhs) return;
+  if (gated && !(st->r[g].need_update && st->r[g].active)) return;
+  const size_t n = (size_t)3 * L.g.Vh, off = (size_t)w * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
+    L.xff[off + idx] = split_ff(L.x[off + idx]);
 }
 
 // FP32 multi-RHS Dslash with the links of the tile staged in shared memory.
@@ -842,6 +991,7 @@ struct BatchPlan {
   const void* b[SQCG_MAX_LATTICES];
   void* x[SQCG_MAX_LATTICES];
   int b_shared;          // every RHS of a lattice reads the same source b[k]
+  int ff;                // reliable updates in float-float arithmetic (else FP64)
   int W, T;              // tuned RHS block width and site block (threads along x)
   int carve;             // tuned shared-memory carveout of the FP32 Dslash (percent; -1 = driver default)
   int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
@@ -1044,6 +1194,33 @@ int launch_f64(const BatchPlan& P, int par, int in_vec, int epi, int gate, int w
   return launch_mrhs_dslash_w<double>(W64, 1, P.ntiles64, P.T, s, margs(P, par, in_vec, epi, gate, write_p));
 }
 
+// The true-residual pass r = b - A x of the RHS that asked for it (gate = GATE_UPDATE) or of all of them
+// (GATE_NONE, the initial residual): FP64 kernels, or the float-float ones after splitting x.
+int launch_true_resid_pass(const BatchPlan& P, int gate, int write_p, cudaStream_t s) {
+  if (!P.ff) {
+    SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, gate, 0, s));
+    return launch_f64(P, 0, V_TMP64, M_TRUE_RESID, gate, write_p, s);
+  }
+  int max_vh = 0;
+  for (int k = 0; k < P.nlat; ++k) max_vh = P.host[k].g.Vh > max_vh ? P.host[k].g.Vh : max_vh;
+  const int gx = (int)(((size_t)3 * max_vh + 255) / 256 < 1024 ? ((size_t)3 * max_vh + 255) / 256 : 1024);
+  k_mrhs_split_x<<<dim3(gx, P.nrhs_total), 256, 0, s>>>(P.dev, P.nlat, P.st, gate == GATE_UPDATE ? 1 : 0);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  const int W64 = P.W < kW64 ? P.W : kW64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const MArgs a = pass == 0 ? margs(P, 1, V_XFF, M_PLAIN, gate, 0) : margs(P, 0, V_TMP64, M_TRUE_RESID, gate, write_p);
+    const dim3 block(P.T, 1);
+    switch (W64) {
+      case 1: k_mrhs_dslash_ff<1><<<P.ntiles64, block, 0, s>>>(a); break;
+      case 2: k_mrhs_dslash_ff<2><<<P.ntiles64, block, 0, s>>>(a); break;
+      case 4: k_mrhs_dslash_ff<4><<<P.ntiles64, block, 0, s>>>(a); break;
+      default: return SQCG_ERR_INVALID_ARG;
+    }
+    SQCG_CUDA_TRY(cudaGetLastError());
+  }
+  return SQCG_OK;
+}
+
 int upload_lats(BatchPlan& P, cudaStream_t s) {
   SQCG_CUDA_TRY(cudaMemcpyAsync(P.dev, P.host, sizeof(LatDev) * P.nlat, cudaMemcpyHostToDevice, s));
   return SQCG_OK;
@@ -1137,10 +1314,11 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   return upload_lats(P, s);
 }
 
-// per lattice: r, p, Ap, tmp in RHS pairs (FP32) and tmp64 (FP64)
-size_t work_bytes(int nrhs, size_t Vh) {
+// per lattice: r, p, Ap, tmp in RHS pairs (FP32), tmp64 (FP64 or float-float) and, with float-float
+// reliable updates, xff
+size_t work_bytes(int nrhs, size_t Vh, int ff) {
   const size_t nf = (size_t)((nrhs + 1) / 2) * 2 * 3 * Vh;
-  return 4 * nf * sizeof(float2) + (size_t)nrhs * 3 * Vh * sizeof(double2);
+  return 4 * nf * sizeof(float2) + (size_t)(ff ? 2 : 1) * nrhs * 3 * Vh * sizeof(double2);
 }
 
 void destroy_plan(BatchPlan* P) {
@@ -1160,6 +1338,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
   if (!P) return SQCG_ERR_NO_MEMORY;
   P->nlat = nctx;
   P->b_shared = b_shared;
+  P->ff = ctx[0]->ru_arith == SQCG_FF ? 1 : 0;
   int total = 0, max_vh = 0;
   for (int k = 0; k < nctx; ++k) {
     sqcg_ctx* c = ctx[k];
@@ -1177,6 +1356,8 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
       L.lng32[par] = c->lng32 + (size_t)par * 4 * nl32 * Vh;
       L.fat64[par] = c->fat64 + (size_t)par * 4 * 9 * Vh;
       L.lng64[par] = c->lng64 + (size_t)par * 4 * 9 * Vh;
+      L.fatff[par] = c->fatff + (size_t)par * 4 * 9 * Vh;
+      L.lngff[par] = c->lngff + (size_t)par * 4 * 9 * Vh;
     }
     L.nl32 = nl32;
     L.recon = c->recon ? 1 : 0;
@@ -1188,7 +1369,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     L.b_stride = b_shared ? 0 : 3 * Vh;
     L.x = (double2*)x[k];
     // FP32 vectors: (nrhs + 1) / 2 RHS pairs each (see pv); FP64 tmp64: nrhs vectors
-    if (cudaMalloc(&P->work[k], work_bytes(nrhs[k], Vh)) != cudaSuccess) {
+    if (cudaMalloc(&P->work[k], work_bytes(nrhs[k], Vh, P->ff)) != cudaSuccess) {
       cudaGetLastError();
       destroy_plan(P);
       return SQCG_ERR_NO_MEMORY;
@@ -1197,6 +1378,7 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     float2* w = (float2*)P->work[k];
     L.r = w; L.p = w + nf; L.Ap = w + 2 * nf; L.tmp = w + 3 * nf;
     L.tmp64 = (double2*)(w + 4 * nf);
+    L.xff = P->ff ? (float4*)(L.tmp64 + (size_t)nrhs[k] * 3 * Vh) : nullptr;
     total += nrhs[k];
     if ((int)Vh > max_vh) max_vh = (int)Vh;
   }
@@ -1212,7 +1394,8 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     return SQCG_ERR_NO_MEMORY;
   }
   SQCG_CUDA_TRY(cudaMemsetAsync(P->st, 0, sizeof(BatchState), s));
-  for (int k = 0; k < nctx; ++k) SQCG_CUDA_TRY(cudaMemsetAsync(P->work[k], 0, work_bytes(nrhs[k], ctx[k]->g.Vh), s));
+  for (int k = 0; k < nctx; ++k)
+    SQCG_CUDA_TRY(cudaMemsetAsync(P->work[k], 0, work_bytes(nrhs[k], ctx[k]->g.Vh, P->ff), s));
   int rc = autotune(*P, s);
   if (rc != SQCG_OK) { destroy_plan(P); return rc; }
   *out = P;
@@ -1233,8 +1416,7 @@ int enqueue_head(BatchPlan& P, cudaStream_t s) {
 }
 
 int enqueue_reliable(BatchPlan& P, cudaStream_t s) {
-  SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_UPDATE, 0, s));
-  SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_UPDATE, 0, s));
+  SQCG_TRY(launch_true_resid_pass(P, GATE_UPDATE, 0, s));
   return launch_finish_b(P, BFIN_TRUE, 0, s);
 }
 
@@ -1335,6 +1517,7 @@ int capture_plan(BatchPlan& P) {
 bool plan_matches(const BatchPlan* P, int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* const* b,
                   int b_shared, void* const* x) {
   if (!P || P->nlat != nctx || P->b_shared != b_shared) return false;
+  if (P->ff != (ctx[0]->ru_arith == SQCG_FF ? 1 : 0)) return false;
   for (int k = 0; k < nctx; ++k)
     if (P->ctx[k] != ctx[k] || P->gen[k] != sqcg_links_generation(ctx[k]) || P->nrhs[k] != nrhs[k] ||
         P->b[k] != b[k] || P->x[k] != x[k])
@@ -1415,8 +1598,7 @@ int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double*
   } else {
     for (int j = 0; j < P.nblk; ++j) h->blk_update[j] = 1;
     SQCG_CUDA_TRY(cudaMemcpyAsync(P.st->blk_update, h->blk_update, sizeof(int) * P.nblk, cudaMemcpyHostToDevice, s));
-    SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, GATE_NONE, 0, s));
-    SQCG_TRY(launch_f64(P, 0, V_TMP64, M_TRUE_RESID, GATE_NONE, 1, s));
+    SQCG_TRY(launch_true_resid_pass(P, GATE_NONE, 1, s));
     SQCG_TRY(launch_finish_b(P, BFIN_INIT, 0, s));
     launches += 3;
   }
@@ -1460,7 +1642,7 @@ int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double*
       SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
       SQCG_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    launches += h->loop_count * 8 + h->if_runs * 3;
+    launches += h->loop_count * 8 + h->if_runs * (P.ff ? 4 : 3);
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int worst = SQCG_OK;

@@ -268,10 +268,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
   finish_partials2(st, partials, n, fin);
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish4(SolverState* st, const double* partials, int n, int fin,
+__global__ void __launch_bounds__(kFinishThreads) k_finish3(SolverState* st, const double* partials, int n, int fin,
                                                             int gate) {
   if (!gate_open(st, gate)) return;
-  finish_partials4(st, partials, n, fin);
+  finish_partials3(st, partials, n, fin);
 }
 
 // One thread: count the WHILE-loop iterations and set its condition. The loop
@@ -321,8 +321,8 @@ int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s
   return SQCG_OK;
 }
 
-int launch_finish4(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
-  k_finish4<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
+int launch_finish3(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
+  k_finish3<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

@@ -122,7 +122,7 @@ int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s) {
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
   L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_SR_DOTS; L.in = ctx->tmp32; L.out = ctx->Ap32;
-  L.y = ctx->r32; L.y2 = ctx->p32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
+  L.y = ctx->r32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
   L.fin = FIN_SR_STEP;
   return launch_dslash(ctx, L, s);
 }

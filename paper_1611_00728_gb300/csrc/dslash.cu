@@ -103,7 +103,6 @@ struct DArgs {
   void* out;
   void* out2;
   const void* y;
-  const void* y2;
   const void* y3;
   const double2* b;
   double sigma;
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0, part2 = 0.0, part3 = 0.0, part4 = 0.0;
+  double part = 0.0, part2 = 0.0, part3 = 0.0;
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -224,28 +223,24 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
       }
       part = (double)dot;
-    } else if constexpr (EPI == EPI_SR_DOTS) {  // s = sigma r - D in; <r,s>, <r,q> + <p,s>, <p,q>, |r|^2
+    } else if constexpr (EPI == EPI_SR_DOTS) {  // s = sigma r - D in; <r,s>, <r,q>, |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
-      const R2* pv = static_cast<const R2*>(a.y2);
       const R2* qv = static_cast<const R2*>(a.y3);
-      R rs = R(0), cross = R(0), pq = R(0), rr = R(0);
+      R rs = R(0), rq = R(0), rr = R(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t k = (size_t)c * Vh + i;
-        const R2 rc = ldg2(rv + k), pc = ldg2(pv + k), qc = ldg2(qv + k);
+        const R2 rc = ldg2(rv + k), qc = ldg2(qv + k);
         O2 o = mk<O2>((RO)(sig * rc.x - acc[c].x), (RO)(sig * rc.y - acc[c].y));
         out[k] = o;
         rs = fma(rc.x, o.x, fma(rc.y, o.y, rs));
-        cross = fma(rc.x, qc.x, fma(rc.y, qc.y, cross));
-        cross = fma(pc.x, o.x, fma(pc.y, o.y, cross));
-        pq = fma(pc.x, qc.x, fma(pc.y, qc.y, pq));
+        rq = fma(rc.x, qc.x, fma(rc.y, qc.y, rq));
         rr = fma(rc.x, rc.x, fma(rc.y, rc.y, rr));
       }
       part = (double)rs;
-      part2 = (double)cross;
-      part3 = (double)pq;
-      part4 = (double)rr;
+      part2 = (double)rq;
+      part3 = (double)rr;
     } else {  // EPI_TRUE_RESID: out = b - sigma*x + D in, in FP64
       const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
       const double2* xv = static_cast<const double2*>(a.y);
@@ -269,9 +264,9 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
   if constexpr (EPI == EPI_SR_DOTS) {
-    if (a.fin != FIN_NONE) block_partial4(part, part2, part3, part4, a.partials);
+    if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
   }
-  (void)part2; (void)part3; (void)part4;
+  (void)part2; (void)part3;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -297,7 +292,6 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   a.out = L.out;
   a.out2 = L.out2;
   a.y = L.y;
-  a.y2 = L.y2;
   a.y3 = L.y3;
   a.b = static_cast<const double2*>(L.b);
   a.sigma = L.sigma;
@@ -311,7 +305,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   const int grid = grid_for(ctx->g.Vh, kThreads);
   const bool reduces = (L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_TRUE_RESID) &&
                        L.fin != FIN_NONE;
-  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 4 * max_blocks
+  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 3 * max_blocks
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
@@ -322,7 +316,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_SR_DOTS ? launch_finish4(ctx, grid, L.fin, L.gate, s)
+    return L.epi == EPI_SR_DOTS ? launch_finish3(ctx, grid, L.fin, L.gate, s)
                                 : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
 }
@@ -348,7 +342,7 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
   if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS) && !L.y) return SQCG_ERR_INVALID_ARG;
-  if (L.epi == EPI_SR_DOTS && (!L.y2 || !L.y3)) return SQCG_ERR_INVALID_ARG;
+  if (L.epi == EPI_SR_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);
   return SQCG_ERR_INVALID_ARG;

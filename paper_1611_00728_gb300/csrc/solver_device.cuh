@@ -190,15 +190,17 @@ __device__ inline void solver_finish_ms(SolverState* s, int fin, double v) {
 
 // Single-reduction CG step (Chronopoulos and Gear's form of CG, one reduction per iteration). The
 // iteration carries p, q = A p (recursively) and r; one Dslash pass gives s = A r_k, and its epilogue
-// reduces gamma = |r_k|^2, d = Re<r_k, s>, c = Re<r_k, q_{k-1}> + Re<p_{k-1}, s>, e = Re<p_{k-1}, q_{k-1}>.
-// Then beta_k = gamma_k / gamma_{k-1} (beta_0 = 0), and the new p_k = r_k + beta p_{k-1},
-// q_k = s + beta q_{k-1} have <p_k, q_k> = d + beta c + beta^2 e exactly (a bilinear expansion of
-// measured dot products, no orthogonality assumed: with FP32 vectors the classical shortcut
-// d - beta gamma / alpha_{k-1} loses its sign after long stretches without a reliable update), and
-// alpha_k = gamma_k / <p_k, q_k>. Before that, gamma_k decides convergence and the reliable update (an
-// FP64 true residual, after which the step runs again on r_true).
-__device__ inline void sr_step(SolverState* s, double d, double c, double e, double g) {
-  if (!isfinite(d) || !isfinite(c) || !isfinite(e) || !isfinite(g)) { finish_breakdown(s); return; }
+// reduces gamma = |r_k|^2, d = Re<r_k, s> and c = Re<r_k, q_{k-1}>. Then beta_k = gamma_k / gamma_{k-1}
+// (beta_0 = 0), and the new p_k = r_k + beta p_{k-1}, q_k = s + beta q_{k-1} have
+//   <p_k, q_k> = d + 2 beta c + beta^2 <p_{k-1}, q_{k-1}>
+// (A is Hermitian, so Re<p_{k-1}, A r_k> = Re<q_{k-1}, r_k>, and <p_{k-1}, q_{k-1}> is the previous step's
+// value), and alpha_k = gamma_k / <p_k, q_k>. The cross term is measured, not taken from the textbook
+// shortcut <r_k, q_{k-1}> = -gamma_k / alpha_{k-1}, which assumes r_k orthogonal to r_{k-1}: with FP32
+// vectors that loses its sign after long stretches without a reliable update. Before that, gamma_k
+// decides convergence and the reliable update (an FP64 true residual, after which the step runs again
+// on r_true).
+__device__ inline void sr_step(SolverState* s, double d, double c, double g) {
+  if (!isfinite(d) || !isfinite(c) || !isfinite(g)) { finish_breakdown(s); return; }
   if (s->after_update) {  // r was just replaced by the FP64 true residual (not converged)
     s->after_update = 0;
     s->rr = g;
@@ -216,7 +218,7 @@ __device__ inline void sr_step(SolverState* s, double d, double c, double e, dou
     if (s->need_update) return;  // the step runs again after the update
   }
   const double beta = (s->iter > 0) ? g / s->rr_prev : 0.0;
-  const double pAp = d + beta * (c + beta * e);
+  const double pAp = (s->iter > 0) ? d + beta * (2.0 * c + beta * s->pAp) : d;
   if (!(pAp > 0.0) || !isfinite(pAp)) { finish_breakdown(s); return; }
   s->beta = beta;
   s->pAp = pAp;
@@ -272,29 +274,54 @@ __device__ __forceinline__ void block_partial2(double v, double w, double* parti
   }
 }
 
-// four sums at once: partials of sum k at offset k * gridDim.x
-__device__ __forceinline__ void block_partial4(double v0, double v1, double v2, double v3, double* partials) {
-  const double a = block_sum(v0);
-  const double b = block_sum(v1);
-  const double c = block_sum(v2);
-  const double d = block_sum(v3);
+// Three sums of a block in one pass (warp shuffles, one shared-memory exchange): the totals are valid in
+// thread 0. blockDim.x a multiple of 32, at most 1024. Fixed tree -> deterministic.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double part3[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  __syncthreads();  // part3 may still be read by an earlier call
+  if (lane == 0) { part3[0][wid] = a; part3[1][wid] = b; part3[2][wid] = c; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? part3[0][lane] : 0.0;
+    b = lane < nw ? part3[1][lane] : 0.0;
+    c = lane < nw ? part3[2][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+  }
+}
+
+// first stage of three sums: partials of sum k at offset k * gridDim.x
+__device__ __forceinline__ void block_partial3(double a, double b, double c, double* partials) {
+  block_sum3(a, b, c);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = a;
     partials[gridDim.x + blockIdx.x] = b;
     partials[2 * gridDim.x + blockIdx.x] = c;
-    partials[3 * gridDim.x + blockIdx.x] = d;
   }
 }
 
-__device__ __forceinline__ void finish_partials4(SolverState* st, const double* partials, int n, int fin) {
-  double t[4] = {0.0, 0.0, 0.0, 0.0};
+__device__ __forceinline__ void finish_partials3(SolverState* st, const double* partials, int n, int fin) {
+  double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll 4
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) t[k] += partials[(size_t)k * n + j];
+    a += partials[j];
+    b += partials[n + j];
+    c += partials[2 * n + j];
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) t[k] = block_sum(t[k]);
-  if (threadIdx.x == 0 && fin == FIN_SR_STEP) sr_step(st, t[0], t[1], t[2], t[3]);
+  block_sum3(a, b, c);
+  if (threadIdx.x == 0 && fin == FIN_SR_STEP) sr_step(st, a, b, c);
 }
 
 __device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {

@@ -141,7 +141,7 @@ enum Finisher {
   FIN_FCG_PAP = 10,    // flexible CG: alpha = <z,r> / <p,Ap>
   FIN_FCG_BETA = 11,   // flexible CG (two sums): beta = (<z,r> - <z,r_old>) / <z_old,r_old>
   FIN_FCG_INIT = 12,   // flexible CG: <z_0, r_0>
-  FIN_SR_STEP = 13,    // single-reduction CG (four sums, see EPI_SR_DOTS): convergence / reliable-update
+  FIN_SR_STEP = 13,    // single-reduction CG (three sums, see EPI_SR_DOTS): convergence / reliable-update
                        // decision, then alpha and beta of the iteration
 };
 
@@ -184,7 +184,7 @@ struct sqcg_ctx {
   float2 *r32, *p32, *Ap32, *tmp32;
   float2 *q32, *xh32;  // single-reduction mixed CG: q = A p, and the FP32 partial solution
   float4* xff;         // float-float copy of x for the reliable update (its odd intermediate lives in tmp64)
-  double* partials;    // four sums' worth: 4 * max_blocks
+  double* partials;    // three sums' worth: 3 * max_blocks
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   SolverState* st;       // device
@@ -220,8 +220,8 @@ enum DslashEpi {
   EPI_NORMAL = 1,         // out = sigma*y - D in
   EPI_NORMAL_DOT = 2,     // out = sigma*y - D in, reduce Re<y, out>
   EPI_TRUE_RESID = 3,     // out = b - sigma*y + D in (b, y FP64), reduce |out|^2
-  EPI_SR_DOTS = 4,        // single-reduction CG: s = sigma*r - D in (r = y, p = y2, q = y3 on the output
-                          // parity); four sums Re<r,s>, Re<r,q> + Re<p,s>, Re<p,q>, |r|^2
+  EPI_SR_DOTS = 4,        // single-reduction CG: s = sigma*r - D in (r = y, q = y3 on the output parity);
+                          // three sums Re<r,s>, Re<r,q>, |r|^2
 };
 
 struct DslashLaunch {
@@ -233,7 +233,6 @@ struct DslashLaunch {
   void* out;
   void* out2;        // EPI_TRUE_RESID: optional second copy of out (same precision as out)
   const void* y;     // EPI_NORMAL*: vector on out_parity (precision prec); EPI_TRUE_RESID: FP64 x
-  const void* y2;    // EPI_SR_DOTS: p on out_parity
   const void* y3;    // EPI_SR_DOTS: q on out_parity
   const void* b;     // EPI_TRUE_RESID: FP64 right-hand side
   double sigma;
@@ -250,7 +249,7 @@ int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 int blas_grid(sqcg_ctx* ctx);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
-int launch_finish4(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
+int launch_finish3(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 // single-reduction mixed CG: p = r + beta p, q = s + beta q, xh += alpha p, r -= alpha q (s in Ap32), with
 // the WHILE-loop control of the captured loop in one thread

@@ -3,8 +3,8 @@
 Every right-hand side must reach a true relative residual <= tol, recomputed
 here by the FP64 oracle from the returned x; a batched solve must agree with
 the single-RHS solver. The full batched workload (16 sources each on 16^4,
-24^4 and 32^3x64, m = 0.02) is checked on the solver's reported residuals for
-all 48 sources and on the oracle for a sample of them.
+24^4 and 32^3x64, m = 0.02) is checked on the oracle's FP64 true residual for
+every one of its 48 solutions.
 """
 
 import numpy as np
@@ -208,3 +208,35 @@ def test_batched_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monk
     assert g[1] == e[1]
     assert all(np.array_equal(a, c) for a, c in zip(g[0], e[0]))
     assert all(st == (0 if max_iter == 5000 else -3) for st, _, _ in g[1])
+
+
+@pytest.mark.parametrize("arith", ["FF", "F64"])
+def test_batched_update_arithmetic_and_initial_guess(sqcg, links_cache, arith):
+    """The batched solve's true-residual passes in float-float (default) or FP64 arithmetic, on two uneven
+    lattices, once from zero and once from a nonzero initial guess (which takes the all-RHS initial
+    residual pass); every solution is checked on the oracle's FP64 true residual."""
+    specs = [((8, 8, 8, 8), 3, 0.1, 1001), ((6, 8, 10, 12), 2, 0.05, 55)]
+    lats, bs, xs, srcs, links = [], [], [], [], []
+    for n, (L, nr, m, seed) in enumerate(specs):
+        fat, lng = links_cache(L, seed)
+        lat = sqcg.Lattice(L)
+        lat.load_links(fat, lng, recon12=True)
+        lat.set_update_arithmetic(getattr(sqcg, arith))
+        s = [synth.gaussian_source(L, 7300 + 10 * n + j) for j in range(nr)]
+        b, x = make_batch(sqcg, lat, s)
+        lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
+    masses = [m for _, _, m, _ in specs]
+    for start in ("zero", "guess"):
+        if start == "guess":
+            for x in xs:
+                x.normal_()
+        infos = sqcg.cg_solve_batched(lats, masses, bs, xs, tol=1e-9, max_iter=5000)
+        for n, (L, nr, m, _) in enumerate(specs):
+            fat, lng = links[n]
+            for j in range(nr):
+                assert infos[n][j].status == 0
+                res = oracle.true_rel_residual(L, fat, lng, 4 * m * m, srcs[n][j], lats[n].unpack(xs[n][j]))
+                assert res <= 1e-9, (arith, start, L, j, res)
+                assert abs(res - infos[n][j].true_rel_resid) <= 1e-12, (res, infos[n][j].true_rel_resid)
+    for lat in lats:
+        lat.close()
