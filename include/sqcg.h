@@ -239,7 +239,7 @@ int sqcg_rational_apply(sqcg_ctx* ctx, int nshift, const double* shifts, const d
  * reductions and reliable updates). This applies the paper's single-mass CG
  * (Sec. 3) to many sources at once; batching is not in the paper. Each link is
  * loaded once per block of W right-hand sides. W (1..16), the RHS per thread,
- * the site-block size and the shared-memory carveout are picked on the first
+ * the site-block size, the warp shape and the shared-memory carveout are picked on the first
  * call for a given set of lattices by timing the multi-RHS Dslash (cached per
  * process, and in the file named by the environment variable SQCG_TUNE_CACHE
  * if set; SQCG_TUNE_VERBOSE=1 prints each timed candidate to stderr), unless
@@ -374,17 +374,20 @@ int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T);
 
 /* The full FP32 Dslash configuration of that batched solve: RHS block width W,
  * right-hand sides per thread WT (W / WT thread groups per site block), site
- * block T and shared-memory carveout in percent (-1 = the driver's default).
- * Any output pointer may be NULL. */
-int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve);
+ * block T, shared-memory carveout in percent (-1 = the driver's default) and
+ * warp_sites, the consecutive sites one warp covers: 32 (one RHS group per
+ * warp), or 16 (two RHS groups per warp, whose link reads from shared memory
+ * are then one broadcast access for both). Any output pointer may be NULL. */
+int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve, int* warp_sites);
 
 /* Pin the FP32 Dslash configuration of batched solves planned from now on in
  * this process instead of autotuning it (plans already cached with a context
  * keep theirs); W = 0 returns to autotuning. Requirements: W in {1, 2, 4, 8,
  * 16}; WT in {1, 2, 4}, WT <= W; T a multiple of 32 in [32, 128] with
- * T * W / WT <= 512; carve -1 or 0..100. SQCG_ERR_INVALID_ARG otherwise
- * (nothing changes). Thread-safe. */
-int sqcg_batched_pin_tuning(int W, int WT, int T, int carve);
+ * T * W / WT <= 512; carve -1 or 0..100; warp_sites 32 (or 0, the same) or 16
+ * with W / WT even. SQCG_ERR_INVALID_ARG otherwise (nothing changes).
+ * Thread-safe. */
+int sqcg_batched_pin_tuning(int W, int WT, int T, int carve, int warp_sites);
 
 const char* sqcg_strerror(int status);
 

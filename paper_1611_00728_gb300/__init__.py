@@ -130,8 +130,8 @@ def library():
         lib.sqcg_rational_apply.argtypes = [P, I, P, P, D, P, P, D, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
         lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
-        lib.sqcg_batched_tuning_ex.argtypes = [P] + [ctypes.POINTER(I)] * 4
-        lib.sqcg_batched_pin_tuning.argtypes = [I] * 4
+        lib.sqcg_batched_tuning_ex.argtypes = [P] + [ctypes.POINTER(I)] * 5
+        lib.sqcg_batched_pin_tuning.argtypes = [I] * 5
         lib.sqcg_nn_create.argtypes = [P, ctypes.POINTER(P)]
         lib.sqcg_nn_destroy.argtypes = [P]
         lib.sqcg_nn_nparams.argtypes = []
@@ -414,16 +414,16 @@ def batched_tuning(lattice) -> tuple[int, int]:
 
 
 def batched_tuning_ex(lattice) -> dict:
-    """The full FP32 Dslash configuration of the last batched solve led by lattice:
-    W, WT (RHS per thread), T and carve (shared-memory carveout in percent, -1 = default)."""
-    v = [ctypes.c_int() for _ in range(4)]
+    """The full FP32 Dslash configuration of the last batched solve led by lattice: W, WT (RHS per thread),
+    T, carve (shared-memory carveout in percent, -1 = default) and warp_sites (32 or 16 sites per warp)."""
+    v = [ctypes.c_int() for _ in range(5)]
     _check(library().sqcg_batched_tuning_ex(lattice._h, *[ctypes.byref(c) for c in v]), "sqcg_batched_tuning_ex")
-    return dict(zip(("W", "WT", "T", "carve"), (c.value for c in v)))
+    return dict(zip(("W", "WT", "T", "carve", "warp_sites"), (c.value for c in v)))
 
 
-def pin_batched_tuning(W: int, WT: int = 1, T: int = 64, carve: int = -1):
+def pin_batched_tuning(W: int, WT: int = 1, T: int = 64, carve: int = -1, warp_sites: int = 32):
     """Pin the FP32 Dslash configuration of batched solves planned from now on (W = 0: autotune again)."""
-    _check(library().sqcg_batched_pin_tuning(int(W), int(WT), int(T), int(carve)),
+    _check(library().sqcg_batched_pin_tuning(int(W), int(WT), int(T), int(carve), int(warp_sites)),
            "sqcg_batched_pin_tuning")
 
 

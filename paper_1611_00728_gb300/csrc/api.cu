@@ -29,7 +29,7 @@ int ensure_workspace(sqcg_ctx* ctx) {
             cudaMalloc((void**)&ctx->q32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->xh32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->xff, n * sizeof(float4)) == cudaSuccess &&
-            cudaMalloc((void**)&ctx->partials, 3 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->partials, 4 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->st, sizeof(SolverState)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) == cudaSuccess;
   if (!ok) {

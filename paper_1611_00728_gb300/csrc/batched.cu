@@ -622,16 +622,80 @@ __global__ void k_mrhs_split_x(const LatDev* lats, int nlat, const BatchState* s
     L.xff[off + idx] = split_ff(L.x[off + idx]);
 }
 
+// Per-RHS block partial of a kernel whose warps hold SUB consecutive sites of 32 / SUB RHS groups:
+// thread (site ax, group ay) holds v[w] for RHS ay * WT + w of the tile. Segmented warp sums over the
+// SUB sites, then a fixed-order sum over the site chunks -> deterministic.
+template <int WT, int SUB>
+__device__ void rhs_block_partial_m(double (&v)[WT], const LatDev& L, int wbase, int nw_tile, int sb, int ax, int ay,
+                                    double* partials, int max_nsb) {
+  __shared__ double red[16][kMaxTSmem / 16];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31;
+  const int nchunk = blockDim.x / SUB;
+#pragma unroll
+  for (int w = 0; w < WT; ++w) {
+    double t = v[w];
+#pragma unroll
+    for (int o = SUB / 2; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o, SUB);
+    if ((lane & (SUB - 1)) == 0) red[ay * WT + w][ax / SUB] = t;
+  }
+  __syncthreads();
+  if (tid < nw_tile) {
+    double t = 0.0;
+    for (int j = 0; j < nchunk; ++j) t += red[tid][j];
+    partials[(size_t)(L.rhs0 + wbase + tid) * max_nsb + sb] = t;
+  }
+}
+
+// half-lattice coordinates of site i of parity par
+struct SiteXY {
+  int x, y, z, t, row;
+};
+
+__device__ __forceinline__ SiteXY site_of(const Geom& g, int i, int par) {
+  SiteXY c;
+  const int xh = i % g.Lxh;
+  int rr = i / g.Lxh;
+  c.y = rr % g.Ly;
+  rr /= g.Ly;
+  c.z = rr % g.Lz;
+  c.t = rr / g.Lz;
+  c.x = 2 * xh + ((c.y + c.z + c.t + par) & 1);
+  c.row = i - xh;
+  return c;
+}
+
+// half index of n + d mu for the site (i, c)
+__device__ __forceinline__ int nbr_of(const Geom& g, int i, const SiteXY& c, int mu, int d) {
+  if (mu == 0) {
+    int xp = c.x + d;
+    if (xp >= g.Lx) xp -= g.Lx;
+    if (xp < 0) xp += g.Lx;
+    return c.row + (xp >> 1);
+  }
+  const int cc = (mu == 1) ? c.y : (mu == 2) ? c.z : c.t;
+  const int Lm = (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+  const int sm = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+  int j = i + d * sm;
+  if (cc + d >= Lm) j -= Lm * sm;
+  if (cc + d < 0) j += Lm * sm;
+  return j;
+}
+
 // FP32 multi-RHS Dslash with the links of the tile staged in shared memory.
-// Thread (x, y): site sb*blockDim.x + x, right-hand sides y*WT .. y*WT+WT-1 of
-// the tile's RHS block (width W = WT*blockDim.y). First the block copies the 16
-// links of each of its sites (8 fat, 8 long; 12-real long links rebuilt here)
-// from global memory into shared memory, the RHS groups sharing the work; then
-// every group applies them to its own right-hand sides. Each link is read from
-// global memory once per RHS block, whatever W is.
+// A block covers T = blockDim.x sites and the tile's W = WT * G right-hand sides
+// (G = blockDim.y groups of WT). First the block copies the 16 links of each of
+// its sites (8 fat, 8 long; 12-real long links rebuilt here) from global memory
+// into shared memory, thread (x, y) staging site x for hops y, y + G, ...; then
+// every (site, group) thread applies them to its WT right-hand sides. Each link
+// is read from global memory once per RHS block, whatever W is.
+// SUB = 32: a warp holds 32 consecutive sites of one group. SUB = 16 (G even):
+// a warp holds 16 sites of two groups, so each link element a warp reads from
+// shared memory serves both groups in one access (a broadcast), which halves the
+// shared-memory wavefronts of the link reads; the neighbour gathers are the same.
 constexpr int kHops = 16;
 
-template <int WT>
+template <int WT, int SUB>
 __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
   extern __shared__ float2 sU[];  // [kHops][9][blockDim.x]
   const int tile = blockIdx.x;
@@ -643,104 +707,91 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
   const int Wtile = WT * G;
   const int wbase = rb * Wtile;
   const int nw_tile = min(Wtile, L.nrhs - wbase);
-  const int w0 = wbase + threadIdx.y * WT;
-  const int nw = max(0, min(WT, L.nrhs - w0));
   const int blk = L.rb0 + rb;
   if (a.gate == GATE_ITER && !a.st->blk_active[blk]) return;
   const Geom& g = L.g;
   const int Vh = g.Vh;
   const int par = a.par, q = 1 - par;
-  const int i = sb * TX + threadIdx.x;
-  const bool valid = i < Vh;
-  // site coordinates
-  int x = 0, y = 0, z = 0, t = 0, row = 0;
-  if (valid) {
-    const int xh = i % g.Lxh;
-    int rr = i / g.Lxh;
-    y = rr % g.Ly;
-    rr /= g.Ly;
-    z = rr % g.Lz;
-    t = rr / g.Lz;
-    x = 2 * xh + ((y + z + t + par) & 1);
-    row = i - xh;
-  }
-  auto nbr = [&](int mu, int d) {  // half index of n + d mu
-    if (mu == 0) {
-      int xp = x + d;
-      if (xp >= g.Lx) xp -= g.Lx;
-      if (xp < 0) xp += g.Lx;
-      return row + (xp >> 1);
-    }
-    const int c = (mu == 1) ? y : (mu == 2) ? z : t;
-    const int Lm = (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
-    const int sm = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
-    int j = i + d * sm;
-    if (c + d >= Lm) j -= Lm * sm;
-    if (c + d < 0) j += Lm * sm;
-    return j;
-  };
-  // ---- stage the links: hop h = 4 * mu + 2 * (long) + (backward) ----
-  const bool recon = L.recon != 0;
-  const int nl = recon ? 6 : 9;
-  for (int h = threadIdx.y; h < kHops; h += G) {
-    const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
-    const int d = lng ? 3 : 1;
-    float2 u[9];
-    if (valid) {
-      const float2* base = lng ? (bwd ? L.lng32[q] : L.lng32[par]) : (bwd ? L.fat32[q] : L.fat32[par]);
-      base += (size_t)mu * (lng ? nl : 9) * Vh;
-      const int idx = bwd ? nbr(mu, -d) : i;
-      const int ne = lng ? nl : 9;
+  // ---- stage the links: thread (x, y) stages site x for hops h = y, y + G, ... ----
+  // hop h = 4 * mu + 2 * (long) + (backward)
+  {
+    const int i = sb * TX + threadIdx.x;
+    const bool valid = i < Vh;
+    const SiteXY c = valid ? site_of(g, i, par) : SiteXY{0, 0, 0, 0, 0};
+    const bool recon = L.recon != 0;
+    const int nl = recon ? 6 : 9;
+    for (int h = threadIdx.y; h < kHops; h += G) {
+      const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
+      const int d = lng ? 3 : 1;
+      float2 u[9];
+      if (valid) {
+        const float2* base = lng ? (bwd ? L.lng32[q] : L.lng32[par]) : (bwd ? L.fat32[q] : L.fat32[par]);
+        base += (size_t)mu * (lng ? nl : 9) * Vh;
+        const int idx = bwd ? nbr_of(g, i, c, mu, -d) : i;
+        const int ne = lng ? nl : 9;
 #pragma unroll
-      for (int e = 0; e < 9; ++e)
-        if (e < ne) u[e] = __ldg(base + (size_t)e * Vh + idx);
-      if (lng && recon) {  // third row = conj(row0 x row1) / s, s = s0 * eta_mu * boundary sign
-        int ep = 0;
-        if (mu == 1) ep = x;
-        if (mu == 2) ep = x + y;
-        if (mu == 3) ep = x + y + z;
-        float inv_s = (ep & 1) ? -L.inv_s0_f : L.inv_s0_f;
-        if (mu == 3 && g.apbc && (bwd ? (t < 3) : (t + 3 >= g.Lt))) inv_s = -inv_s;
+        for (int e = 0; e < 9; ++e)
+          if (e < ne) u[e] = __ldg(base + (size_t)e * Vh + idx);
+        if (lng && recon) {  // third row = conj(row0 x row1) / s, s = s0 * eta_mu * boundary sign
+          int ep = 0;
+          if (mu == 1) ep = c.x;
+          if (mu == 2) ep = c.x + c.y;
+          if (mu == 3) ep = c.x + c.y + c.z;
+          float inv_s = (ep & 1) ? -L.inv_s0_f : L.inv_s0_f;
+          if (mu == 3 && g.apbc && (bwd ? (c.t < 3) : (c.t + 3 >= g.Lt))) inv_s = -inv_s;
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const int kk = (jj + 1) % 3, ll = (jj + 2) % 3;
-          const float2 ak = u[kk], al = u[ll], bk = u[3 + kk], bl = u[3 + ll];
-          const float re = ak.x * bl.x - ak.y * bl.y - (al.x * bk.x - al.y * bk.y);
-          const float im = ak.x * bl.y + ak.y * bl.x - (al.x * bk.y + al.y * bk.x);
-          u[6 + jj] = make_float2(re * inv_s, -im * inv_s);
+          for (int jj = 0; jj < 3; ++jj) {
+            const int kk = (jj + 1) % 3, ll = (jj + 2) % 3;
+            const float2 ak = u[kk], al = u[ll], bk = u[3 + kk], bl = u[3 + ll];
+            const float re = ak.x * bl.x - ak.y * bl.y - (al.x * bk.x - al.y * bk.y);
+            const float im = ak.x * bl.y + ak.y * bl.x - (al.x * bk.y + al.y * bk.x);
+            u[6 + jj] = make_float2(re * inv_s, -im * inv_s);
+          }
         }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) u[e] = make_float2(0.f, 0.f);
       }
-    } else {
 #pragma unroll
-      for (int e = 0; e < 9; ++e) u[e] = make_float2(0.f, 0.f);
+      for (int e = 0; e < 9; ++e) sU[(h * 9 + e) * TX + threadIdx.x] = u[e];
     }
-#pragma unroll
-    for (int e = 0; e < 9; ++e) sU[(h * 9 + e) * TX + threadIdx.x] = u[e];
   }
   __syncthreads();
-  // ---- apply to this thread's right-hand sides ----
+  // ---- apply to this thread's right-hand sides: thread (site ax, group ay) ----
+  int ax = threadIdx.x, ay = threadIdx.y;
+  if constexpr (SUB == 16) {
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5, cpr = TX / 16;
+    ax = (warp % cpr) * 16 + (lane & 15);
+    ay = (warp / cpr) * 2 + (lane >> 4);
+  }
+  const int w0 = wbase + ay * WT;
+  const int nw = max(0, min(WT, L.nrhs - w0));
+  const int i = sb * TX + ax;
+  const bool valid = i < Vh;
   double part[WT];
 #pragma unroll
   for (int w = 0; w < WT; ++w) part[w] = 0.0;
   const float2* in = (a.in_vec == V_P ? (const float2*)L.p : (const float2*)L.tmp);
   if (valid && nw > 0) {
+    const SiteXY c = site_of(g, i, par);
     float2 acc[WT][3];
 #pragma unroll
     for (int w = 0; w < WT; ++w)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[w][c] = make_float2(0.f, 0.f);
+      for (int cc = 0; cc < 3; ++cc) acc[w][cc] = make_float2(0.f, 0.f);
     // one-hop software pipeline: the next hop's neighbour vectors are in flight while
     // this hop's products run (the gathers, not the FMAs, set the pace of this kernel)
     float2 vin[WT][3], vnx[WT][3];
     auto gather = [&](int h, float2 (&v)[WT][3]) {
       const int mu = h >> 2, lng = (h >> 1) & 1, bwd = h & 1;
-      const int j = nbr(mu, bwd ? (lng ? -3 : -1) : (lng ? 3 : 1));
+      const int j = nbr_of(g, i, c, mu, bwd ? (lng ? -3 : -1) : (lng ? 3 : 1));
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int cc = 0; cc < 3; ++cc) {
         float2 t[WT];
-        pv_load<WT>(in, w0, nw, c, j, Vh, t);  // one 16-byte gather per RHS pair
+        pv_load<WT>(in, w0, nw, cc, j, Vh, t);  // one 16-byte gather per RHS pair
 #pragma unroll
-        for (int w = 0; w < WT; ++w) v[w][c] = t[w];
+        for (int w = 0; w < WT; ++w) v[w][cc] = t[w];
       }
     };
     gather(0, vin);
@@ -750,41 +801,41 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
       const bool bwd = h & 1;
       float2 U[9];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) U[e] = sU[(h * 9 + e) * TX + threadIdx.x];
+      for (int e = 0; e < 9; ++e) U[e] = sU[(h * 9 + e) * TX + ax];
 #pragma unroll
       for (int w = 0; w < WT; ++w)
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
             const float2 v = vin[w][b];
             if (!bwd) {
-              const float2 u = U[a * 3 + b];
-              acc[w][a].x = fmaf(u.x, v.x, acc[w][a].x);
-              acc[w][a].x = fmaf(-u.y, v.y, acc[w][a].x);
-              acc[w][a].y = fmaf(u.x, v.y, acc[w][a].y);
-              acc[w][a].y = fmaf(u.y, v.x, acc[w][a].y);
+              const float2 u = U[aa * 3 + b];
+              acc[w][aa].x = fmaf(u.x, v.x, acc[w][aa].x);
+              acc[w][aa].x = fmaf(-u.y, v.y, acc[w][aa].x);
+              acc[w][aa].y = fmaf(u.x, v.y, acc[w][aa].y);
+              acc[w][aa].y = fmaf(u.y, v.x, acc[w][aa].y);
             } else {
-              const float2 u = U[b * 3 + a];
-              acc[w][a].x = fmaf(-u.x, v.x, acc[w][a].x);
-              acc[w][a].x = fmaf(-u.y, v.y, acc[w][a].x);
-              acc[w][a].y = fmaf(-u.x, v.y, acc[w][a].y);
-              acc[w][a].y = fmaf(u.y, v.x, acc[w][a].y);
+              const float2 u = U[b * 3 + aa];
+              acc[w][aa].x = fmaf(-u.x, v.x, acc[w][aa].x);
+              acc[w][aa].x = fmaf(-u.y, v.y, acc[w][aa].x);
+              acc[w][aa].y = fmaf(-u.x, v.y, acc[w][aa].y);
+              acc[w][aa].y = fmaf(u.y, v.x, acc[w][aa].y);
             }
           }
       if (h + 1 < kHops)
 #pragma unroll
         for (int w = 0; w < WT; ++w)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) vin[w][c] = vnx[w][c];
+          for (int cc = 0; cc < 3; ++cc) vin[w][cc] = vnx[w][cc];
     }
     if (a.epi == M_PLAIN) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int cc = 0; cc < 3; ++cc) {
         float2 t[WT];
 #pragma unroll
-        for (int w = 0; w < WT; ++w) t[w] = acc[w][c];
-        pv_store<WT>(L.tmp, w0, nw, c, i, Vh, t);
+        for (int w = 0; w < WT; ++w) t[w] = acc[w][cc];
+        pv_store<WT>(L.tmp, w0, nw, cc, i, Vh, t);
       }
     } else {  // M_NORMAL_DOT: Ap = sigma p - D tmp, <p, Ap>
       float sig[WT], dot[WT];
@@ -794,15 +845,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
         dot[w] = 0.f;
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int cc = 0; cc < 3; ++cc) {
         float2 yc[WT], v[WT];
-        pv_load<WT>(L.p, w0, nw, c, i, Vh, yc);
+        pv_load<WT>(L.p, w0, nw, cc, i, Vh, yc);
 #pragma unroll
         for (int w = 0; w < WT; ++w) {
-          v[w] = make_float2(sig[w] * yc[w].x - acc[w][c].x, sig[w] * yc[w].y - acc[w][c].y);
+          v[w] = make_float2(sig[w] * yc[w].x - acc[w][cc].x, sig[w] * yc[w].y - acc[w][cc].y);
           dot[w] = fmaf(yc[w].x, v[w].x, fmaf(yc[w].y, v[w].y, dot[w]));
         }
-        pv_store<WT>(L.Ap, w0, nw, c, i, Vh, v);
+        pv_store<WT>(L.Ap, w0, nw, cc, i, Vh, v);
       }
 #pragma unroll
       for (int w = 0; w < WT; ++w)
@@ -810,7 +861,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash_smem(MArgs a) {
     }
   }
   if (a.epi != M_PLAIN)
-    rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
+    rhs_block_partial_m<WT, SUB>(part, L, wbase, nw_tile, sb, ax, ay, a.partials, a.max_nsb);
 }
 
 // ---------------------------------------------------------------------------
@@ -995,6 +1046,7 @@ struct BatchPlan {
   int W, T;              // tuned RHS block width and site block (threads along x)
   int carve;             // tuned shared-memory carveout of the FP32 Dslash (percent; -1 = driver default)
   int WT;                // RHS per thread in the FP32 Dslash (W / WT thread groups per site block)
+  int sub;               // sites per warp row of the FP32 Dslash: 32, or 16 (two RHS groups per warp)
   int ntiles, ntiles64;  // FP32 / FP64 tiles over all lattices
   int ntiles_b;          // BLAS tiles over all lattices
   int nblk;              // FP32 RHS blocks over all lattices
@@ -1015,8 +1067,18 @@ extern unsigned long long sqcg_links_generation(const sqcg_ctx* ctx);
 namespace {
 
 struct TuneChoice {
-  int W, WT, T, carve;
+  int W, WT, T, carve, sub;
 };
+
+// shape rules of the FP32 Dslash: T a multiple of 32 up to kMaxTSmem, T * W / WT threads at most
+// kMaxThreads, SUB = 16 only with an even number of RHS groups
+bool smem_shape_ok(int W, int WT, int T, int sub) {
+  if (WT < 1 || W % WT) return false;
+  const int G = W / WT;
+  if (T < 32 || T % 32 || T > kMaxTSmem || T * G > kMaxThreads) return false;
+  return sub == 32 || (sub == 16 && G % 2 == 0);
+}
+
 
 // Guards the process-wide tuning state (the cache and file, and the per-kernel shared-memory
 // attributes) when several host threads run batched solves on their own contexts.
@@ -1026,7 +1088,7 @@ std::recursive_mutex& tune_mutex() {
 }
 
 TuneChoice& tune_pin() {  // W = 0: autotune
-  static TuneChoice c = {0, 0, 0, -1};
+  static TuneChoice c = {0, 0, 0, -1, 32};
   return c;
 }
 
@@ -1046,9 +1108,10 @@ void tune_file_load() {
   if (!f) return;
   char line[768], key[512];
   while (fgets(line, sizeof(line), f)) {
-    int W, WT, T, carve = -1;
-    const int got = sscanf(line, "%511s %d %d %d %d", key, &W, &WT, &T, &carve);
-    if (got >= 4) tune_cache()[key] = {W, WT, T, got == 5 ? carve : -1};
+    int W, WT, T, carve = -1, sub = 32;
+    const int got = sscanf(line, "%511s %d %d %d %d %d", key, &W, &WT, &T, &carve, &sub);
+    if (got >= 4 && smem_shape_ok(W, WT, T, got == 6 ? sub : 32))
+      tune_cache()[key] = {W, WT, T, got >= 5 ? carve : -1, got == 6 ? sub : 32};
   }
   fclose(f);
 }
@@ -1058,7 +1121,7 @@ void tune_file_store(const std::string& key, const TuneChoice& c) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.W, c.WT, c.T, c.carve);
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.W, c.WT, c.T, c.carve, c.sub);
   fclose(f);
 }
 
@@ -1145,46 +1208,50 @@ int launch_finish_b(const BatchPlan& P, int fin, int blas, cudaStream_t s) {
   return SQCG_OK;
 }
 
+// The FP32 Dslash instantiations: (WT, SUB) for WT in {1, 2, 4} and SUB in {32, 16}.
+typedef void (*SmemKernel)(MArgs);
+int smem_index(int WT, int sub) {
+  const int k = WT == 1 ? 0 : WT == 2 ? 1 : WT == 4 ? 2 : -1;
+  if (k < 0 || (sub != 32 && sub != 16)) return -1;
+  return 2 * k + (sub == 16 ? 1 : 0);
+}
+SmemKernel smem_kernel(int idx) {
+  static const SmemKernel fns[6] = {k_mrhs_dslash_smem<1, 32>, k_mrhs_dslash_smem<1, 16>,
+                                    k_mrhs_dslash_smem<2, 32>, k_mrhs_dslash_smem<2, 16>,
+                                    k_mrhs_dslash_smem<4, 32>, k_mrhs_dslash_smem<4, 16>};
+  return fns[idx];
+}
+
 // The shared-memory carveout of each FP32 Dslash instantiation: a smaller carveout leaves
 // more of the SM's 256 KB to L1, which serves the neighbour gathers, at fewer resident blocks.
 // Set outside graph capture (by the tuner, before the plan's graph is captured).
-int set_carve(int WT, int carve) {
+int set_carve(int WT, int sub, int carve) {
   std::lock_guard<std::recursive_mutex> lock(tune_mutex());
-  static int cur[3] = {-2, -2, -2};
-  const int k = WT == 1 ? 0 : WT == 2 ? 1 : WT == 4 ? 2 : -1;
+  static int cur[6] = {-2, -2, -2, -2, -2, -2};
+  const int k = smem_index(WT, sub);
   if (k < 0) return SQCG_ERR_INVALID_ARG;
   if (cur[k] == carve) return SQCG_OK;
-  const void* fn = k == 0 ? (const void*)k_mrhs_dslash_smem<1> : k == 1 ? (const void*)k_mrhs_dslash_smem<2>
-                                                                          : (const void*)k_mrhs_dslash_smem<4>;
-  SQCG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  SQCG_CUDA_TRY(cudaFuncSetAttribute((const void*)smem_kernel(k), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     carve));
   cur[k] = carve;
   return SQCG_OK;
 }
 
 int launch_f32(const BatchPlan& P, int par, int in_vec, int epi, int gate, cudaStream_t s) {
   const int G = P.W / P.WT, T = P.T;
-  if (T * G > kMaxThreads || T % 32) return SQCG_ERR_INVALID_ARG;
+  if (!smem_shape_ok(P.W, P.WT, T, P.sub)) return SQCG_ERR_INVALID_ARG;
   const size_t smem = (size_t)kHops * 9 * T * sizeof(float2);
   std::lock_guard<std::recursive_mutex> lock(tune_mutex());
-  static bool attr_set[3] = {false, false, false};  // per WT instantiation
-  const MArgs a = margs(P, par, in_vec, epi, gate, 0);
-  const dim3 block(T, G);
-  switch (P.WT) {
-    case 1:
-      if (!attr_set[0]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[0] = true; }
-      k_mrhs_dslash_smem<1><<<P.ntiles, block, smem, s>>>(a);
-      break;
-    case 2:
-      if (!attr_set[1]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[1] = true; }
-      k_mrhs_dslash_smem<2><<<P.ntiles, block, smem, s>>>(a);
-      break;
-    case 4:
-      if (!attr_set[2]) { SQCG_CUDA_TRY(cudaFuncSetAttribute(k_mrhs_dslash_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHops * 9 * kMaxTSmem * (int)sizeof(float2))); attr_set[2] = true; }
-      k_mrhs_dslash_smem<4><<<P.ntiles, block, smem, s>>>(a);
-      break;
-    default:
-      return SQCG_ERR_INVALID_ARG;
+  static bool attr_set[6] = {false, false, false, false, false, false};  // per instantiation
+  const int k = smem_index(P.WT, P.sub);
+  if (k < 0) return SQCG_ERR_INVALID_ARG;
+  if (!attr_set[k]) {
+    SQCG_CUDA_TRY(cudaFuncSetAttribute((const void*)smem_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kHops * 9 * kMaxTSmem * (int)sizeof(float2)));
+    attr_set[k] = true;
   }
+  const MArgs a = margs(P, par, in_vec, epi, gate, 0);
+  smem_kernel(k)<<<P.ntiles, dim3(T, G), smem, s>>>(a);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }
@@ -1238,29 +1305,32 @@ int autotune(BatchPlan& P, cudaStream_t s) {
     const TuneChoice& c = tune_pin();
     layout_tiles(P, c.W, c.WT, c.T);
     P.carve = c.carve;
-    SQCG_TRY(set_carve(P.WT, P.carve));
+    P.sub = c.sub;
+    SQCG_TRY(set_carve(P.WT, P.sub, P.carve));
     return upload_lats(P, s);
   }
   if (it != tune_cache().end()) {
     layout_tiles(P, it->second.W, it->second.WT, it->second.T);
     P.carve = it->second.carve;
-    SQCG_TRY(set_carve(P.WT, P.carve));
+    P.sub = it->second.sub;
+    SQCG_TRY(set_carve(P.WT, P.sub, P.carve));
     return upload_lats(P, s);
   }
   cudaEvent_t e0, e1;
   SQCG_CUDA_TRY(cudaEventCreate(&e0));
   SQCG_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  TuneChoice bestc = {1, 1, 128, -1};
+  TuneChoice bestc = {1, 1, 128, -1, 32};
   const int Ws[] = {1, 2, 4, 8, 16};
   const int WTs[] = {1, 2, 4};
   const int Ts[] = {32, 64, 128, 256};
   int rc = SQCG_OK;
   // time one configuration (5 launches after 2 warm-up launches); keep it if fastest
-  auto trial = [&](int W, int WT, int T, int carve) {
+  auto trial = [&](int W, int WT, int T, int carve, int sub) {
     layout_tiles(P, W, WT, T);
     P.carve = carve;
-    if ((rc = set_carve(WT, carve)) != SQCG_OK) return;
+    P.sub = sub;
+    if ((rc = set_carve(WT, sub, carve)) != SQCG_OK) return;
     if ((rc = upload_lats(P, s)) != SQCG_OK) return;
     for (int rep = 0; rep < 2 && rc == SQCG_OK; ++rep) rc = launch_f32(P, 1, V_P, M_PLAIN, GATE_NONE, s);
     if (rc != SQCG_OK) return;
@@ -1272,8 +1342,9 @@ int autotune(BatchPlan& P, cudaStream_t s) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (getenv("SQCG_TUNE_VERBOSE"))
-      fprintf(stderr, "sqcg tune %s W=%d WT=%d T=%d carve=%d %.4f ms\n", key.c_str(), W, WT, T, carve, ms / 5);
-    if (ms < best) { best = ms; bestc = {W, WT, T, carve}; }
+      fprintf(stderr, "sqcg tune %s W=%d WT=%d T=%d carve=%d sub=%d %.4f ms\n", key.c_str(), W, WT, T, carve, sub,
+              ms / 5);
+    if (ms < best) { best = ms; bestc = {W, WT, T, carve, sub}; }
   };
   // 1: block shapes at the driver's default carveout
   for (int W : Ws) {
@@ -1283,7 +1354,11 @@ int autotune(BatchPlan& P, cudaStream_t s) {
       const int G = W / WT;
       for (int T : Ts) {
         if (T * G > kMaxThreads || T > kMaxTSmem) break;
-        trial(W, WT, T, -1);
+        for (int sub : {32, 16}) {
+          if (!smem_shape_ok(W, WT, T, sub)) continue;
+          trial(W, WT, T, -1, sub);
+          if (rc != SQCG_OK) break;
+        }
         if (rc != SQCG_OK) break;
       }
       if (rc != SQCG_OK) break;
@@ -1292,12 +1367,12 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   }
   // 2: the best W and WT again with smaller shared-memory carveouts (more L1 for the gathers)
   if (rc == SQCG_OK) {
-    const int W = bestc.W, WT = bestc.WT, G = W / WT;
+    const int W = bestc.W, WT = bestc.WT, G = W / WT, sub = bestc.sub;
     const int carves[] = {25, 50, 75};
     for (int T : Ts) {
       if (T * G > kMaxThreads || T > kMaxTSmem) break;
       for (int cv : carves) {
-        trial(W, WT, T, cv);
+        trial(W, WT, T, cv, sub);
         if (rc != SQCG_OK) break;
       }
       if (rc != SQCG_OK) break;
@@ -1310,7 +1385,8 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   tune_file_store(key, bestc);
   layout_tiles(P, bestc.W, bestc.WT, bestc.T);
   P.carve = bestc.carve;
-  SQCG_TRY(set_carve(P.WT, P.carve));
+  P.sub = bestc.sub;
+  SQCG_TRY(set_carve(P.WT, P.sub, P.carve));
   return upload_lats(P, s);
 }
 
@@ -1685,26 +1761,28 @@ extern "C" int sqcg_batched_tuning(const sqcg_ctx* ctx, int* W, int* T) {
   return SQCG_OK;
 }
 
-extern "C" int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve) {
+extern "C" int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* carve, int* warp_sites) {
   if (!ctx || !ctx->batch) return SQCG_ERR_INVALID_ARG;
   const BatchPlan& P = *ctx->batch;
   if (W) *W = P.W;
   if (WT) *WT = P.WT;
   if (T) *T = P.T;
   if (carve) *carve = P.carve;
+  if (warp_sites) *warp_sites = P.sub;
   return SQCG_OK;
 }
 
-extern "C" int sqcg_batched_pin_tuning(int W, int WT, int T, int carve) {
+extern "C" int sqcg_batched_pin_tuning(int W, int WT, int T, int carve, int warp_sites) {
   std::lock_guard<std::recursive_mutex> lock(tune_mutex());
   if (W == 0) {
-    tune_pin() = {0, 0, 0, -1};
+    tune_pin() = {0, 0, 0, -1, 32};
     return SQCG_OK;
   }
+  if (warp_sites == 0) warp_sites = 32;
   if ((W != 1 && W != 2 && W != 4 && W != 8 && W != 16) || (WT != 1 && WT != 2 && WT != 4) || WT > W)
     return SQCG_ERR_INVALID_ARG;
-  if (T < 32 || T > kMaxTSmem || T % 32 || T * (W / WT) > kMaxThreads) return SQCG_ERR_INVALID_ARG;
+  if (!smem_shape_ok(W, WT, T, warp_sites)) return SQCG_ERR_INVALID_ARG;
   if (carve < -1 || carve > 100) return SQCG_ERR_INVALID_ARG;
-  tune_pin() = {W, WT, T, carve};
+  tune_pin() = {W, WT, T, carve, warp_sites};
   return SQCG_OK;
 }

@@ -80,13 +80,14 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
 }
 
 // Single-reduction CG update, one pass over five FP32 vectors (s = A r, written by the Dslash epilogue):
-//   p = r + beta p,  q = s + beta q  (= A p),  xh += alpha p,  r -= alpha q.
-// xh is the FP32 partial solution, flushed into the FP64 x at every reliable update. Thread 0 of block 0
-// also runs the control step of the captured WHILE loop (count, hard bound, condition), so no separate
-// loop-control kernel follows it.
+//   p = r + beta p,  q = s + beta q  (= A p),  xh += alpha p,  r -= alpha q,
+// and the block partials of Re<r_new, q_new>, the next step's cross term (the next Dslash epilogue then
+// reads only r). xh is the FP32 partial solution, flushed into the FP64 x at every reliable update.
+// Thread 0 of block 0 also runs the control step of the captured WHILE loop (count, hard bound,
+// condition), so no separate loop-control kernel follows it.
 __global__ void __launch_bounds__(kThreads)
 k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __restrict__ p, float2* __restrict__ q,
-            float2* __restrict__ xh, int Vh, SolverState* st) {
+            float2* __restrict__ xh, int Vh, SolverState* st, double* cpart) {
   const volatile SolverState* vs = st;
   if (blockIdx.x == 0 && threadIdx.x == 0 && st->h_while) {
     // the loop continues while the solve is not done and the hard bound is not reached; on the bound,
@@ -97,8 +98,9 @@ k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __res
     if (!go && !vs->done) st->status = SQCG_ERR_NOT_CONVERGED;
     cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, go ? 1u : 0u);
   }
-  if (vs->done) return;
+  if (vs->done) return;  // uniform over the grid
   const float alpha = (float)st->alpha, beta = (float)st->beta;
+  double cross = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     float2 rc[3], sc[3], pc[3], qc[3], xc[3];
 #pragma unroll
@@ -126,7 +128,12 @@ k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __res
       xh[k] = xc[c];
       r[k] = rc[c];
     }
+    float rq = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rq = fmaf(rc[c].x, qc[c].x, fmaf(rc[c].y, qc[c].y, rq));
+    cross += (double)rq;
   }
+  block_partial(cross, cpart);
 }
 
 // x += xh (the FP32 partial solution, added in FP64), xh = 0
@@ -268,10 +275,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
   finish_partials2(st, partials, n, fin);
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish3(SolverState* st, const double* partials, int n, int fin,
-                                                            int gate) {
+__global__ void __launch_bounds__(kFinishThreads) k_finish_sr(SolverState* st, const double* partials, int n,
+                                                              int coff, int cn, int gate) {
   if (!gate_open(st, gate)) return;
-  finish_partials3(st, partials, n, fin);
+  finish_partials_sr(st, partials, n, coff, cn);
 }
 
 // One thread: count the WHILE-loop iterations and set its condition. The loop
@@ -321,8 +328,8 @@ int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s
   return SQCG_OK;
 }
 
-int launch_finish3(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
-  k_finish3<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
+int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s) {
+  k_finish_sr<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, coff, cn, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }
@@ -357,7 +364,9 @@ int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
 
 int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
-  k_sr_update<<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, ctx->p32, ctx->q32, ctx->xh32, Vh, ctx->st);
+  if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
+  k_sr_update<<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, ctx->p32, ctx->q32, ctx->xh32, Vh, ctx->st,
+                                        ctx->partials + sr_update_partials(ctx));
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

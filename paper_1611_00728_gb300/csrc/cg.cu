@@ -113,15 +113,17 @@ int enqueue_cg_reliable(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaSt
 }
 
 // Single-reduction mixed CG, head of one iteration: tmp = D_oe r; s = sigma r - D_eo tmp (into Ap32)
-// with the four sums of the step (see EPI_SR_DOTS) from one reduction; the finisher decides on
-// convergence and the reliable update and, without one, computes alpha and beta.
-int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s) {
+// with <r, s> and |r|^2 from its epilogue and <r, q> from the previous update kernel (or, right after a
+// reliable update replaced r, from this epilogue: after_update); the finisher decides on convergence
+// and the reliable update and, without one, computes alpha and beta.
+int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s, bool after_update = false) {
   DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->r32; L.out = ctx->tmp32;
   L.gate = GATE_ITER;
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
-  L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_SR_DOTS; L.in = ctx->tmp32; L.out = ctx->Ap32;
+  L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = after_update ? EPI_SR_DOTS : EPI_SR_DOTS2;
+  L.in = ctx->tmp32; L.out = ctx->Ap32;
   L.y = ctx->r32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
   L.fin = FIN_SR_STEP;
   return launch_dslash(ctx, L, s);
@@ -141,7 +143,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
     F.out_parity = 0; F.true_resid = 1; F.in = ctx->tmp64; F.out32 = ctx->r32; F.x = x; F.b = b;
     F.sigma_dev = &ctx->st->sigma; F.gate = GATE_UPDATE; F.fin = FIN_TRUE_RESID;
     SQCG_TRY(launch_dslash_ff(ctx, F, s));
-    return enqueue_sr_head(ctx, s);
+    return enqueue_sr_head(ctx, s, true);
   }
   SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_UPDATE, s));
   DslashLaunch L = {};
@@ -153,7 +155,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
   L.in = ctx->tmp64; L.out = ctx->r32; L.y = x; L.b = b; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_UPDATE;
   L.fin = FIN_TRUE_RESID;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  return enqueue_sr_head(ctx, s);  // gated on the loop going on (GATE_ITER)
+  return enqueue_sr_head(ctx, s, true);  // gated on the loop going on (GATE_ITER)
 }
 
 int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
@@ -425,11 +427,13 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
   if (!h->done) {
     void* xs[1] = {x};
     const int kind = mixed ? KIND_SR : KIND_CG;
-    if (mixed) {  // p, q and the FP32 partial solution start at zero
+    if (mixed) {  // p, q, the FP32 partial solution and the first step's <r, q> partials start at zero
       const size_t wb = (size_t)ctx->g.Vh * 3 * sizeof(float2);
       SQCG_CUDA_TRY(cudaMemsetAsync(ctx->p32, 0, wb, s));
       SQCG_CUDA_TRY(cudaMemsetAsync(ctx->q32, 0, wb, s));
       SQCG_CUDA_TRY(cudaMemsetAsync(ctx->xh32, 0, wb, s));
+      SQCG_CUDA_TRY(cudaMemsetAsync(ctx->partials + sr_update_partials(ctx), 0,
+                                    (size_t)ctx->max_blocks * sizeof(double), s));
     }
     if (eager_mode()) {
       SQCG_TRY(run_eager(ctx, kind, mixed, b, xs, 1, max_iter, s, &loops));

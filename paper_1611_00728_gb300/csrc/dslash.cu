@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
       }
       part = (double)dot;
-    } else if constexpr (EPI == EPI_SR_DOTS) {  // s = sigma r - D in; <r,s>, <r,q>, |r|^2
+    } else if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_SR_DOTS2) {  // s = sigma r - D in; <r,s>, [<r,q>], |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
       const R2* qv = static_cast<const R2*>(a.y3);
@@ -231,12 +231,15 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t k = (size_t)c * Vh + i;
-        const R2 rc = ldg2(rv + k), qc = ldg2(qv + k);
+        const R2 rc = ldg2(rv + k);
         O2 o = mk<O2>((RO)(sig * rc.x - acc[c].x), (RO)(sig * rc.y - acc[c].y));
         out[k] = o;
         rs = fma(rc.x, o.x, fma(rc.y, o.y, rs));
-        rq = fma(rc.x, qc.x, fma(rc.y, qc.y, rq));
         rr = fma(rc.x, rc.x, fma(rc.y, rc.y, rr));
+        if constexpr (EPI == EPI_SR_DOTS) {
+          const R2 qc = ldg2(qv + k);
+          rq = fma(rc.x, qc.x, fma(rc.y, qc.y, rq));
+        }
       }
       part = (double)rs;
       part2 = (double)rq;
@@ -265,6 +268,15 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
   }
   if constexpr (EPI == EPI_SR_DOTS) {
     if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
+  } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
+    if (a.fin != FIN_NONE) {
+      double unused = 0.0;
+      block_sum3(part, unused, part3);
+      if (threadIdx.x == 0) {
+        a.partials[blockIdx.x] = part;
+        a.partials[2 * gridDim.x + blockIdx.x] = part3;
+      }
+    }
   }
   (void)part2; (void)part3;
 }
@@ -303,8 +315,8 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
     return SQCG_ERR_INVALID_ARG;
   const int grid = grid_for(ctx->g.Vh, kThreads);
-  const bool reduces = (L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_TRUE_RESID) &&
-                       L.fin != FIN_NONE;
+  const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2;
+  const bool reduces = (L.epi == EPI_NORMAL_DOT || sr || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE;
   if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 3 * max_blocks
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
@@ -312,12 +324,14 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     case EPI_NORMAL_DOT: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL_DOT><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_SR_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_SR_DOTS2: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS2><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_SR_DOTS ? launch_finish3(ctx, grid, L.fin, L.gate, s)
-                                : launch_finish(ctx, grid, L.fin, L.gate, s);
+    return L.epi == EPI_SR_DOTS    ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
+           : L.epi == EPI_SR_DOTS2 ? launch_finish_sr(ctx, grid, sr_update_partials(ctx), blas_grid(ctx), L.gate, s)
+                                   : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
 }
 
@@ -341,7 +355,8 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
-  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS) && !L.y) return SQCG_ERR_INVALID_ARG;
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2) && !L.y)
+    return SQCG_ERR_INVALID_ARG;
   if (L.epi == EPI_SR_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);

@@ -312,16 +312,18 @@ __device__ __forceinline__ void block_partial3(double a, double b, double c, dou
   }
 }
 
-__device__ __forceinline__ void finish_partials3(SolverState* st, const double* partials, int n, int fin) {
+// the single-reduction step: d = sum partials[0, n), c = sum partials[coff, coff + cn), g = sum partials[2n, 3n)
+__device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff,
+                                                   int cn) {
   double a = 0.0, b = 0.0, c = 0.0;
 #pragma unroll 4
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     a += partials[j];
-    b += partials[n + j];
     c += partials[2 * n + j];
   }
+  for (int j = threadIdx.x; j < cn; j += blockDim.x) b += partials[coff + j];
   block_sum3(a, b, c);
-  if (threadIdx.x == 0 && fin == FIN_SR_STEP) sr_step(st, a, b, c);
+  if (threadIdx.x == 0) sr_step(st, a, b, c);
 }
 
 __device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {

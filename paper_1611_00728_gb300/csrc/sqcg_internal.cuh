@@ -184,7 +184,7 @@ struct sqcg_ctx {
   float2 *r32, *p32, *Ap32, *tmp32;
   float2 *q32, *xh32;  // single-reduction mixed CG: q = A p, and the FP32 partial solution
   float4* xff;         // float-float copy of x for the reliable update (its odd intermediate lives in tmp64)
-  double* partials;    // three sums' worth: 3 * max_blocks
+  double* partials;    // 4 * max_blocks: three sums of a Dslash epilogue, then the update kernel's sum
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   SolverState* st;       // device
@@ -221,7 +221,8 @@ enum DslashEpi {
   EPI_NORMAL_DOT = 2,     // out = sigma*y - D in, reduce Re<y, out>
   EPI_TRUE_RESID = 3,     // out = b - sigma*y + D in (b, y FP64), reduce |out|^2
   EPI_SR_DOTS = 4,        // single-reduction CG: s = sigma*r - D in (r = y, q = y3 on the output parity);
-                          // three sums Re<r,s>, Re<r,q>, |r|^2
+                          // three sums Re<r,s>, Re<r,q>, |r|^2 (after a reliable update)
+  EPI_SR_DOTS2 = 5,       // the same without q: sums Re<r,s> and |r|^2; Re<r,q> comes from the update kernel
 };
 
 struct DslashLaunch {
@@ -249,7 +250,11 @@ int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 int blas_grid(sqcg_ctx* ctx);
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
-int launch_finish3(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
+// the single-reduction step's finisher: sums <r,s> = partials[0, n), <r,q> = partials[coff, coff + cn),
+// |r|^2 = partials[2n, 3n)
+int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s);
+// offset of the update kernel's partials of <r_new, q> in ctx->partials
+inline int sr_update_partials(const sqcg_ctx* ctx) { return 3 * ctx->max_blocks; }
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 // single-reduction mixed CG: p = r + beta p, q = s + beta q, xh += alpha p, r -= alpha q (s in Ap32), with
 // the WHILE-loop control of the captured loop in one thread

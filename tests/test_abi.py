@@ -116,15 +116,16 @@ def test_batched_pin_tuning_checks(libpath):
     """The pinned batched Dslash configuration is validated on the host (no CUDA call)."""
     lib = ctypes.CDLL(libpath)
     pin = lib.sqcg_batched_pin_tuning
-    pin.argtypes = [ctypes.c_int] * 4
-    bad = [(3, 1, 64, -1), (4, 8, 64, -1), (2, 4, 64, -1), (4, 3, 64, -1),  # W, WT
-           (4, 1, 48, -1), (4, 1, 256, -1), (16, 1, 64, -1),  # T: multiple of 32, <= 128, T * W / WT <= 512
-           (4, 1, 64, 101), (4, 1, 64, -2)]  # carveout
+    pin.argtypes = [ctypes.c_int] * 5
+    bad = [(3, 1, 64, -1, 32), (4, 8, 64, -1, 32), (2, 4, 64, -1, 32), (4, 3, 64, -1, 32),  # W, WT
+           (4, 1, 48, -1, 32), (4, 1, 256, -1, 32), (16, 1, 64, -1, 32),  # T: multiple of 32, <= 128, T W/WT <= 512
+           (4, 1, 64, 101, 32), (4, 1, 64, -2, 32),  # carveout
+           (4, 4, 64, -1, 16), (8, 2, 32, -1, 8), (2, 1, 32, -1, 24)]  # warp_sites: 16 needs W / WT even
     for args in bad:
         assert pin(*args) == -1, args
-    for args in [(1, 1, 32, -1), (16, 4, 128, 50), (8, 4, 128, -1), (16, 2, 64, 25)]:
+    for args in [(1, 1, 32, -1, 32), (16, 4, 128, 50, 0), (8, 4, 128, -1, 16), (16, 2, 64, 25, 16), (2, 1, 32, -1, 16)]:
         assert pin(*args) == 0, args
-    assert pin(0, 0, 0, 0) == 0  # back to autotuning
+    assert pin(0, 0, 0, 0, 0) == 0  # back to autotuning
 
 
 def test_binding_pin_batched_tuning(libpath):

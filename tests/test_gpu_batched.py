@@ -150,12 +150,19 @@ def test_batched_from_two_host_threads(sqcg, links_cache):
         assert all(st == 0 and res <= 1e-9 for st, res in results[k]), results[k]
 
 
-@pytest.mark.parametrize("cfg", [dict(W=4, WT=1, T=64, carve=-1), dict(W=8, WT=2, T=128, carve=-1),
-                                 dict(W=16, WT=4, T=64, carve=50), dict(W=2, WT=2, T=32, carve=25),
-                                 dict(W=4, WT=4, T=32, carve=-1)])
+@pytest.mark.parametrize("cfg", [dict(W=4, WT=1, T=64, carve=-1, warp_sites=32),
+                                 dict(W=4, WT=1, T=32, carve=-1, warp_sites=16),
+                                 dict(W=8, WT=2, T=128, carve=-1, warp_sites=32),
+                                 dict(W=8, WT=2, T=64, carve=-1, warp_sites=16),
+                                 dict(W=16, WT=2, T=32, carve=-1, warp_sites=16),
+                                 dict(W=16, WT=4, T=64, carve=50, warp_sites=32),
+                                 dict(W=16, WT=4, T=128, carve=-1, warp_sites=16),
+                                 dict(W=2, WT=2, T=32, carve=25, warp_sites=32),
+                                 dict(W=4, WT=4, T=32, carve=-1, warp_sites=32)])
 def test_batched_pinned_configurations(sqcg, links_cache, cfg):
-    """Every FP32 Dslash instantiation (1, 2 or 4 RHS per thread), pinned instead of tuned, on an uneven batch
-    with a ragged RHS block and a 12-real long-link lattice: each RHS reaches tol on the oracle."""
+    """Every FP32 Dslash instantiation (1, 2 or 4 RHS per thread; warps of 32 sites of one RHS group or 16 sites
+    of two), pinned instead of tuned, on an uneven batch with a ragged RHS block and a 12-real long-link
+    lattice: each RHS reaches tol on the oracle."""
     specs = [((8, 8, 8, 8), 5, 0.1), ((6, 8, 10, 12), 3, 0.05), ((4, 4, 4, 8), 1, 0.2)]
     tol = 1e-9
     sqcg.pin_batched_tuning(**cfg)
