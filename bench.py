@@ -13,8 +13,11 @@ loop and FP64 reliable updates; from x0 = 0 the initial residual is b itself);
 whole-job over all ranks.
 Also reported: the plain FP64 GPU CG time to the same residual, the
 Dslash-only HBM roofline of the dominant kernel (FP32 Dslash), an end-to-end
-number through the C ABI with host buffers, and the FP64 CPU oracle timed on
-the host cores on a bounded sample of the same workload.
+number through the C ABI with host buffers, the FP64 CPU oracle timed on
+the host cores on a bounded sample of the same workload, and (one GPU) a
+`forms` block: the multi-shift, rational, batched, learned and HISQ-link
+forms of the solve, each against plain FP64 GPU CG at the same residual,
+each with its own clock record.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -75,6 +78,9 @@ def parse():
     ap.add_argument("--lattice", default=None,
                     help="hisq and batched workloads: extents as Lx,Ly,Lz,Lt (hisq default 32^4; batched: one "
                          "lattice with 16 sources instead of the three; for profiling)")
+    ap.add_argument("--pin", default=None,
+                    help="batched: pin the FP32 Dslash configuration W,WT,T,carve,warp_sites instead of tuning "
+                         "(for profiling runs)")
     ap.add_argument("--save-params", default=None, help="learned: write the trained network parameters (.npy)")
     ap.add_argument("--load-params", default=None, help="learned: skip training, use these parameters (.npy)")
     ap.add_argument("--no-forms", action="store_true",
@@ -879,6 +885,8 @@ def run_batched(args):
     specs = BATCHED_SPECS
     if args.lattice:
         specs = (tuple(int(v) for v in args.lattice.split(",")),)
+    if args.pin:
+        sq.pin_batched_tuning(*[int(v) for v in args.pin.split(",")])
     lats, bs, xs = make_batched(sq, torch, specs)
     clk = ClockSampler(gpu_uuid(torch, 0)).start()
     res = measure_batched(torch, sq, clk, lats, bs, xs, args.steps, compare=not args.no_compare)

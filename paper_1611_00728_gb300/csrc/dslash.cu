@@ -270,8 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_dslash(DArgs<R> a) {
     if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
   } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
     if (a.fin != FIN_NONE) {
-      double unused = 0.0;
-      block_sum3(part, unused, part3);
+      block_sum2(part, part3);
       if (threadIdx.x == 0) {
         a.partials[blockIdx.x] = part;
         a.partials[2 * gridDim.x + blockIdx.x] = part3;

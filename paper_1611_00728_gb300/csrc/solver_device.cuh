@@ -302,6 +302,30 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
+// Two sums of a block in one pass; the totals are valid in thread 0 (same rules as block_sum3).
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double part2[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) { part2[0][wid] = a; part2[1][wid] = b; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? part2[0][lane] : 0.0;
+    b = lane < nw ? part2[1][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
 // first stage of three sums: partials of sum k at offset k * gridDim.x
 __device__ __forceinline__ void block_partial3(double a, double b, double c, double* partials) {
   block_sum3(a, b, c);
