@@ -398,6 +398,7 @@ struct MArgs {
   int max_nsb;
   int W;         // RHS block width of the FP32 blocks (gates refer to these blocks)
   int write_p;   // M_TRUE_RESID at initialisation: also copy r into p
+  int ntiles;    // tiles of the launch (float-float kernel: several tiles per CTA)
 };
 
 // Thread (x, y) of a tile: site sb*blockDim.x + x, right-hand sides y*WT .. y*WT+WT-1
@@ -480,34 +481,47 @@ __global__ void __launch_bounds__(kMaxThreads) k_mrhs_dslash(MArgs a) {
 // The reliable-update passes in float-float arithmetic (ff_arith.cuh): the same tiles, gates and
 // epilogues as k_mrhs_dslash<double, WT>, with links and vectors as float4 (hi, lo) pairs. On this GPU
 // the FP64 kernel is bound by the FP64 FMA rate (1/64 of FP32); this one runs on the FP32 pipe.
+// Per-RHS partials of a CTA that holds NB = blockDim.y independent tiles of blockDim.x sites (slice y is
+// tile tile0 + y): each slice reduces its WT sums over its sites (warp shuffles, then a fixed-order sum
+// over the slice's warps) and writes partials[rhs][sb]. Every thread of the CTA must call it.
 template <int WT>
-__device__ __forceinline__ void apply_w_ff(float4 (&acc)[WT][3], const float4 (&U)[9], const float4* __restrict__ in,
-                                           int Vh, int idx, int nw, unsigned mask, bool dag) {
+__device__ void slice_partials(double (&v)[WT], const LatDev* L, int wbase, int nw_tile, int sb, double* partials,
+                               int max_nsb) {
+  __shared__ double red[4][4][WT];  // [slice][warp of the slice][rhs]; blockDim.x * blockDim.y <= 128
+  const int lane = threadIdx.x & 31, wx = threadIdx.x >> 5, nwx = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int w = 0; w < WT; ++w) {
-    if (w < nw && ((mask >> w) & 1u)) {
-      float4 v[3];
+    double t = v[w];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[c] = __ldg(in + ((size_t)w * 3 + c) * Vh + idx);
-      if (dag) ff_mdv_sub(acc[w], U, v);
-      else ff_mv(acc[w], U, v);
-    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) red[threadIdx.y][wx][w] = t;
+  }
+  __syncthreads();
+  if (L && (int)threadIdx.x < nw_tile) {
+    double t = 0.0;
+    for (int j = 0; j < nwx; ++j) t += red[threadIdx.y][j][threadIdx.x];
+    partials[(size_t)(L->rhs0 + wbase + threadIdx.x) * max_nsb + sb] = t;
   }
 }
 
+// 128 threads per CTA and at least 6 CTAs per SM: at most 80 registers per thread, so 24 warps per SM
+// keep the gathers in flight (at 4 RHS per thread in registers this kernel needed 128 and held 16)
 template <int WT>
-__global__ void __launch_bounds__(256) k_mrhs_dslash_ff(MArgs a) {
-  const int tile = blockIdx.x;
-  const int k = find_lat(a.lats, a.nlat, tile, true);
+__global__ void __launch_bounds__(128, 6) k_mrhs_dslash_ff(MArgs a) {
+  // slice y of the CTA is one tile (blockDim.x sites x WT right-hand sides); no early return before the
+  // partials, whose reduction synchronises the CTA
+  const int tile = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool have_tile = tile < a.ntiles;
+  const int k = have_tile ? find_lat(a.lats, a.nlat, tile, true) : 0;
   const LatDev& L = a.lats[k];
   const int local = tile - L.tile640;
-  const int rb = local % L.nrb64, sb = local / L.nrb64;
-  const int wbase = rb * WT;  // one thread group per tile: the tile's RHS block is this thread's WT RHS
-  const int nw_tile = min(WT, L.nrhs - wbase);
+  const int rb = have_tile ? local % L.nrb64 : 0, sb = have_tile ? local / L.nrb64 : 0;
+  const int wbase = rb * WT;
+  const int nw_tile = have_tile ? min(WT, L.nrhs - wbase) : 0;
   const int w0 = wbase;
-  const int nw = max(0, min(WT, L.nrhs - w0));
+  const int nw = have_tile ? max(0, min(WT, L.nrhs - w0)) : 0;
   const int blk = L.rb0 + wbase / a.W;
-  if (a.gate == GATE_UPDATE && !a.st->blk_update[blk]) return;
+  bool run = have_tile && !(a.gate == GATE_UPDATE && !a.st->blk_update[blk]);
   const Geom& g = L.g;
   const int Vh = g.Vh;
   const int i = sb * blockDim.x + threadIdx.x;
@@ -515,14 +529,13 @@ __global__ void __launch_bounds__(256) k_mrhs_dslash_ff(MArgs a) {
 #pragma unroll
   for (int w = 0; w < WT; ++w) part[w] = 0.0;
   unsigned mask = 0xffffffffu;
-  if (a.gate == GATE_UPDATE) {
+  if (run && a.gate == GATE_UPDATE) {
     mask = 0u;
 #pragma unroll
     for (int w = 0; w < WT; ++w)
       if (w < nw && a.st->r[L.rhs0 + w0 + w].need_update && a.st->r[L.rhs0 + w0 + w].active) mask |= 1u << w;
   }
-  const float4* in = (a.in_vec == V_XFF ? (const float4*)L.xff : (const float4*)L.tmp64) + (size_t)w0 * 3 * Vh;
-  if (i < Vh && nw > 0 && mask) {
+  if (run && i < Vh && nw > 0 && mask) {
     const int xh = i % g.Lxh;
     int rr = i / g.Lxh;
     const int y = rr % g.Ly;
@@ -531,80 +544,79 @@ __global__ void __launch_bounds__(256) k_mrhs_dslash_ff(MArgs a) {
     const int t = rr / g.Lz;
     const int x = 2 * xh + ((y + z + t + a.par) & 1);
     const int row = i - xh;
-    float4 acc[WT][3];
+    // one RHS at a time: the registers of the single-RHS float-float kernel, so the CTA keeps many warps
+    // resident; the tile's links come from HBM for its first RHS and from L1/L2 for the others
+#pragma unroll 1
+    for (int w = 0; w < WT; ++w) {
+      if (!(w < nw && ((mask >> w) & 1u))) continue;
+      const float4* in = (a.in_vec == V_XFF ? (const float4*)L.xff : (const float4*)L.tmp64) +
+                         (size_t)(w0 + w) * 3 * Vh;
+      float4 acc[3];
 #pragma unroll
-    for (int w = 0; w < WT; ++w)
+      for (int c = 0; c < 3; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 U[9], v[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[w][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 U[9];
+      for (int mu = 0; mu < 4; ++mu) {
+        const int cmu = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
+        const int Lmu = (mu == 0) ? g.Lx : (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
+        const int smu = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      const int cmu = (mu == 0) ? x : (mu == 1) ? y : (mu == 2) ? z : t;
-      const int Lmu = (mu == 0) ? g.Lx : (mu == 1) ? g.Ly : (mu == 2) ? g.Lz : g.Lt;
-      const int smu = (mu == 1) ? g.sy : (mu == 2) ? g.sz : g.st;
+        for (int kk = 0; kk < 2; ++kk) {
+          const int d = (kk == 0) ? 1 : 3;
+          int fwd, bwd;
+          if (mu == 0) {
+            int xp = x + d; if (xp >= g.Lx) xp -= g.Lx;
+            int xm = x - d; if (xm < 0) xm += g.Lx;
+            fwd = row + (xp >> 1);
+            bwd = row + (xm >> 1);
+          } else {
+            fwd = i + d * smu; if (cmu + d >= Lmu) fwd -= Lmu * smu;
+            bwd = i - d * smu; if (cmu - d < 0) bwd += Lmu * smu;
+          }
+          const float4* fl = (kk == 0) ? L.fatff[a.par] : L.lngff[a.par];
+          const float4* bl = (kk == 0) ? L.fatff[1 - a.par] : L.lngff[1 - a.par];
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        const int d = (kk == 0) ? 1 : 3;
-        int fwd, bwd;
-        if (mu == 0) {
-          int xp = x + d; if (xp >= g.Lx) xp -= g.Lx;
-          int xm = x - d; if (xm < 0) xm += g.Lx;
-          fwd = row + (xp >> 1);
-          bwd = row + (xm >> 1);
-        } else {
-          fwd = i + d * smu; if (cmu + d >= Lmu) fwd -= Lmu * smu;
-          bwd = i - d * smu; if (cmu - d < 0) bwd += Lmu * smu;
+          for (int e = 0; e < 9; ++e) U[e] = __ldg(fl + ((size_t)mu * 9 + e) * Vh + i);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] = __ldg(in + (size_t)c * Vh + fwd);
+          ff_mv(acc, U, v);
+#pragma unroll
+          for (int e = 0; e < 9; ++e) U[e] = __ldg(bl + ((size_t)mu * 9 + e) * Vh + bwd);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] = __ldg(in + (size_t)c * Vh + bwd);
+          ff_mdv_sub(acc, U, v);
         }
-        const float4* fl = (kk == 0) ? L.fatff[a.par] : L.lngff[a.par];
-        const float4* bl = (kk == 0) ? L.fatff[1 - a.par] : L.lngff[1 - a.par];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) U[e] = __ldg(fl + ((size_t)mu * 9 + e) * Vh + i);
-        apply_w_ff<WT>(acc, U, in, Vh, fwd, nw, mask, false);
-#pragma unroll
-        for (int e = 0; e < 9; ++e) U[e] = __ldg(bl + ((size_t)mu * 9 + e) * Vh + bwd);
-        apply_w_ff<WT>(acc, U, in, Vh, bwd, nw, mask, true);
       }
-    }
-#pragma unroll
-    for (int w = 0; w < WT; ++w)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        ff_norm(acc[w][c].x, acc[w][c].y);
-        ff_norm(acc[w][c].z, acc[w][c].w);
+        ff_norm(acc[c].x, acc[c].y);
+        ff_norm(acc[c].z, acc[c].w);
       }
-    if (a.epi == M_PLAIN) {
-      float4* out = (float4*)L.tmp64 + (size_t)w0 * 3 * Vh;
+      if (a.epi == M_PLAIN) {
+        float4* out = (float4*)L.tmp64 + (size_t)(w0 + w) * 3 * Vh;
 #pragma unroll
-      for (int w = 0; w < WT; ++w)
-        if (w < nw && ((mask >> w) & 1u))
+        for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = acc[c];
+      } else {  // M_TRUE_RESID: r = b - sigma x + D tmp, the sum in FP64; r (FP32) and optionally p
+        const double2* xb = L.x + (size_t)(w0 + w) * 3 * Vh;
+        const double2* bb = L.b + (size_t)(w0 + w) * L.b_stride;
+        const double sig = a.st->r[L.rhs0 + w0 + w].sigma;
+        double n2 = 0.0;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) out[((size_t)w * 3 + c) * Vh + i] = acc[w][c];
-    } else {  // M_TRUE_RESID: r = b - sigma x + D tmp, the sum in FP64; r (FP32) and optionally p
-      const double2* xb = L.x + (size_t)w0 * 3 * Vh;
-      const double2* bb = L.b + (size_t)w0 * L.b_stride;
-#pragma unroll
-      for (int w = 0; w < WT; ++w) {
-        if (w < nw && ((mask >> w) & 1u)) {
-          const double sig = a.st->r[L.rhs0 + w0 + w].sigma;
-          double n2 = 0.0;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const size_t o = ((size_t)w * 3 + c) * Vh + i;
-            const double2 xc = __ldg(xb + o), bc = __ldg(bb + (size_t)w * L.b_stride + (size_t)c * Vh + i);
-            const double2 dv = join_ff(acc[w][c]);
-            const double re = bc.x - sig * xc.x + dv.x;
-            const double im = bc.y - sig * xc.y + dv.y;
-            const float2 f = make_float2((float)re, (float)im);
-            L.r[pv(w0 + w, c, i, Vh)] = f;
-            if (a.write_p) L.p[pv(w0 + w, c, i, Vh)] = f;
-            n2 += re * re + im * im;
-          }
-          part[w] = n2;
+        for (int c = 0; c < 3; ++c) {
+          const double2 xc = __ldg(xb + (size_t)c * Vh + i), bc = __ldg(bb + (size_t)c * Vh + i);
+          const double2 dv = join_ff(acc[c]);
+          const double re = bc.x - sig * xc.x + dv.x;
+          const double im = bc.y - sig * xc.y + dv.y;
+          const float2 f = make_float2((float)re, (float)im);
+          L.r[pv(w0 + w, c, i, Vh)] = f;
+          if (a.write_p) L.p[pv(w0 + w, c, i, Vh)] = f;
+          n2 += re * re + im * im;
         }
+        part[w] = n2;  // one local-memory store per RHS (a register array would cost the loop registers)
       }
     }
   }
-  if (a.epi != M_PLAIN) rhs_block_partial<WT>(part, L, wbase, nw_tile, sb, a.partials, a.max_nsb);
+  if (a.epi != M_PLAIN) slice_partials<WT>(part, run ? &L : nullptr, wbase, nw_tile, sb, a.partials, a.max_nsb);
 }
 
 // xff = float-float copy of x for every RHS that takes the reliable update (all RHS when not gated)
@@ -1199,6 +1211,7 @@ MArgs margs(const BatchPlan& P, int par, int in_vec, int epi, int gate, int writ
   MArgs a;
   a.lats = P.dev; a.nlat = P.nlat; a.par = par; a.in_vec = in_vec; a.epi = epi; a.gate = gate; a.st = P.st;
   a.partials = P.partials; a.max_nsb = P.max_nsb; a.W = P.W; a.write_p = write_p;
+  a.ntiles = 0;
   return a;
 }
 
@@ -1274,13 +1287,19 @@ int launch_true_resid_pass(const BatchPlan& P, int gate, int write_p, cudaStream
   k_mrhs_split_x<<<dim3(gx, P.nrhs_total), 256, 0, s>>>(P.dev, P.nlat, P.st, gate == GATE_UPDATE ? 1 : 0);
   SQCG_CUDA_TRY(cudaGetLastError());
   const int W64 = P.W < kW64 ? P.W : kW64;
+  // several tiles per CTA (128 threads): the kernel keeps 128 registers per thread, and one-tile CTAs of
+  // 32 threads would leave most warp slots empty
+  if (P.T > 128 || 128 % P.T) return SQCG_ERR_INVALID_ARG;
+  const int NB = 128 / P.T;
+  const dim3 block(P.T, NB);
+  const int grid = (P.ntiles64 + NB - 1) / NB;
   for (int pass = 0; pass < 2; ++pass) {
-    const MArgs a = pass == 0 ? margs(P, 1, V_XFF, M_PLAIN, gate, 0) : margs(P, 0, V_TMP64, M_TRUE_RESID, gate, write_p);
-    const dim3 block(P.T, 1);
+    MArgs a = pass == 0 ? margs(P, 1, V_XFF, M_PLAIN, gate, 0) : margs(P, 0, V_TMP64, M_TRUE_RESID, gate, write_p);
+    a.ntiles = P.ntiles64;
     switch (W64) {
-      case 1: k_mrhs_dslash_ff<1><<<P.ntiles64, block, 0, s>>>(a); break;
-      case 2: k_mrhs_dslash_ff<2><<<P.ntiles64, block, 0, s>>>(a); break;
-      case 4: k_mrhs_dslash_ff<4><<<P.ntiles64, block, 0, s>>>(a); break;
+      case 1: k_mrhs_dslash_ff<1><<<grid, block, 0, s>>>(a); break;
+      case 2: k_mrhs_dslash_ff<2><<<grid, block, 0, s>>>(a); break;
+      case 4: k_mrhs_dslash_ff<4><<<grid, block, 0, s>>>(a); break;
       default: return SQCG_ERR_INVALID_ARG;
     }
     SQCG_CUDA_TRY(cudaGetLastError());
