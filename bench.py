@@ -599,6 +599,8 @@ def measure_multishift(torch, sq, clk, lat, b, steps, compare=True, tag="multish
         ms, infos = _repeat(torch, clk, f"{tag}.{name}", run, steps if name == "mixed" else 1)
         res[name] = {"ms": ms, "iters": [i.iters for i in infos],
                      "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
+        if name == "mixed":  # the batched refinement's tuned Dslash configuration (its plan stays with lat)
+            res[name]["refinement_tuning"] = sq.batched_tuning_ex(lat)
     if compare:  # plain FP64 CG, one solve per shift (the same buffers: one captured graph)
         x = lat.new_spinor()
         _solve_sigma(lat, shifts[0], b, x, sq)

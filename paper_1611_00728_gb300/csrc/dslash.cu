@@ -223,6 +223,24 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
       }
       part = (double)dot;
+    } else if constexpr (EPI == EPI_MS_DOTS) {  // Ap = sigma p - D in; <p,Ap>, <r,Ap>, |Ap|^2
+      const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
+      const R2* pv = static_cast<const R2*>(a.y);
+      const R2* rv = static_cast<const R2*>(a.y3);
+      R pa = R(0), ra = R(0), aa = R(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * Vh + i;
+        const R2 pc = ldg2(pv + k), rc = ldg2(rv + k);
+        O2 o = mk<O2>((RO)(sig * pc.x - acc[c].x), (RO)(sig * pc.y - acc[c].y));
+        out[k] = o;
+        pa = fma(pc.x, o.x, fma(pc.y, o.y, pa));
+        ra = fma(rc.x, o.x, fma(rc.y, o.y, ra));
+        aa = fma(o.x, o.x, fma(o.y, o.y, aa));
+      }
+      part = (double)pa;
+      part2 = (double)ra;
+      part3 = (double)aa;
     } else if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_SR_DOTS2) {  // s = sigma r - D in; <r,s>, [<r,q>], |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
@@ -266,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
-  if constexpr (EPI == EPI_SR_DOTS) {
+  if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_MS_DOTS) {
     if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
   } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
     if (a.fin != FIN_NONE) {
@@ -314,7 +332,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
     return SQCG_ERR_INVALID_ARG;
   const int grid = grid_for(ctx->g.Vh, kThreads);
-  const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2;
+  const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2 || L.epi == EPI_MS_DOTS;
   const bool reduces = (L.epi == EPI_NORMAL_DOT || sr || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE;
   if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 3 * max_blocks
   switch (L.epi) {
@@ -324,11 +342,13 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_SR_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_SR_DOTS2: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS2><<<grid, kThreads, 0, s>>>(a); break;
+    case EPI_MS_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_MS_DOTS><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_SR_DOTS    ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
+    return L.epi == EPI_MS_DOTS    ? launch_finish_ms3(ctx, grid, L.gate, s)
+           : L.epi == EPI_SR_DOTS  ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
            : L.epi == EPI_SR_DOTS2 ? launch_finish_sr(ctx, grid, sr_update_partials(ctx), blas_grid(ctx), L.gate, s)
                                    : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
@@ -354,8 +374,10 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
-  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2) && !L.y)
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2 ||
+       L.epi == EPI_MS_DOTS) && !L.y)
     return SQCG_ERR_INVALID_ARG;
+  if (L.epi == EPI_MS_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.epi == EPI_SR_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);

@@ -336,6 +336,34 @@ __device__ __forceinline__ void block_partial3(double a, double b, double c, dou
   }
 }
 
+// The mixed multi-shift step from one reduction (run by the whole finisher block): the three sums of
+// the second Dslash's epilogue give alpha = |r|^2 / <p,Ap> and, since the update r_new = r - alpha Ap
+// follows in the next kernel, |r_new|^2 = |r|^2 - 2 alpha Re<r,Ap> + alpha^2 |Ap|^2 (every term measured on
+// the current vectors, in FP64). Then the two multi-shift steps run in their usual order.
+__device__ __forceinline__ void finish_partials_ms3(SolverState* st, const double* partials, int n) {
+  double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll 4
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    a += partials[j];
+    b += partials[n + j];
+    c += partials[2 * n + j];
+  }
+  block_sum3(a, b, c);
+  __shared__ double tot[3];
+  if (threadIdx.x == 0) { tot[0] = a; tot[1] = b; tot[2] = c; }
+  __syncthreads();
+  const double pAp = tot[0], rAp = tot[1], ApAp = tot[2];
+  solver_finish_ms(st, FIN_MS_PAP, pAp);
+  __syncthreads();  // alpha and the breakdown flag written by thread 0
+  const volatile SolverState* vs = st;
+  if (vs->done) return;  // breakdown: uniform over the block
+  const double al = vs->alpha;
+  // a rounding-level negative value (only possible at a breakdown-level loss of accuracy) counts as zero:
+  // every shift then stops and is judged by its FP64 true residual in the refinement
+  const double rr_new = fmax(vs->rr - 2.0 * al * rAp + al * al * ApAp, 0.0);
+  solver_finish_ms(st, FIN_MS_UPDATE, rr_new);
+}
+
 // the single-reduction step: d = sum partials[0, n), c = sum partials[coff, coff + cn), g = sum partials[2n, 3n)
 __device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff,
                                                    int cn) {
