@@ -61,6 +61,7 @@ struct LatDev {
   int nsb_b, tile0_b;  // BLAS tiling: site blocks of kTB sites, first BLAS tile
   int sbt0;            // first BLAS site block of this lattice over all lattices
   float2 *r, *p, *Ap, *tmp;  // RHS pairs: element (w, c, i) at pv(w, c, i, Vh)
+  float2* xh;                // FP32 partial solutions (RHS pairs), flushed into x at each reliable update
   double2* x;
   double2* tmp64;       // FP64 intermediate, or the float-float one (float4 [w][c][Vh]) of the float-float passes
   const float4* fatff[2];  // float-float links (reliable updates in float-float arithmetic)
@@ -619,8 +620,10 @@ __global__ void __launch_bounds__(128, 6) k_mrhs_dslash_ff(MArgs a) {
   if (a.epi != M_PLAIN) slice_partials<WT>(part, run ? &L : nullptr, wbase, nw_tile, sb, a.partials, a.max_nsb);
 }
 
-// xff = float-float copy of x for every RHS that takes the reliable update (all RHS when not gated)
-__global__ void k_mrhs_split_x(const LatDev* lats, int nlat, const BatchState* st, int gated) {
+// For every RHS that takes the reliable update (all RHS when not gated): x += xh (the FP32 partial
+// solution, added in FP64), xh = 0, and, with float-float updates (split), xff = the float-float copy of
+// the new x. Ungated without split, it is the final flush after the loop.
+__global__ void k_mrhs_flush_x(const LatDev* lats, int nlat, const BatchState* st, int gated, int split) {
   const int g = blockIdx.y;
   int k = 0;
   for (int j = 1; j < nlat; ++j)
@@ -629,9 +632,19 @@ __global__ void k_mrhs_split_x(const LatDev* lats, int nlat, const BatchState* s
   const int w = g - L.rhs0;
   if (w >= L.nrhs) return;
   if (gated && !(st->r[g].need_update && st->r[g].active)) return;
-  const size_t n = (size_t)3 * L.g.Vh, off = (size_t)w * n;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
-    L.xff[off + idx] = split_ff(L.x[off + idx]);
+  const int Vh = L.g.Vh;
+  const size_t n = (size_t)3 * Vh, off = (size_t)w * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / Vh), i = (int)(idx % Vh);
+    float2* hp = L.xh + pv(w, c, i, Vh);
+    const float2 h = *hp;
+    double2 v = L.x[off + idx];
+    v.x += (double)h.x;
+    v.y += (double)h.y;
+    L.x[off + idx] = v;
+    *hp = make_float2(0.f, 0.f);
+    if (split) L.xff[off + idx] = split_ff(v);
+  }
 }
 
 // Per-RHS block partial of a kernel whose warps hold SUB consecutive sites of 32 / SUB RHS groups:
@@ -950,20 +963,18 @@ __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
         pv_load<2>(L.Ap, w0, nw, c, i, Vh, apc[c]);
         pv_load<2>(L.r, w0, nw, c, i, Vh, rc[c]);
       }
+      float2 xc[3][2];  // the FP32 partial solutions of the pair (flushed into x at reliable updates)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv_load<2>(L.xh, w0, nw, c, i, Vh, xc[c]);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         if (!act[u]) continue;
-        double2* x = L.x + (size_t)(w0 + u) * 3 * Vh;
-        double2 xc[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) xc[c] = x[(size_t)c * Vh + i];
         const float fa = (float)alpha[u];
         float n2 = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          xc[c].x = fma(alpha[u], (double)pc[c][u].x, xc[c].x);
-          xc[c].y = fma(alpha[u], (double)pc[c][u].y, xc[c].y);
-          x[(size_t)c * Vh + i] = xc[c];
+          xc[c][u].x = fmaf(fa, pc[c][u].x, xc[c][u].x);
+          xc[c][u].y = fmaf(fa, pc[c][u].y, xc[c][u].y);
           rc[c][u].x = fmaf(-fa, apc[c][u].x, rc[c][u].x);
           rc[c][u].y = fmaf(-fa, apc[c][u].y, rc[c][u].y);
           n2 = fmaf(rc[c][u].x, rc[c][u].x, fmaf(rc[c][u].y, rc[c][u].y, n2));
@@ -971,7 +982,10 @@ __global__ void __launch_bounds__(kTB) k_mrhs_blas(BArgs a) {
         part[u] = (double)n2;
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) pv_store<2>(L.r, w0, nw, c, i, Vh, rc[c]);
+      for (int c = 0; c < 3; ++c) {
+        pv_store<2>(L.r, w0, nw, c, i, Vh, rc[c]);
+        pv_store<2>(L.xh, w0, nw, c, i, Vh, xc[c]);
+      }
     } else {  // B_XPAY
       float2 rc[3][2], pc[3][2];
 #pragma unroll
@@ -1066,7 +1080,7 @@ struct BatchPlan {
   int nrhs_total;
   LatDev host[SQCG_MAX_LATTICES];
   LatDev* dev;           // device copy of host[]
-  void* work[SQCG_MAX_LATTICES];  // per lattice: r, p, Ap, tmp (FP32) and tmp64 (FP64)
+  void* work[SQCG_MAX_LATTICES];  // per lattice: r, p, Ap, tmp, xh (FP32), tmp64 and xff
   double* partials;
   BatchState* st;
   BatchState* st_host;
@@ -1274,18 +1288,25 @@ int launch_f64(const BatchPlan& P, int par, int in_vec, int epi, int gate, int w
   return launch_mrhs_dslash_w<double>(W64, 1, P.ntiles64, P.T, s, margs(P, par, in_vec, epi, gate, write_p));
 }
 
+// x += xh for the RHS that take the reliable update (gated) or for all (the initial residual, and the
+// final flush after the loop); split: also their float-float copies
+int launch_flush_x(const BatchPlan& P, int gated, int split, cudaStream_t s) {
+  int max_vh = 0;
+  for (int k = 0; k < P.nlat; ++k) max_vh = P.host[k].g.Vh > max_vh ? P.host[k].g.Vh : max_vh;
+  const int gx = (int)(((size_t)3 * max_vh + 255) / 256 < 1024 ? ((size_t)3 * max_vh + 255) / 256 : 1024);
+  k_mrhs_flush_x<<<dim3(gx, P.nrhs_total), 256, 0, s>>>(P.dev, P.nlat, P.st, gated, split);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
 // The true-residual pass r = b - A x of the RHS that asked for it (gate = GATE_UPDATE) or of all of them
-// (GATE_NONE, the initial residual): FP64 kernels, or the float-float ones after splitting x.
+// (GATE_NONE, the initial residual), after x += xh: FP64 kernels, or the float-float ones.
 int launch_true_resid_pass(const BatchPlan& P, int gate, int write_p, cudaStream_t s) {
+  SQCG_TRY(launch_flush_x(P, gate == GATE_UPDATE ? 1 : 0, P.ff, s));
   if (!P.ff) {
     SQCG_TRY(launch_f64(P, 1, V_X, M_PLAIN, gate, 0, s));
     return launch_f64(P, 0, V_TMP64, M_TRUE_RESID, gate, write_p, s);
   }
-  int max_vh = 0;
-  for (int k = 0; k < P.nlat; ++k) max_vh = P.host[k].g.Vh > max_vh ? P.host[k].g.Vh : max_vh;
-  const int gx = (int)(((size_t)3 * max_vh + 255) / 256 < 1024 ? ((size_t)3 * max_vh + 255) / 256 : 1024);
-  k_mrhs_split_x<<<dim3(gx, P.nrhs_total), 256, 0, s>>>(P.dev, P.nlat, P.st, gate == GATE_UPDATE ? 1 : 0);
-  SQCG_CUDA_TRY(cudaGetLastError());
   const int W64 = P.W < kW64 ? P.W : kW64;
   // several tiles per CTA (128 threads): the kernel keeps 128 registers per thread, and one-tile CTAs of
   // 32 threads would leave most warp slots empty
@@ -1409,11 +1430,11 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   return upload_lats(P, s);
 }
 
-// per lattice: r, p, Ap, tmp in RHS pairs (FP32), tmp64 (FP64 or float-float) and, with float-float
-// reliable updates, xff
+// per lattice: r, p, Ap, tmp and the partial solutions xh in RHS pairs (FP32), tmp64 (FP64 or
+// float-float) and, with float-float reliable updates, xff
 size_t work_bytes(int nrhs, size_t Vh, int ff) {
   const size_t nf = (size_t)((nrhs + 1) / 2) * 2 * 3 * Vh;
-  return 4 * nf * sizeof(float2) + (size_t)(ff ? 2 : 1) * nrhs * 3 * Vh * sizeof(double2);
+  return 5 * nf * sizeof(float2) + (size_t)(ff ? 2 : 1) * nrhs * 3 * Vh * sizeof(double2);
 }
 
 void destroy_plan(BatchPlan* P) {
@@ -1471,8 +1492,8 @@ int build_plan(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const void* cons
     }
     const size_t nf = (size_t)((nrhs[k] + 1) / 2) * 2 * 3 * Vh;
     float2* w = (float2*)P->work[k];
-    L.r = w; L.p = w + nf; L.Ap = w + 2 * nf; L.tmp = w + 3 * nf;
-    L.tmp64 = (double2*)(w + 4 * nf);
+    L.r = w; L.p = w + nf; L.Ap = w + 2 * nf; L.tmp = w + 3 * nf; L.xh = w + 4 * nf;
+    L.tmp64 = (double2*)(w + 5 * nf);
     L.xff = P->ff ? (float4*)(L.tmp64 + (size_t)nrhs[k] * 3 * Vh) : nullptr;
     total += nrhs[k];
     if ((int)Vh > max_vh) max_vh = (int)Vh;
@@ -1674,6 +1695,9 @@ int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double*
     }
   for (int j = 0; j < P.nblk; ++j) h->blk_active[j] = 1;
   SQCG_CUDA_TRY(cudaMemcpyAsync(P.st, h, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+  for (int k = 0; k < nctx; ++k)  // the FP32 partial solutions start at zero
+    SQCG_CUDA_TRY(cudaMemsetAsync(P.host[k].xh, 0,
+                                  (size_t)((nrhs[k] + 1) / 2) * 2 * 3 * ctx[k]->g.Vh * sizeof(float2), s));
   // |b|^2 per RHS; r = b - A x0 in FP64 (x holds the initial guess), p = r
   SQCG_TRY(launch_mrhs_blas(P, B_NORM_B, s));
   SQCG_TRY(launch_finish_b(P, BFIN_BB, 1, s));
@@ -1737,7 +1761,10 @@ int batched_solve(int nctx, sqcg_ctx* const* ctx, const int* nrhs, const double*
       SQCG_CUDA_TRY(cudaMemcpyAsync(h, P.st, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
       SQCG_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    launches += h->loop_count * 8 + h->if_runs * (P.ff ? 4 : 3);
+    // whatever the partial solutions still hold (nothing for an RHS whose last update converged)
+    SQCG_TRY(launch_flush_x(P, 0, 0, s));
+    SQCG_CUDA_TRY(cudaStreamSynchronize(s));
+    launches += h->loop_count * 8 + h->if_runs * 4 + 1;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int worst = SQCG_OK;

@@ -337,10 +337,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
   finish_partials2(st, partials, n, fin);
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish_ms3(SolverState* st, const double* partials, int n,
+__global__ void __launch_bounds__(kFinishThreads) k_finish_ms4(SolverState* st, const double* partials, int n,
                                                                int gate) {
   if (!gate_open(st, gate)) return;
-  finish_partials_ms3(st, partials, n);
+  finish_partials_ms4(st, partials, n);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish_sr(SolverState* st, const double* partials, int n,
@@ -396,8 +396,8 @@ int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s
   return SQCG_OK;
 }
 
-int launch_finish_ms3(sqcg_ctx* ctx, int nblocks, int gate, cudaStream_t s) {
-  k_finish_ms3<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, gate);
+int launch_finish_ms4(sqcg_ctx* ctx, int nblocks, int gate, cudaStream_t s) {
+  k_finish_ms4<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

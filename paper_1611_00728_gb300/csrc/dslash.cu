@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0, part2 = 0.0, part3 = 0.0;
+  double part = 0.0, part2 = 0.0, part3 = 0.0, part4 = 0.0;
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* pv = static_cast<const R2*>(a.y);
       const R2* rv = static_cast<const R2*>(a.y3);
-      R pa = R(0), ra = R(0), aa = R(0);
+      R pa = R(0), ra = R(0), aa = R(0), rr = R(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t k = (size_t)c * Vh + i;
@@ -237,10 +237,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
         pa = fma(pc.x, o.x, fma(pc.y, o.y, pa));
         ra = fma(rc.x, o.x, fma(rc.y, o.y, ra));
         aa = fma(o.x, o.x, fma(o.y, o.y, aa));
+        rr = fma(rc.x, rc.x, fma(rc.y, rc.y, rr));
       }
       part = (double)pa;
       part2 = (double)ra;
       part3 = (double)aa;
+      part4 = (double)rr;
     } else if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_SR_DOTS2) {  // s = sigma r - D in; <r,s>, [<r,q>], |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
@@ -284,7 +286,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
-  if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_MS_DOTS) {
+  if constexpr (EPI == EPI_MS_DOTS) {
+    if (a.fin != FIN_NONE) block_partial4(part, part2, part3, part4, a.partials);
+  } else if constexpr (EPI == EPI_SR_DOTS) {
     if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
   } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
     if (a.fin != FIN_NONE) {
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
       }
     }
   }
-  (void)part2; (void)part3;
+  (void)part2; (void)part3; (void)part4;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -334,7 +338,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   const int grid = grid_for(ctx->g.Vh, kThreads);
   const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2 || L.epi == EPI_MS_DOTS;
   const bool reduces = (L.epi == EPI_NORMAL_DOT || sr || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE;
-  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 3 * max_blocks
+  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 4 * max_blocks
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
@@ -347,7 +351,7 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_MS_DOTS    ? launch_finish_ms3(ctx, grid, L.gate, s)
+    return L.epi == EPI_MS_DOTS    ? launch_finish_ms4(ctx, grid, L.gate, s)
            : L.epi == EPI_SR_DOTS  ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
            : L.epi == EPI_SR_DOTS2 ? launch_finish_sr(ctx, grid, sr_update_partials(ctx), blas_grid(ctx), L.gate, s)
                                    : launch_finish(ctx, grid, L.fin, L.gate, s);
