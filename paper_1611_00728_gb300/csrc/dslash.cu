@@ -197,7 +197,7 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
 constexpr int kThreads = 128;
 
 template <typename R, typename RO, bool RECON, bool EIGHT, int EPI>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOTS2) ? 9 : 0) k_dslash(DArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && (EPI == EPI_SR_DOTS2 || EPI == EPI_MS_DOTS)) ? 9 : 0) k_dslash(DArgs<R> a) {
   typedef typename V2<R>::T R2;
   typedef typename V2<RO>::T O2;
   if (!gate_open(a.st, a.gate)) return;
