@@ -262,68 +262,6 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
   }
 }
 
-// Mixed multi-shift, one pass after the single finisher: r = r - alpha Ap (base residual), then for every
-// shift x_s += alpha_s p_s (the old p_s; also for a shift that has just converged) and, while the loop
-// goes on, p_s = zeta_s r + beta_s p_s with the new r (shift 0 is the base direction, p = r + beta p).
-// Runs while the loop goes on, and once more in the iteration that ends it (x updates only).
-__global__ void __launch_bounds__(kThreads)
-k_ms_update_xpay(MSPtrs P, float2* __restrict__ r, const float2* __restrict__ Ap, float2* __restrict__ p, int Vh,
-                 const SolverState* st) {
-  const volatile SolverState* vs = st;
-  const int done = vs->done;
-  if (done && !vs->ms_final) return;
-  const int ns = st->nshift;
-  const float ra = (float)st->alpha;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
-    float2 rc[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) rc[c] = r[(size_t)c * Vh + i];
-    if (!done) {
-      float2 apc[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) apc[c] = Ap[(size_t)c * Vh + i];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rc[c].x = fmaf(-ra, apc[c].x, rc[c].x);
-        rc[c].y = fmaf(-ra, apc[c].y, rc[c].y);
-        r[(size_t)c * Vh + i] = rc[c];
-      }
-    }
-    for (int j = 0; j < ns; ++j) {
-      const int act = st->active[j];
-      const bool upd_p = !done && (j == 0 || act == 1);
-      if (!act && !upd_p) continue;
-      float2* ps = (j == 0) ? p : static_cast<float2*>(P.p[j]);
-      const double as = st->alpha_s[j];
-      const float z = (j == 0) ? 1.f : (float)st->zeta[j];
-      const float bs = (j == 0) ? (float)st->beta : (float)st->beta_s[j];
-      double2* xs = P.x[j];
-      float2 pc[3];
-      double2 xc[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {  // loads before stores (see k_cg_update)
-        pc[c] = ps[(size_t)c * Vh + i];
-        if (act) xc[c] = xs[(size_t)c * Vh + i];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t k = (size_t)c * Vh + i;
-        if (act) {
-          xc[c].x = fma(as, (double)pc[c].x, xc[c].x);
-          xc[c].y = fma(as, (double)pc[c].y, xc[c].y);
-          xs[k] = xc[c];
-        }
-        if (upd_p) {
-          float2 pn;
-          pn.x = fmaf(bs, pc[c].x, z * rc[c].x);
-          pn.y = fmaf(bs, pc[c].y, z * rc[c].y);
-          ps[k] = pn;
-        }
-      }
-    }
-  }
-}
-
 // Second stage of a grid reduction: sum the block partials, run the scalar step.
 __global__ void __launch_bounds__(kFinishThreads) k_finish(SolverState* st, const double* partials, int n, int fin,
                                                            int gate) {
@@ -335,12 +273,6 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
                                                             int gate) {
   if (!gate_open(st, gate)) return;
   finish_partials2(st, partials, n, fin);
-}
-
-__global__ void __launch_bounds__(kFinishThreads) k_finish_ms4(SolverState* st, const double* partials, int n,
-                                                               int gate) {
-  if (!gate_open(st, gate)) return;
-  finish_partials_ms4(st, partials, n);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish_sr(SolverState* st, const double* partials, int n,
@@ -392,25 +324,6 @@ int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s)
 
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
   k_finish2<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
-  SQCG_CUDA_TRY(cudaGetLastError());
-  return SQCG_OK;
-}
-
-int launch_finish_ms4(sqcg_ctx* ctx, int nblocks, int gate, cudaStream_t s) {
-  k_finish_ms4<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, gate);
-  SQCG_CUDA_TRY(cudaGetLastError());
-  return SQCG_OK;
-}
-
-int launch_ms_update_xpay(sqcg_ctx* ctx, int nshift, double2* const* x, cudaStream_t s) {
-  const int Vh = ctx->g.Vh, grid = grid_for(Vh, kThreads);
-  if (nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
-  MSPtrs P;
-  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
-    P.x[j] = (j < nshift) ? x[j] : nullptr;
-    P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
-  }
-  k_ms_update_xpay<<<grid, kThreads, 0, s>>>(P, ctx->r32, ctx->Ap32, ctx->p32, Vh, ctx->st);
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

@@ -18,8 +18,7 @@ namespace {
 
 constexpr int kCGKernelsPerIter = 7;  // enqueue_cg_head (3 + 2 finishers) + xpay + loop control
 constexpr int kCGKernelsPerUpdate = 3;  // enqueue_cg_reliable (2 + finisher)
-constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control (FP64 mode)
-constexpr int kMSMixedKernelsPerIter = 5;  // mixed: 2 Dslash + 1 finisher + the fused update + loop control
+constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control
 constexpr int kSRKernelsPerIter = 4;  // enqueue_sr_head (2 + finisher) + the update (with loop control)
 constexpr int kSRKernelsPerUpdate = 7;  // enqueue_sr_reliable: flush, 2 FP64 + finisher, 2 FP32 + finisher
 
@@ -160,17 +159,6 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
 }
 
 int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
-  if (mixed) {  // one reduction per iteration: D_oe p; A p with <p,Ap>, <r,Ap>, |Ap|^2; finisher; fused update
-    DslashLaunch L = {};
-    L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->p32; L.out = ctx->tmp32;
-    L.gate = GATE_ITER;
-    SQCG_TRY(launch_dslash(ctx, L, s));
-    L = DslashLaunch{};
-    L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_MS_DOTS; L.in = ctx->tmp32; L.out = ctx->Ap32;
-    L.y = ctx->p32; L.y3 = ctx->r32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_MS_STEP;
-    SQCG_TRY(launch_dslash(ctx, L, s));
-    return launch_ms_update_xpay(ctx, nshift, x, s);
-  }
   const int wp = mixed ? SQCG_F32 : SQCG_F64;
   void* p = mixed ? (void*)ctx->p32 : (void*)ctx->p64;
   void* Ap = mixed ? (void*)ctx->Ap32 : (void*)ctx->Ap64;
@@ -577,7 +565,7 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
     SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
   }
-  int launches = 2 + 1 + nshift + loops * (mixed ? kMSMixedKernelsPerIter : kMSKernelsPerIter);
+  int launches = 2 + 1 + nshift + loops * kMSKernelsPerIter;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];
   for (int j = 0; j < nshift; ++j) iters_s[j] = h->iters_s[j];

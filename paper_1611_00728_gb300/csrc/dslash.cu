@@ -197,13 +197,13 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
 constexpr int kThreads = 128;
 
 template <typename R, typename RO, bool RECON, bool EIGHT, int EPI>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && (EPI == EPI_SR_DOTS2 || EPI == EPI_MS_DOTS)) ? 9 : 0) k_dslash(DArgs<R> a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOTS2) ? 9 : 0) k_dslash(DArgs<R> a) {
   typedef typename V2<R>::T R2;
   typedef typename V2<RO>::T O2;
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0, part2 = 0.0, part3 = 0.0, part4 = 0.0;
+  double part = 0.0, part2 = 0.0, part3 = 0.0;
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -223,26 +223,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && (EPI == EPI_SR_DO
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
       }
       part = (double)dot;
-    } else if constexpr (EPI == EPI_MS_DOTS) {  // Ap = sigma p - D in; <p,Ap>, <r,Ap>, |Ap|^2
-      const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
-      const R2* pv = static_cast<const R2*>(a.y);
-      const R2* rv = static_cast<const R2*>(a.y3);
-      R pa = R(0), ra = R(0), aa = R(0), rr = R(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t k = (size_t)c * Vh + i;
-        const R2 pc = ldg2(pv + k), rc = ldg2(rv + k);
-        O2 o = mk<O2>((RO)(sig * pc.x - acc[c].x), (RO)(sig * pc.y - acc[c].y));
-        out[k] = o;
-        pa = fma(pc.x, o.x, fma(pc.y, o.y, pa));
-        ra = fma(rc.x, o.x, fma(rc.y, o.y, ra));
-        aa = fma(o.x, o.x, fma(o.y, o.y, aa));
-        rr = fma(rc.x, rc.x, fma(rc.y, rc.y, rr));
-      }
-      part = (double)pa;
-      part2 = (double)ra;
-      part3 = (double)aa;
-      part4 = (double)rr;
     } else if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_SR_DOTS2) {  // s = sigma r - D in; <r,s>, [<r,q>], |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
@@ -286,9 +266,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && (EPI == EPI_SR_DO
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
-  if constexpr (EPI == EPI_MS_DOTS) {
-    if (a.fin != FIN_NONE) block_partial4(part, part2, part3, part4, a.partials);
-  } else if constexpr (EPI == EPI_SR_DOTS) {
+  if constexpr (EPI == EPI_SR_DOTS) {
     if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
   } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
     if (a.fin != FIN_NONE) {
@@ -299,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && (EPI == EPI_SR_DO
       }
     }
   }
-  (void)part2; (void)part3; (void)part4;
+  (void)part2; (void)part3;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -336,9 +314,9 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
   if ((L.gate != GATE_NONE || L.fin != FIN_NONE) && (ctx->st == nullptr || ctx->partials == nullptr))
     return SQCG_ERR_INVALID_ARG;
   const int grid = grid_for(ctx->g.Vh, kThreads);
-  const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2 || L.epi == EPI_MS_DOTS;
+  const bool sr = L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2;
   const bool reduces = (L.epi == EPI_NORMAL_DOT || sr || L.epi == EPI_TRUE_RESID) && L.fin != FIN_NONE;
-  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 4 * max_blocks
+  if (reduces && grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 3 sums and more
   switch (L.epi) {
     case EPI_PLAIN: k_dslash<R, RO, RECON, EIGHT, EPI_PLAIN><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_NORMAL: k_dslash<R, RO, RECON, EIGHT, EPI_NORMAL><<<grid, kThreads, 0, s>>>(a); break;
@@ -346,13 +324,11 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     case EPI_TRUE_RESID: k_dslash<R, RO, RECON, EIGHT, EPI_TRUE_RESID><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_SR_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS><<<grid, kThreads, 0, s>>>(a); break;
     case EPI_SR_DOTS2: k_dslash<R, RO, RECON, EIGHT, EPI_SR_DOTS2><<<grid, kThreads, 0, s>>>(a); break;
-    case EPI_MS_DOTS: k_dslash<R, RO, RECON, EIGHT, EPI_MS_DOTS><<<grid, kThreads, 0, s>>>(a); break;
     default: return SQCG_ERR_INVALID_ARG;
   }
   SQCG_CUDA_TRY(cudaGetLastError());
   if (reduces)
-    return L.epi == EPI_MS_DOTS    ? launch_finish_ms4(ctx, grid, L.gate, s)
-           : L.epi == EPI_SR_DOTS  ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
+    return L.epi == EPI_SR_DOTS    ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s)
            : L.epi == EPI_SR_DOTS2 ? launch_finish_sr(ctx, grid, sr_update_partials(ctx), blas_grid(ctx), L.gate, s)
                                    : launch_finish(ctx, grid, L.fin, L.gate, s);
   return SQCG_OK;
@@ -378,10 +354,8 @@ int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.out_prec == SQCG_F64 ? launch_r<double, double>(ctx, L, s) : launch_r<double, float>(ctx, L, s);
   }
   if (L.out_prec != L.prec) return SQCG_ERR_INVALID_ARG;
-  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2 ||
-       L.epi == EPI_MS_DOTS) && !L.y)
+  if ((L.epi == EPI_NORMAL || L.epi == EPI_NORMAL_DOT || L.epi == EPI_SR_DOTS || L.epi == EPI_SR_DOTS2) && !L.y)
     return SQCG_ERR_INVALID_ARG;
-  if (L.epi == EPI_MS_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.epi == EPI_SR_DOTS && !L.y3) return SQCG_ERR_INVALID_ARG;
   if (L.prec == SQCG_F64) return launch_r<double, double>(ctx, L, s);
   if (L.prec == SQCG_F32) return launch_r<float, float>(ctx, L, s);

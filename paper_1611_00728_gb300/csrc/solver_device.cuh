@@ -336,81 +336,6 @@ __device__ __forceinline__ void block_partial3(double a, double b, double c, dou
   }
 }
 
-// Four sums of a block in one pass; the totals are valid in thread 0 (same rules as block_sum3).
-__device__ __forceinline__ void block_sum4(double& a, double& b, double& c, double& d) {
-  __shared__ double part4[4][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-    d += __shfl_down_sync(0xffffffffu, d, o);
-  }
-  __syncthreads();
-  if (lane == 0) { part4[0][wid] = a; part4[1][wid] = b; part4[2][wid] = c; part4[3][wid] = d; }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    a = lane < nw ? part4[0][lane] : 0.0;
-    b = lane < nw ? part4[1][lane] : 0.0;
-    c = lane < nw ? part4[2][lane] : 0.0;
-    d = lane < nw ? part4[3][lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-      d += __shfl_down_sync(0xffffffffu, d, o);
-    }
-  }
-}
-
-// first stage of four sums: partials of sum k at offset k * gridDim.x
-__device__ __forceinline__ void block_partial4(double a, double b, double c, double d, double* partials) {
-  block_sum4(a, b, c, d);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = a;
-    partials[gridDim.x + blockIdx.x] = b;
-    partials[2 * gridDim.x + blockIdx.x] = c;
-    partials[3 * gridDim.x + blockIdx.x] = d;
-  }
-}
-
-// The mixed multi-shift step from one reduction (run by the whole finisher block). The second Dslash's
-// epilogue measures, on the current vectors, <p,Ap>, <r,Ap>, |Ap|^2 and |r|^2. The step takes |r|^2 from
-// that measurement (not from the previous step's scalar, which would drift from the FP32 vector), then
-// alpha = |r|^2 / <p,Ap> and, since the update r_new = r - alpha Ap follows in the next kernel,
-// |r_new|^2 = |r|^2 - 2 alpha Re<r,Ap> + alpha^2 |Ap|^2. Then the two multi-shift steps run in their usual
-// order.
-__device__ __forceinline__ void finish_partials_ms4(SolverState* st, const double* partials, int n) {
-  double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-#pragma unroll 4
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    a += partials[j];
-    b += partials[n + j];
-    c += partials[2 * n + j];
-    d += partials[3 * n + j];
-  }
-  block_sum4(a, b, c, d);
-  __shared__ double tot[4];
-  if (threadIdx.x == 0) {
-    tot[0] = a; tot[1] = b; tot[2] = c; tot[3] = d;
-    st->rr = d;  // the measured |r_k|^2
-  }
-  __syncthreads();
-  const double pAp = tot[0], rAp = tot[1], ApAp = tot[2], rr = tot[3];
-  solver_finish_ms(st, FIN_MS_PAP, pAp);
-  __syncthreads();  // alpha and the breakdown flag written by thread 0
-  const volatile SolverState* vs = st;
-  if (vs->done) return;  // breakdown: uniform over the block
-  const double al = vs->alpha;
-  // a rounding-level negative value counts as zero: every shift then stops and is judged by its FP64
-  // true residual in the refinement
-  const double rr_new = fmax(rr - 2.0 * al * rAp + al * al * ApAp, 0.0);
-  solver_finish_ms(st, FIN_MS_UPDATE, rr_new);
-}
-
 // the single-reduction step: d = sum partials[0, n), c = sum partials[coff, coff + cn), g = sum partials[2n, 3n)
 __device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff,
                                                    int cn) {

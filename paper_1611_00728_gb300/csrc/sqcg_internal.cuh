@@ -141,8 +141,6 @@ enum Finisher {
   FIN_FCG_PAP = 10,    // flexible CG: alpha = <z,r> / <p,Ap>
   FIN_FCG_BETA = 11,   // flexible CG (two sums): beta = (<z,r> - <z,r_old>) / <z_old,r_old>
   FIN_FCG_INIT = 12,   // flexible CG: <z_0, r_0>
-  FIN_MS_STEP = 14,    // mixed multi-shift (four sums, see EPI_MS_DOTS): alpha, the zeta recurrences,
-                       // |r_new|^2 = |r|^2 - 2 alpha <r,Ap> + alpha^2 |Ap|^2, beta and per-shift convergence
   FIN_SR_STEP = 13,    // single-reduction CG (three sums, see EPI_SR_DOTS): convergence / reliable-update
                        // decision, then alpha and beta of the iteration
 };
@@ -225,8 +223,6 @@ enum DslashEpi {
   EPI_SR_DOTS = 4,        // single-reduction CG: s = sigma*r - D in (r = y, q = y3 on the output parity);
                           // three sums Re<r,s>, Re<r,q>, |r|^2 (after a reliable update)
   EPI_SR_DOTS2 = 5,       // the same without q: sums Re<r,s> and |r|^2; Re<r,q> comes from the update kernel
-  EPI_MS_DOTS = 6,        // mixed multi-shift: Ap = sigma*p - D in (p = y, r = y3); sums Re<p,Ap>, Re<r,Ap>,
-                          // |Ap|^2 and |r|^2
 };
 
 struct DslashLaunch {
@@ -269,10 +265,7 @@ int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
 int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, double a, cudaStream_t s);
 
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
-// mixed multi-shift: the finisher of the four EPI_MS_DOTS sums (partials at 0, n, 2n, 3n)
-int launch_finish_ms4(sqcg_ctx* ctx, int nblocks, int gate, cudaStream_t s);
-// mixed multi-shift: r -= alpha Ap, then every shift's x_s and p_s update in the same pass (FP32 vectors)
-int launch_ms_update_xpay(sqcg_ctx* ctx, int nshift, double2* const* x, cudaStream_t s);
+
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 
 // float-float Dslash (dslash_ff.cu): in and out_ff are float4 [3][Vh] (re_hi, re_lo, im_hi, im_lo);
