@@ -95,6 +95,10 @@ int sqcg_create(const int dims[4], int flags, void* cuda_stream, sqcg_ctx** out)
   g.apbc = (flags & SQCG_ANTIPERIODIC_T) ? 1 : 0;
   c->stream = (cudaStream_t)cuda_stream;
   c->ru_arith = SQCG_FF;
+  {  // SQCG_PDL=0: launch the loop kernels without programmatic dependent launch
+    const char* pdl = getenv("SQCG_PDL");
+    c->pdl = (pdl && strcmp(pdl, "0") == 0) ? 0 : 1;
+  }
   c->ru_delta = 0.001;
   c->ru_interval = 100;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

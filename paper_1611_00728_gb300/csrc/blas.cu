@@ -265,6 +265,7 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
 // Second stage of a grid reduction: sum the block partials, run the scalar step.
 __global__ void __launch_bounds__(kFinishThreads) k_finish(SolverState* st, const double* partials, int n, int fin,
                                                            int gate) {
+  pdl_wait();
   if (!gate_open(st, gate)) return;
   finish_partials(st, partials, n, fin);
 }
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish_sr(SolverState* st, const double* partials, int n,
                                                               int coff, int cn, int gate) {
+  pdl_wait();
   if (!gate_open(st, gate)) return;
   finish_partials_sr(st, partials, n, coff, cn);
 }
@@ -316,9 +318,8 @@ int blas_grid(sqcg_ctx* ctx) {
   return ctx->blas_grid;
 }
 
-int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
-  k_finish<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
-  SQCG_CUDA_TRY(cudaGetLastError());
+int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl) {
+  SQCG_CUDA_TRY(launch_kernel(k_finish, 1, kFinishThreads, 0, s, pdl, ctx->st, ctx->partials, nblocks, fin, gate));
   return SQCG_OK;
 }
 
@@ -328,9 +329,9 @@ int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s
   return SQCG_OK;
 }
 
-int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s) {
-  k_finish_sr<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, coff, cn, gate);
-  SQCG_CUDA_TRY(cudaGetLastError());
+int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s, bool pdl) {
+  SQCG_CUDA_TRY(launch_kernel(k_finish_sr, 1, kFinishThreads, 0, s, pdl, ctx->st, ctx->partials, nblocks, coff, cn,
+                              gate));
   return SQCG_OK;
 }
 

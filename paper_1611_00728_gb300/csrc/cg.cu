@@ -90,7 +90,7 @@ int enqueue_cg_head(sqcg_ctx* ctx, int mixed, void* x, cudaStream_t s) {
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
   L.out_parity = 0; L.prec = L.out_prec = wp; L.epi = EPI_NORMAL_DOT; L.in = tmp; L.out = Ap; L.y = p;
-  L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_PAP;
+  L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_PAP; L.pdl = 1;
   SQCG_TRY(launch_dslash(ctx, L, s));
   SQCG_TRY(launch_cg_update_x(ctx, mixed, (double2*)x, s));
   return SQCG_OK;
@@ -125,7 +125,7 @@ int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s, bool after_update = false) {
   L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = after_update ? EPI_SR_DOTS : EPI_SR_DOTS2;
   L.in = ctx->tmp32; L.out = ctx->Ap32;
   L.y = ctx->r32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
-  L.fin = FIN_SR_STEP;
+  L.fin = FIN_SR_STEP; L.pdl = 1;
   return launch_dslash(ctx, L, s);
 }
 
@@ -168,7 +168,7 @@ int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
   L.out_parity = 0; L.prec = L.out_prec = wp; L.epi = EPI_NORMAL_DOT; L.in = tmp; L.out = Ap; L.y = p;
-  L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_MS_PAP;
+  L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER; L.fin = FIN_MS_PAP; L.pdl = 1;
   SQCG_TRY(launch_dslash(ctx, L, s));
   SQCG_TRY(launch_ms_update_x(ctx, mixed, nshift, x, s));
   SQCG_TRY(launch_ms_xpay(ctx, mixed, nshift, x, s));
@@ -230,9 +230,7 @@ int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const*
   return SQCG_OK;
 }
 
-int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, CGGraph** out) {
-  CGGraph* g = find_graph(ctx, kind, mixed, b, x, nx);
-  if (g) { *out = g; return SQCG_OK; }
+int capture_new(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, CGGraph** out) {
   cudaGraph_t top = nullptr;
   SQCG_CUDA_TRY(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle hw = 0, hif = 0;
@@ -258,7 +256,7 @@ int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, i
   }
   cudaGraphDestroy(top);
   if (rc != SQCG_OK) return rc;
-  g = (CGGraph*)calloc(1, sizeof(CGGraph));
+  CGGraph* g = (CGGraph*)calloc(1, sizeof(CGGraph));
   if (!g) { cudaGraphExecDestroy(exec); return SQCG_ERR_NO_MEMORY; }
   g->kind = kind; g->mixed = mixed; g->nshift = nx; g->b = b; g->exec = exec;
   g->h_while = hw; g->h_if = hif;
@@ -266,6 +264,21 @@ int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, i
   add_graph(ctx, g);
   *out = g;
   return SQCG_OK;
+}
+
+// The cached graph of this loop, or a new capture. Programmatic edges inside a conditional node's body
+// need a recent driver: if the capture with them fails, the context drops programmatic dependent launch
+// and captures again with plain edges (same kernels, same results).
+int capture(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, CGGraph** out) {
+  CGGraph* g = find_graph(ctx, kind, mixed, b, x, nx);
+  if (g) { *out = g; return SQCG_OK; }
+  int rc = capture_new(ctx, kind, mixed, b, x, nx, out);
+  if (rc == SQCG_ERR_CUDA && ctx->pdl) {
+    cudaGetLastError();
+    ctx->pdl = 0;
+    rc = capture_new(ctx, kind, mixed, b, x, nx, out);
+  }
+  return rc;
 }
 
 int read_state(sqcg_ctx* ctx, cudaStream_t s) {

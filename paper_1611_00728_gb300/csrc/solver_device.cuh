@@ -9,6 +9,14 @@
 
 #include "sqcg_internal.cuh"
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later). A kernel launched with the
+// programmatic-serialization attribute may be scheduled while the kernel before it on the stream still
+// drains its last wave; pdl_wait() blocks until that kernel has completed and its writes are visible,
+// and pdl_launch_dependents() lets the next such kernel be scheduled once every block of this one has
+// issued it. Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
   if (gate == GATE_NONE) return true;
   const volatile SolverState* v = st;

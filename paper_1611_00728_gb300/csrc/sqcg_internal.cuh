@@ -200,6 +200,7 @@ struct sqcg_ctx {
   int ms_prec;
 
   int ru_arith;        // arithmetic of the mixed solvers' true residuals: SQCG_F64 or SQCG_FF (default)
+  int pdl;             // launch the loop kernels that follow a kernel with programmatic dependent launch
   double ru_delta;     // reliable update when |r| < ru_delta * max |r| since the last one
   int ru_interval;     // ... or after this many iterations
   CGGraph* graphs;  // cached captured solver loops
@@ -240,6 +241,7 @@ struct DslashLaunch {
   const double* sigma_dev;  // if non-null, sigma is read from here (solver state)
   int gate;
   int fin;
+  int pdl;  // the kernel before it on the stream is a kernel: launch with programmatic dependent launch
 };
 
 int launch_dslash(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s);
@@ -248,11 +250,29 @@ int launch_cg_update_x(sqcg_ctx* ctx, int mixed, double2* x, cudaStream_t s);
 int launch_loop_control(sqcg_ctx* ctx, cudaStream_t s);
 // blocks of the streaming BLAS kernels (one wave on every SM; each thread loops over sites)
 int blas_grid(sqcg_ctx* ctx);
-int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
+// Launch kern<<<grid, block, smem, s>>>(args...), with the programmatic-serialization attribute when pdl
+// is set (the kernel must then call pdl_wait() before it reads what the kernel before it wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                          Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl = false);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 // the single-reduction step's finisher: sums <r,s> = partials[0, n), <r,q> = partials[coff, coff + cn),
 // |r|^2 = partials[2n, 3n)
-int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s);
+int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s, bool pdl = false);
 // offset of the update kernel's partials of <r_new, q> in ctx->partials
 inline int sr_update_partials(const sqcg_ctx* ctx) { return 3 * ctx->max_blocks; }
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
