@@ -46,6 +46,10 @@ void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->r32); cudaFree(ctx->p32); cudaFree(ctx->Ap32); cudaFree(ctx->tmp32);
   cudaFree(ctx->q32); cudaFree(ctx->xh32); cudaFree(ctx->xff);
   cudaFree(ctx->partials); cudaFree(ctx->st);
+  cudaFree(ctx->pers_part); cudaFree(ctx->pers_bar);
+  ctx->pers_part = nullptr;
+  ctx->pers_bar = nullptr;
+  ctx->pers_grid = 0;
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   ctx->r64 = ctx->p64 = ctx->Ap64 = ctx->tmp64 = nullptr;
   ctx->r32 = ctx->p32 = ctx->Ap32 = ctx->tmp32 = nullptr;

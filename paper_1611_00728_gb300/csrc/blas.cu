@@ -100,7 +100,7 @@ k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __res
   }
   if (vs->done) return;  // uniform over the grid
   const float alpha = (float)st->alpha, beta = (float)st->beta;
-  double cross = 0.0;
+  float2 cross[1] = {make_float2(0.f, 0.f)};  // float-float, as the step's other sums
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     float2 rc[3], sc[3], pc[3], qc[3], xc[3];
 #pragma unroll
@@ -131,9 +131,10 @@ k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __res
     float rq = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) rq = fmaf(rc[c].x, qc[c].x, fmaf(rc[c].y, qc[c].y, rq));
-    cross += (double)rq;
+    cross[0] = ffs_add(cross[0], make_float2(rq, 0.f));
   }
-  block_partial(cross, cpart);
+  block_sum_ffs<1>(cross);
+  if (threadIdx.x == 0) ffs_slots(cpart)[blockIdx.x] = cross[0];
 }
 
 // x += xh (the FP32 partial solution, added in FP64), xh = 0

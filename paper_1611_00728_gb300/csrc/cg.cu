@@ -20,6 +20,10 @@ constexpr int kCGKernelsPerIter = 7;  // enqueue_cg_head (3 + 2 finishers) + xpa
 constexpr int kCGKernelsPerUpdate = 3;  // enqueue_cg_reliable (2 + finisher)
 constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control
 constexpr int kSRKernelsPerIter = 4;  // enqueue_sr_head (2 + finisher) + the update (with loop control)
+// the persistent loop runs where a parity has at most this many 128-site tiles a SM (measured
+// crossover on the GB300: 20^4, 4.1 tiles a SM, gains; 24^4, 8.5, loses)
+constexpr int kPersistentMaxTilesPerSM = 5;
+constexpr int kSRKernelsPerUpdatePersistent = 4;  // flush, Dslash pair, finisher (no head)
 constexpr int kSRKernelsPerUpdate = 7;  // enqueue_sr_reliable: flush, 2 FP64 + finisher, 2 FP32 + finisher
 
 // KIND_CG: Hestenes-Stiefel CG (FP64 mode); KIND_MS: multi-shift; KIND_SR: single-reduction mixed CG
@@ -133,7 +137,7 @@ int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s, bool after_update = false) {
 // convergence check), then A r and the step's scalars again from the true residual. The true residual's
 // Dslash pair runs in float-float (default) or FP64 arithmetic (sqcg_set_update_arithmetic); the sum
 // b - sigma x + D x and its norm are FP64 either way.
-int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
+int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s, bool head = true) {
   if (ctx->ru_arith == SQCG_FF) {
     SQCG_TRY(launch_flush_split(ctx, (double2*)x, ctx->xh32, ctx->xff, GATE_UPDATE, s));
     FFLaunch F = {};
@@ -143,7 +147,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
     F.out_parity = 0; F.true_resid = 1; F.in = ctx->tmp64; F.out32 = ctx->r32; F.x = x; F.b = b;
     F.sigma_dev = &ctx->st->sigma; F.gate = GATE_UPDATE; F.fin = FIN_TRUE_RESID;
     SQCG_TRY(launch_dslash_ff(ctx, F, s));
-    return enqueue_sr_head(ctx, s, true);
+    return head ? enqueue_sr_head(ctx, s, true) : SQCG_OK;
   }
   SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_UPDATE, s));
   DslashLaunch L = {};
@@ -155,7 +159,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s) {
   L.in = ctx->tmp64; L.out = ctx->r32; L.y = x; L.b = b; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_UPDATE;
   L.fin = FIN_TRUE_RESID;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  return enqueue_sr_head(ctx, s, true);  // gated on the loop going on (GATE_ITER)
+  return head ? enqueue_sr_head(ctx, s, true) : SQCG_OK;  // gated on the loop going on (GATE_ITER)
 }
 
 int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
@@ -352,6 +356,48 @@ int run_eager(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x,
   return SQCG_OK;
 }
 
+// The single-reduction mixed loop as the persistent kernel (cg_persistent.cu): one launch runs the
+// iterations up to the next reliable update; the host reads the state, runs the true-residual pass
+// and launches again. *segments = persistent launches, *updates_run = true-residual passes.
+//
+// Which loop runs: the persistent kernel where every 128-site tile of a parity has its own resident
+// block (each phase is one wave, so a grid barrier replaces a kernel boundary at no cost in balance,
+// and the launch and finisher latency it removes dominates small lattices); the graph-launched
+// loop on larger lattices, where a phase takes several waves and the barrier across all resident
+// blocks costs more than the kernel boundaries it replaces. SQCG_PERSISTENT=0 or 1 forces one.
+bool use_persistent(sqcg_ctx* ctx) {
+  const char* m = getenv("SQCG_PERSISTENT");
+  if (m && strcmp(m, "0") == 0) return false;
+  const int G = persistent_grid(ctx);
+  if (G <= 0) return false;
+  if (m && strcmp(m, "1") == 0) return true;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int ntiles = grid_for(ctx->g.Vh, 128);
+  return G >= ntiles && ntiles <= kPersistentMaxTilesPerSM * nsm;  // one block a tile, few a SM
+}
+
+int run_persistent(sqcg_ctx* ctx, const void* b, void* x, int max_iter, cudaStream_t s, int* segments,
+                   int* updates_run) {
+  SolverState* h = ctx->st_host;
+  h->use_if = 0;
+  SQCG_TRY(write_state(ctx, s));
+  *segments = 0;
+  *updates_run = 0;
+  for (int k = 0; k < max_iter + 4; ++k) {
+    SQCG_TRY(launch_sr_persistent(ctx, max_iter + 2 - h->iter, s));
+    *segments += 1;
+    SQCG_TRY(read_state(ctx, s));
+    if (h->done || !h->need_update) break;
+    SQCG_TRY(enqueue_sr_reliable(ctx, b, x, s, false));
+    *updates_run += 1;
+  }
+  return SQCG_OK;
+}
+
 int validate_vec(const void* p, int prec) {
   if (!p) return SQCG_ERR_INVALID_ARG;
   const uintptr_t a = (uintptr_t)p;
@@ -448,7 +494,10 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
       SQCG_CUDA_TRY(cudaMemsetAsync(ctx->partials + sr_update_partials(ctx), 0,
                                     (size_t)ctx->max_blocks * sizeof(double), s));
     }
-    if (eager_mode()) {
+    int segments = -1, pupdates = 0;
+    if (mixed && !eager_mode() && use_persistent(ctx)) {
+      SQCG_TRY(run_persistent(ctx, b, x, max_iter, s, &segments, &pupdates));
+    } else if (eager_mode()) {
       SQCG_TRY(run_eager(ctx, kind, mixed, b, xs, 1, max_iter, s, &loops));
     } else {
       CGGraph* g = nullptr;
@@ -458,7 +507,10 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
     if (mixed) {  // whatever the partial solution still holds (nothing after a converged update)
       SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_NONE, s));
       SQCG_CUDA_TRY(cudaStreamSynchronize(s));
-      launches += loops * kSRKernelsPerIter + h->updates * kSRKernelsPerUpdate + 1;
+      if (segments >= 0)  // persistent launches, true-residual passes, final flush
+        launches += segments + pupdates * kSRKernelsPerUpdatePersistent + 1;
+      else
+        launches += loops * kSRKernelsPerIter + h->updates * kSRKernelsPerUpdate + 1;
     } else {
       launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
     }

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   if (!gate_open(a.st, a.gate)) return;
   const int Vh = a.g.Vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double part = 0.0, part2 = 0.0, part3 = 0.0;
+  double part = 0.0;
+  float srs = 0.f, srq = 0.f, srr = 0.f;  // EPI_SR_DOTS*: the site's <r,s>, <r,q>, |r|^2 (FP32)
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -68,9 +69,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
           rq = fma(rc.x, qc.x, fma(rc.y, qc.y, rq));
         }
       }
-      part = (double)rs;
-      part2 = (double)rq;
-      part3 = (double)rr;
+      srs = rs;
+      srq = rq;
+      srr = rr;
     } else {  // EPI_TRUE_RESID: out = b - sigma*x + D in, in FP64
       const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
       const double2* xv = static_cast<const double2*>(a.y);
@@ -93,18 +94,29 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
   }
-  if constexpr (EPI == EPI_SR_DOTS) {
-    if (a.fin != FIN_NONE) block_partial3(part, part2, part3, a.partials);
+  if constexpr (EPI == EPI_SR_DOTS) {  // float-float partials of the three sums
+    if (a.fin != FIN_NONE) {
+      float2 v[3] = {make_float2(srs, 0.f), make_float2(srq, 0.f), make_float2(srr, 0.f)};
+      block_sum_ffs<3>(v);
+      if (threadIdx.x == 0) {
+        float2* slot = ffs_slots(a.partials);
+        slot[blockIdx.x] = v[0];
+        slot[gridDim.x + blockIdx.x] = v[1];
+        slot[2 * gridDim.x + blockIdx.x] = v[2];
+      }
+    }
   } else if constexpr (EPI == EPI_SR_DOTS2) {  // sums 1 and 3 (the second comes from the update kernel)
     if (a.fin != FIN_NONE) {
-      block_sum2(part, part3);
+      float2 v[2] = {make_float2(srs, 0.f), make_float2(srr, 0.f)};
+      block_sum_ffs<2>(v);
       if (threadIdx.x == 0) {
-        a.partials[blockIdx.x] = part;
-        a.partials[2 * gridDim.x + blockIdx.x] = part3;
+        float2* slot = ffs_slots(a.partials);
+        slot[blockIdx.x] = v[0];
+        slot[2 * gridDim.x + blockIdx.x] = v[1];
       }
     }
   }
-  (void)part2; (void)part3;
+  (void)srs; (void)srq; (void)srr;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>

@@ -310,52 +310,106 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
-// Two sums of a block in one pass; the totals are valid in thread 0 (same rules as block_sum3).
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double part2[2][32];
+// ---------------------------------------------------------------------------
+// Float-float sums for the single-reduction step. On the GB300 an FP64 add issues at 1/64 of the
+// FP32 rate (about two per clock on an SM), so a one-block tree over thousands of FP64 partials
+// (measured: 13 us for the 10.6 k partials of a 32^4 step, with the FP64 pipe the stall) and the
+// per-block FP64 trees are bound by it. The step's sums instead carry each value as an unevaluated
+// sum hi + lo of two floats: a sum of two such pairs is TwoSum of the high parts (Knuth, TAOCP
+// vol. 2, 4.2.2) with both low parts added to its error term, then renormalised (Dekker's
+// add): about 2^-44 relative per addition, on the FP32 pipe. A partial is stored as a float2 in
+// one 8-byte slot of the partials array. Site values are FP32 (as before); the totals become FP64
+// only for the scalar step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 ffs_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float v = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ double ffs_value(float2 v) { return (double)v.x + (double)v.y; }
+
+__device__ __forceinline__ float2* ffs_slots(double* partials) { return reinterpret_cast<float2*>(partials); }
+__device__ __forceinline__ const float2* ffs_slots(const double* partials) {
+  return reinterpret_cast<const float2*>(partials);
+}
+
+// N float-float sums over the block in one pass; the totals are valid in thread 0. blockDim.x a
+// multiple of 32 and at most 1024; a fixed tree (deterministic).
+template <int N>
+__device__ __forceinline__ void block_sum_ffs(float2 (&v)[N]) {
+  __shared__ float2 part[N][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  __syncthreads();
-  if (lane == 0) { part2[0][wid] = a; part2[1][wid] = b; }
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      v[k] = ffs_add(v[k], make_float2(__shfl_down_sync(0xffffffffu, v[k].x, o), __shfl_down_sync(0xffffffffu, v[k].y, o)));
+  __syncthreads();  // part may still be read by an earlier call
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) part[k][wid] = v[k];
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
-    a = lane < nw ? part2[0][lane] : 0.0;
-    b = lane < nw ? part2[1][lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
+    for (int k = 0; k < N; ++k) v[k] = lane < nw ? part[k][lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        v[k] = ffs_add(v[k], make_float2(__shfl_down_sync(0xffffffffu, v[k].x, o), __shfl_down_sync(0xffffffffu, v[k].y, o)));
+  }
+}
+
+// Three float-float sums over slots [o0, o0 + n), [o1, o1 + n1), [o2, o2 + n) of ffs partials, each
+// thread taking every blockDim.x-th slot into four interleaved accumulators (four rows of loads in
+// flight), merged in a fixed order; then the block tree. Totals in thread 0 as FP64.
+__device__ __forceinline__ void ffs_sum_partials3(const double* partials, int o0, int o1, int n1, int o2, int n,
+                                                  double& a, double& b, double& c) {
+  const float2* p = ffs_slots(partials);
+  const int bd = blockDim.x;
+  float2 z = make_float2(0.f, 0.f);
+  float2 a4[4] = {z, z, z, z}, b4[4] = {z, z, z, z}, c4[4] = {z, z, z, z};
+  int j = threadIdx.x;
+  for (; j + 3 * bd < n; j += 4 * bd)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a4[u] = ffs_add(a4[u], p[o0 + j + u * bd]);
+      c4[u] = ffs_add(c4[u], p[o2 + j + u * bd]);
     }
-  }
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+    if (j + u * bd < n) {
+      a4[u] = ffs_add(a4[u], p[o0 + j + u * bd]);
+      c4[u] = ffs_add(c4[u], p[o2 + j + u * bd]);
+    }
+  j = threadIdx.x;
+  for (; j + 3 * bd < n1; j += 4 * bd)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b4[u] = ffs_add(b4[u], p[o1 + j + u * bd]);
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+    if (j + u * bd < n1) b4[u] = ffs_add(b4[u], p[o1 + j + u * bd]);
+  float2 v[3] = {ffs_add(ffs_add(a4[0], a4[1]), ffs_add(a4[2], a4[3])),
+                 ffs_add(ffs_add(b4[0], b4[1]), ffs_add(b4[2], b4[3])),
+                 ffs_add(ffs_add(c4[0], c4[1]), ffs_add(c4[2], c4[3]))};
+  block_sum_ffs<3>(v);
+  a = ffs_value(v[0]);
+  b = ffs_value(v[1]);
+  c = ffs_value(v[2]);
 }
 
-// first stage of three sums: partials of sum k at offset k * gridDim.x
-__device__ __forceinline__ void block_partial3(double a, double b, double c, double* partials) {
-  block_sum3(a, b, c);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = a;
-    partials[gridDim.x + blockIdx.x] = b;
-    partials[2 * gridDim.x + blockIdx.x] = c;
-  }
-}
-
-// the single-reduction step: d = sum partials[0, n), c = sum partials[coff, coff + cn), g = sum partials[2n, 3n)
+// the single-reduction step: d = sum of slots [0, n), c = sum of [coff, coff + cn), g = sum of
+// [2n, 3n) (ffs partials)
 __device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff,
                                                    int cn) {
-  double a = 0.0, b = 0.0, c = 0.0;
-#pragma unroll 4
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    a += partials[j];
-    c += partials[2 * n + j];
-  }
-  for (int j = threadIdx.x; j < cn; j += blockDim.x) b += partials[coff + j];
-  block_sum3(a, b, c);
-  if (threadIdx.x == 0) sr_step(st, a, b, c);
+  double d, c, g;
+  ffs_sum_partials3(partials, 0, coff, cn, 2 * n, n, d, c, g);
+  if (threadIdx.x == 0) sr_step(st, d, c, g);
 }
 
 __device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {

@@ -187,6 +187,9 @@ struct sqcg_ctx {
   double* partials;    // 4 * max_blocks: three sums of a Dslash epilogue, then the update kernel's sum
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
+  int pers_grid;        // blocks of the persistent CG loop (0 until first use, -1 unavailable)
+  double* pers_part;    // its partial sums: [3][pers_grid] step sums, [2][pers_grid] cross terms
+  unsigned* pers_bar;   // its grid-barrier words
   SolverState* st;       // device
   SolverState* st_host;  // pinned host mirror
 
@@ -269,6 +272,10 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 }
 
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl = false);
+// persistent single-reduction mixed CG (cg_persistent.cu): grid size (0: unavailable) and one launch,
+// which runs iterations until the state asks for a reliable update or the solve ends
+int persistent_grid(sqcg_ctx* ctx);
+int launch_sr_persistent(sqcg_ctx* ctx, int max_steps, cudaStream_t s);
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s);
 // the single-reduction step's finisher: sums <r,s> = partials[0, n), <r,q> = partials[coff, coff + cn),
 // |r|^2 = partials[2n, 3n)

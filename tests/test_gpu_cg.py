@@ -223,6 +223,7 @@ def test_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch)
     with sqcg.Lattice(L) as lat:
         lat.load_links(fat, lng)
         db = lat.pack(b)
+        monkeypatch.setenv("SQCG_PERSISTENT", "0")  # the graph loop, not the persistent kernel
         for mode in ("graph", "eager"):
             if mode == "eager":
                 monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
@@ -238,6 +239,83 @@ def test_eager_and_graph_modes_are_bit_identical(sqcg, links_cache, monkeypatch)
     assert g[0] == e[0] and g[1] == e[1] and g[3] == e[3]
     assert np.array_equal(g[2], e[2])
     assert all(np.array_equal(a, c) for a, c in zip(g[4], e[4]))
+
+
+@pytest.mark.parametrize("L,form,m,guess", [
+    ((8, 10, 12, 14), "recon12", 0.02, False),
+    ((8, 10, 12, 14), "full", 0.01, True),
+    ((8, 8, 8, 8), "8way", 0.05, False),       # fewer tiles than resident blocks: one block a tile
+    ((16, 16, 16, 16), "8way-recon12", 0.01, False),
+    ((6, 8, 10, 22), "recon12", 0.01, True),   # ragged last tile
+    ((32, 32, 32, 32), "recon12", 0.01, False),  # the benchmarked case
+])
+def test_persistent_loop_matches_graph_loop(sqcg, links_cache, monkeypatch, L, form, m, guess):
+    """The mixed single-reduction CG as one persistent kernel per reliable-update segment (grid barriers
+    between its phases) against the graph-launched loop of the same steps: both reach the oracle's
+    FP64 true residual, with the same iteration count up to the rounding of the partial sums (the
+    persistent grid groups sites into different blocks), in a handful of launches."""
+    tol = 1e-8 if L == (32, 32, 32, 32) else 1e-9
+    fat, lng = links_cache(L, 1002 if L == (32, 32, 32, 32) else 88)
+    b = synth.gaussian_source(L, 2200 if L == (32, 32, 32, 32) else 4)
+    x0 = synth.gaussian_source(L, 5) * 1e-3 if guess else None
+    res = {}
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12="recon12" in form, eight_way="8way" in form)
+        db = lat.pack(b)
+        for loop in ("graph", "persistent"):
+            monkeypatch.setenv("SQCG_PERSISTENT", "0" if loop == "graph" else "1")
+            dx = lat.pack(x0) if guess else lat.new_spinor()
+            info = lat.cg_solve(m, db, dx, tol=tol, max_iter=20000, mode=1)
+            assert info.status == 0 and info.true_rel_resid <= tol, (loop, info.status, info.true_rel_resid)
+            res[loop] = (info.iters, info.reliable_updates, info.launches, lat.unpack(dx))
+    (ig, ug, lg, xg), (ip, up, lp, xp) = res["graph"], res["persistent"]
+    assert abs(ip - ig) <= max(3, ig // 50), (ig, ip)
+    assert abs(up - ug) <= 1, (ug, up)
+    assert lp <= 8 + 5 * (up + 1) < lg, (lp, lg)
+    for x in (xg, xp):
+        assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
+
+
+def test_loop_form_follows_lattice_size(sqcg, links_cache, monkeypatch):
+    """Unforced, the mixed solve runs the persistent kernel when every tile has a resident block (a
+    few launches per solve) and the graph loop when a phase takes several waves (four kernels per
+    iteration)."""
+    monkeypatch.delenv("SQCG_PERSISTENT", raising=False)
+    launches = {}
+    for L in ((8, 10, 12, 14), (32, 32, 32, 32)):
+        fat, lng = links_cache(L, 1002 if L == (32, 32, 32, 32) else 88)
+        b = synth.gaussian_source(L, 4)
+        with sqcg.Lattice(L) as lat:
+            lat.load_links(fat, lng, recon12=True)
+            dx = lat.new_spinor()
+            info = lat.cg_solve(0.02, lat.pack(b), dx, tol=1e-8, max_iter=20000, mode=1)
+            assert info.status == 0
+            launches[L] = (info.launches, info.iters)
+    small, large = launches[(8, 10, 12, 14)], launches[(32, 32, 32, 32)]
+    assert small[0] < 40, small
+    assert large[0] > 3 * large[1], large
+
+
+def test_persistent_loop_ends_on_max_iter(sqcg, links_cache, monkeypatch):
+    """A persistent solve that runs out of iterations ends like the graph loop: NOT_CONVERGED after a
+    final true residual, info filled, x holding the last iterate (its residual is the one reported)."""
+    L, m = (8, 10, 12, 14), 0.01
+    fat, lng = links_cache(L, 88)
+    b = synth.gaussian_source(L, 4)
+    out = {}
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        db = lat.pack(b)
+        for loop in ("graph", "persistent"):
+            monkeypatch.setenv("SQCG_PERSISTENT", "0" if loop == "graph" else "1")
+            dx = lat.new_spinor()
+            info = lat.cg_solve(m, db, dx, tol=1e-12, max_iter=25, mode=1, raise_on_error=False)
+            out[loop] = (info.status, info.iters, info.true_rel_resid, lat.unpack(dx))
+    for loop, (status, iters, lib_res, x) in out.items():
+        assert status == -3 and iters == 25, (loop, status, iters)
+        res = oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x)
+        assert 1e-12 < res < 1.0
+        assert abs(res - lib_res) <= 1e-6 * res, (loop, res, lib_res)
 
 
 @pytest.mark.parametrize("delta,interval", [(0.001, 100), (0.01, 100), (0.5, 5), (0.1, 1000), (1e-5, 100)])
