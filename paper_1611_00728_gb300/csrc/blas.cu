@@ -83,22 +83,13 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
 //   p = r + beta p,  q = s + beta q  (= A p),  xh += alpha p,  r -= alpha q,
 // and the block partials of Re<r_new, q_new>, the next step's cross term (the next Dslash epilogue then
 // reads only r). xh is the FP32 partial solution, flushed into the FP64 x at every reliable update.
-// Thread 0 of block 0 also runs the control step of the captured WHILE loop (count, hard bound,
-// condition), so no separate loop-control kernel follows it.
+// Skipped (uniformly) when the step before it asked for a reliable update or ended the solve.
 __global__ void __launch_bounds__(kThreads)
 k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __restrict__ p, float2* __restrict__ q,
             float2* __restrict__ xh, int Vh, SolverState* st, double* cpart) {
+  pdl_wait();
   const volatile SolverState* vs = st;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && st->h_while) {
-    // the loop continues while the solve is not done and the hard bound is not reached; on the bound,
-    // the status says so and the host sees done == 0 (done itself is not written here: other blocks read it)
-    const int n = st->loop_count + 1;
-    st->loop_count = n;
-    const int go = !vs->done && n < st->loop_limit;
-    if (!go && !vs->done) st->status = SQCG_ERR_NOT_CONVERGED;
-    cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, go ? 1u : 0u);
-  }
-  if (vs->done) return;  // uniform over the grid
+  if (vs->done || vs->need_update) return;  // uniform over the grid: the step did not complete
   const float alpha = (float)st->alpha, beta = (float)st->beta;
   float2 cross[1] = {make_float2(0.f, 0.f)};  // float-float, as the step's other sums
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
@@ -189,7 +180,8 @@ k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restri
   typedef typename V2<R>::T R2;
   if (!gate_open(st, GATE_ITER)) return;
   const R ra = (R)st->alpha;
-  double nrm = 0.0;
+  double nrm = 0.0;                             // FP64 vectors: FP64 partials
+  float2 nrm_ff[1] = {make_float2(0.f, 0.f)};  // FP32 vectors: float-float partials
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     R2 rc[3], apc[3];
 #pragma unroll
@@ -205,9 +197,17 @@ k_ms_update(typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restri
       r[(size_t)c * Vh + i] = rc[c];
       part = fma(rc[c].x, rc[c].x, fma(rc[c].y, rc[c].y, part));
     }
-    nrm += (double)part;
+    if constexpr (sizeof(R) == 4)
+      nrm_ff[0] = ffs_add(nrm_ff[0], make_float2(part, 0.f));
+    else
+      nrm += (double)part;
   }
-  block_partial(nrm, partials);
+  if constexpr (sizeof(R) == 4) {
+    block_sum_ffs<1>(nrm_ff);
+    if (threadIdx.x == 0) ffs_slots(partials)[blockIdx.x] = nrm_ff[0];
+  } else {
+    block_partial(nrm, partials);
+  }
 }
 
 // One pass over every shift's direction: x_s += alpha_s p_s (the old p_s; for
@@ -271,6 +271,13 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(SolverState* st, cons
   finish_partials(st, partials, n, fin);
 }
 
+__global__ void __launch_bounds__(kFinishThreads) k_finish_ffs(SolverState* st, const double* partials, int n, int fin,
+                                                               int gate) {
+  pdl_wait();
+  if (!gate_open(st, gate)) return;
+  finish_partials_ffs(st, partials, n, fin);
+}
+
 __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, const double* partials, int n, int fin,
                                                             int gate) {
   if (!gate_open(st, gate)) return;
@@ -324,6 +331,11 @@ int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s,
   return SQCG_OK;
 }
 
+int launch_finish_ffs(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl) {
+  SQCG_CUDA_TRY(launch_kernel(k_finish_ffs, 1, kFinishThreads, 0, s, pdl, ctx->st, ctx->partials, nblocks, fin, gate));
+  return SQCG_OK;
+}
+
 int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s) {
   k_finish2<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, nblocks, fin, gate);
   SQCG_CUDA_TRY(cudaGetLastError());
@@ -364,12 +376,11 @@ int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s) {
   return SQCG_OK;
 }
 
-int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s) {
+int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s, bool after_kernel) {
   const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   if (grid > ctx->max_blocks) return SQCG_ERR_INVALID_ARG;
-  k_sr_update<<<grid, kThreads, 0, s>>>(ctx->r32, ctx->Ap32, ctx->p32, ctx->q32, ctx->xh32, Vh, ctx->st,
-                                        ctx->partials + sr_update_partials(ctx));
-  SQCG_CUDA_TRY(cudaGetLastError());
+  SQCG_CUDA_TRY(launch_kernel(k_sr_update, grid, kThreads, 0, s, after_kernel && ctx->pdl, ctx->r32, ctx->Ap32,
+                              ctx->p32, ctx->q32, ctx->xh32, Vh, ctx->st, ctx->partials + sr_update_partials(ctx)));
   return SQCG_OK;
 }
 
@@ -405,7 +416,8 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
   else
     k_ms_update<double><<<grid, kThreads, 0, s>>>(ctx->r64, ctx->Ap64, Vh, ctx->st, ctx->partials);
   SQCG_CUDA_TRY(cudaGetLastError());
-  return launch_finish(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s);
+  return mixed ? launch_finish_ffs(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s)
+               : launch_finish(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s);
 }
 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {

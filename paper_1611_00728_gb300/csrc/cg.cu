@@ -19,7 +19,13 @@ namespace {
 constexpr int kCGKernelsPerIter = 7;  // enqueue_cg_head (3 + 2 finishers) + xpay + loop control
 constexpr int kCGKernelsPerUpdate = 3;  // enqueue_cg_reliable (2 + finisher)
 constexpr int kMSKernelsPerIter = 7;  // enqueue_ms_iteration (4 + 2 finishers) + loop control
-constexpr int kSRKernelsPerIter = 4;  // enqueue_sr_head (2 + finisher) + the update (with loop control)
+constexpr int kSRKernelsPerIter = 4;  // enqueue_sr_head (2 + finisher) + the update
+// Steps of the single-reduction loop per pass of its WHILE node. Each pass ends with the reliable-update
+// IF node and the loop control; a step that asks for a reliable update closes the pass (the steps
+// after it are skipped by their gate), and the IF node completes it. On the GB300 an IF node costs
+// about 3.4 us and a WHILE pass 3.5 us (a CUDA-graph probe of empty bodies), against ~200 us a step
+// at 32^4; the 32^4 mixed solve took 44.6, 43.5, 43.0 and 42.9 ms with 1, 2, 4 and 8 steps a pass.
+constexpr int kSRUnroll = 8;
 // the persistent loop runs where a parity has at most this many 128-site tiles a SM (measured
 // crossover on the GB300: 20^4, 4.1 tiles a SM, gains; 24^4, 8.5, loses)
 constexpr int kPersistentMaxTilesPerSM = 5;
@@ -120,15 +126,15 @@ int enqueue_cg_reliable(sqcg_ctx* ctx, int mixed, const void* b, void* x, cudaSt
 // with <r, s> and |r|^2 from its epilogue and <r, q> from the previous update kernel (or, right after a
 // reliable update replaced r, from this epilogue: after_update); the finisher decides on convergence
 // and the reliable update and, without one, computes alpha and beta.
-int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s, bool after_update = false) {
+int enqueue_sr_head(sqcg_ctx* ctx, cudaStream_t s, bool after_update = false, bool after_kernel = false) {
   DslashLaunch L = {};
   L.out_parity = 1; L.prec = L.out_prec = SQCG_F32; L.epi = EPI_PLAIN; L.in = ctx->r32; L.out = ctx->tmp32;
-  L.gate = GATE_ITER;
+  L.gate = GATE_STEP; L.pdl = after_kernel;
   SQCG_TRY(launch_dslash(ctx, L, s));
   L = DslashLaunch{};
   L.out_parity = 0; L.prec = L.out_prec = SQCG_F32; L.epi = after_update ? EPI_SR_DOTS : EPI_SR_DOTS2;
   L.in = ctx->tmp32; L.out = ctx->Ap32;
-  L.y = ctx->r32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_ITER;
+  L.y = ctx->r32; L.y3 = ctx->q32; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_STEP;
   L.fin = FIN_SR_STEP; L.pdl = 1;
   return launch_dslash(ctx, L, s);
 }
@@ -147,7 +153,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s, b
     F.out_parity = 0; F.true_resid = 1; F.in = ctx->tmp64; F.out32 = ctx->r32; F.x = x; F.b = b;
     F.sigma_dev = &ctx->st->sigma; F.gate = GATE_UPDATE; F.fin = FIN_TRUE_RESID;
     SQCG_TRY(launch_dslash_ff(ctx, F, s));
-    return head ? enqueue_sr_head(ctx, s, true) : SQCG_OK;
+    return head ? enqueue_sr_head(ctx, s, true, true) : SQCG_OK;
   }
   SQCG_TRY(launch_flush_partial_x(ctx, (double2*)x, GATE_UPDATE, s));
   DslashLaunch L = {};
@@ -159,7 +165,7 @@ int enqueue_sr_reliable(sqcg_ctx* ctx, const void* b, void* x, cudaStream_t s, b
   L.in = ctx->tmp64; L.out = ctx->r32; L.y = x; L.b = b; L.sigma_dev = &ctx->st->sigma; L.gate = GATE_UPDATE;
   L.fin = FIN_TRUE_RESID;
   SQCG_TRY(launch_dslash(ctx, L, s));
-  return head ? enqueue_sr_head(ctx, s, true) : SQCG_OK;  // gated on the loop going on (GATE_ITER)
+  return head ? enqueue_sr_head(ctx, s, true, true) : SQCG_OK;  // gated on the loop going on (GATE_STEP)
 }
 
 int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {
@@ -179,18 +185,24 @@ int enqueue_ms_iteration(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x
   return SQCG_OK;
 }
 
-// Build the solver graph: one WHILE node whose body is one iteration followed
-// by the loop-control kernel. For single-mass CG the FP64 reliable update sits
-// in an IF node inside the body, so iterations without an update launch no
-// FP64 kernels. The conditional handles are passed to the kernels through the
-// device state (h_while, h_if).
+// Build the solver graph: one WHILE node whose body is one iteration (kSRUnroll
+// steps for the single-reduction loop) followed by the loop-control kernel. For
+// single-mass CG the reliable update sits in an IF node inside the body, so
+// iterations without an update launch none of its kernels. The conditional
+// handles are passed to the kernels through the device state (h_while, h_if).
 int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x, int nx, cudaGraph_t body,
                  cudaGraphConditionalHandle* hif, cudaGraph_t* ifbody) {
   cudaStream_t cs = ctx->cap_stream;
   SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int rc = SQCG_OK;
+  if (kind == KIND_SR) {  // kSRUnroll steps, each skipped once a reliable update is pending
+    for (int k = 0; k < kSRUnroll && rc == SQCG_OK; ++k) {
+      rc = enqueue_sr_head(ctx, cs, false, k > 0);
+      if (rc == SQCG_OK) rc = launch_sr_update(ctx, cs, true);
+    }
+  }
   if (kind == KIND_CG || kind == KIND_SR) {
-    rc = (kind == KIND_CG) ? enqueue_cg_head(ctx, mixed, x[0], cs) : enqueue_sr_head(ctx, cs);
+    if (kind == KIND_CG) rc = enqueue_cg_head(ctx, mixed, x[0], cs);
     if (rc == SQCG_OK) {
       cudaStreamCaptureStatus status;
       cudaGraph_t capg = nullptr;
@@ -214,11 +226,11 @@ int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const*
           *ifbody = ip.conditional.phGraph_out[0];
       }
     }
-    if (rc == SQCG_OK) rc = (kind == KIND_CG) ? launch_cg_xpay(ctx, mixed, cs) : launch_sr_update(ctx, cs);
+    if (rc == SQCG_OK && kind == KIND_CG) rc = launch_cg_xpay(ctx, mixed, cs);
   } else {
     rc = enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, cs);
   }
-  if (rc == SQCG_OK && kind != KIND_SR) rc = launch_loop_control(ctx, cs);  // KIND_SR: inside the update
+  if (rc == SQCG_OK) rc = launch_loop_control(ctx, cs);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &out);
   if (rc == SQCG_ERR_CUDA) sqcg_set_last_cuda_error(cudaGetLastError(), "conditional node", __FILE__, __LINE__);
@@ -226,7 +238,12 @@ int capture_body(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const*
   if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
   if (kind == KIND_CG || kind == KIND_SR) {
     SQCG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, *ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = (kind == KIND_CG) ? enqueue_cg_reliable(ctx, mixed, b, x[0], cs) : enqueue_sr_reliable(ctx, b, x[0], cs);
+    if (kind == KIND_CG) {
+      rc = enqueue_cg_reliable(ctx, mixed, b, x[0], cs);
+    } else {  // the update, the step's head again from the true residual, and the step's vector update
+      rc = enqueue_sr_reliable(ctx, b, x[0], cs);
+      if (rc == SQCG_OK) rc = launch_sr_update(ctx, cs, true);
+    }
     e = cudaStreamEndCapture(cs, &out);
     if (rc != SQCG_OK) return rc;
     if (e != cudaSuccess) { sqcg_set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return SQCG_ERR_CUDA; }
@@ -510,7 +527,9 @@ int cg_solve_sigma(sqcg_ctx* ctx, double sigma, const void* b, void* x, double t
       if (segments >= 0)  // persistent launches, true-residual passes, final flush
         launches += segments + pupdates * kSRKernelsPerUpdatePersistent + 1;
       else
-        launches += loops * kSRKernelsPerIter + h->updates * kSRKernelsPerUpdate + 1;
+        launches += eager_mode() ? loops * kSRKernelsPerIter + h->updates * kSRKernelsPerUpdate + 1
+                                 : loops * (kSRUnroll * kSRKernelsPerIter + 1) +  // passes: steps, control
+                                       h->updates * (kSRKernelsPerUpdate + 1) + 1;  // IF bodies; final flush
     } else {
       launches += loops * kCGKernelsPerIter + h->updates * kCGKernelsPerUpdate;
     }

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
   float srs = 0.f, srq = 0.f, srr = 0.f;  // EPI_SR_DOTS*: the site's <r,s>, <r,q>, |r|^2 (FP32)
+  float sdot = 0.f;                       // EPI_NORMAL_DOT with FP32 vectors: the site's dot
   if (i < Vh) {
     R2 acc[3];
     dslash_site<R, RECON, EIGHT>(a, i, acc);
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
         dot = fma(yc.x, o.x, fma(yc.y, o.y, dot));
       }
       part = (double)dot;
+      sdot = (float)dot;
     } else if constexpr (EPI == EPI_SR_DOTS || EPI == EPI_SR_DOTS2) {  // s = sigma r - D in; <r,s>, [<r,q>], |r|^2
       const R sig = (R)(a.sigma_dev ? *a.sigma_dev : a.sigma);
       const R2* rv = static_cast<const R2*>(a.y);
@@ -91,8 +93,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
       part = nrm;
     }
   }
-  if constexpr (EPI == EPI_NORMAL_DOT || EPI == EPI_TRUE_RESID) {
+  if constexpr ((EPI == EPI_NORMAL_DOT && sizeof(R) == 8) || EPI == EPI_TRUE_RESID) {
     if (a.fin != FIN_NONE) block_partial(part, a.partials);
+  } else if constexpr (EPI == EPI_NORMAL_DOT) {  // FP32: the site's dot is FP32; float-float partials
+    if (a.fin != FIN_NONE) {
+      float2 v[1] = {make_float2(sdot, 0.f)};
+      block_sum_ffs<1>(v);
+      if (threadIdx.x == 0) ffs_slots(a.partials)[blockIdx.x] = v[0];
+    }
   }
   if constexpr (EPI == EPI_SR_DOTS) {  // float-float partials of the three sums
     if (a.fin != FIN_NONE) {
@@ -116,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && EPI == EPI_SR_DOT
       }
     }
   }
-  (void)srs; (void)srq; (void)srr;
+  (void)srs; (void)srq; (void)srr; (void)sdot;
 }
 
 template <typename R, typename RO, bool RECON, bool EIGHT>
@@ -174,7 +182,8 @@ int launch_t(sqcg_ctx* ctx, const DslashLaunch& L, cudaStream_t s) {
     return L.epi == EPI_SR_DOTS ? launch_finish_sr(ctx, grid, grid, grid, L.gate, s, fpdl)
            : L.epi == EPI_SR_DOTS2
                ? launch_finish_sr(ctx, grid, sr_update_partials(ctx), blas_grid(ctx), L.gate, s, fpdl)
-               : launch_finish(ctx, grid, L.fin, L.gate, s, fpdl);
+           : (L.epi == EPI_NORMAL_DOT && sizeof(R) == 4) ? launch_finish_ffs(ctx, grid, L.fin, L.gate, s, fpdl)
+                                                          : launch_finish(ctx, grid, L.fin, L.gate, s, fpdl);
   return SQCG_OK;
 }
 

@@ -22,6 +22,7 @@ __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
   const volatile SolverState* v = st;
   if (v->done) return false;
   if (gate == GATE_UPDATE) return v->need_update != 0;
+  if (gate == GATE_STEP) return v->need_update == 0;
   return true;
 }
 
@@ -401,6 +402,37 @@ __device__ __forceinline__ void ffs_sum_partials3(const double* partials, int o0
   a = ffs_value(v[0]);
   b = ffs_value(v[1]);
   c = ffs_value(v[2]);
+}
+
+// One float-float sum over slots [0, n) of ffs partials (same order rules); total in thread 0 as FP64.
+__device__ __forceinline__ double ffs_sum_partials1(const double* partials, int n) {
+  const float2* p = ffs_slots(partials);
+  const int bd = blockDim.x;
+  const float2 z = make_float2(0.f, 0.f);
+  float2 a4[4] = {z, z, z, z};
+  int j = threadIdx.x;
+  for (; j + 3 * bd < n; j += 4 * bd)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a4[u] = ffs_add(a4[u], p[j + u * bd]);
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+    if (j + u * bd < n) a4[u] = ffs_add(a4[u], p[j + u * bd]);
+  float2 v[1] = {ffs_add(ffs_add(a4[0], a4[1]), ffs_add(a4[2], a4[3]))};
+  block_sum_ffs<1>(v);
+  return ffs_value(v[0]);
+}
+
+// finish_partials for float-float partials (the FP32 passes of the mixed multi-shift loop)
+__device__ __forceinline__ void finish_partials_ffs(SolverState* st, const double* partials, int n, int fin) {
+  const double s = ffs_sum_partials1(partials, n);
+  if (fin == FIN_MS_PAP || fin == FIN_MS_UPDATE) {
+    __shared__ double total;
+    if (threadIdx.x == 0) total = s;
+    __syncthreads();
+    solver_finish_ms(st, fin, total);
+  } else if (threadIdx.x == 0) {
+    solver_finish(st, fin, s);
+  }
 }
 
 // the single-reduction step: d = sum of slots [0, n), c = sum of [coff, coff + cn), g = sum of

@@ -124,7 +124,9 @@ struct BatchState {
 struct BatchPlan;  // defined in batched.cu
 
 // gates: which kernels of a captured iteration actually run
-enum Gate { GATE_NONE = 0, GATE_ITER = 1, GATE_UPDATE = 2 };
+// GATE_ITER: the loop goes on; GATE_UPDATE: a reliable update is due; GATE_STEP: the loop goes on and
+// no reliable update is pending (the unrolled single-reduction body, whose IF node comes after K steps)
+enum Gate { GATE_NONE = 0, GATE_ITER = 1, GATE_UPDATE = 2, GATE_STEP = 3 };
 
 // what the finisher of a grid reduction does with the total
 enum Finisher {
@@ -272,6 +274,8 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 }
 
 int launch_finish(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl = false);
+// the same for float-float partials (ffs slots; the FP32 Dslash's EPI_NORMAL_DOT, k_ms_update<float>)
+int launch_finish_ffs(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s, bool pdl = false);
 // persistent single-reduction mixed CG (cg_persistent.cu): grid size (0: unavailable) and one launch,
 // which runs iterations until the state asks for a reliable update or the solve ends
 int persistent_grid(sqcg_ctx* ctx);
@@ -285,7 +289,8 @@ inline int sr_update_partials(const sqcg_ctx* ctx) { return 3 * ctx->max_blocks;
 int launch_cg_xpay(sqcg_ctx* ctx, int mixed, cudaStream_t s);
 // single-reduction mixed CG: p = r + beta p, q = s + beta q, xh += alpha p, r -= alpha q (s in Ap32), with
 // the WHILE-loop control of the captured loop in one thread
-int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s);
+// (after_kernel: a kernel precedes it on the stream; it then launches with programmatic dependent launch)
+int launch_sr_update(sqcg_ctx* ctx, cudaStream_t s, bool after_kernel = false);
 // x += xh (FP64 += FP32), xh = 0
 int launch_flush_partial_x(sqcg_ctx* ctx, double2* x, int gate, cudaStream_t s);
 int launch_norm2_f64(sqcg_ctx* ctx, const double2* v, int fin, cudaStream_t s);
