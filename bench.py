@@ -4,7 +4,7 @@
 Workload: the single-mass 32^4 lattice, m = 0.01, seeded random fat/long
 links (fat = 0.9 SU(3), long = -1/24 times a product of three SU(3)),
 antiperiodic time, one Gaussian source; the mixed-precision CG (FP32 Dslash
-and vectors, FP64 x, reductions and reliable updates) solved from x0 = 0 to
+and vectors, float-float sums, FP64 x, scalars and true residuals) solved from x0 = 0 to
 a true relative residual of 1e-8. One step = one such solve.
 
 value: sustained Dslash GFLOP/s inside the solve, counting MILC's 1146 flops
@@ -546,8 +546,9 @@ def run_ours(args, ranks: Ranks):
                     "vs_all_cores_32^4": dslash["f32_recon12"]["gflops"]
                     / cpu["dslash"]["x".join(map(str, LATTICE))]["all_cores_gflops"]},
                 "paper_context": PAPER_CONTEXT,
-                "notes": "dtype f32: FP32 Dslash and Krylov vectors; FP64 x, reductions, scalar recurrences and "
-                         "reliable updates. Roofline: Dslash-only loop timed with CUDA events in this run."}
+                "notes": "dtype f32: FP32 Dslash and Krylov vectors; float-float grid sums; FP64 x, scalar "
+                         "recurrences and reliable-update residuals (float-float Dslash, FP64 sum). Roofline: "
+                         "Dslash-only loop timed with CUDA events in this run."}
         print(json.dumps(line), flush=True)
 
 
