@@ -55,7 +55,12 @@ FALLBACK_HBM_GBS = 6800.0
 PAPER_CONTEXT = {"milc_multimass_cg_one_knl7250_gflops": 65, "qphix_speedup_one_knl": 1.5,
                  "qphix_multimass_cg_16_knl7210_gflops": 900,
                  "qphix_dslash_fraction_of_knl_read_bandwidth": 0.8, "precision": "FP64"}
-NOMINAL_FP64_GFLOPS = 1250.0  # GB300 FP64 rate (nominal figure of the hardware table)
+# The HISQ construction runs its 3x3 products in float-float arithmetic on the FP32 pipe. A counted complex
+# multiply-add (8 flops) executes as four float-float accumulations (TwoProduct and TwoSum: 10 FP32
+# instructions each) plus a share of 2 for the renormalisation after every three: 42 FP32 instructions.
+# The FP32 pipe issues 128 lanes per SM and clock: 152 SMs at 2.07 GHz (nominal unit counts and clock).
+FF_INSTR_PER_COUNTED_CFMA = 42
+HISQ_FF_ALU_PEAK_GFLOPS = 128 * 152 * 2.07e9 / FF_INSTR_PER_COUNTED_CFMA * 8 / 1e9
 
 # DRAM bytes per launch (read + write) of the FP32 Dslash with 12-real long links
 # at 32^4, measured by ncu (profiles/dslash_f32_recon12_32x32x32x32.md), with the
@@ -769,7 +774,7 @@ def measure_hisq(torch, sq, clk, lattice, steps, tag="hisq"):
         ms, info = _repeat(torch, clk, f"{tag}.cg_{name}", solve, steps if name == "mixed" else 1)
         cg[name] = {"ms": ms, "iters": info.iters, "true_rel_resid": info.true_rel_resid}
     lat.close()
-    return {"smear_ms": t_ms, "smear_gflops": gflops, "smear_frac_of_nominal_fp64": gflops / NOMINAL_FP64_GFLOPS,
+    return {"smear_ms": t_ms, "smear_gflops": gflops, "smear_frac_of_ff_alu_peak": gflops / HISQ_FF_ALU_PEAK_GFLOPS,
             "cg_on_hisq_links": cg, "cg_speedup_mixed_vs_fp64": cg["fp64"]["ms"] / cg["mixed"]["ms"]}
 
 
@@ -934,16 +939,19 @@ def run_hisq(args):
                "seconds": dt, "sample": "oracle (numpy path sums, FP64) HISQ links of an 8^4 lattice, same counted "
                                         "flops per link"}
     gflops = res["smear_gflops"]
-    _workload_line("HISQ link construction time (thin -> fat, long; FP64) and CG time on the HISQ links",
+    _workload_line("HISQ link construction time (thin -> fat, long; float-float products, FP64 links) and CG time "
+                   "on the HISQ links",
                    res["smear_ms"], args,
                    {"workload": "x".join(map(str, lattice)) + " HISQ smearing of random SU(3) thin links (width 0.3, "
                                 "seed 1002); CG m=0.01 to true rel. residual 1e-8 on the result", "sites": V,
                     "l2": f"thin links {V * 576 / 1e9:.2f} GB, workspace {V * 56 * 144 / 1e9:.2f} GB (L2 129 MB)"},
-                   clk, {"roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, FP64 3x3 products)",
-                                      "achieved": gflops, "peak": NOMINAL_FP64_GFLOPS, "unit": "GFLOP/s",
-                                      "frac": gflops / NOMINAL_FP64_GFLOPS, "peak_kind": "nominal FP64 rate",
+                   clk, {"roofline": {"bound": "alu", "kernel": "sqcg_hisq_smear (8 kernels, float-float 3x3 products)",
+                                      "achieved": gflops, "peak": HISQ_FF_ALU_PEAK_GFLOPS, "unit": "GFLOP/s",
+                                      "frac": gflops / HISQ_FF_ALU_PEAK_GFLOPS,
+                                      "peak_kind": "FP32 pipe (128 lanes x 152 SMs x 2.07 GHz, nominal) at 42 FP32 "
+                                                   "instructions per counted float-float complex multiply-add",
                                       "counted_flops_per_link": sq.HISQ_FLOPS_PER_LINK, "traffic": None},
-                         "cpu_baseline": cpu, "hisq": res}, dtype="f64")
+                         "cpu_baseline": cpu, "hisq": res}, dtype="ff")
 
 
 # The learned preconditioner's training set: (residual, error) pairs from plain FP64 CG on seeded 16^4 gauge

@@ -24,10 +24,20 @@
 // Expanding C gives every 5-link staple (outer nu, inner rho) with c5, every
 // 7-link staple (outer nu, middle rho, inner sig) with c7 and every Lepage
 // staple (nu twice, same sign) with cL, at 48 3x3 products per link per level
-// (12 in A, 24 in B, 12 in C). The work is FP64 arithmetic bound on this GPU.
+// (12 in A, 24 in B, 12 in C).
+//
+// Arithmetic: on this GPU an FP64 FMA issues at 1/64 of the FP32 rate, and the FP64 version of these
+// kernels ran with the FP64 pipe 90-97% busy. The staple products therefore run in float-float
+// arithmetic: every real is an unevaluated sum hi + lo of two floats (48-bit significand), a complex
+// number a float4 (re_hi, re_lo, im_hi, im_lo) of the same 16 bytes as a double2, and each product
+// is accumulated by error-free transformations on the FP32 pipe (ff_arith.cuh: TwoProduct with an
+// FMA, Dekker 1971; TwoSum, Knuth). The fields in the workspace are float-float; the thin links are
+// split at the first kernel, the U(3) projection runs in FP64 on the joined values (its Newton
+// steps need division and square roots), and the outputs are joined back to FP64.
 #include <math.h>
 #include <string.h>
 
+#include "ff_arith.cuh"
 #include "sqcg_internal.cuh"
 
 namespace {
@@ -39,104 +49,141 @@ struct Lat {
   long V;
 };
 
-struct M3 {
-  double2 e[9];
+// ---- float-float 3x3 complex matrices (the staple products) ----
+struct F3 {
+  float4 e[9];
 };
 
-__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {  // acc += a b
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+// acc += a b, acc += a conj(b), acc += conj(a) b (float-float complex; the low words are not
+// renormalised in between: fnorm after a few terms)
+__device__ __forceinline__ void fcfma(float4& acc, float4 a, float4 b) {
+  ff_acc(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  ff_acc(acc.x, acc.y, -a.z, -a.w, b.z, b.w);
+  ff_acc(acc.z, acc.w, a.x, a.y, b.z, b.w);
+  ff_acc(acc.z, acc.w, a.z, a.w, b.x, b.y);
 }
-__device__ __forceinline__ void cfma_cb(double2& acc, double2 a, double2 b) {  // acc += a conj(b)
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
+__device__ __forceinline__ void fcfma_cb(float4& acc, float4 a, float4 b) {
+  ff_acc(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  ff_acc(acc.x, acc.y, a.z, a.w, b.z, b.w);
+  ff_acc(acc.z, acc.w, a.z, a.w, b.x, b.y);
+  ff_acc(acc.z, acc.w, -a.x, -a.y, b.z, b.w);
 }
-__device__ __forceinline__ void cfma_ca(double2& acc, double2 a, double2 b) {  // acc += conj(a) b
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+__device__ __forceinline__ void fcfma_ca(float4& acc, float4 a, float4 b) {
+  ff_acc(acc.x, acc.y, a.x, a.y, b.x, b.y);
+  ff_acc(acc.x, acc.y, a.z, a.w, b.z, b.w);
+  ff_acc(acc.z, acc.w, a.x, a.y, b.z, b.w);
+  ff_acc(acc.z, acc.w, -a.z, -a.w, b.x, b.y);
 }
-
-__device__ __forceinline__ M3 mm(const M3& A, const M3& B) {  // A B
-  M3 C;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cfma(s, A.e[i * 3 + k], B.e[k * 3 + j]);
-      C.e[i * 3 + j] = s;
-    }
-  return C;
+__device__ __forceinline__ void fnorm(float4& v) {
+  ff_norm(v.x, v.y);
+  ff_norm(v.z, v.w);
 }
-__device__ __forceinline__ M3 mm_nd(const M3& A, const M3& B) {  // A B^+
-  M3 C;
+__device__ __forceinline__ F3 fzero() {
+  F3 m;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cfma_cb(s, A.e[i * 3 + k], B.e[j * 3 + k]);
-      C.e[i * 3 + j] = s;
-    }
-  return C;
-}
-__device__ __forceinline__ M3 mm_dn(const M3& A, const M3& B) {  // A^+ B
-  M3 C;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cfma_ca(s, A.e[k * 3 + i], B.e[k * 3 + j]);
-      C.e[i * 3 + j] = s;
-    }
-  return C;
-}
-// C += A B and C += A B^+ (the product accumulated into C directly)
-__device__ __forceinline__ void mm_acc(M3& C, const M3& A, const M3& B) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cfma(C.e[i * 3 + j], A.e[i * 3 + k], B.e[k * 3 + j]);
-}
-__device__ __forceinline__ void mm_nd_acc(M3& C, const M3& A, const M3& B) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cfma_cb(C.e[i * 3 + j], A.e[i * 3 + k], B.e[j * 3 + k]);
-}
-__device__ __forceinline__ void axpy(M3& Y, double a, const M3& X) {
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    Y.e[e].x = fma(a, X.e[e].x, Y.e[e].x);
-    Y.e[e].y = fma(a, X.e[e].y, Y.e[e].y);
-  }
-}
-__device__ __forceinline__ void addto(M3& Y, const M3& X) {
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    Y.e[e].x += X.e[e].x;
-    Y.e[e].y += X.e[e].y;
-  }
+  for (int e = 0; e < 9; ++e) m.e[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  return m;
 }
 
-// field k of a structure-of-arrays buffer: elements [k][e][V]
-__device__ __forceinline__ M3 ld(const double2* __restrict__ f, int k, long V, long n) {
-  M3 m;
-  const double2* p = f + (size_t)k * 9 * V + n;
+__device__ __forceinline__ F3 fmm(const F3& A, const F3& B) {  // A B
+  F3 C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fcfma(s, A.e[i * 3 + k], B.e[k * 3 + j]);
+      fnorm(s);
+      C.e[i * 3 + j] = s;
+    }
+  return C;
+}
+__device__ __forceinline__ F3 fmm_nd(const F3& A, const F3& B) {  // A B^+
+  F3 C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fcfma_cb(s, A.e[i * 3 + k], B.e[j * 3 + k]);
+      fnorm(s);
+      C.e[i * 3 + j] = s;
+    }
+  return C;
+}
+__device__ __forceinline__ F3 fmm_dn(const F3& A, const F3& B) {  // A^+ B
+  F3 C;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fcfma_ca(s, A.e[k * 3 + i], B.e[k * 3 + j]);
+      fnorm(s);
+      C.e[i * 3 + j] = s;
+    }
+  return C;
+}
+// C += A B and C += A B^+, renormalised after the three terms of each element
+__device__ __forceinline__ void fmm_acc(F3& C, const F3& A, const F3& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fcfma(C.e[i * 3 + j], A.e[i * 3 + k], B.e[k * 3 + j]);
+      fnorm(C.e[i * 3 + j]);
+    }
+}
+__device__ __forceinline__ void fmm_nd_acc(F3& C, const F3& A, const F3& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fcfma_cb(C.e[i * 3 + j], A.e[i * 3 + k], B.e[j * 3 + k]);
+      fnorm(C.e[i * 3 + j]);
+    }
+}
+// Y += a X for a float-float real a = (ah, al)
+__device__ __forceinline__ void faxpy(F3& Y, float2 a, const F3& X) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    ff_acc(Y.e[e].x, Y.e[e].y, a.x, a.y, X.e[e].x, X.e[e].y);
+    ff_acc(Y.e[e].z, Y.e[e].w, a.x, a.y, X.e[e].z, X.e[e].w);
+    fnorm(Y.e[e]);
+  }
+}
+// Y += X (float-float: TwoSum of the high words, low words added to the error, renormalised)
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh);
+  const float v = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, v)), __fsub_rn(bh, v));
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+__device__ __forceinline__ void faddto(F3& Y, const F3& X) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    ff_add(Y.e[e].x, Y.e[e].y, X.e[e].x, X.e[e].y);
+    ff_add(Y.e[e].z, Y.e[e].w, X.e[e].z, X.e[e].w);
+  }
+}
+
+// field k of a structure-of-arrays float-float buffer: elements [k][e][V]
+__device__ __forceinline__ F3 fld(const float4* __restrict__ f, int k, long V, long n) {
+  F3 m;
+  const float4* p = f + (size_t)k * 9 * V + n;
 #pragma unroll
   for (int e = 0; e < 9; ++e) m.e[e] = __ldg(p + (size_t)e * V);
   return m;
 }
-__device__ __forceinline__ void st(double2* __restrict__ f, int k, long V, long n, const M3& m) {
-  double2* p = f + (size_t)k * 9 * V + n;
+__device__ __forceinline__ void fst(float4* __restrict__ f, int k, long V, long n, const F3& m) {
+  float4* p = f + (size_t)k * 9 * V + n;
 #pragma unroll
   for (int e = 0; e < 9; ++e) p[(size_t)e * V] = m.e[e];
 }
@@ -169,62 +216,63 @@ constexpr int kNumS = 36;
 __device__ __forceinline__ int s3_field(int mu, int d) { return 24 + mu * 3 + other_index(mu, d); }
 
 // wrap^s_d X (n) for the direction-mu field X given at the displaced site
-__device__ __forceinline__ M3 wrap(const Lat& g, const double2* __restrict__ U, const int c[4], long n, int mu,
-                                   int d, int s, const M3& Xd) {
+__device__ __forceinline__ F3 wrap(const Lat& g, const float4* __restrict__ U, const int c[4], long n, int mu, int d,
+                                   int s, const F3& Xd) {
   if (s == 0) {
-    const M3 a = ld(U, d, g.V, n);
-    const M3 b = ld(U, d, g.V, nb(g, c, mu, 1));
-    return mm_nd(mm(a, Xd), b);
+    const F3 a = fld(U, d, g.V, n);
+    const F3 b = fld(U, d, g.V, nb(g, c, mu, 1));
+    return fmm_nd(fmm(a, Xd), b);
   }
-  const M3 a = ld(U, d, g.V, nb(g, c, d, -1));
-  const M3 b = ld(U, d, g.V, nb(g, c, d, -1, mu, 1));
-  return mm(mm_dn(a, Xd), b);
+  const F3 a = fld(U, d, g.V, nb(g, c, d, -1));
+  const F3 b = fld(U, d, g.V, nb(g, c, d, -1, mu, 1));
+  return fmm(fmm_dn(a, Xd), b);
 }
 
 // acc += wrap^s_d X (n)
-__device__ __forceinline__ void wrap_acc(M3& acc, const Lat& g, const double2* __restrict__ U, const int c[4], long n,
-                                         int mu, int d, int s, const M3& Xd) {
+__device__ __forceinline__ void wrap_acc(F3& acc, const Lat& g, const float4* __restrict__ U, const int c[4], long n,
+                                         int mu, int d, int s, const F3& Xd) {
   if (s == 0) {
-    const M3 a = ld(U, d, g.V, n);
-    const M3 b = ld(U, d, g.V, nb(g, c, mu, 1));
-    mm_nd_acc(acc, mm(a, Xd), b);
+    const F3 a = fld(U, d, g.V, n);
+    const F3 b = fld(U, d, g.V, nb(g, c, mu, 1));
+    fmm_nd_acc(acc, fmm(a, Xd), b);
     return;
   }
-  const M3 a = ld(U, d, g.V, nb(g, c, d, -1));
-  const M3 b = ld(U, d, g.V, nb(g, c, d, -1, mu, 1));
-  mm_acc(acc, mm_dn(a, Xd), b);
+  const F3 a = fld(U, d, g.V, nb(g, c, d, -1));
+  const F3 b = fld(U, d, g.V, nb(g, c, d, -1, mu, 1));
+  fmm_acc(acc, fmm_dn(a, Xd), b);
 }
 
-// host AoS [V][4][9] -> [mu][e][V]
+// host AoS [V][4][9] (FP64) -> [mu][e][V] (float-float)
 __global__ void __launch_bounds__(kThreads) k_links_to_fields(Lat g, const double2* __restrict__ aos,
-                                                              double2* __restrict__ U) {
+                                                              float4* __restrict__ U) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int mu = blockIdx.y;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) U[((size_t)mu * 9 + e) * g.V + n] = aos[((size_t)n * 4 + mu) * 9 + e];
+  for (int e = 0; e < 9; ++e) U[((size_t)mu * 9 + e) * g.V + n] = split_ff(aos[((size_t)n * 4 + mu) * 9 + e]);
 }
 
 // A: 3-staples S^+_{mu nu}, S^-_{mu nu} (s = 0 forward, 1 backward) and S3_{mu nu} = S^+ + S^-
-__global__ void __launch_bounds__(kThreads) k_staple3(Lat g, const double2* __restrict__ U, double2* __restrict__ S) {
+__global__ void __launch_bounds__(kThreads) k_staple3(Lat g, const float4* __restrict__ U, float4* __restrict__ S) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int f = blockIdx.y;  // mu*3 + nu index
   const int mu = f / 3, nu = other(mu, f % 3);
   int c[4];
   coords(g, n, c);
-  const M3 sp = wrap(g, U, c, n, mu, nu, 0, ld(U, mu, g.V, nb(g, c, nu, 1)));
-  st(S, 2 * f, g.V, n, sp);
-  M3 sm = wrap(g, U, c, n, mu, nu, 1, ld(U, mu, g.V, nb(g, c, nu, -1)));
-  st(S, 2 * f + 1, g.V, n, sm);
-  addto(sm, sp);
-  st(S, 24 + f, g.V, n, sm);
+  const F3 sp = wrap(g, U, c, n, mu, nu, 0, fld(U, mu, g.V, nb(g, c, nu, 1)));
+  fst(S, 2 * f, g.V, n, sp);
+  F3 sm = wrap(g, U, c, n, mu, nu, 1, fld(U, mu, g.V, nb(g, c, nu, -1)));
+  fst(S, 2 * f + 1, g.V, n, sm);
+  faddto(sm, sp);
+  fst(S, 24 + f, g.V, n, sm);
 }
 
 // B: Z_{mu nu} = c5 (S3_{mu rho} + S3_{mu sig}) + c7 (wrap_rho S3_{mu sig} + wrap_sig S3_{mu rho})
-__global__ void __launch_bounds__(kThreads) k_staple57(Lat g, const double2* __restrict__ U,
-                                                       const double2* __restrict__ S, double c5, double c7,
-                                                       double2* __restrict__ Z) {
+// (c5, c7 as float-float pairs; a zero coefficient skips its term)
+__global__ void __launch_bounds__(kThreads) k_staple57(Lat g, const float4* __restrict__ U,
+                                                       const float4* __restrict__ S, float2 c5, float2 c7,
+                                                       float4* __restrict__ Z) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int f = blockIdx.y;  // mu*3 + nu index
@@ -234,75 +282,63 @@ __global__ void __launch_bounds__(kThreads) k_staple57(Lat g, const double2* __r
     if (d != mu && d != nu) rs[k++] = d;
   int c[4];
   coords(g, n, c);
-  M3 z;
-#pragma unroll
-  for (int e = 0; e < 9; ++e) z.e[e] = make_double2(0.0, 0.0);
-  if (c5 != 0.0) {
-    M3 t = ld(S, s3_field(mu, rs[0]), g.V, n);
-    addto(t, ld(S, s3_field(mu, rs[1]), g.V, n));
-    axpy(z, c5, t);
+  F3 z = fzero();
+  if (c5.x != 0.f) {
+    F3 t = fld(S, s3_field(mu, rs[0]), g.V, n);
+    faddto(t, fld(S, s3_field(mu, rs[1]), g.V, n));
+    faxpy(z, c5, t);
   }
-  if (c7 != 0.0) {
-    M3 w;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) w.e[e] = make_double2(0.0, 0.0);
+  if (c7.x != 0.f) {
+    F3 w = fzero();
     for (int q = 0; q < 2; ++q) {
       const int d = rs[q], inner = rs[1 - q];
       for (int s = 0; s < 2; ++s) {
-        const M3 x = ld(S, s3_field(mu, inner), g.V, nb(g, c, d, s == 0 ? 1 : -1));
+        const F3 x = fld(S, s3_field(mu, inner), g.V, nb(g, c, d, s == 0 ? 1 : -1));
         wrap_acc(w, g, U, c, n, mu, d, s, x);
       }
     }
-    axpy(z, c7, w);
+    faxpy(z, c7, w);
   }
-  st(Z, f, g.V, n, z);
+  fst(Z, f, g.V, n, z);
 }
 
 // C: F_mu = c1 U_mu + sum_{nu,s} [ c3 S^s_{mu nu} + wrap^s_nu (Z_{mu nu} + cL S^s_{mu nu}) ]
-// out: structure of arrays [mu][e][V], or the host order [V][4][9] when aos != 0
-__global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const double2* __restrict__ U,
-                                                          const double2* __restrict__ S,
-                                                          const double2* __restrict__ Z, double c1, double c3,
-                                                          double cL, int use_z, int aos, double2* __restrict__ out) {
+// out: float-float structure of arrays [mu][e][V], or FP64 in the host order [V][4][9] when aos != 0
+__global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const float4* __restrict__ U,
+                                                          const float4* __restrict__ S,
+                                                          const float4* __restrict__ Z, float2 c1, float2 c3,
+                                                          float2 cL, int use_z, int aos, void* __restrict__ out) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int mu = blockIdx.y;
   int c[4];
   coords(g, n, c);
-  M3 F = ld(U, mu, g.V, n);
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    F.e[e].x *= c1;
-    F.e[e].y *= c1;
-  }
+  F3 F = fzero();
+  faxpy(F, c1, fld(U, mu, g.V, n));
   for (int i = 0; i < 3; ++i) {
     const int nu = other(mu, i);
-    if (c3 != 0.0) axpy(F, c3, ld(S, 24 + mu * 3 + i, g.V, n));  // both signs: S3_{mu nu}
+    if (c3.x != 0.f) faxpy(F, c3, fld(S, 24 + mu * 3 + i, g.V, n));  // both signs: S3_{mu nu}
     for (int s = 0; s < 2; ++s) {
       const int fs = (mu * 3 + i) * 2 + s;
-      if (!use_z && cL == 0.0) continue;
+      if (!use_z && cL.x == 0.f) continue;
       const long y = nb(g, c, nu, s == 0 ? 1 : -1);
-      M3 x;
+      F3 x;
       if (use_z) {
-        x = ld(Z, mu * 3 + i, g.V, y);
-        if (cL != 0.0) axpy(x, cL, ld(S, fs, g.V, y));
+        x = fld(Z, mu * 3 + i, g.V, y);
+        if (cL.x != 0.f) faxpy(x, cL, fld(S, fs, g.V, y));
       } else {
-        x = ld(S, fs, g.V, y);
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-          x.e[e].x *= cL;
-          x.e[e].y *= cL;
-        }
+        x = fzero();
+        faxpy(x, cL, fld(S, fs, g.V, y));
       }
       wrap_acc(F, g, U, c, n, mu, nu, s, x);
     }
   }
   if (aos) {
-    double2* p = out + ((size_t)n * 4 + mu) * 9;
+    double2* p = static_cast<double2*>(out) + ((size_t)n * 4 + mu) * 9;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) p[e] = F.e[e];
+    for (int e = 0; e < 9; ++e) p[e] = join_ff(F.e[e]);
   } else {
-    st(out, mu, g.V, n, F);
+    fst(static_cast<float4*>(out), mu, g.V, n, F);
   }
 }
 
@@ -311,60 +347,70 @@ __global__ void __launch_bounds__(kThreads) k_smear_links(Lat g, const double2* 
 // convergence (Higham, SIAM J. Sci. Stat. Comput. 7 (1986) 1160). X^{-+} is the
 // conjugated cofactor matrix over conj(det X). At most kMaxPolar steps; a singular or
 // non-finite link, or no convergence, sets *err and leaves the link as it is.
+// The matrix arithmetic (cofactors, determinant, update) is float-float. Any g > 0 keeps the
+// polar factor, so g comes from FP32 norms; X^{-+} must be exact to the working precision, so
+// 1 / |det|^2 is one FP64 division on the joined value, split back. The step size is measured in
+// FP32 from the float-float differences.
 constexpr int kMaxPolar = 40;
 
-__global__ void __launch_bounds__(kThreads) k_u3_project(Lat g, double2* __restrict__ F, int* __restrict__ err) {
+__device__ __forceinline__ float4 fneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+
+__global__ void __launch_bounds__(kThreads) k_u3_project(Lat g, float4* __restrict__ F, int* __restrict__ err) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int mu = blockIdx.y;
-  M3 X = ld(F, mu, g.V, n);
+  F3 X = fld(F, mu, g.V, n);
   bool ok = false;
   for (int it = 0; it < kMaxPolar; ++it) {
-    // cofactors C_ij and det = sum_j X_0j C_0j
-    M3 C;
+    // cofactors C_ij = X_{i1 j1} X_{i2 j2} - X_{i1 j2} X_{i2 j1} and det = sum_j X_0j C_0j
+    F3 C;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-        double2 a = make_double2(0.0, 0.0);
-        cfma(a, X.e[i1 * 3 + j1], X.e[i2 * 3 + j2]);
-        const double2 b = X.e[i1 * 3 + j2], d = X.e[i2 * 3 + j1];
-        a.x -= b.x * d.x - b.y * d.y;
-        a.y -= b.x * d.y + b.y * d.x;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        fcfma(a, X.e[i1 * 3 + j1], X.e[i2 * 3 + j2]);
+        fcfma(a, fneg(X.e[i1 * 3 + j2]), X.e[i2 * 3 + j1]);
+        fnorm(a);
         C.e[i * 3 + j] = a;
       }
-    double2 det = make_double2(0.0, 0.0);
+    float4 det = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) cfma(det, X.e[j], C.e[j]);
-    const double dn = det.x * det.x + det.y * det.y;
+    for (int j = 0; j < 3; ++j) fcfma(det, X.e[j], C.e[j]);
+    fnorm(det);
+    const double2 dd = join_ff(det);
+    const double dn = dd.x * dd.x + dd.y * dd.y;
     if (!(dn > 0.0) || !isfinite(dn)) break;
     const double inv_dn = 1.0 / dn;
-    double nx = 0.0, nc = 0.0;
+    float nx = 0.f, nc = 0.f;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-      nx += X.e[e].x * X.e[e].x + X.e[e].y * X.e[e].y;
-      nc += C.e[e].x * C.e[e].x + C.e[e].y * C.e[e].y;
+      nx = fmaf(X.e[e].x, X.e[e].x, fmaf(X.e[e].z, X.e[e].z, nx));
+      nc = fmaf(C.e[e].x, C.e[e].x, fmaf(C.e[e].z, C.e[e].z, nc));
     }
     // Frobenius scaling gamma = sqrt(|X^-1|_F / |X|_F) = (|C|_F^2 / (|det|^2 |X|_F^2))^(1/4)
-    const double gam = sqrt(sqrt(nc * inv_dn / nx));
-    const bool scale = fabs(gam - 1.0) > 1e-3;
-    const double g1 = scale ? 0.5 * gam : 0.5, g2 = scale ? 0.5 / gam : 0.5;
-    // X^{-+} = conj(C) det / |det|^2, elementwise; q = g2 det / |det|^2
-    const double2 q = make_double2(g2 * det.x * inv_dn, g2 * det.y * inv_dn);
-    double diff = 0.0;
+    const float gam = sqrtf(sqrtf(nc * (float)inv_dn / nx));
+    const bool scale = fabsf(gam - 1.f) > 1e-3f;
+    const float g1 = scale ? 0.5f * gam : 0.5f, g2 = scale ? 0.5f / gam : 0.5f;
+    // X^{-+} = conj(C) det / |det|^2, elementwise; q = g2 det / |det|^2 (float-float)
+    const float4 q = split_ff(make_double2((double)g2 * dd.x * inv_dn, (double)g2 * dd.y * inv_dn));
+    const float4 g1c = make_float4(g1, 0.f, 0.f, 0.f);
+    float diff = 0.f;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-      const double2 cc = C.e[e];
-      const double2 xn = make_double2(fma(g1, X.e[e].x, cc.x * q.x + cc.y * q.y),
-                                      fma(g1, X.e[e].y, cc.x * q.y - cc.y * q.x));
-      const double dx = xn.x - X.e[e].x, dy = xn.y - X.e[e].y;
-      diff += dx * dx + dy * dy;
+      float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
+      fcfma(xn, g1c, X.e[e]);
+      fcfma_ca(xn, C.e[e], q);
+      fnorm(xn);
+      const float dx = __fadd_rn(__fsub_rn(xn.x, X.e[e].x), __fsub_rn(xn.y, X.e[e].y));
+      const float dy = __fadd_rn(__fsub_rn(xn.z, X.e[e].z), __fsub_rn(xn.w, X.e[e].w));
+      diff = fmaf(dx, dx, fmaf(dy, dy, diff));
       X.e[e] = xn;
     }
     if (!isfinite(diff)) break;
     // unscaled and the step below 1e-9: Newton's quadratic convergence leaves an error ~1e-18
-    if (!scale && diff < 1e-18) {
+    if (!scale && diff < 1e-18f) {
       ok = true;
       break;
     }
@@ -373,24 +419,27 @@ __global__ void __launch_bounds__(kThreads) k_u3_project(Lat g, double2* __restr
     atomicExch(err, 1);
     return;
   }
-  st(F, mu, g.V, n, X);
+  fst(F, mu, g.V, n, X);
 }
 
-// long_mu(n) = naik W_mu(n) W_mu(n+mu) W_mu(n+2mu), written in host order [V][4][9]
-__global__ void __launch_bounds__(kThreads) k_naik(Lat g, const double2* __restrict__ W, double naik,
+// long_mu(n) = naik W_mu(n) W_mu(n+mu) W_mu(n+2mu), written in FP64 in host order [V][4][9]
+__global__ void __launch_bounds__(kThreads) k_naik(Lat g, const float4* __restrict__ W, double naik,
                                                    double2* __restrict__ out) {
   const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int mu = blockIdx.y;
   int c[4];
   coords(g, n, c);
-  const M3 a = ld(W, mu, g.V, n);
-  const M3 b = ld(W, mu, g.V, nb(g, c, mu, 1));
-  const M3 d = ld(W, mu, g.V, nb(g, c, mu, 2));
-  const M3 p = mm(mm(a, b), d);
+  const F3 a = fld(W, mu, g.V, n);
+  const F3 b = fld(W, mu, g.V, nb(g, c, mu, 1));
+  const F3 d = fld(W, mu, g.V, nb(g, c, mu, 2));
+  const F3 p = fmm(fmm(a, b), d);
   double2* o = out + ((size_t)n * 4 + mu) * 9;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) o[e] = make_double2(naik * p.e[e].x, naik * p.e[e].y);
+  for (int e = 0; e < 9; ++e) {
+    const double2 v = join_ff(p.e[e]);
+    o[e] = make_double2(naik * v.x, naik * v.y);
+  }
 }
 
 int check_dims(const int dims[4], Lat* g) {
@@ -417,17 +466,24 @@ bool finite_level(const sqcg_smear_level& l) {
          isfinite(l.lepage);
 }
 
-// one smearing level: U (fields) -> out (fields or host order)
-int smear_level(const Lat& g, const double2* U, double2* S, double2* Z, const sqcg_smear_level& c, int aos,
-                double2* out, cudaStream_t s) {
+// a coefficient as a float-float pair (hi = fl32(c), lo = fl32(c - hi)); zero stays (0, 0)
+float2 ff_coeff(double c) {
+  const float h = (float)c;
+  return make_float2(h, (float)(c - (double)h));
+}
+
+// one smearing level: U (float-float fields) -> out (float-float fields, or FP64 host order when aos)
+int smear_level(const Lat& g, const float4* U, float4* S, float4* Z, const sqcg_smear_level& c, int aos, void* out,
+                cudaStream_t s) {
   const dim3 blk(kThreads);
   const unsigned gx = (unsigned)((g.V + kThreads - 1) / kThreads);
   const bool need_s = c.three_staple != 0.0 || c.five_staple != 0.0 || c.seven_staple != 0.0 || c.lepage != 0.0;
   const bool use_z = c.five_staple != 0.0 || c.seven_staple != 0.0;
   if (need_s) k_staple3<<<dim3(gx, 12), blk, 0, s>>>(g, U, S);
-  if (use_z) k_staple57<<<dim3(gx, 12), blk, 0, s>>>(g, U, S, c.five_staple, c.seven_staple, Z);
-  k_smear_links<<<dim3(gx, 4), blk, 0, s>>>(g, U, S, Z, c.one_link, c.three_staple, c.lepage, use_z ? 1 : 0, aos,
-                                             out);
+  if (use_z)
+    k_staple57<<<dim3(gx, 12), blk, 0, s>>>(g, U, S, ff_coeff(c.five_staple), ff_coeff(c.seven_staple), Z);
+  k_smear_links<<<dim3(gx, 4), blk, 0, s>>>(g, U, S, Z, ff_coeff(c.one_link), ff_coeff(c.three_staple),
+                                             ff_coeff(c.lepage), use_z ? 1 : 0, aos, out);
   return cudaGetLastError() == cudaSuccess ? SQCG_OK : SQCG_ERR_CUDA;
 }
 
@@ -452,10 +508,10 @@ extern "C" int sqcg_hisq_smear(const int dims[4], const void* thin, void* fat, v
   if (!finite_level(c.level1) || !finite_level(c.level2) || !isfinite(c.naik)) return SQCG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nf = 9 * (size_t)g.V;
-  double2* U = (double2*)workspace;
-  double2* S = U + 4 * nf;
-  double2* Z = S + kNumS * nf;
-  double2* W = Z + 12 * nf;
+  float4* U = (float4*)workspace;  // float-float fields, 16 bytes per complex element
+  float4* S = U + 4 * nf;
+  float4* Z = S + kNumS * nf;
+  float4* W = Z + 12 * nf;
   int* err = (int*)(W + 4 * nf);
   const unsigned gx = (unsigned)((g.V + kThreads - 1) / kThreads);
   SQCG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -464,7 +520,7 @@ extern "C" int sqcg_hisq_smear(const int dims[4], const void* thin, void* fat, v
   SQCG_TRY(smear_level(g, U, S, Z, c.level1, 0, W, s));
   k_u3_project<<<dim3(gx, 4), kThreads, 0, s>>>(g, W, err);
   SQCG_CUDA_TRY(cudaGetLastError());
-  SQCG_TRY(smear_level(g, W, S, Z, c.level2, 1, (double2*)fat, s));
+  SQCG_TRY(smear_level(g, W, S, Z, c.level2, 1, fat, s));
   k_naik<<<dim3(gx, 4), kThreads, 0, s>>>(g, W, c.naik, (double2*)lng);
   SQCG_CUDA_TRY(cudaGetLastError());
   int h_err = 0;
