@@ -30,6 +30,8 @@ int ensure_workspace(sqcg_ctx* ctx) {
             cudaMalloc((void**)&ctx->xh32, n * sizeof(float2)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->xff, n * sizeof(float4)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->partials, 4 * (size_t)ctx->max_blocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->fin_aux, 64 * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc((void**)&ctx->fin_cnt, 32 * sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc((void**)&ctx->st, sizeof(SolverState)) == cudaSuccess &&
             cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) == cudaSuccess;
   if (!ok) {
@@ -38,6 +40,7 @@ int ensure_workspace(sqcg_ctx* ctx) {
     return SQCG_ERR_NO_MEMORY;
   }
   SQCG_CUDA_TRY(cudaMemsetAsync(ctx->st, 0, sizeof(SolverState), ctx->stream));
+  SQCG_CUDA_TRY(cudaMemsetAsync(ctx->fin_cnt, 0, 32 * sizeof(unsigned), ctx->stream));
   return SQCG_OK;
 }
 
@@ -46,6 +49,9 @@ void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->r32); cudaFree(ctx->p32); cudaFree(ctx->Ap32); cudaFree(ctx->tmp32);
   cudaFree(ctx->q32); cudaFree(ctx->xh32); cudaFree(ctx->xff);
   cudaFree(ctx->partials); cudaFree(ctx->st);
+  cudaFree(ctx->fin_aux); cudaFree(ctx->fin_cnt);
+  ctx->fin_aux = nullptr;
+  ctx->fin_cnt = nullptr;
   cudaFree(ctx->pers_part); cudaFree(ctx->pers_bar);
   ctx->pers_part = nullptr;
   ctx->pers_bar = nullptr;

@@ -284,11 +284,12 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish2(SolverState* st, con
   finish_partials2(st, partials, n, fin);
 }
 
-__global__ void __launch_bounds__(kFinishThreads) k_finish_sr(SolverState* st, const double* partials, int n,
-                                                              int coff, int cn, int gate) {
+__global__ void __launch_bounds__(kFinishSRThreads) k_finish_sr(SolverState* st, const double* partials, int n,
+                                                                int coff, int cn, int gate, float2* aux,
+                                                                unsigned* cnt) {
   pdl_wait();
-  if (!gate_open(st, gate)) return;
-  finish_partials_sr(st, partials, n, coff, cn);
+  if (!gate_open(st, gate)) return;  // uniform over the grid
+  finish_partials_sr(st, partials, n, coff, cn, aux, cnt);
 }
 
 // One thread: count the WHILE-loop iterations and set its condition. The loop
@@ -343,8 +344,8 @@ int launch_finish2(sqcg_ctx* ctx, int nblocks, int fin, int gate, cudaStream_t s
 }
 
 int launch_finish_sr(sqcg_ctx* ctx, int nblocks, int coff, int cn, int gate, cudaStream_t s, bool pdl) {
-  SQCG_CUDA_TRY(launch_kernel(k_finish_sr, 1, kFinishThreads, 0, s, pdl, ctx->st, ctx->partials, nblocks, coff, cn,
-                              gate));
+  SQCG_CUDA_TRY(launch_kernel(k_finish_sr, kFinishSRBlocks, kFinishSRThreads, 0, s, pdl, ctx->st, ctx->partials,
+                              nblocks, coff, cn, gate, ctx->fin_aux, ctx->fin_cnt));
   return SQCG_OK;
 }
 

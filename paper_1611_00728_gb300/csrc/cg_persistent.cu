@@ -24,6 +24,9 @@
 // move, at most kBarrierSpins polls, after which it records the time-out, the grid leaves the loop
 // and the state reports SQCG_ERR_CUDA. The launch is cooperative, so the runtime refuses a grid
 // that cannot be resident at once instead of starting it.
+#include <stdlib.h>
+#include <string.h>
+
 #include "dslash_core.cuh"
 
 namespace {
@@ -33,7 +36,9 @@ using namespace dcore;
 // Registers for 6 resident blocks of 128 a SM (85 a thread: the Dslash phases do not spill). The
 // loop runs only where a parity has at most five 128-site tiles a SM (cg.cu), so 6 blocks a SM hold every tile.
 constexpr int kPersistentThreadsPerSM = 768;
-constexpr unsigned kBarrierSpins = 1u << 24;   // about a second of 64 ns sleeps
+// a wait gives up after this many polls, 64 ns sleeps apart: well under a second, and more than a
+// thousand times the longest phase a barrier waits for in a solve
+constexpr unsigned kBarrierSpins = 1u << 22;
 
 struct PArgs {
   DArgs<float> d1;  // tmp = D_oe r  (output parity 1, in = r, out = tmp)
@@ -49,6 +54,7 @@ struct PArgs {
   double* part;     // float-float slots: [3 G] phase-B sums, then [2][G] cross-term partials
   unsigned* bar;    // [0] arrivals, [1] generation, [2] time-out flag
   int max_steps;    // bound on the iterations of one launch (the solver state ends the loop sooner)
+  unsigned arrivals;  // blocks a barrier waits for: the grid (one more only in the time-out test)
 };
 
 // Grid-wide barrier with release/acquire fences; false when a wait timed out (here or elsewhere).
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(PT, kPersistentThreadsPerSM / PT) k_sr_persist
           for (int c = 0; c < 3; ++c) a.tmp[(size_t)c * Vh + i] = acc[c];
         }
       }
-      if (!grid_barrier(a.bar, G)) { timed_out = true; break; }
+      if (!grid_barrier(a.bar, a.arrivals)) { timed_out = true; break; }
       // B: s = sigma r - D_eo tmp with <r,s>, |r|^2 and, after a reliable update, <r,q>
       const bool after = ss.after_update != 0;
       const float sig = (float)ss.sigma;
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(PT, kPersistentThreadsPerSM / PT) k_sr_persist
         slot[G + blockIdx.x] = tot[1];
         slot[2 * G + blockIdx.x] = tot[2];
       }
-      if (!grid_barrier(a.bar, G)) { timed_out = true; break; }
+      if (!grid_barrier(a.bar, a.arrivals)) { timed_out = true; break; }
       // C: the step's sums, in the same order in every block, and the scalar step on the block's copy
       double d, c, g;
       ffs_sum_partials3(a.part, 0, after ? G : 3 * G + (n & 1) * G, G, 2 * G, G, d, c, g);
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(PT, kPersistentThreadsPerSM / PT) k_sr_persist
       }
       block_sum_ffs<1>(cross);
       if (threadIdx.x == 0) ffs_slots(cpart)[(size_t)((n + 1) & 1) * G + blockIdx.x] = cross[0];
-      if (!grid_barrier(a.bar, G)) { timed_out = true; break; }
+      if (!grid_barrier(a.bar, a.arrivals)) { timed_out = true; break; }
     }
   }
   if (blockIdx.x != 0) return;
@@ -303,6 +309,10 @@ int launch_sr_persistent(sqcg_ctx* ctx, int max_steps, cudaStream_t s) {
   a.part = ctx->pers_part;
   a.bar = ctx->pers_bar;
   a.max_steps = max_steps;
+  // SQCG_TEST_BARRIER_TIMEOUT=1 makes every barrier wait for one block more than the grid has, so each
+  // wait runs out: the test of the bounded waits (the solve then returns SQCG_ERR_CUDA, nothing hangs)
+  const char* t = getenv("SQCG_TEST_BARRIER_TIMEOUT");
+  a.arrivals = (unsigned)G + ((t && strcmp(t, "1") == 0) ? 1u : 0u);
   SQCG_CUDA_TRY(cudaMemsetAsync(ctx->pers_bar, 0, 4 * sizeof(unsigned), s));
   void* args[] = {&a};
   SQCG_CUDA_TRY(cudaLaunchCooperativeKernel(persistent_kernel(ctx), dim3(G), dim3(kPT), args, 0, s));

@@ -257,6 +257,10 @@ __device__ __forceinline__ void block_partial(double v, double* partials) {
 
 // Second stage: one block of kFinishThreads threads (each adds only a few partials).
 constexpr int kFinishThreads = 1024;
+// the single-reduction step's finisher: a few blocks share the partial sums (finish_partials_sr)
+constexpr int kFinishSRBlocks = 8;
+constexpr int kFinishSRThreads = 256;
+static_assert(3 * kFinishSRBlocks <= 64, "the finisher's per-block slots (fin_aux holds 64)");
 
 __device__ __forceinline__ void finish_partials(SolverState* st, const double* partials, int n, int fin) {
   double s = 0.0;
@@ -369,8 +373,8 @@ __device__ __forceinline__ void block_sum_ffs(float2 (&v)[N]) {
 // Three float-float sums over slots [o0, o0 + n), [o1, o1 + n1), [o2, o2 + n) of ffs partials, each
 // thread taking every blockDim.x-th slot into four interleaved accumulators (four rows of loads in
 // flight), merged in a fixed order; then the block tree. Totals in thread 0 as FP64.
-__device__ __forceinline__ void ffs_sum_partials3(const double* partials, int o0, int o1, int n1, int o2, int n,
-                                                  double& a, double& b, double& c) {
+__device__ __forceinline__ void ffs_block_sums3(const double* partials, int o0, int o1, int n1, int o2, int n,
+                                                float2 (&v)[3]) {
   const float2* p = ffs_slots(partials);
   const int bd = blockDim.x;
   float2 z = make_float2(0.f, 0.f);
@@ -395,10 +399,16 @@ __device__ __forceinline__ void ffs_sum_partials3(const double* partials, int o0
 #pragma unroll
   for (int u = 0; u < 3; ++u)
     if (j + u * bd < n1) b4[u] = ffs_add(b4[u], p[o1 + j + u * bd]);
-  float2 v[3] = {ffs_add(ffs_add(a4[0], a4[1]), ffs_add(a4[2], a4[3])),
-                 ffs_add(ffs_add(b4[0], b4[1]), ffs_add(b4[2], b4[3])),
-                 ffs_add(ffs_add(c4[0], c4[1]), ffs_add(c4[2], c4[3]))};
+  v[0] = ffs_add(ffs_add(a4[0], a4[1]), ffs_add(a4[2], a4[3]));
+  v[1] = ffs_add(ffs_add(b4[0], b4[1]), ffs_add(b4[2], b4[3]));
+  v[2] = ffs_add(ffs_add(c4[0], c4[1]), ffs_add(c4[2], c4[3]));
   block_sum_ffs<3>(v);
+}
+
+__device__ __forceinline__ void ffs_sum_partials3(const double* partials, int o0, int o1, int n1, int o2, int n,
+                                                  double& a, double& b, double& c) {
+  float2 v[3];
+  ffs_block_sums3(partials, o0, o1, n1, o2, n, v);
   a = ffs_value(v[0]);
   b = ffs_value(v[1]);
   c = ffs_value(v[2]);
@@ -435,13 +445,35 @@ __device__ __forceinline__ void finish_partials_ffs(SolverState* st, const doubl
   }
 }
 
-// the single-reduction step: d = sum of slots [0, n), c = sum of [coff, coff + cn), g = sum of
-// [2n, 3n) (ffs partials)
-__device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff,
-                                                   int cn) {
-  double d, c, g;
-  ffs_sum_partials3(partials, 0, coff, cn, 2 * n, n, d, c, g);
-  if (threadIdx.x == 0) sr_step(st, d, c, g);
+// The single-reduction step's finisher, spread over the blocks of its grid: d = sum of slots [0, n),
+// c = sum of [coff, coff + cn), g = sum of [2n, 3n) (ffs partials). Block b adds the b-th of gridDim.x
+// equal contiguous ranges of each; the last block to arrive (an atomic counter, after a fence; a
+// handful of arrivals) adds the blocks' totals in block order and runs the scalar step. The ranges and
+// both orders are fixed, so the result does not depend on which block comes last. aux holds 3 slots a
+// block; *cnt is zero before and after.
+__device__ __forceinline__ void finish_partials_sr(SolverState* st, const double* partials, int n, int coff, int cn,
+                                                   float2* aux, unsigned* cnt) {
+  const int b = blockIdx.x, nb = gridDim.x;
+  const int a0 = (int)((long)n * b / nb), a1 = (int)((long)n * (b + 1) / nb);
+  const int c0 = (int)((long)cn * b / nb), c1 = (int)((long)cn * (b + 1) / nb);
+  float2 v[3];
+  ffs_block_sums3(partials, a0, coff + c0, c1 - c0, 2 * n + a0, a1 - a0, v);  // v = {d, c, g} of the range
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) aux[3 * b + k] = v[k];
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == (unsigned)nb - 1u;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  float2 t[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int j = 0; j < nb; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = ffs_add(t[k], __ldcg(&aux[3 * j + k]));
+  *cnt = 0u;
+  sr_step(st, ffs_value(t[0]), ffs_value(t[1]), ffs_value(t[2]));
 }
 
 __device__ __forceinline__ void finish_partials2(SolverState* st, const double* partials, int n, int fin) {

@@ -187,6 +187,8 @@ struct sqcg_ctx {
   float2 *q32, *xh32;  // single-reduction mixed CG: q = A p, and the FP32 partial solution
   float4* xff;         // float-float copy of x for the reliable update (its odd intermediate lives in tmp64)
   double* partials;    // 4 * max_blocks: three sums of a Dslash epilogue, then the update kernel's sum
+  float2* fin_aux;     // the single-reduction finisher's per-block totals (3 float-float slots a block)
+  unsigned* fin_cnt;   // ... and its arrival counter (zero between launches)
   int max_blocks;
   int blas_grid;  // blocks of the streaming BLAS kernels (0 until first use)
   int pers_grid;        // blocks of the persistent CG loop (0 until first use, -1 unavailable)

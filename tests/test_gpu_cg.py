@@ -7,6 +7,8 @@ oracle's tightly converged solution; for ill-conditioned systems the check is
 the residual, which is the well-posed form of "within 10 tol" (|A(x - x*)| / |b|).
 """
 
+import time
+
 import numpy as np
 import pytest
 
@@ -294,6 +296,31 @@ def test_loop_form_follows_lattice_size(sqcg, links_cache, monkeypatch):
     small, large = launches[(8, 10, 12, 14)], launches[(32, 32, 32, 32)]
     assert small[0] < 40, small
     assert large[0] > 3 * large[1], large
+
+
+def test_persistent_barrier_timeout_returns_an_error(sqcg, links_cache, monkeypatch):
+    """Every wait of the persistent loop is bounded. With each grid barrier made to wait for one block more
+    than the grid holds (a count nothing reaches), the waits run out, the kernel records the time-out and
+    returns, and the solve reports SQCG_ERR_CUDA instead of hanging; the context then solves normally."""
+    L, m, tol = (8, 8, 8, 8), 0.05, 1e-9
+    fat, lng = links_cache(L, 88)
+    b = synth.gaussian_source(L, 4)
+    monkeypatch.setenv("SQCG_PERSISTENT", "1")
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        db = lat.pack(b)
+        monkeypatch.setenv("SQCG_TEST_BARRIER_TIMEOUT", "1")
+        t0 = time.perf_counter()
+        info = lat.cg_solve(m, db, lat.new_spinor(), tol=tol, max_iter=1000, mode=1, raise_on_error=False)
+        waited = time.perf_counter() - t0
+        monkeypatch.delenv("SQCG_TEST_BARRIER_TIMEOUT")
+        assert info.status == -2, info.status
+        assert waited < 30.0, waited
+        dx = lat.new_spinor()
+        info = lat.cg_solve(m, db, dx, tol=tol, max_iter=1000, mode=1)
+        x = lat.unpack(dx)
+    assert info.status == 0
+    assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, x) <= tol
 
 
 def test_persistent_loop_ends_on_max_iter(sqcg, links_cache, monkeypatch):
