@@ -383,7 +383,7 @@ int sqcg_batched_tuning_ex(const sqcg_ctx* ctx, int* W, int* WT, int* T, int* ca
 /* Pin the FP32 Dslash configuration of batched solves planned from now on in
  * this process instead of autotuning it (plans already cached with a context
  * keep theirs); W = 0 returns to autotuning. Requirements: W in {1, 2, 4, 8,
- * 16}; WT in {1, 2, 4}, WT <= W; T a multiple of 32 in [32, 128] with
+ * 12, 16}; WT in {1, 2, 4}, WT <= W and dividing W; T a multiple of 32 in [32, 128] with
  * T * W / WT <= 512; carve -1 or 0..100; warp_sites 32 (or 0, the same) or 16
  * with W / WT even. SQCG_ERR_INVALID_ARG otherwise (nothing changes).
  * Thread-safe. */

@@ -1361,7 +1361,9 @@ int autotune(BatchPlan& P, cudaStream_t s) {
   SQCG_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
   TuneChoice bestc = {1, 1, 128, -1, 32};
-  const int Ws[] = {1, 2, 4, 8, 16};
+  // 12 for batches of 9 to 12 right-hand sides (the 11-shift refinement, 12-pole rational
+  // functions), where a block of 16 would leave a quarter of its RHS groups empty
+  const int Ws[] = {1, 2, 4, 8, 12, 16};
   const int WTs[] = {1, 2, 4};
   const int Ts[] = {32, 64, 128, 256};
   int rc = SQCG_OK;
@@ -1825,7 +1827,7 @@ extern "C" int sqcg_batched_pin_tuning(int W, int WT, int T, int carve, int warp
     return SQCG_OK;
   }
   if (warp_sites == 0) warp_sites = 32;
-  if ((W != 1 && W != 2 && W != 4 && W != 8 && W != 16) || (WT != 1 && WT != 2 && WT != 4) || WT > W)
+  if ((W != 1 && W != 2 && W != 4 && W != 8 && W != 12 && W != 16) || (WT != 1 && WT != 2 && WT != 4) || WT > W)
     return SQCG_ERR_INVALID_ARG;
   if (!smem_shape_ok(W, WT, T, warp_sites)) return SQCG_ERR_INVALID_ARG;
   if (carve < -1 || carve > 100) return SQCG_ERR_INVALID_ARG;

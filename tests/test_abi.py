@@ -118,12 +118,14 @@ def test_batched_pin_tuning_checks(libpath):
     pin = lib.sqcg_batched_pin_tuning
     pin.argtypes = [ctypes.c_int] * 5
     bad = [(3, 1, 64, -1, 32), (4, 8, 64, -1, 32), (2, 4, 64, -1, 32), (4, 3, 64, -1, 32),  # W, WT
+           (6, 2, 32, -1, 32), (12, 8, 32, -1, 32), (24, 2, 32, -1, 32),
            (4, 1, 48, -1, 32), (4, 1, 256, -1, 32), (16, 1, 64, -1, 32),  # T: multiple of 32, <= 128, T W/WT <= 512
            (4, 1, 64, 101, 32), (4, 1, 64, -2, 32),  # carveout
            (4, 4, 64, -1, 16), (8, 2, 32, -1, 8), (2, 1, 32, -1, 24)]  # warp_sites: 16 needs W / WT even
     for args in bad:
         assert pin(*args) == -1, args
-    for args in [(1, 1, 32, -1, 32), (16, 4, 128, 50, 0), (8, 4, 128, -1, 16), (16, 2, 64, 25, 16), (2, 1, 32, -1, 16)]:
+    for args in [(1, 1, 32, -1, 32), (16, 4, 128, 50, 0), (8, 4, 128, -1, 16), (16, 2, 64, 25, 16), (2, 1, 32, -1, 16),
+                 (12, 2, 64, -1, 16), (12, 4, 128, -1, 32)]:
         assert pin(*args) == 0, args
     assert pin(0, 0, 0, 0, 0) == 0  # back to autotuning
 

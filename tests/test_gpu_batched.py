@@ -37,7 +37,7 @@ def test_batched_small_uneven(sqcg, links_cache, recon):
         lats.append(lat); bs.append(b); xs.append(x); srcs.append(s); links.append((fat, lng))
     infos = sqcg.cg_solve_batched(lats, [m for _, _, m in specs], bs, xs, tol=tol, max_iter=5000)
     W, T = sqcg.batched_tuning(lats[0])
-    assert W in (1, 2, 4, 8, 16) and T in (32, 64, 128, 256)
+    assert W in (1, 2, 4, 8, 12, 16) and T in (32, 64, 128, 256)
     for n, (L, nr, m) in enumerate(specs):
         fat, lng = links[n]
         for j in range(nr):
@@ -158,10 +158,12 @@ def test_batched_from_two_host_threads(sqcg, links_cache):
                                  dict(W=16, WT=4, T=64, carve=50, warp_sites=32),
                                  dict(W=16, WT=4, T=128, carve=-1, warp_sites=16),
                                  dict(W=2, WT=2, T=32, carve=25, warp_sites=32),
-                                 dict(W=4, WT=4, T=32, carve=-1, warp_sites=32)])
+                                 dict(W=4, WT=4, T=32, carve=-1, warp_sites=32),
+                                 dict(W=12, WT=2, T=32, carve=-1, warp_sites=16),
+                                 dict(W=12, WT=4, T=64, carve=-1, warp_sites=32)])
 def test_batched_pinned_configurations(sqcg, links_cache, cfg):
     """Every FP32 Dslash instantiation (1, 2 or 4 RHS per thread; warps of 32 sites of one RHS group or 16 sites
-    of two), pinned instead of tuned, on an uneven batch with a ragged RHS block and a 12-real long-link
+    of two; block widths W of powers of two and 12), pinned instead of tuned, on an uneven batch with a ragged RHS block and a 12-real long-link
     lattice: each RHS reaches tol on the oracle."""
     specs = [((8, 8, 8, 8), 5, 0.1), ((6, 8, 10, 12), 3, 0.05), ((4, 4, 4, 8), 1, 0.2)]
     tol = 1e-9
