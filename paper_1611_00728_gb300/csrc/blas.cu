@@ -16,9 +16,11 @@ template <typename R> struct V2;
 template <> struct V2<double> { typedef double2 T; };
 template <> struct V2<float> { typedef float2 T; };
 
-// x += alpha p (x FP64); r -= alpha Ap; reduce |r|^2 -> FIN_UPDATE
+// x += alpha p (x FP64); r -= alpha Ap; reduce |r|^2 -> FIN_UPDATE. Held to 5 blocks of 256 a SM: the
+// one-wave grid of blas_grid() is sized by this kernel's FP32 instance, and the FP64 one (64 registers
+// unbounded) would run it as 1.25 waves.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
 k_cg_update(double2* __restrict__ x, typename V2<R>::T* __restrict__ r, const typename V2<R>::T* __restrict__ p,
             const typename V2<R>::T* __restrict__ Ap, int Vh, SolverState* st, double* partials) {
   typedef typename V2<R>::T R2;
@@ -83,8 +85,10 @@ k_cg_xpay(const typename V2<R>::T* __restrict__ r, typename V2<R>::T* __restrict
 //   p = r + beta p,  q = s + beta q  (= A p),  xh += alpha p,  r -= alpha q,
 // and the block partials of Re<r_new, q_new>, the next step's cross term (the next Dslash epilogue then
 // reads only r). xh is the FP32 partial solution, flushed into the FP64 x at every reliable update.
-// Skipped (uniformly) when the step before it asked for a reliable update or ended the solve.
-__global__ void __launch_bounds__(kThreads)
+// Skipped (uniformly) when the step before it asked for a reliable update or ended the solve. Held to
+// the residency of k_cg_update (5 blocks of 256 a SM), which sizes the one-wave grid of blas_grid():
+// with 64 registers it fit 4, and that grid ran as 1.25 waves.
+__global__ void __launch_bounds__(kThreads, 5)
 k_sr_update(float2* __restrict__ r, const float2* __restrict__ sv, float2* __restrict__ p, float2* __restrict__ q,
             float2* __restrict__ xh, int Vh, SolverState* st, double* cpart) {
   pdl_wait();

@@ -1021,8 +1021,9 @@ int sqcg_nn_train(sqcg_nn* nn, double sigma, int npairs, const void* r, const vo
 // ---------------------------------------------------------------------------
 namespace {
 
-// r_old = r; x += alpha p (x FP64); r -= alpha q; |r|^2 partials
-__global__ void __launch_bounds__(kRedThreads) k_fcg_update(double2* __restrict__ x, float2* __restrict__ r,
+// r_old = r; x += alpha p (x FP64); r -= alpha q; |r|^2 partials. Held to 5 blocks a SM, the residency that
+// sizes the one-wave grid of blas_grid() (56 registers unbounded fit 4: 1.25 waves).
+__global__ void __launch_bounds__(kRedThreads, 5) k_fcg_update(double2* __restrict__ x, float2* __restrict__ r,
                                                             float2* __restrict__ r_old, const float2* __restrict__ p,
                                                             const float2* __restrict__ q, int Vh, SolverState* st,
                                                             double* partials) {
