@@ -298,6 +298,30 @@ def test_loop_form_follows_lattice_size(sqcg, links_cache, monkeypatch):
     assert large[0] > 3 * large[1], large
 
 
+def test_programmatic_dependent_launch_changes_nothing(sqcg, links_cache, monkeypatch):
+    """The graph loops with and without programmatic dependent launch (SQCG_PDL=0, read when a context is
+    created) run the same kernels on the same data: identical iterates, bit for bit."""
+    L, m = (8, 10, 12, 14), 0.02
+    fat, lng = links_cache(L, 88)
+    b = synth.gaussian_source(L, 4)
+    monkeypatch.setenv("SQCG_PERSISTENT", "0")
+    out = {}
+    for pdl in ("1", "0"):
+        monkeypatch.setenv("SQCG_PDL", pdl)
+        with sqcg.Lattice(L) as lat:
+            lat.load_links(fat, lng, recon12=True)
+            db = lat.pack(b)
+            dx = lat.new_spinor()
+            info = lat.cg_solve(m, db, dx, tol=1e-10, max_iter=5000, mode=1)
+            xs = [lat.new_spinor() for _ in range(3)]
+            ms = lat.multishift_cg_solve([0.01, 0.1, 1.0], db, xs, tol=1e-9, mode=1)
+            out[pdl] = (info.iters, lat.unpack(dx), [i.iters for i in ms], [lat.unpack(x) for x in xs])
+    a, c = out["1"], out["0"]
+    assert a[0] == c[0] and a[2] == c[2]
+    assert np.array_equal(a[1], c[1])
+    assert all(np.array_equal(u, v) for u, v in zip(a[3], c[3]))
+
+
 def test_persistent_barrier_timeout_returns_an_error(sqcg, links_cache, monkeypatch):
     """Every wait of the persistent loop is bounded. With each grid barrier made to wait for one block more
     than the grid holds (a count nothing reaches), the waits run out, the kernel records the time-out and
