@@ -85,7 +85,9 @@ extern "C" {
 
 /* ---- solver modes ---- */
 #define SQCG_MODE_F64 0   /* everything in FP64 */
-#define SQCG_MODE_MIXED 1 /* FP32 Dslash and vectors, FP64 x, reductions and reliable updates */
+#define SQCG_MODE_MIXED 1 /* FP32 Dslash and vectors; FP64 x and scalars; grid sums in float-float;
+                             true residuals of the reliable updates in float-float (SQCG_FF, default) or
+                             FP64 arithmetic, summed in FP64 */
 
 typedef struct sqcg_ctx sqcg_ctx; /* opaque, library-owned */
 
@@ -195,8 +197,15 @@ int sqcg_normal_op_noalloc(sqcg_ctx* ctx, double sigma, int prec, const void* x,
  * Stops when the FP64
  * true relative residual |b - A x|/|b| <= tol, or after max_iter iterations
  * (SQCG_ERR_NOT_CONVERGED, x = last iterate). mode: SQCG_MODE_F64 or
- * SQCG_MODE_MIXED (FP32 Krylov vectors with FP64 reliable updates). info may
- * be NULL. Synchronises the stream. */
+ * SQCG_MODE_MIXED (FP32 Krylov vectors with reliable updates). The FP64 mode
+ * runs as one CUDA graph launch; the mixed mode too (eight steps per WHILE
+ * pass), except on lattices of at most five 128-site tiles per SM, where one
+ * persistent cooperative kernel runs each segment between reliable updates
+ * (environment SQCG_PERSISTENT=0 or 1 forces one form; SQCG_LAUNCH_MODE=eager
+ * launches the graph's kernels one at a time, for profilers; SQCG_PDL=0, read
+ * when a context is created, launches without programmatic dependent launch).
+ * A persistent grid barrier that waits past its bound ends the solve with
+ * SQCG_ERR_CUDA. info may be NULL. Synchronises the stream. */
 int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol, int max_iter,
                   int mode, sqcg_info* info);
 
