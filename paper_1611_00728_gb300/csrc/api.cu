@@ -52,7 +52,8 @@ void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->fin_aux); cudaFree(ctx->fin_cnt);
   ctx->fin_aux = nullptr;
   ctx->fin_cnt = nullptr;
-  cudaFree(ctx->pers_part); cudaFree(ctx->pers_bar);
+  cudaFree(ctx->pers_part); cudaFree(ctx->pers_bar); cudaFree(ctx->pers_rq);
+  ctx->pers_rq = nullptr;
   ctx->pers_part = nullptr;
   ctx->pers_bar = nullptr;
   ctx->pers_grid = 0;

@@ -109,8 +109,25 @@ struct DArgs {
 
 // D at output site i of parity a.par; returns the three colour components.
 // EIGHT: the backward links are read, already daggered and negated, at i.
+// The input vector at a site: plain loads of a.in (the kernels), or another functor with
+// operator()(R2 (&v)[3], int idx) (the persistent CG forms its input on the fly).
+template <typename R2, bool NC>
+struct PlainIn {
+  const R2* in;
+  int Vh;
+  __device__ __forceinline__ void operator()(R2 (&v)[3], int idx) const { load_vec<NC>(v, in, Vh, idx); }
+};
+
+template <typename R, bool RECON, bool EIGHT, typename In>
+__device__ __forceinline__ void dslash_site_in(const DArgs<R>& a, int i, typename V2<R>::T (&acc)[3], const In& in_at);
+
 template <typename R, bool RECON, bool EIGHT, bool NC = true>
 __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V2<R>::T (&acc)[3]) {
+  dslash_site_in<R, RECON, EIGHT>(a, i, acc, PlainIn<typename V2<R>::T, NC>{a.in, a.g.Vh});
+}
+
+template <typename R, bool RECON, bool EIGHT, typename In>
+__device__ __forceinline__ void dslash_site_in(const DArgs<R>& a, int i, typename V2<R>::T (&acc)[3], const In& in_at) {
   typedef typename V2<R>::T R2;
   const Geom& g = a.g;
   const int Vh = g.Vh;
@@ -162,9 +179,9 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
       }
       if (k == 0) {
         load_link<R, R2, false>(U, a.fat_p + (size_t)mu * 9 * Vh, Vh, i, R(1));
-        load_vec<NC>(v, a.in, Vh, fwd);
+        in_at(v, fwd);
         acc_mv<R>(acc, U, v);
-        load_vec<NC>(v, a.in, Vh, bwd);
+        in_at(v, bwd);
         if (EIGHT) {
           load_link<R, R2, false>(U, a.fatb_p + (size_t)mu * 9 * Vh, Vh, i, R(1));
           acc_mv<R>(acc, U, v);
@@ -174,9 +191,9 @@ __device__ __forceinline__ void dslash_site(const DArgs<R>& a, int i, typename V
         }
       } else {
         load_link<R, R2, RECON>(U, a.lng_p + (size_t)mu * a.nl * Vh, Vh, i, inv_s_f);
-        load_vec<NC>(v, a.in, Vh, fwd);
+        in_at(v, fwd);
         acc_mv<R>(acc, U, v);
-        load_vec<NC>(v, a.in, Vh, bwd);
+        in_at(v, bwd);
         if (EIGHT) {  // -L^+ = (-s) V^+: its third row is rebuilt with the scale -s
           load_link<R, R2, RECON>(U, a.lngb_p + (size_t)mu * a.nl * Vh, Vh, i, -inv_s_b);
           acc_mv<R>(acc, U, v);

@@ -194,6 +194,7 @@ struct sqcg_ctx {
   int pers_grid;        // blocks of the persistent CG loop (0 until first use, -1 unavailable)
   double* pers_part;    // its partial sums: [3][pers_grid] step sums, [2][pers_grid] cross terms
   unsigned* pers_bar;   // its grid-barrier words
+  float2* pers_rq;      // its second buffers of r and q ([3][Vh] each)
   SolverState* st;       // device
   SolverState* st_host;  // pinned host mirror
 
