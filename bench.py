@@ -237,7 +237,7 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-DSLASH_SOURCES = ("dslash.cu", "solver_device.cuh", "sqcg_internal.cuh")  # what k_dslash is compiled from
+DSLASH_SOURCES = ("dslash_core.cuh", "dslash.cu", "solver_device.cuh", "sqcg_internal.cuh")  # what k_dslash is compiled from
 
 
 def sources_sha256() -> str:
@@ -964,8 +964,8 @@ TRAIN_STEPS_PER_FIELD = 60
 
 
 def train_network(torch, sq, log=None):
-    """Train the network at 16^4 on about 10^4 CG pairs (R13 of the design notes: iterates well before
-    convergence against an FP64 x* solved to 1e-13, A^2-norm loss). Returns (params, record)."""
+    """Train the network at 16^4 on about 10^4 CG pairs: CG iterates well before convergence, each against
+    an FP64 x* solved to 1e-13, with the A^2-norm loss. Returns (params, record)."""
     import synth
 
     m, sigma = LEARNED_MASS, 4 * LEARNED_MASS ** 2
