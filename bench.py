@@ -728,7 +728,12 @@ def measure_learned(torch, sq, clk, L, params, steps, compare=True, tag="learned
     b = lat.pack(synth.gaussian_source(L, LEARNED_HELD_OUT[1]))
     x = lat.new_spinor()
     out = {}
-    solvers = [("fcg_nn", lambda: net.fcg_solve(m, b, x, tol=TOL, max_iter=50000))]
+    def fcg(mix):
+        net.set_mixing(mix)
+        return net.fcg_solve(m, b, x, tol=TOL, max_iter=50000)
+
+    # the network's inference 8 -> 8 mixing in FP32 on the CUDA cores (default), and in BF16 on the tensor cores
+    solvers = [("fcg_nn", lambda: fcg(sq.NN_MIX_FP32)), ("fcg_nn_bf16_mixing", lambda: fcg(sq.NN_MIX_BF16))]
     if compare:
         solvers += [("mixed_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_MIXED)),
                     ("fp64_cg", lambda: lat.cg_solve(m, b, x, tol=TOL, max_iter=50000, mode=sq.MODE_F64))]
@@ -743,6 +748,7 @@ def measure_learned(torch, sq, clk, L, params, steps, compare=True, tag="learned
     if compare:
         out["speedup_vs_fp64_cg"] = out["fp64_cg"]["ms"] / out["fcg_nn"]["ms"]
         out["speedup_vs_mixed_cg"] = out["mixed_cg"]["ms"] / out["fcg_nn"]["ms"]
+        out["bf16_mixing_speedup_vs_mixed_cg"] = out["mixed_cg"]["ms"] / out["fcg_nn_bf16_mixing"]["ms"]
     net.close()
     lat.close()
     return out

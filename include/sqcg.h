@@ -300,6 +300,15 @@ int sqcg_nn_set_params(sqcg_nn* nn, const float* params);
 int sqcg_nn_get_params(const sqcg_nn* nn, float* params, int bf16_rounded);
 /* z = N(r). Asynchronous. */
 int sqcg_nn_apply(sqcg_nn* nn, const void* r, void* z);
+/* Arithmetic of the 8 -> 8 layer's channel mixing in inference (sqcg_nn_apply and the flexible
+ * CG): SQCG_NN_MIX_FP32 (default; FP32 on the CUDA cores, the results of the training forward pass)
+ * or SQCG_NN_MIX_BF16 (warp-level tensor-core MMAs, m16n8k16: the transported activations rounded
+ * to BF16, the BF16 weights as they are, FP32 accumulation; a relative change of the layer's output
+ * of order 2^-9). Training always uses FP32. A captured flexible-CG loop is recaptured after a
+ * change. SQCG_ERR_INVALID_ARG for another mode. */
+#define SQCG_NN_MIX_FP32 0
+#define SQCG_NN_MIX_BF16 1
+int sqcg_nn_set_mixing(sqcg_nn* nn, int mode);
 /* Training loss of one (residual r, error e) pair, d = N(r) - e,
  * A = sigma - D_eo D_oe, in the norm chosen by sqcg_nn_set_loss:
  *   1 (default): L = <d, A d> / <e, r>  (A-norm of the error relative to that of e)

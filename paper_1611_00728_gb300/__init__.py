@@ -27,6 +27,7 @@ __all__ = [
 ]
 
 F64, F32, FF = 0, 1, 2  # FF: float-float (hi, lo floats per real), device vectors (3, Vh, 4) float32
+NN_MIX_FP32, NN_MIX_BF16 = 0, 1  # arithmetic of the inference 8 -> 8 channel mixing (sqcg_nn_set_mixing)
 MODE_F64, MODE_MIXED = 0, 1
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
@@ -139,6 +140,7 @@ def library():
         lib.sqcg_nn_get_params.argtypes = [P, P, I]
         lib.sqcg_nn_apply.argtypes = [P, P, P]
         lib.sqcg_nn_set_loss.argtypes = [P, I]
+        lib.sqcg_nn_set_mixing.argtypes = [P, I]
         lib.sqcg_nn_loss_grad.argtypes = [P, D, P, P, ctypes.POINTER(D), P]
         lib.sqcg_nn_train.argtypes = [P, D, I, P, P, I, I, D, ctypes.c_ulonglong, ctypes.POINTER(D),
                                       ctypes.POINTER(D)]
@@ -155,7 +157,7 @@ def library():
                      "sqcg_load_links",
                      "sqcg_pack_spinor", "sqcg_unpack_spinor", "sqcg_dslash", "sqcg_normal_op", "sqcg_cg_solve",
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
-                     "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_loss_grad", "sqcg_nn_train",
+                     "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_set_mixing", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
                      "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply",
                      "sqcg_batched_tuning_ex", "sqcg_batched_pin_tuning",
@@ -466,6 +468,10 @@ class Network:
     def set_loss(self, norm: int):
         """Training loss norm: 1 = A-norm of the error (default), 2 = A^2-norm (preconditioned residual)."""
         _check(library().sqcg_nn_set_loss(self._h, int(norm)), "sqcg_nn_set_loss")
+
+    def set_mixing(self, mode: int):
+        """Inference 8 -> 8 channel mixing: NN_MIX_FP32 (CUDA cores, default) or NN_MIX_BF16 (tensor cores)."""
+        _check(library().sqcg_nn_set_mixing(self._h, int(mode)), "sqcg_nn_set_mixing")
 
     def apply(self, r, z):
         lat = self.lattice

@@ -386,6 +386,146 @@ __global__ void __launch_bounds__(kThreads, 5) k_conv88(ConvArgs a) {
   }
 }
 
+// The 8 -> 8 inference layer with its channel mixing on the tensor cores (BF16 operands, FP32
+// accumulation): for each colour the mixing of one tap is a real GEMM of 16 sites x 16 inputs (8 channels,
+// re and im) by 16 x 16 (8 output channels, re and im; a complex weight w acts on (re, im) as the 2 x 2 block
+// [[w.x, w.y], [-w.y, w.x]]), one m16n8k16 warp MMA per colour and 8-column half. A warp takes 16 sites; lane
+// (g, t) = (lane / 4, lane % 4) transports input channels t and t + 4 of sites g and g + 8 on the CUDA cores,
+// which are exactly the elements of the MMA's A fragment it holds (rows g, g + 8; columns 2t, 2t + 1 and
+// 2t + 8, 2t + 9), and receives output channels t and t + 4 of the same sites in its accumulator fragment,
+// so nothing is exchanged between lanes. The transported vectors are rounded to BF16 (the weights are BF16
+// values already); sums and the gate are FP32.
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+               "{%0, %1, %2, %3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kThreads, 4) k_conv88_tc(ConvArgs a) {
+  if (a.st && !gate_open(a.st, a.gate)) return;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  const int lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3;
+  const long base = ((long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16;
+  const long nsites = (long)a.npar * Vh;
+  // B fragments of every tap: rows k = 2 ci + comp (ci = tq, tq + 4), column n = g of each 8-column half,
+  // i.e. output channel o = 4 nt + g / 2, component g % 2
+  unsigned bf[NT][2][2];
+#pragma unroll
+  for (int tap = 0; tap < NT; ++tap)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int o = 4 * nt + (gq >> 1), oc = gq & 1;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const float2 w = a.W[(tap * CH + o) * CH + tq + 4 * half];
+        // (re, im) input component -> output component oc: re: (w.x, -w.y); im: (w.y, w.x)
+        bf[tap][nt][half] = oc == 0 ? pack_bf16(w.x, -w.y) : pack_bf16(w.y, w.x);
+      }
+    }
+  // this lane's two sites (rows g and g + 8 of the warp's 16)
+  int par[2], idx[2];
+  bool ok[2];
+  Site st2[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const long site = base + gq + 8 * r;
+    ok[r] = site < nsites;
+    const long sv = ok[r] ? site : 0;
+    par[r] = a.par0 + (int)(sv / Vh);
+    idx[r] = (int)(sv % Vh);
+    st2[r] = site_of(g, idx[r], par[r]);
+  }
+  float acc[3][2][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[c][nt][e] = 0.f;
+  // t[r][h][c]: the tap's input channel tq + 4 h at site r, colour c
+  auto mma_tap = [&](int tap, const float2 (&t)[2][2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const unsigned af[4] = {pack_bf16(t[0][0][c].x, t[0][0][c].y), pack_bf16(t[1][0][c].x, t[1][0][c].y),
+                              pack_bf16(t[0][1][c].x, t[0][1][c].y), pack_bf16(t[1][1][c].x, t[1][1][c].y)};
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(acc[c][nt], af, bf[tap][nt][0], bf[tap][nt][1]);
+    }
+  };
+  // self tap
+  {
+    float2 t[2][2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          t[r][h][c] = ok[r] ? __ldg(a.in + (((size_t)(tq + 4 * h) * 2 + par[r]) * 3 + c) * Vh + idx[r])
+                             : make_float2(0.f, 0.f);
+    mma_tap(0, t);
+  }
+  // hops: each lane transports its two channels at its two sites
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      float2 t[2][2][3];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = 1 - par[r];
+        const int j = nbr(g, st2[r], mu, dir == 0 ? +1 : -1);
+        float2 u[9];
+        if (dir == 0) load_link9(a.fat[par[r]] + (size_t)mu * 9 * Vh, Vh, idx[r], u);  // F_mu(n)
+        else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);                     // F_mu(n - mu)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float2 v[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)(tq + 4 * h) * 2 + q) * 3 + c) * Vh + j);
+          apply_link(u, dir == 1, v, t[r][h]);
+          if (!ok[r])
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[r][h][c] = make_float2(0.f, 0.f);
+        }
+      }
+      mma_tap(1 + 2 * mu + dir, t);
+    }
+  }
+  // epilogue: accumulator element (row g or g + 8, column 2 tq + {0, 1}) of half nt is output channel
+  // o = 4 nt + tq, (re, im), at site r
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (!ok[r]) continue;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int o = 4 * nt + tq;
+      float2 v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] = make_float2(acc[c][nt][2 * r], acc[c][nt][2 * r + 1]);
+      float gf = 1.f;
+      if (OUT == OUT_GATE_INFER) {
+        float n2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) n2 = fmaf(v[c].x, v[c].x, fmaf(v[c].y, v[c].y, n2));
+        gf = 1.f / (1.f + __expf(-(a.gate_a[o] * n2 + a.gate_b[o])));
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        a.out[(((size_t)o * 2 + par[r]) * 3 + c) * Vh + idx[r]] = make_float2(v[c].x * gf, v[c].y * gf);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // training kernels
 // ---------------------------------------------------------------------------
@@ -688,6 +828,7 @@ struct sqcg_nn {
   unsigned long long fcg_gen;
   bool train_ready;
   int loss_norm;           // 1: A-norm of the error, 2: A^2-norm (preconditioned residual)
+  int mixing;              // inference 8 -> 8 layer: SQCG_NN_MIX_FP32 (CUDA cores) or SQCG_NN_MIX_BF16 (tensor cores)
 };
 
 namespace {
@@ -723,6 +864,9 @@ int conv_launch(sqcg_nn* nn, int layer, bool adjoint, int in_mode, int out_mode,
     k_conv<1, CH, IN_EVEN_SCALED, OUT_GATE_INFER><<<grid, kThreads, 0, s>>>(a);
   else if (cin == 1 && cout == CH && in_mode == IN_EVEN_SCALED && out_mode == OUT_GATE_TRAIN)
     k_conv<1, CH, IN_EVEN_SCALED, OUT_GATE_TRAIN><<<grid, kThreads, 0, s>>>(a);
+  else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_INFER && !adjoint &&
+           nn->mixing == SQCG_NN_MIX_BF16)
+    k_conv88_tc<OUT_GATE_INFER><<<grid_for(npar * (int)Vh, 16 * (kThreads / 32)), kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_INFER)
     k_conv88<OUT_GATE_INFER><<<grid2, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_TRAIN)
@@ -930,6 +1074,17 @@ int sqcg_nn_nparams(void) { return NPARAM; }
 int sqcg_nn_set_loss(sqcg_nn* nn, int norm) {
   if (!nn || (norm != 1 && norm != 2)) return SQCG_ERR_INVALID_ARG;
   nn->loss_norm = norm;
+  return SQCG_OK;
+}
+
+int sqcg_nn_set_mixing(sqcg_nn* nn, int mode) {
+  if (!nn || (mode != SQCG_NN_MIX_FP32 && mode != SQCG_NN_MIX_BF16)) return SQCG_ERR_INVALID_ARG;
+  if (mode != nn->mixing && nn->fcg_exec) {  // the captured loop holds the other kernel
+    cudaStreamSynchronize(nn->ctx->stream);
+    cudaGraphExecDestroy(nn->fcg_exec);
+    nn->fcg_exec = nullptr;
+  }
+  nn->mixing = mode;
   return SQCG_OK;
 }
 

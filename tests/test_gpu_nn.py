@@ -45,6 +45,50 @@ def to_f32(x):
     return np.asarray(x, dtype=np.complex64).astype(np.complex128)
 
 
+def bf16c(z):
+    """Round each real component to bfloat16, to nearest even (the GPU's conversion of the taps)."""
+    def r(x):
+        b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(np.real(z)) + 1j * r(np.imag(z))
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 6), (8, 8, 8, 8), (6, 8, 10, 12)])
+def test_network_bf16_mixing_matches_the_rounded_oracle(sqcg, links_cache, L):
+    """The tensor-core 8 -> 8 mixing (NN_MIX_BF16) computes the FP64 network with the second layer's nine
+    tap fields rounded to BF16 (the weights are BF16 values already) and FP32 sums. So it matches the oracle
+    forward pass with exactly that rounding inserted, to FP32 accuracy, up to the rare component whose FP32
+    and FP64 values round to different BF16 neighbours (one in 2^16, each a 2^-8 change of one term); and
+    it differs from the unrounded network by about the BF16 unit roundoff 2^-9."""
+    fat, lng = links_cache(L, 51)
+    r = to_f32(synth.gaussian_source(L, 52))
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(5, scale=0.6)))
+        net.set_mixing(sqcg.NN_MIX_BF16)
+        got = lat.unpack(net.apply(lat.pack(r, sqcg.F32), lat.new_spinor(sqcg.F32)), sqcg.F32)
+        params = flat_to_params(net.get_params(bf16_rounded=True))
+        with pytest.raises(sqcg.SqcgError):
+            net.set_mixing(2)
+        net.close()
+    U = onn.folded_fat(L, fat)
+    par = oracle.parity_of_sites(L)
+    s = np.sqrt(r.size) / np.linalg.norm(r)
+    h0 = np.zeros((1, par.size, 3), dtype=np.complex128)
+    h0[0, par == 0] = r * s
+    W, gates = params["W"], params["gates"]
+    h1, _ = onn.gate(onn.conv(L, U, W[0], h0), *gates[0])
+    taps = [bf16c(t) for t in onn.transports(L, U, h1)]
+    a2 = sum(np.einsum("oi,inc->onc", W[1][k], taps[k]) for k in range(len(taps)))
+    h2, _ = onn.gate(a2, *gates[1])
+    want = onn.conv(L, U, W[2], h2)[0, par == 0] / s
+    assert rel(got, want) <= 1e-4
+    exact = onn.apply(L, fat, params, r)
+    assert 1e-5 < rel(got, exact) <= 2.0 ** -6
+
+
 @pytest.mark.parametrize("L", [(4, 4, 4, 6), (8, 8, 8, 8), (6, 8, 10, 12)])
 def test_network_forward_matches_oracle(sqcg, links_cache, L):
     fat, lng = links_cache(L, 51)
@@ -198,6 +242,43 @@ def test_fcg_reuses_its_graph_and_follows_new_links(sqcg, links_cache):
         i4 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
         assert i4.status == 0
         assert oracle.true_rel_residual(L, fat2, lng2, 4 * m * m, b, lat.unpack(x)) <= tol
+        # the tensor-core mixing: the loop is recaptured with it and still ends on the FP64 true residual (this
+        # untrained network stalls the flexible loop with either mixing, so plain CG finishes both solves)
+        net.set_mixing(sqcg.NN_MIX_BF16)
+        x.zero_()
+        i5 = net.fcg_solve(m, db, x, tol=tol, max_iter=2000)
+        assert i5.status == 0 and i5.fallback == i4.fallback
+        assert oracle.true_rel_residual(L, fat2, lng2, 4 * m * m, b, lat.unpack(x)) <= tol
+        net.close()
+
+
+def test_fcg_with_tensor_core_mixing_on_the_trained_network(sqcg):
+    """The committed trained network (16^4, m = 0.005, held-out gauge field and source): flexible CG with the
+    BF16 tensor-core mixing needs the iterations of the FP32 mixing within 10 %, without falling back to plain
+    CG, and reaches the true relative residual recomputed by the FP64 oracle."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1611_00728_gb300",
+                        "trained", "fcg_network_16x16x16x16.npy")
+    if not os.path.exists(path):
+        pytest.skip("no trained parameters")
+    L, m, tol = (16, 16, 16, 16), 0.005, 1e-8
+    fat, lng = synth.fat_long_links(L, 9000)
+    b = synth.gaussian_source(L, 9100)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        net = sqcg.Network(lat)
+        net.set_params(np.load(path).astype(np.float32))
+        db, x = lat.pack(b), lat.new_spinor()
+        info = {}
+        for mix in (sqcg.NN_MIX_FP32, sqcg.NN_MIX_BF16):
+            net.set_mixing(mix)
+            x.zero_()
+            info[mix] = net.fcg_solve(m, db, x, tol=tol, max_iter=5000)
+            assert info[mix].status == 0 and info[mix].fallback == 0
+            assert oracle.true_rel_residual(L, fat, lng, 4 * m * m, b, lat.unpack(x)) <= tol
+        i32, i16 = info[sqcg.NN_MIX_FP32].iters, info[sqcg.NN_MIX_BF16].iters
+        assert abs(i16 - i32) <= max(2, i32 // 10), (i32, i16)
         net.close()
 
 
