@@ -88,6 +88,19 @@ extern "C" {
 #define SQCG_MODE_MIXED 1 /* FP32 Dslash and vectors; FP64 x and scalars; grid sums in float-float;
                              true residuals of the reliable updates in float-float (SQCG_FF, default) or
                              FP64 arithmetic, summed in FP64 */
+/* Multi-shift only: OR-ed into the mode of sqcg_multishift_cg_solve (and
+ * sqcg_rational_apply), shift-aware reliable updates of the shared Krylov loop.
+ * Each time the base residual has fallen by the reliable-update factor (1e-3
+ * by default), the loop pauses and, in FP64: r_0 = b - A_0 x_0 replaces the
+ * iterated base residual; every shift still iterating gets its true residual
+ * r_s = b - A_s x_s, the least-squares factor zeta'_s = Re<r_0, r_s> / |r_0|^2
+ * and the collinearity loss |r_s - zeta'_s r_0| / |b|. Where that loss is at
+ * most tol_s / 2 the shift continues from zeta'_s (its zeta recurrence
+ * rescaled, its stopping threshold lowered by the loss, which later iterations
+ * of the shared space do not remove); otherwise it continues unchanged and is
+ * refined after the loop as without the flag. The losses are kept for
+ * sqcg_multishift_ru_record. Not in the paper (its multi-mass CG is FP64). */
+#define SQCG_MS_SHIFT_RU 0x10
 
 typedef struct sqcg_ctx sqcg_ctx; /* opaque, library-owned */
 
@@ -221,13 +234,27 @@ int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol
  * its FP64 true residual; where that is above tol[s] (expected with FP32
  * vectors) it is refined from x_s: in mixed mode all shifts together as one
  * batched mixed-precision CG (one right-hand side per shift, held in the
- * context's batched workspace), in FP64 mode by one CG per shift.
+ * context's batched workspace), in FP64 mode by one CG per shift. mode:
+ * SQCG_MODE_F64 or SQCG_MODE_MIXED, either optionally | SQCG_MS_SHIFT_RU (the
+ * shift-aware reliable updates above; info[s].reliable_updates then also
+ * counts the updates in which shift s continued from zeta'_s).
  * info: NULL or an array of nshift (per-shift iterations including refinement,
  * status, true residual; seconds = whole call). Returns SQCG_OK when every
  * shift converged, else the first failing status. Synchronises the stream. */
 int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, const void* b,
                              void* const* x, const double* tol, int max_iter, int mode,
                              sqcg_info* info);
+
+/* The shift-aware reliable updates (SQCG_MS_SHIFT_RU) of the last multi-shift
+ * solve on ctx. *nupdates = how many ran (0 without the flag). For update
+ * u < min(*nupdates, max_updates, 16): iter[u] = the loop iteration it followed,
+ * base[u] = |r_0| / |b| (FP64 true base residual), loss[u * nshift + s] =
+ * |r_s - zeta'_s r_0| / |b| for shift s in the order the caller passed them
+ * (0 for the base system, NaN for a shift that had already stopped). *nshift_out
+ * = that solve's shift count; loss holds max_updates * nshift entries. iter, base
+ * and loss may be NULL. Host-only: reads what the solve left. */
+int sqcg_multishift_ru_record(const sqcg_ctx* ctx, int max_updates, int* nupdates, int* nshift_out, int* iter,
+                              double* base, double* loss);
 
 /* Rational-function application, the multi-mass CG's use inside RHMC evolution
  * (paper Sec. 4: su3_rhmc_hisq, about nine masses):

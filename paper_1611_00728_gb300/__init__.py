@@ -23,12 +23,13 @@ __all__ = [
     "F64", "F32", "FF", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
     "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "NN_LAYERS", "NN_GATES", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
-    "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK",
+    "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK", "MS_SHIFT_RU", "NN_MIX_FP32", "NN_MIX_BF16",
 ]
 
 F64, F32, FF = 0, 1, 2  # FF: float-float (hi, lo floats per real), device vectors (3, Vh, 4) float32
 NN_MIX_FP32, NN_MIX_BF16 = 0, 1  # arithmetic of the inference 8 -> 8 channel mixing (sqcg_nn_set_mixing)
 MODE_F64, MODE_MIXED = 0, 1
+MS_SHIFT_RU = 0x10  # OR-ed into a multi-shift mode: shift-aware reliable updates (sqcg_multishift_ru_record)
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
 EIGHT_WAY = 2
@@ -128,6 +129,7 @@ def library():
         lib.sqcg_normal_op_noalloc.argtypes = [P, D, I, P, P]
         lib.sqcg_cg_solve.argtypes = [P, D, P, P, D, I, I, ctypes.POINTER(Info)]
         lib.sqcg_multishift_cg_solve.argtypes = [P, I, P, P, P, P, I, I, P]
+        lib.sqcg_multishift_ru_record.argtypes = [P, I, P, P, P, P, P]
         lib.sqcg_rational_apply.argtypes = [P, I, P, P, D, P, P, D, I, I, P]
         lib.sqcg_cg_solve_batched.argtypes = [I, P, P, P, P, P, D, I, P]
         lib.sqcg_batched_tuning.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -159,7 +161,7 @@ def library():
                      "sqcg_normal_op_noalloc", "sqcg_nn_create", "sqcg_nn_destroy", "sqcg_nn_nparams",
                      "sqcg_nn_set_params", "sqcg_nn_get_params", "sqcg_nn_apply", "sqcg_nn_set_loss", "sqcg_nn_set_mixing", "sqcg_nn_loss_grad", "sqcg_nn_train",
                      "sqcg_make_training_pair", "sqcg_fcg_solve_nn",
-                     "sqcg_multishift_cg_solve", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply",
+                     "sqcg_multishift_cg_solve", "sqcg_multishift_ru_record", "sqcg_cg_solve_batched", "sqcg_batched_tuning", "sqcg_rational_apply",
                      "sqcg_batched_tuning_ex", "sqcg_batched_pin_tuning",
                      "sqcg_hisq_smear", "sqcg_hisq_load_links"):
             getattr(lib, name).restype = I
@@ -368,6 +370,20 @@ class Lattice:
         if raise_on_error:
             _check(rc, "sqcg_multishift_cg_solve")
         return list(infos)
+
+    def multishift_ru_record(self):
+        """Shift-aware reliable updates of the last multi-shift solve (mode | MS_SHIFT_RU): a list of
+        (iteration, |r_0| / |b|, losses |r_s - zeta'_s r_0| / |b| per shift in the caller's order)."""
+        nu, ns = ctypes.c_int(), ctypes.c_int()
+        _check(library().sqcg_multishift_ru_record(self._h, 0, ctypes.byref(nu), ctypes.byref(ns), None, None, None),
+               "sqcg_multishift_ru_record")
+        m = min(nu.value, 16)
+        it = (ctypes.c_int * max(m, 1))()
+        base = (ctypes.c_double * max(m, 1))()
+        loss = (ctypes.c_double * max(m * ns.value, 1))()
+        _check(library().sqcg_multishift_ru_record(self._h, m, ctypes.byref(nu), ctypes.byref(ns), it, base, loss),
+               "sqcg_multishift_ru_record")
+        return [(it[u], base[u], [loss[u * ns.value + j] for j in range(ns.value)]) for u in range(m)]
 
 
 def cg_solve_batched(lattices, masses, bs, xs, tol: float = 1e-8, max_iter: int = 10000,

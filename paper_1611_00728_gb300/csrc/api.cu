@@ -73,6 +73,8 @@ void free_workspace(sqcg_ctx* ctx) {
   cudaFree(ctx->ms_stack);
   ctx->ms_stack = nullptr;
   ctx->ms_stack_n = 0;
+  cudaFree(ctx->ms_ru_vec);
+  ctx->ms_ru_vec = nullptr;
   ctx->rat_n = 0;
 }
 

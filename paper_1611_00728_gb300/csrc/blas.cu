@@ -267,6 +267,76 @@ k_ms_xpay(MSPtrs P, const typename V2<R>::T* __restrict__ r, typename V2<R>::T* 
   }
 }
 
+// Shift-aware reliable update of the multi-shift loop (host-driven, a few times a solve; FP64 on
+// FP64 vectors): the block partials of Re<a, b>, |b - z a|^2 and |a|^2 at partials[0, nb, 2 nb).
+__global__ void __launch_bounds__(kThreads)
+k_ms_ru_dots(const double2* __restrict__ a, const double2* __restrict__ b, double z, int Vh, double* partials) {
+  double ab = 0.0, d2 = 0.0, aa = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 u = a[(size_t)c * Vh + i], v = b[(size_t)c * Vh + i];
+      ab = fma(u.x, v.x, fma(u.y, v.y, ab));
+      const double dx = fma(-z, u.x, v.x), dy = fma(-z, u.y, v.y);
+      d2 = fma(dx, dx, fma(dy, dy, d2));
+      aa = fma(u.x, u.x, fma(u.y, u.y, aa));
+    }
+  }
+  block_sum3(ab, d2, aa);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = ab;
+    partials[gridDim.x + blockIdx.x] = d2;
+    partials[2 * gridDim.x + blockIdx.x] = aa;
+  }
+}
+
+// ... and their totals, in block order, into the device state for the host to read
+__global__ void __launch_bounds__(kFinishThreads) k_ms_ru_sum3(SolverState* st, const double* partials, int n) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    a += partials[j];
+    b += partials[n + j];
+    c += partials[2 * n + j];
+  }
+  block_sum3(a, b, c);
+  if (threadIdx.x == 0) {
+    st->ms_sums[0] = a;
+    st->ms_sums[1] = b;
+    st->ms_sums[2] = c;
+  }
+}
+
+// The FP64 base residual r_t replaces the iterated r, and every direction still moving takes the
+// same change scaled by its shift's zeta (the base direction's is 1): p_s += zeta_s (r_t - r).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_ms_ru_fix(MSPtrs P, typename V2<R>::T* __restrict__ r, const double2* __restrict__ rt, int Vh,
+            const SolverState* st) {
+  typedef typename V2<R>::T R2;
+  const int ns = st->nshift;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * Vh + i;
+      const double2 t = rt[k];
+      R2 rc = r[k];
+      const double dx = t.x - (double)rc.x, dy = t.y - (double)rc.y;
+      rc.x = (R)t.x;
+      rc.y = (R)t.y;
+      r[k] = rc;
+      for (int j = 0; j < ns; ++j) {
+        if (j > 0 && st->active[j] != 1) continue;
+        R2* ps = static_cast<R2*>(P.p[j]);
+        const double z = (j == 0) ? 1.0 : st->zeta[j];
+        R2 pc = ps[k];
+        pc.x = (R)fma(z, dx, (double)pc.x);
+        pc.y = (R)fma(z, dy, (double)pc.y);
+        ps[k] = pc;
+      }
+    }
+  }
+}
+
 // Second stage of a grid reduction: sum the block partials, run the scalar step.
 __global__ void __launch_bounds__(kFinishThreads) k_finish(SolverState* st, const double* partials, int n, int fin,
                                                            int gate) {
@@ -301,8 +371,10 @@ __global__ void __launch_bounds__(kFinishSRThreads) k_finish_sr(SolverState* st,
 __global__ void k_loop_control(SolverState* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->loop_count += 1;
-  int go = !st->done && st->loop_count < st->loop_limit;
-  if (!go && !st->done) {
+  // a multi-shift loop with shift-aware reliable updates pauses for the host-driven update
+  const int pause = st->ms_ru && st->need_update && !st->done;
+  int go = !st->done && !pause && st->loop_count < st->loop_limit;
+  if (!go && !st->done && !pause) {
     st->done = 1;
     st->status = SQCG_ERR_NOT_CONVERGED;
   }
@@ -423,6 +495,32 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
   SQCG_CUDA_TRY(cudaGetLastError());
   return mixed ? launch_finish_ffs(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s)
                : launch_finish(ctx, grid, FIN_MS_UPDATE, GATE_ITER, s);
+}
+
+int launch_ms_ru_sums(sqcg_ctx* ctx, const double2* a, const double2* b, double z, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
+  if (3 * grid > 4 * ctx->max_blocks) return SQCG_ERR_INVALID_ARG;  // partials hold 4 * max_blocks
+  k_ms_ru_dots<<<grid, kThreads, 0, s>>>(a, b, z, Vh, ctx->partials);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  k_ms_ru_sum3<<<1, kFinishThreads, 0, s>>>(ctx->st, ctx->partials, grid);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
+}
+
+int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const double2* rt, cudaStream_t s) {
+  const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
+  if (nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
+  MSPtrs P;
+  for (int j = 0; j < SQCG_MAX_SHIFTS; ++j) {
+    P.x[j] = nullptr;
+    P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
+  }
+  if (mixed)
+    k_ms_ru_fix<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, rt, Vh, ctx->st);
+  else
+    k_ms_ru_fix<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, rt, Vh, ctx->st);
+  SQCG_CUDA_TRY(cudaGetLastError());
+  return SQCG_OK;
 }
 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s) {

@@ -366,7 +366,7 @@ int run_eager(sqcg_ctx* ctx, int kind, int mixed, const void* b, void* const* x,
     } else {
       SQCG_TRY(enqueue_ms_iteration(ctx, mixed, nx, (double2* const*)x, s));
       SQCG_TRY(read_state(ctx, s));
-      if (h->done) break;
+      if (h->done || (h->ms_ru && h->need_update)) break;  // finished, or paused for the host-driven update
     }
   }
   *iters_run = it + 1;
@@ -554,6 +554,94 @@ extern "C" int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x,
   return cg_solve_sigma(ctx, 4.0 * mass * mass, b, x, tol, max_iter, mode, info);
 }
 
+namespace {
+
+// Shift-aware reliable update of the multi-shift loop (SQCG_MS_SHIFT_RU), run by the host while the
+// loop is paused after a whole iteration (x_s, r and the directions all at step k + 1), in FP64:
+// r_0 = b - A_0 x_0; for every shift still iterating r_s = b - A_s x_s, the least-squares factor
+// zeta'_s = Re<r_0, r_s> / |r_0|^2 and the loss |r_s - zeta'_s r_0|. A shift whose loss is at most
+// half its tolerance continues from zeta'_s: zeta_{k+1} and zeta_k both scale by zeta'_s / zeta_s
+// (the zeta recurrence is homogeneous of degree one in the pair, so alpha_s and beta_s keep their
+// values), and its stopping threshold drops by the loss, which later steps in the shared Krylov
+// space do not remove. Then r_0 replaces the iterated base residual and every moving direction takes
+// the change, p_s += zeta_s (r_0 - r). sig, tl: shifts and tolerances in the loop's order (base
+// first); perm maps that order to the caller's. ru_count[j] counts the updates shift j continued from.
+int ms_shift_aware_update(sqcg_ctx* ctx, int mixed, int nshift, const double* sig, const double* tl,
+                          const int* perm, const void* b, void* const* xs, cudaStream_t s, int* ru_count,
+                          int* launches) {
+  SolverState* h = ctx->st_host;
+  const size_t n = (size_t)ctx->g.Vh * 3;
+  if (!ctx->ms_ru_vec && cudaMalloc(&ctx->ms_ru_vec, 2 * n * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    return SQCG_ERR_NO_MEMORY;
+  }
+  double2* r0 = ctx->ms_ru_vec;
+  double2* rs = ctx->ms_ru_vec + n;
+  auto true_resid = [&](const void* x, double sigma, double2* out) -> int {  // out = b - A_sigma x, FP64
+    DslashLaunch L = {};
+    L.out_parity = 1; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_PLAIN; L.in = x; L.out = ctx->tmp64;
+    SQCG_TRY(launch_dslash(ctx, L, s));
+    L = DslashLaunch{};
+    L.out_parity = 0; L.prec = L.out_prec = SQCG_F64; L.epi = EPI_TRUE_RESID; L.in = ctx->tmp64; L.out = out;
+    L.y = x; L.b = b; L.sigma = sigma;
+    *launches += 2;
+    return launch_dslash(ctx, L, s);
+  };
+  SQCG_TRY(true_resid(xs[0], sig[0], r0));
+  SQCG_TRY(launch_ms_ru_sums(ctx, r0, r0, 0.0, s));
+  *launches += 2;
+  SQCG_TRY(read_state(ctx, s));
+  const double r0n = h->ms_sums[2], bb = h->bb;
+  const int u = ctx->ms_rec_n++;
+  if (u < SQCG_MS_RU_RECORD) {
+    ctx->ms_rec_iter[u] = h->iter;
+    ctx->ms_rec_base[u] = sqrt(r0n / bb);
+    for (int j = 0; j < nshift; ++j) ctx->ms_rec_loss[u][perm[j]] = (j == 0) ? 0.0 : NAN;
+  }
+  if (!isfinite(r0n)) {
+    h->status = SQCG_ERR_BREAKDOWN;
+    h->done = 1;
+    h->need_update = 0;
+    return write_state(ctx, s);
+  }
+  double scale[SQCG_MAX_SHIFTS], l2s[SQCG_MAX_SHIFTS];
+  int keep[SQCG_MAX_SHIFTS] = {};
+  for (int j = 1; j < nshift; ++j) {
+    if (h->active[j] != 1) continue;
+    SQCG_TRY(true_resid(xs[j], sig[j], rs));
+    SQCG_TRY(launch_ms_ru_sums(ctx, r0, rs, 0.0, s));
+    SQCG_TRY(read_state(ctx, s));
+    const double zp = r0n > 0.0 ? h->ms_sums[0] / r0n : 0.0;
+    SQCG_TRY(launch_ms_ru_sums(ctx, r0, rs, zp, s));
+    SQCG_TRY(read_state(ctx, s));
+    *launches += 4;
+    const double l2 = h->ms_sums[1], loss = sqrt(l2 / bb);
+    if (u < SQCG_MS_RU_RECORD) ctx->ms_rec_loss[u][perm[j]] = loss;
+    if (isfinite(loss) && loss <= 0.5 * tl[j] && zp != 0.0 && h->zeta[j] != 0.0) {
+      keep[j] = 1;
+      scale[j] = zp / h->zeta[j];
+      l2s[j] = l2;
+    }
+  }
+  // the state read last is the device's: apply the decisions to it
+  for (int j = 1; j < nshift; ++j) {
+    if (!keep[j]) continue;
+    h->zeta[j] *= scale[j];
+    h->zeta_prev[j] *= scale[j];
+    h->stop_rr_s[j] = tl[j] * tl[j] * bb - l2s[j];
+    ru_count[j] += 1;
+  }
+  ru_count[0] += 1;
+  h->rr = h->rr_true = h->rr_max = r0n;
+  h->need_update = 0;
+  h->updates += 1;
+  SQCG_TRY(write_state(ctx, s));
+  *launches += 1;
+  return launch_ms_ru_fix(ctx, mixed, nshift, r0, s);
+}
+
+}  // namespace
+
 // Multi-shift CG: (sigma_s - D_eo D_oe) x_s = b for all shifts from one Krylov
 // space built on the smallest shift; FP64 scalar recurrences. In mixed mode
 // each shift whose FP64 true residual is above its tolerance is then refined
@@ -562,6 +650,8 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
                                         void* const* x, const double* tol, int max_iter, int mode,
                                         sqcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
+  const int ru = (mode & SQCG_MS_SHIFT_RU) != 0;
+  mode &= ~SQCG_MS_SHIFT_RU;
   if (!ctx || nshift < 1 || nshift > SQCG_MAX_SHIFTS || !shifts || !x || !tol || max_iter <= 0 ||
       (mode != SQCG_MODE_F64 && mode != SQCG_MODE_MIXED))
     return SQCG_ERR_INVALID_ARG;
@@ -617,6 +707,10 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
   h->nshift = nshift;
   h->alpha_prev = 1.0;
   h->beta_prev = 0.0;
+  h->ms_ru = ru;
+  h->delta2 = ctx->ru_delta * ctx->ru_delta;
+  ctx->ms_rec_n = 0;
+  ctx->ms_rec_nshift = nshift;
   for (int j = 0; j < nshift; ++j) {
     h->active[j] = 1;
     h->dsig[j] = shifts[perm[j]] - sigma0;
@@ -638,18 +732,29 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
       if (info) info[j] = sqcg_info{0, 0, SQCG_OK, 0.0, 0.0, 3 + nshift};
     return SQCG_OK;
   }
-  h->rr = h->rr_prev = h->bb;
+  h->rr = h->rr_prev = h->rr_max = h->bb;
   SQCG_TRY(write_state(ctx, s));
 
-  int loops = 0;
-  if (eager_mode()) {
-    SQCG_TRY(run_eager(ctx, KIND_MS, mixed, b, xs, nshift, max_iter, s, &loops));
-  } else {
-    CGGraph* g = nullptr;
-    SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
-    SQCG_TRY(run_loop(ctx, g, max_iter, s, &loops));
+  // the shared loop; with SQCG_MS_SHIFT_RU it pauses for each shift-aware reliable update
+  int loops = 0, ru_launches = 0;
+  int ru_count[SQCG_MAX_SHIFTS] = {};
+  double sig_l[SQCG_MAX_SHIFTS], tol_l[SQCG_MAX_SHIFTS];
+  for (int j = 0; j < nshift; ++j) {
+    sig_l[j] = shifts[perm[j]];
+    tol_l[j] = tol[perm[j]];
   }
-  int launches = 2 + 1 + nshift + loops * kMSKernelsPerIter;
+  const bool eager = eager_mode();
+  CGGraph* g = nullptr;
+  if (!eager) SQCG_TRY(capture(ctx, KIND_MS, mixed, b, xs, nshift, &g));
+  for (;;) {
+    int seg = 0;
+    if (eager) SQCG_TRY(run_eager(ctx, KIND_MS, mixed, b, xs, nshift, max_iter, s, &seg));
+    else SQCG_TRY(run_loop(ctx, g, max_iter, s, &seg));
+    loops += seg;
+    if (h->done || !(h->ms_ru && h->need_update)) break;
+    SQCG_TRY(ms_shift_aware_update(ctx, mixed, nshift, sig_l, tol_l, perm, b, xs, s, ru_count, &ru_launches));
+  }
+  int launches = 2 + 1 + nshift + loops * kMSKernelsPerIter + ru_launches;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;
   int iters_s[SQCG_MAX_SHIFTS];
   for (int j = 0; j < nshift; ++j) iters_s[j] = h->iters_s[j];
@@ -716,7 +821,7 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     const int st = ri[j].status;
     if (info) {
       info[u].iters = iters_s[j] + ri[j].iters;
-      info[u].reliable_updates = ri[j].reliable_updates;
+      info[u].reliable_updates = ri[j].reliable_updates + ru_count[j];
       info[u].status = st;
       info[u].true_rel_resid = ri[j].true_rel_resid;
     }
@@ -729,6 +834,23 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
       info[j].launches = launches;
     }
   return worst;
+}
+
+extern "C" int sqcg_multishift_ru_record(const sqcg_ctx* ctx, int max_updates, int* nupdates, int* nshift_out,
+                                         int* iter, double* base, double* loss) {
+  if (!ctx || !nupdates || !nshift_out || max_updates < 0) return SQCG_ERR_INVALID_ARG;
+  *nupdates = ctx->ms_rec_n;
+  *nshift_out = ctx->ms_rec_nshift;
+  int m = ctx->ms_rec_n < max_updates ? ctx->ms_rec_n : max_updates;
+  if (m > SQCG_MS_RU_RECORD) m = SQCG_MS_RU_RECORD;
+  const int ns = ctx->ms_rec_nshift;
+  for (int u = 0; u < m; ++u) {
+    if (iter) iter[u] = ctx->ms_rec_iter[u];
+    if (base) base[u] = ctx->ms_rec_base[u];
+    if (loss)
+      for (int j = 0; j < ns; ++j) loss[(size_t)u * ns + j] = ctx->ms_rec_loss[u][j];
+  }
+  return SQCG_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -192,6 +192,10 @@ __device__ inline void solver_finish_ms(SolverState* s, int fin, double v) {
         s->beta_prev = b;
         if (!any) { s->done = 1; s->status = SQCG_OK; s->ms_final = 1; }
         else if (it >= s->max_iter) { s->done = 1; s->status = SQCG_ERR_NOT_CONVERGED; s->ms_final = 1; }
+        else if (s->ms_ru) {  // shift-aware reliable update: the loop pauses after this iteration
+          if (v > s->rr_max) s->rr_max = v;
+          if (v < s->delta2 * s->rr_max) s->need_update = 1;
+        }
       }
     }
   }

@@ -95,11 +95,14 @@ struct SolverState {
   double alpha_s[SQCG_MAX_SHIFTS], beta_s[SQCG_MAX_SHIFTS];
   double alpha_prev, beta_prev;
   int iters_s[SQCG_MAX_SHIFTS];
+  int ms_ru;           // shift-aware reliable updates: the loop pauses when need_update is set
+  double ms_sums[3];   // the host-driven update's sums (k_ms_ru_sum3)
 };
 
 // ---------------------------------------------------------------------------
 // batched multi-RHS CG over several lattices (one state entry per RHS)
 // ---------------------------------------------------------------------------
+#define SQCG_MS_RU_RECORD 16  // shift-aware reliable updates recorded per multi-shift solve
 #define SQCG_MAX_BATCH_RHS 256
 #define SQCG_MAX_LATTICES 16
 
@@ -204,6 +207,12 @@ struct sqcg_ctx {
   int rat_n;
   double2* ms_stack;  // batched refinement (FP64): per-shift solutions [nshift][3][Vh], then a copy of b
   int ms_stack_n;
+  // shift-aware reliable updates of the multi-shift loop (SQCG_MS_SHIFT_RU)
+  double2* ms_ru_vec;  // FP64 [2][3][Vh]: the base true residual r_0, then one shift's r_s
+  int ms_rec_n, ms_rec_nshift;  // updates recorded by the last multi-shift solve; its shift count
+  int ms_rec_iter[SQCG_MS_RU_RECORD];
+  double ms_rec_base[SQCG_MS_RU_RECORD];
+  double ms_rec_loss[SQCG_MS_RU_RECORD][SQCG_MAX_SHIFTS];  // caller's shift order
   int ms_nalloc;
   int ms_prec;
 
@@ -302,6 +311,10 @@ int launch_scale_copy_f64(sqcg_ctx* ctx, const double2* src, double2* dst, doubl
 int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
+// shift-aware reliable update of the multi-shift loop: Re<a, b>, |b - z a|^2 and |a|^2 (FP64 vectors) into
+// st->ms_sums; then r <- rt with p_s += zeta_s (rt - r) for every direction still moving
+int launch_ms_ru_sums(sqcg_ctx* ctx, const double2* a, const double2* b, double z, cudaStream_t s);
+int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const double2* rt, cudaStream_t s);
 
 // float-float Dslash (dslash_ff.cu): in and out_ff are float4 [3][Vh] (re_hi, re_lo, im_hi, im_lo);
 // true_resid: out32 (FP32) = b - sigma x + D in with |.|^2 reduced in FP64 (x, b FP64)

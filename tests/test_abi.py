@@ -112,6 +112,16 @@ def test_host_side_argument_checks(libpath):
     assert lib.sqcg_hisq_workspace_bytes(None) == 0
 
 
+def test_multishift_record_checks_its_arguments(libpath):
+    """The shift-aware update record is read on the host; a missing context or output is refused."""
+    lib = ctypes.CDLL(libpath)
+    f = lib.sqcg_multishift_ru_record
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5
+    n, ns = ctypes.c_int(), ctypes.c_int()
+    assert f(None, 4, ctypes.byref(n), ctypes.byref(ns), None, None, None) == -1
+    assert f(None, 4, None, None, None, None, None) == -1
+
+
 def test_batched_pin_tuning_checks(libpath):
     """The pinned batched Dslash configuration is validated on the host (no CUDA call)."""
     lib = ctypes.CDLL(libpath)

@@ -471,6 +471,55 @@ def test_multishift_mixed_zero_source(sqcg, links_cache):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_multishift_shift_aware_reliable_updates(sqcg, links_cache, monkeypatch, mode):
+    """Shift-aware reliable updates (MS_SHIFT_RU): every shift still reaches its FP64 true residual
+    (oracle-checked), the record maps each loss to the caller's shift order (the base system's is 0),
+    and the graph and eager forms of the paused loop give identical solutions. In FP64 the shifted
+    residuals of the shared Krylov space are collinear with the base residual (r_s = zeta_s r_0 in
+    exact arithmetic), so the measured loss is rounding only and every shift continues from its fitted
+    zeta."""
+    L, tol = (8, 8, 8, 8), 1e-8
+    fat, lng = links_cache(L, 1001)
+    shifts = [0.3, 0.0004, 0.02, 0.0012, 0.1, 1.0]
+    base = int(np.argmin(shifts))
+    b = synth.gaussian_source(L, 2301)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=(mode == 1))
+        db = lat.pack(b)
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, db, xs, tol=tol, max_iter=20000, mode=mode | sqcg.MS_SHIFT_RU)
+        got = [lat.unpack(x) for x in xs]
+        rec = lat.multishift_ru_record()
+        monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
+        xe = [lat.new_spinor() for _ in shifts]
+        lat.multishift_cg_solve(shifts, db, xe, tol=tol, max_iter=20000, mode=mode | sqcg.MS_SHIFT_RU)
+        monkeypatch.delenv("SQCG_LAUNCH_MODE")
+        assert all(np.array_equal(g, lat.unpack(x)) for g, x in zip(got, xe))
+        plain = lat.multishift_cg_solve(shifts, db, [lat.new_spinor() for _ in shifts], tol=tol, max_iter=20000,
+                                        mode=mode)
+        assert lat.multishift_ru_record() == []  # without the flag nothing is recorded
+    for s, info, x in zip(shifts, infos, got):
+        assert info.status == 0 and info.true_rel_resid <= tol
+        assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
+    assert len(rec) >= 2
+    prev = 1.0
+    for it, r0, loss in rec:
+        assert 0 < it and 0 < r0 < prev  # the trigger: |r| fell by 1e-3 from its maximum since the last update
+        prev = r0
+        assert loss[base] == 0.0
+        assert all(np.isnan(v) or v >= 0 for v in loss)
+    live = [[j for j, v in enumerate(loss) if not np.isnan(v) and j != base] for _, _, loss in rec]
+    assert live[0], "some shift is still iterating at the first update"
+    if mode == 0:
+        assert max(loss[j] for (_, _, loss), js in zip(rec, live) for j in js) <= 1e-10
+        for j in range(len(shifts)):
+            assert infos[j].reliable_updates >= sum(j in js for js in live) + (j == base) * len(rec)
+            assert abs(infos[j].iters - plain[j].iters) <= 2
+    else:
+        assert all(np.isfinite(loss[j]) for (_, _, loss), js in zip(rec, live) for j in js)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_multishift_degenerate_and_maximum_shift_counts(sqcg, links_cache, mode):
     """One shift is plain CG; 32 shifts (the maximum) with duplicates all converge; bad arguments are refused."""
     L, tol = (6, 8, 10, 12), 1e-8
