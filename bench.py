@@ -606,6 +606,7 @@ def measure_multishift(torch, sq, clk, lat, b, steps, compare=True, tag="multish
         res[name] = {"ms": ms, "iters": [i.iters for i in infos],
                      "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
         if name == "mixed":  # the batched refinement's tuned Dslash configuration (its plan stays with lat)
+            res[name]["base_reliable_updates"] = len(lat.multishift_ru_record())
             res[name]["refinement_tuning"] = sq.batched_tuning_ex(lat)
     # the same mixed solve with shift-aware reliable updates: at each base update every shift still
     # iterating gets its FP64 true residual and its collinearity loss |r_s - zeta'_s r_0| / |b|; a shift
@@ -623,6 +624,13 @@ def measure_multishift(torch, sq, clk, lat, b, steps, compare=True, tag="multish
                      "shifts_continuing": sum(1 for j, v in enumerate(loss) if j != base and v <= 0.5 * TOL),
                      "shifts_iterating": sum(1 for j, v in enumerate(loss) if j != base and not np.isnan(v))}
                     for it, r0, loss in rec]}
+    # the shared loop without the mixed mode's base reliable updates
+    def run_no_ru():
+        return lat.multishift_cg_solve(shifts, b, xs, tol=TOL, max_iter=20000, mode=sq.MODE_MIXED | sq.MS_NO_RU)
+    run_no_ru()
+    ms, infos = _repeat(torch, clk, f"{tag}.mixed_no_ru", run_no_ru, steps)
+    res["mixed_no_ru"] = {"ms": ms, "iters": [i.iters for i in infos],
+                          "max_true_rel_resid": max(i.true_rel_resid for i in infos)}
     if compare:  # plain FP64 CG, one solve per shift (the same buffers: one captured graph)
         x = lat.new_spinor()
         _solve_sigma(lat, shifts[0], b, x, sq)

@@ -101,6 +101,15 @@ extern "C" {
  * refined after the loop as without the flag. The losses are kept for
  * sqcg_multishift_ru_record. Not in the paper (its multi-mass CG is FP64). */
 #define SQCG_MS_SHIFT_RU 0x10
+/* Multi-shift only, OR-ed into the mode: no reliable updates in the shared
+ * loop. Without this flag (and without SQCG_MS_SHIFT_RU) the mixed multi-shift
+ * takes base reliable updates: the same pauses, but only the base residual is
+ * recomputed (with the context's update arithmetic, float-float by default)
+ * and replaces the iterated one, every moving direction taking the change; no
+ * shift's residual is formed and no zeta changes. Either way every shift is
+ * then checked and refined. The FP64 mode has no reliable updates unless
+ * SQCG_MS_SHIFT_RU asks for them. */
+#define SQCG_MS_NO_RU 0x20
 
 typedef struct sqcg_ctx sqcg_ctx; /* opaque, library-owned */
 
@@ -237,7 +246,8 @@ int sqcg_cg_solve(sqcg_ctx* ctx, double mass, const void* b, void* x, double tol
  * context's batched workspace), in FP64 mode by one CG per shift. mode:
  * SQCG_MODE_F64 or SQCG_MODE_MIXED, either optionally | SQCG_MS_SHIFT_RU (the
  * shift-aware reliable updates above; info[s].reliable_updates then also
- * counts the updates in which shift s continued from zeta'_s).
+ * counts the updates in which shift s continued from zeta'_s) or
+ * | SQCG_MS_NO_RU (mixed mode without its base reliable updates).
  * info: NULL or an array of nshift (per-shift iterations including refinement,
  * status, true residual; seconds = whole call). Returns SQCG_OK when every
  * shift converged, else the first failing status. Synchronises the stream. */
@@ -245,12 +255,13 @@ int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double* shifts, co
                              void* const* x, const double* tol, int max_iter, int mode,
                              sqcg_info* info);
 
-/* The shift-aware reliable updates (SQCG_MS_SHIFT_RU) of the last multi-shift
- * solve on ctx. *nupdates = how many ran (0 without the flag). For update
+/* The reliable updates of the last multi-shift solve on ctx (SQCG_MS_SHIFT_RU,
+ * or the mixed mode's base updates). *nupdates = how many ran. For update
  * u < min(*nupdates, max_updates, 16): iter[u] = the loop iteration it followed,
  * base[u] = |r_0| / |b| (FP64 true base residual), loss[u * nshift + s] =
  * |r_s - zeta'_s r_0| / |b| for shift s in the order the caller passed them
- * (0 for the base system, NaN for a shift that had already stopped). *nshift_out
+ * (0 for the base system; NaN where not measured: a shift that had already
+ * stopped, or every other shift in a base update). *nshift_out
  * = that solve's shift count; loss holds max_updates * nshift entries. iter, base
  * and loss may be NULL. Host-only: reads what the solve left. */
 int sqcg_multishift_ru_record(const sqcg_ctx* ctx, int max_updates, int* nupdates, int* nshift_out, int* iter,

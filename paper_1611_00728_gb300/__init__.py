@@ -23,13 +23,14 @@ __all__ = [
     "F64", "F32", "FF", "MODE_F64", "MODE_MIXED", "ANTIPERIODIC_T", "PHASES_FOLDED", "RECON12_LONG",
     "SqcgError", "Info", "Lattice", "library", "library_path", "FLOPS_PER_SITE", "cg_solve_batched",
     "batched_tuning", "batched_tuning_ex", "pin_batched_tuning", "Network", "NN_NPARAMS", "NN_LAYERS", "NN_GATES", "HisqCoeffs", "SmearLevel", "hisq_coeffs", "hisq_smear",
-    "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK", "MS_SHIFT_RU", "NN_MIX_FP32", "NN_MIX_BF16",
+    "hisq_workspace_bytes", "HISQ_FLOPS_PER_LINK", "MS_SHIFT_RU", "MS_NO_RU", "NN_MIX_FP32", "NN_MIX_BF16",
 ]
 
 F64, F32, FF = 0, 1, 2  # FF: float-float (hi, lo floats per real), device vectors (3, Vh, 4) float32
 NN_MIX_FP32, NN_MIX_BF16 = 0, 1  # arithmetic of the inference 8 -> 8 channel mixing (sqcg_nn_set_mixing)
 MODE_F64, MODE_MIXED = 0, 1
 MS_SHIFT_RU = 0x10  # OR-ed into a multi-shift mode: shift-aware reliable updates (sqcg_multishift_ru_record)
+MS_NO_RU = 0x20  # OR-ed into a mixed multi-shift mode: no base reliable updates in the shared loop
 ANTIPERIODIC_T, PHASES_FOLDED = 1, 2
 RECON12_LONG = 1
 EIGHT_WAY = 2
@@ -372,8 +373,9 @@ class Lattice:
         return list(infos)
 
     def multishift_ru_record(self):
-        """Shift-aware reliable updates of the last multi-shift solve (mode | MS_SHIFT_RU): a list of
-        (iteration, |r_0| / |b|, losses |r_s - zeta'_s r_0| / |b| per shift in the caller's order)."""
+        """Reliable updates of the last multi-shift solve (the mixed mode's base updates, or shift-aware with
+        mode | MS_SHIFT_RU): a list of (iteration, |r_0| / |b|, losses |r_s - zeta'_s r_0| / |b| per shift in
+        the caller's order; NaN where not measured)."""
         nu, ns = ctypes.c_int(), ctypes.c_int()
         _check(library().sqcg_multishift_ru_record(self._h, 0, ctypes.byref(nu), ctypes.byref(ns), None, None, None),
                "sqcg_multishift_ru_record")

@@ -308,17 +308,16 @@ __global__ void __launch_bounds__(kFinishThreads) k_ms_ru_sum3(SolverState* st, 
 
 // The FP64 base residual r_t replaces the iterated r, and every direction still moving takes the
 // same change scaled by its shift's zeta (the base direction's is 1): p_s += zeta_s (r_t - r).
-template <typename R>
+template <typename R, typename RT>
 __global__ void __launch_bounds__(kThreads)
-k_ms_ru_fix(MSPtrs P, typename V2<R>::T* __restrict__ r, const double2* __restrict__ rt, int Vh,
-            const SolverState* st) {
+k_ms_ru_fix(MSPtrs P, typename V2<R>::T* __restrict__ r, const RT* __restrict__ rt, int Vh, const SolverState* st) {
   typedef typename V2<R>::T R2;
   const int ns = st->nshift;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * Vh + i;
-      const double2 t = rt[k];
+      const double2 t = make_double2((double)rt[k].x, (double)rt[k].y);
       R2 rc = r[k];
       const double dx = t.x - (double)rc.x, dy = t.y - (double)rc.y;
       rc.x = (R)t.x;
@@ -507,7 +506,7 @@ int launch_ms_ru_sums(sqcg_ctx* ctx, const double2* a, const double2* b, double 
   return SQCG_OK;
 }
 
-int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const double2* rt, cudaStream_t s) {
+int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const void* rt, int rt_prec, cudaStream_t s) {
   const int Vh = ctx->g.Vh, grid = blas_grid(ctx);
   if (nshift < 1 || nshift > ctx->ms_nalloc) return SQCG_ERR_INVALID_ARG;
   MSPtrs P;
@@ -515,10 +514,16 @@ int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const double2* rt, cu
     P.x[j] = nullptr;
     P.p[j] = (j < nshift) ? ctx->ms_p[j] : nullptr;
   }
-  if (mixed)
-    k_ms_ru_fix<float><<<grid, kThreads, 0, s>>>(P, ctx->r32, rt, Vh, ctx->st);
+  const double2* t64 = static_cast<const double2*>(rt);
+  const float2* t32 = static_cast<const float2*>(rt);
+  if (mixed && rt_prec == SQCG_F32)
+    k_ms_ru_fix<float, float2><<<grid, kThreads, 0, s>>>(P, ctx->r32, t32, Vh, ctx->st);
+  else if (mixed)
+    k_ms_ru_fix<float, double2><<<grid, kThreads, 0, s>>>(P, ctx->r32, t64, Vh, ctx->st);
+  else if (rt_prec == SQCG_F64)
+    k_ms_ru_fix<double, double2><<<grid, kThreads, 0, s>>>(P, ctx->r64, t64, Vh, ctx->st);
   else
-    k_ms_ru_fix<double><<<grid, kThreads, 0, s>>>(P, ctx->r64, rt, Vh, ctx->st);
+    return SQCG_ERR_INVALID_ARG;
   SQCG_CUDA_TRY(cudaGetLastError());
   return SQCG_OK;
 }

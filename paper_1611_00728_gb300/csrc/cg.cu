@@ -566,11 +566,46 @@ namespace {
 // space do not remove. Then r_0 replaces the iterated base residual and every moving direction takes
 // the change, p_s += zeta_s (r_0 - r). sig, tl: shifts and tolerances in the loop's order (base
 // first); perm maps that order to the caller's. ru_count[j] counts the updates shift j continued from.
+// shifts_too = 0 (the mixed mode's base updates) skips the shifts' residuals: only the base residual is replaced,
+// in mixed mode computed with the float-float Dslash (as the single-mass reliable update) when that is
+// the context's update arithmetic, and written as FP32 into the free A p vector.
 int ms_shift_aware_update(sqcg_ctx* ctx, int mixed, int nshift, const double* sig, const double* tl,
                           const int* perm, const void* b, void* const* xs, cudaStream_t s, int* ru_count,
-                          int* launches) {
+                          int* launches, bool shifts_too) {
   SolverState* h = ctx->st_host;
   const size_t n = (size_t)ctx->g.Vh * 3;
+  if (!shifts_too && mixed && ctx->ru_arith == SQCG_FF) {
+    SQCG_TRY(launch_split_ff((const double2*)xs[0], ctx->xff, n, s));
+    FFLaunch F = {};
+    F.out_parity = 1; F.in = ctx->xff; F.out_ff = ctx->tmp64;  // tmp64 holds float4 [3][Vh]
+    SQCG_TRY(launch_dslash_ff(ctx, F, s));
+    F = FFLaunch{};
+    F.out_parity = 0; F.true_resid = 1; F.in = ctx->tmp64; F.out32 = ctx->Ap32; F.x = xs[0]; F.b = b;
+    F.sigma = sig[0]; F.fin = FIN_STORE;  // |r_0|^2 (FP64 sum) into st->pAp, free while the loop pauses
+    SQCG_TRY(launch_dslash_ff(ctx, F, s));
+    *launches += 4;
+    SQCG_TRY(read_state(ctx, s));
+    const double r0n = h->pAp;
+    const int u = ctx->ms_rec_n++;
+    if (u < SQCG_MS_RU_RECORD) {
+      ctx->ms_rec_iter[u] = h->iter;
+      ctx->ms_rec_base[u] = sqrt(r0n / h->bb);
+      for (int j = 0; j < nshift; ++j) ctx->ms_rec_loss[u][perm[j]] = (j == 0) ? 0.0 : NAN;
+    }
+    if (!isfinite(r0n)) {
+      h->status = SQCG_ERR_BREAKDOWN;
+      h->done = 1;
+      h->need_update = 0;
+      return write_state(ctx, s);
+    }
+    ru_count[0] += 1;
+    h->rr = h->rr_true = h->rr_max = r0n;
+    h->need_update = 0;
+    h->updates += 1;
+    SQCG_TRY(write_state(ctx, s));
+    *launches += 1;
+    return launch_ms_ru_fix(ctx, mixed, nshift, ctx->Ap32, SQCG_F32, s);
+  }
   if (!ctx->ms_ru_vec && cudaMalloc(&ctx->ms_ru_vec, 2 * n * sizeof(double2)) != cudaSuccess) {
     cudaGetLastError();
     return SQCG_ERR_NO_MEMORY;
@@ -606,7 +641,7 @@ int ms_shift_aware_update(sqcg_ctx* ctx, int mixed, int nshift, const double* si
   }
   double scale[SQCG_MAX_SHIFTS], l2s[SQCG_MAX_SHIFTS];
   int keep[SQCG_MAX_SHIFTS] = {};
-  for (int j = 1; j < nshift; ++j) {
+  for (int j = 1; j < nshift && shifts_too; ++j) {
     if (h->active[j] != 1) continue;
     SQCG_TRY(true_resid(xs[j], sig[j], rs));
     SQCG_TRY(launch_ms_ru_sums(ctx, r0, rs, 0.0, s));
@@ -637,7 +672,7 @@ int ms_shift_aware_update(sqcg_ctx* ctx, int mixed, int nshift, const double* si
   h->updates += 1;
   SQCG_TRY(write_state(ctx, s));
   *launches += 1;
-  return launch_ms_ru_fix(ctx, mixed, nshift, r0, s);
+  return launch_ms_ru_fix(ctx, mixed, nshift, r0, SQCG_F64, s);
 }
 
 }  // namespace
@@ -650,8 +685,11 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
                                         void* const* x, const double* tol, int max_iter, int mode,
                                         sqcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
-  const int ru = (mode & SQCG_MS_SHIFT_RU) != 0;
-  mode &= ~SQCG_MS_SHIFT_RU;
+  const int ru_shifts = (mode & SQCG_MS_SHIFT_RU) != 0, no_ru = (mode & SQCG_MS_NO_RU) != 0;
+  mode &= ~(SQCG_MS_SHIFT_RU | SQCG_MS_NO_RU);
+  if (ru_shifts && no_ru) return SQCG_ERR_INVALID_ARG;
+  // mixed: base reliable updates unless SQCG_MS_NO_RU; FP64: only with SQCG_MS_SHIFT_RU
+  const int ru = ru_shifts || (mode == SQCG_MODE_MIXED && !no_ru);
   if (!ctx || nshift < 1 || nshift > SQCG_MAX_SHIFTS || !shifts || !x || !tol || max_iter <= 0 ||
       (mode != SQCG_MODE_F64 && mode != SQCG_MODE_MIXED))
     return SQCG_ERR_INVALID_ARG;
@@ -735,7 +773,7 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
   h->rr = h->rr_prev = h->rr_max = h->bb;
   SQCG_TRY(write_state(ctx, s));
 
-  // the shared loop; with SQCG_MS_SHIFT_RU it pauses for each shift-aware reliable update
+  // the shared loop; it pauses for each reliable update (base, or shift-aware with SQCG_MS_SHIFT_RU)
   int loops = 0, ru_launches = 0;
   int ru_count[SQCG_MAX_SHIFTS] = {};
   double sig_l[SQCG_MAX_SHIFTS], tol_l[SQCG_MAX_SHIFTS];
@@ -752,7 +790,8 @@ extern "C" int sqcg_multishift_cg_solve(sqcg_ctx* ctx, int nshift, const double*
     else SQCG_TRY(run_loop(ctx, g, max_iter, s, &seg));
     loops += seg;
     if (h->done || !(h->ms_ru && h->need_update)) break;
-    SQCG_TRY(ms_shift_aware_update(ctx, mixed, nshift, sig_l, tol_l, perm, b, xs, s, ru_count, &ru_launches));
+    SQCG_TRY(ms_shift_aware_update(ctx, mixed, nshift, sig_l, tol_l, perm, b, xs, s, ru_count, &ru_launches,
+                                   ru_shifts != 0));
   }
   int launches = 2 + 1 + nshift + loops * kMSKernelsPerIter + ru_launches;
   const int loop_status = h->done ? h->status : SQCG_ERR_NOT_CONVERGED;

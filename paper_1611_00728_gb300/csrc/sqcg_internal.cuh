@@ -312,9 +312,10 @@ int launch_ms_update_x(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, 
 
 int launch_ms_xpay(sqcg_ctx* ctx, int mixed, int nshift, double2* const* x, cudaStream_t s);
 // shift-aware reliable update of the multi-shift loop: Re<a, b>, |b - z a|^2 and |a|^2 (FP64 vectors) into
-// st->ms_sums; then r <- rt with p_s += zeta_s (rt - r) for every direction still moving
+// st->ms_sums; then r <- rt (FP64, or FP32 in mixed mode) with p_s += zeta_s (rt - r) for every direction
+// still moving
 int launch_ms_ru_sums(sqcg_ctx* ctx, const double2* a, const double2* b, double z, cudaStream_t s);
-int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const double2* rt, cudaStream_t s);
+int launch_ms_ru_fix(sqcg_ctx* ctx, int mixed, int nshift, const void* rt, int rt_prec, cudaStream_t s);
 
 // float-float Dslash (dslash_ff.cu): in and out_ff are float4 [3][Vh] (re_hi, re_lo, im_hi, im_lo);
 // true_resid: out32 (FP32) = b - sigma x + D in with |.|^2 reduced in FP64 (x, b FP64)

@@ -496,8 +496,8 @@ def test_multishift_shift_aware_reliable_updates(sqcg, links_cache, monkeypatch,
         monkeypatch.delenv("SQCG_LAUNCH_MODE")
         assert all(np.array_equal(g, lat.unpack(x)) for g, x in zip(got, xe))
         plain = lat.multishift_cg_solve(shifts, db, [lat.new_spinor() for _ in shifts], tol=tol, max_iter=20000,
-                                        mode=mode)
-        assert lat.multishift_ru_record() == []  # without the flag nothing is recorded
+                                        mode=mode | (sqcg.MS_NO_RU if mode == 1 else 0))
+        assert lat.multishift_ru_record() == []  # no reliable update in that loop
     for s, info, x in zip(shifts, infos, got):
         assert info.status == 0 and info.true_rel_resid <= tol
         assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
@@ -517,6 +517,47 @@ def test_multishift_shift_aware_reliable_updates(sqcg, links_cache, monkeypatch,
             assert abs(infos[j].iters - plain[j].iters) <= 2
     else:
         assert all(np.isfinite(loss[j]) for (_, _, loss), js in zip(rec, live) for j in js)
+
+
+def test_multishift_base_reliable_updates(sqcg, links_cache, monkeypatch):
+    """The mixed multi-shift pauses for float-float base residuals (no shift is measured or rescaled);
+    every shift reaches its true residual (oracle-checked) on a ragged lattice with unsorted shifts, the
+    graph and eager forms agree bit for bit, and MS_NO_RU runs the loop without updates, to the same
+    tolerance."""
+    L, tol = (8, 10, 12, 14), 1e-8
+    fat, lng = links_cache(L, 88)
+    shifts = [0.3, 0.0004, 0.02, 0.0012]
+    base = int(np.argmin(shifts))
+    b = synth.gaussian_source(L, 4101)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        db = lat.pack(b)
+        xs = [lat.new_spinor() for _ in shifts]
+        infos = lat.multishift_cg_solve(shifts, db, xs, tol=tol, max_iter=20000, mode=sqcg.MODE_MIXED)
+        got = [lat.unpack(x) for x in xs]
+        rec = lat.multishift_ru_record()
+        monkeypatch.setenv("SQCG_LAUNCH_MODE", "eager")
+        xe = [lat.new_spinor() for _ in shifts]
+        lat.multishift_cg_solve(shifts, db, xe, tol=tol, max_iter=20000, mode=sqcg.MODE_MIXED)
+        monkeypatch.delenv("SQCG_LAUNCH_MODE")
+        assert all(np.array_equal(g, lat.unpack(x)) for g, x in zip(got, xe))
+        xn = [lat.new_spinor() for _ in shifts]
+        no_ru = lat.multishift_cg_solve(shifts, db, xn, tol=tol, max_iter=20000, mode=sqcg.MODE_MIXED | sqcg.MS_NO_RU)
+        assert lat.multishift_ru_record() == []
+        got_n = [lat.unpack(x) for x in xn]
+        with pytest.raises(sqcg.SqcgError):
+            lat.multishift_cg_solve(shifts, db, xn, tol=tol, mode=sqcg.MODE_MIXED | sqcg.MS_NO_RU | sqcg.MS_SHIFT_RU)
+    for s, info, x, i_n, x_n in zip(shifts, infos, got, no_ru, got_n):
+        assert info.status == 0 and info.true_rel_resid <= tol
+        assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
+        assert i_n.status == 0 and oracle.true_rel_residual(L, fat, lng, s, b, x_n) <= tol
+    assert len(rec) >= 2
+    prev = 1.0
+    for it, r0, loss in rec:
+        assert 0 < it and 0 < r0 < prev
+        prev = r0
+        assert loss[base] == 0.0 and all(np.isnan(v) for j, v in enumerate(loss) if j != base)
+    assert infos[base].reliable_updates >= len(rec)
 
 
 @pytest.mark.parametrize("mode", [0, 1])
