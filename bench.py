@@ -773,6 +773,7 @@ def measure_learned(torch, sq, clk, L, params, steps, compare=True, tag="learned
         out["speedup_vs_fp64_cg"] = out["fp64_cg"]["ms"] / out["fcg_nn"]["ms"]
         out["speedup_vs_mixed_cg"] = out["mixed_cg"]["ms"] / out["fcg_nn"]["ms"]
         out["bf16_mixing_speedup_vs_mixed_cg"] = out["mixed_cg"]["ms"] / out["fcg_nn_bf16_mixing"]["ms"]
+        out["bf16_mixing_speedup_vs_fp64_cg"] = out["fp64_cg"]["ms"] / out["fcg_nn_bf16_mixing"]["ms"]
     net.close()
     lat.close()
     return out

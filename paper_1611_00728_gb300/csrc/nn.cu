@@ -387,14 +387,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_conv88(ConvArgs a) {
 }
 
 // The 8 -> 8 inference layer with its channel mixing on the tensor cores (BF16 operands, FP32
-// accumulation): for each colour the mixing of one tap is a real GEMM of 16 sites x 16 inputs (8 channels,
-// re and im) by 16 x 16 (8 output channels, re and im; a complex weight w acts on (re, im) as the 2 x 2 block
-// [[w.x, w.y], [-w.y, w.x]]), one m16n8k16 warp MMA per colour and 8-column half. A warp takes 16 sites; lane
-// (g, t) = (lane / 4, lane % 4) transports input channels t and t + 4 of sites g and g + 8 on the CUDA cores,
-// which are exactly the elements of the MMA's A fragment it holds (rows g, g + 8; columns 2t, 2t + 1 and
-// 2t + 8, 2t + 9), and receives output channels t and t + 4 of the same sites in its accumulator fragment,
-// so nothing is exchanged between lanes. The transported vectors are rounded to BF16 (the weights are BF16
-// values already); sums and the gate are FP32.
+// accumulation). For each colour the mixing of one tap is a real GEMM of sites x 16 inputs (8 channels,
+// re and im) by 16 x 16 (8 output channels, re and im; a complex weight w acts on (re, im) as the 2 x 2
+// block [[w.x, w.y], [-w.y, w.x]]): per 16 sites, one m16n8k16 warp MMA per colour and 8-column half.
+// The gathers are those of k_conv88: two lanes per site, each transporting four input channels; a step
+// gathers four hops (both directions of two dimensions), so their loads are in flight together (the layer
+// is bound by gather latency, not by its arithmetic). Each lane rounds its transported channels to BF16 and writes
+// them, one 16-byte half row per colour, into its warp's shared-memory tile of 16 sites; ldmatrix then
+// hands the MMA its A fragments (16 sites x 16 inputs per colour). The weights' B fragments are built
+// once per block in shared memory. Sums and the gate are FP32.
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const unsigned*>(&v);
@@ -407,43 +408,53 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a
                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&a)[4], const void* smem_row) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+               : "r"(addr)
+               : "memory");
+}
+
+// A tile row is one site's 16 BF16 inputs of one colour: two 16-byte halves (channels 0-3, 4-7). The
+// half index is XOR-ed with bit 2 of the row, so the 8 rows an ldmatrix phase reads (32-byte stride)
+// fall on distinct banks.
+__device__ __forceinline__ int tc_half(int row, int half) { return half ^ ((row >> 2) & 1); }
+
 template <int OUT>
-__global__ void __launch_bounds__(kThreads, 4) k_conv88_tc(ConvArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_conv88_tc(ConvArgs a) {
   if (a.st && !gate_open(a.st, a.gate)) return;
+  constexpr int kWarps = kThreads / 32;
+  // B fragments [tap][nt][half][lane]: rows k = 2 ci + comp (ci = t, t + 4 for half 0, 1), column n = g of
+  // each 8-column half nt, i.e. output channel o = 4 nt + g / 2, component g % 2 (lane = 4 g + t)
+  __shared__ unsigned sB[NT][2][2][32];
+  __shared__ __align__(16) uint4 sA[kWarps][4][3][16][2];  // [warp][hop][colour][site][half], BF16 inputs
+  for (int e = threadIdx.x; e < NT * 2 * 2 * 32; e += blockDim.x) {
+    const int l = e & 31, half = (e >> 5) & 1, nt = (e >> 6) & 1, tap = e >> 7;
+    const int o = 4 * nt + (l >> 3), oc = (l >> 2) & 1;
+    const float2 w = a.W[(tap * CH + o) * CH + (l & 3) + 4 * half];
+    // (re, im) input component -> output component oc: re: (w.x, -w.y); im: (w.y, w.x)
+    sB[tap][nt][half][l] = oc == 0 ? pack_bf16(w.x, -w.y) : pack_bf16(w.y, w.x);
+  }
+  __syncthreads();
   const Geom& g = a.g;
   const int Vh = g.Vh;
-  const int lane = threadIdx.x & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  const long base = ((long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long nsites = (long)a.npar * Vh;
-  // B fragments of every tap: rows k = 2 ci + comp (ci = tq, tq + 4), column n = g of each 8-column half,
-  // i.e. output channel o = 4 nt + g / 2, component g % 2
-  unsigned bf[NT][2][2];
-#pragma unroll
-  for (int tap = 0; tap < NT; ++tap)
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int o = 4 * nt + (gq >> 1), oc = gq & 1;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const float2 w = a.W[(tap * CH + o) * CH + tq + 4 * half];
-        // (re, im) input component -> output component oc: re: (w.x, -w.y); im: (w.y, w.x)
-        bf[tap][nt][half] = oc == 0 ? pack_bf16(w.x, -w.y) : pack_bf16(w.y, w.x);
-      }
-    }
-  // this lane's two sites (rows g and g + 8 of the warp's 16)
-  int par[2], idx[2];
-  bool ok[2];
-  Site st2[2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const long site = base + gq + 8 * r;
-    ok[r] = site < nsites;
-    const long sv = ok[r] ? site : 0;
-    par[r] = a.par0 + (int)(sv / Vh);
-    idx[r] = (int)(sv % Vh);
-    st2[r] = site_of(g, idx[r], par[r]);
-  }
+  const long site0 = ((long)blockIdx.x * kWarps + warp) * 16;  // the warp's first site
+  // two lanes per site, as k_conv88: lane 2 s + h gathers and transports input channels 4 h .. 4 h + 3 of
+  // site s (a site past the end reads site 0; its rows are not stored)
+  const int sl = lane >> 1, h = lane & 1;
+  const long site = site0 + sl;
+  const long sv = site < nsites ? site : 0;
+  const int par = a.par0 + (int)(sv / Vh), idx = (int)(sv % Vh);
+  const int q = 1 - par;
+  const Site st = site_of(g, idx, par);
+  uint4(*tile)[3][16][2] = sA[warp];
+  const int my_half = tc_half(sl, h);
+  // ldmatrix: lane l addresses row l % 8 (+ 8 for matrices 1, 3) of half l / 16
+  const int mrow = (lane & 7) + 8 * ((lane >> 3) & 1);
+  const int mhalf = tc_half(mrow, lane >> 4);
   float acc[3][2][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -451,61 +462,71 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv88_tc(ConvArgs a) {
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[c][nt][e] = 0.f;
-  // t[r][h][c]: the tap's input channel tq + 4 h at site r, colour c
-  auto mma_tap = [&](int tap, const float2 (&t)[2][2][3]) {
+  auto mma_tap = [&](int tap, int slot) {
+    const unsigned b00 = sB[tap][0][0][lane], b01 = sB[tap][0][1][lane];
+    const unsigned b10 = sB[tap][1][0][lane], b11 = sB[tap][1][1][lane];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const unsigned af[4] = {pack_bf16(t[0][0][c].x, t[0][0][c].y), pack_bf16(t[1][0][c].x, t[1][0][c].y),
-                              pack_bf16(t[0][1][c].x, t[0][1][c].y), pack_bf16(t[1][1][c].x, t[1][1][c].y)};
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(acc[c][nt], af, bf[tap][nt][0], bf[tap][nt][1]);
+      unsigned af[4];
+      ldmatrix_x4(af, &tile[slot][c][mrow][mhalf]);
+      mma_bf16_16816(acc[c][0], af, b00, b01);
+      mma_bf16_16816(acc[c][1], af, b10, b11);
     }
   };
-  // self tap
+  // self tap: this lane's four channels at its site
   {
-    float2 t[2][2][3];
+    unsigned w[3][4];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          t[r][h][c] = ok[r] ? __ldg(a.in + (((size_t)(tq + 4 * h) * 2 + par[r]) * 3 + c) * Vh + idx[r])
-                             : make_float2(0.f, 0.f);
-    mma_tap(0, t);
-  }
-  // hops: each lane transports its two channels at its two sites
-#pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll 1
-    for (int dir = 0; dir < 2; ++dir) {
-      float2 t[2][2][3];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int q = 1 - par[r];
-        const int j = nbr(g, st2[r], mu, dir == 0 ? +1 : -1);
-        float2 u[9];
-        if (dir == 0) load_link9(a.fat[par[r]] + (size_t)mu * 9 * Vh, Vh, idx[r], u);  // F_mu(n)
-        else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);                     // F_mu(n - mu)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float2 v[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)(tq + 4 * h) * 2 + q) * 3 + c) * Vh + j);
-          apply_link(u, dir == 1, v, t[r][h]);
-          if (!ok[r])
-#pragma unroll
-            for (int c = 0; c < 3; ++c) t[r][h][c] = make_float2(0.f, 0.f);
-        }
+      for (int c = 0; c < 3; ++c) {
+        const float2 v = __ldg(a.in + (((size_t)(4 * h + k) * 2 + par) * 3 + c) * Vh + idx);
+        w[c][k] = pack_bf16(v.x, v.y);
       }
-      mma_tap(1 + 2 * mu + dir, t);
-    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tile[0][c][sl][my_half] = make_uint4(w[c][0], w[c][1], w[c][2], w[c][3]);
+    __syncwarp();
+    mma_tap(0, 0);
   }
-  // epilogue: accumulator element (row g or g + 8, column 2 tq + {0, 1}) of half nt is output channel
-  // o = 4 nt + tq, (re, im), at site r
+  // hops: two directions, forward and backward, per step (four hops)
+#pragma unroll 1
+  for (int mp = 0; mp < 2; ++mp) {
+    unsigned w[4][3][4];
+#pragma unroll
+    for (int hop = 0; hop < 4; ++hop) {
+      const int mu = 2 * mp + (hop >> 1), dir = hop & 1;
+      const int j = nbr(g, st, mu, dir == 0 ? +1 : -1);
+      float2 u[9];
+      if (dir == 0) load_link9(a.fat[par] + (size_t)mu * 9 * Vh, Vh, idx, u);  // F_mu(n)
+      else load_link9(a.fat[q] + (size_t)mu * 9 * Vh, Vh, j, u);               // F_mu(n - mu)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 v[3], t[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = __ldg(a.in + (((size_t)(4 * h + k) * 2 + q) * 3 + c) * Vh + j);
+        apply_link(u, dir == 1, v, t);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[hop][c][k] = pack_bf16(t[c].x, t[c].y);
+      }
+    }
+    __syncwarp();  // the previous step's ldmatrix reads of this warp's tiles are done
+#pragma unroll
+    for (int hop = 0; hop < 4; ++hop)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        tile[hop][c][sl][my_half] = make_uint4(w[hop][c][0], w[hop][c][1], w[hop][c][2], w[hop][c][3]);
+    __syncwarp();
+#pragma unroll
+    for (int hop = 0; hop < 4; ++hop) mma_tap(1 + 4 * mp + hop, hop);
+  }
+  // epilogue: accumulator element (row g or g + 8, column 2 t + {0, 1}) of half nt is output channel
+  // o = 4 nt + t, (re, im), at site site0 + g (+ 8)
+  const int gq = lane >> 2, tq = lane & 3;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    if (!ok[r]) continue;
+    const long s2 = site0 + gq + 8 * r;
+    if (s2 >= nsites) continue;
+    const int par2 = a.par0 + (int)(s2 / Vh), idx2 = (int)(s2 % Vh);
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
       const int o = 4 * nt + tq;
@@ -521,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_conv88_tc(ConvArgs a) {
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        a.out[(((size_t)o * 2 + par[r]) * 3 + c) * Vh + idx[r]] = make_float2(v[c].x * gf, v[c].y * gf);
+        a.out[(((size_t)o * 2 + par2) * 3 + c) * Vh + idx2] = make_float2(v[c].x * gf, v[c].y * gf);
     }
   }
 }
@@ -866,7 +887,7 @@ int conv_launch(sqcg_nn* nn, int layer, bool adjoint, int in_mode, int out_mode,
     k_conv<1, CH, IN_EVEN_SCALED, OUT_GATE_TRAIN><<<grid, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_INFER && !adjoint &&
            nn->mixing == SQCG_NN_MIX_BF16)
-    k_conv88_tc<OUT_GATE_INFER><<<grid_for(npar * (int)Vh, 16 * (kThreads / 32)), kThreads, 0, s>>>(a);
+    k_conv88_tc<OUT_GATE_INFER><<<grid_for(npar * (int)Vh, kThreads / 2), kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_INFER)
     k_conv88<OUT_GATE_INFER><<<grid2, kThreads, 0, s>>>(a);
   else if (cin == CH && cout == CH && in_mode == IN_FULL && out_mode == OUT_GATE_TRAIN)
