@@ -33,6 +33,25 @@ def test_header_declares_the_boundary():
         assert want in names
 
 
+def test_binding_constants_match_the_header():
+    """Every mode, flag and precision the binding passes through the ABI has the header's value."""
+    import paper_1611_00728_gb300 as sq
+
+    text = open(HEADER).read()
+    defs = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define SQCG_([A-Z0-9_]+)\s+\(?(-?(?:0x)?[0-9a-fA-F]+)\)?", text)}
+    pairs = {"F64": "F64", "F32": "F32", "FF": "FF", "MODE_F64": "MODE_F64", "MODE_MIXED": "MODE_MIXED",
+             "ANTIPERIODIC_T": "ANTIPERIODIC_T", "PHASES_FOLDED": "PHASES_FOLDED", "RECON12_LONG": "RECON12_LONG",
+             "EIGHT_WAY": "EIGHT_WAY", "MS_SHIFT_RU": "MS_SHIFT_RU", "MS_NO_RU": "MS_NO_RU",
+             "NN_MIX_FP32": "NN_MIX_FP32", "NN_MIX_BF16": "NN_MIX_BF16", "NN_NPARAMS": "NN_NPARAMS"}
+    for py, c in pairs.items():
+        assert getattr(sq, py) == defs[c], (py, getattr(sq, py), defs[c])
+    errs = {v: k[len("ERR_"):] for k, v in defs.items() if k.startswith("ERR_")}
+    assert sq.ERR_NAMES == errs
+    # the multi-shift flags sit above every mode value and apart from each other
+    assert defs["MS_SHIFT_RU"] & defs["MS_NO_RU"] == 0
+    assert max(defs["MODE_F64"], defs["MODE_MIXED"]) < min(defs["MS_SHIFT_RU"], defs["MS_NO_RU"])
+
+
 def test_library_loads_and_exports_every_declared_symbol(libpath):
     lib = ctypes.CDLL(libpath)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
