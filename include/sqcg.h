@@ -139,14 +139,17 @@ int sqcg_set_stream(sqcg_ctx* ctx, void* cuda_stream);
  * FP64 true residual is recomputed when the iterated |r| falls below
  * delta * (max |r| since the last update), or after `interval` iterations,
  * whichever comes first (0 < delta < 1, interval >= 1; defaults 0.001 and 100).
- * The batched solve uses the settings of its first context. */
+ * The batched solve uses the settings of its first context. The multi-shift
+ * loop's reliable updates use delta only. */
 int sqcg_set_reliable_update(sqcg_ctx* ctx, double delta, int interval);
 
 /* Arithmetic of the true-residual recomputations (reliable updates and the
- * final convergence check) of the single-mass mixed-precision solve on this
- * context: SQCG_FF (default; float-float Dslash from float-float copies of the
- * FP64 links, the sum b - sigma x + D x and the norm in FP64) or SQCG_F64 (the
- * FP64 Dslash). The FP64 solver mode always uses FP64. Not in the paper. */
+ * final convergence check) of the single-mass mixed-precision solve, and of the
+ * mixed multi-shift loop's base reliable updates, on this context: SQCG_FF
+ * (default; float-float Dslash from float-float copies of the FP64 links, the
+ * sum b - sigma x + D x and the norm in FP64) or SQCG_F64 (the FP64 Dslash).
+ * The FP64 solver mode, and the shift-aware updates (SQCG_MS_SHIFT_RU), always
+ * use FP64. Not in the paper. */
 int sqcg_set_update_arithmetic(sqcg_ctx* ctx, int prec);
 
 /* Bytes of one device colour vector on one parity in precision prec (Vh * 3 * 2 * sizeof(real);

@@ -523,7 +523,7 @@ def test_multishift_base_reliable_updates(sqcg, links_cache, monkeypatch):
     """The mixed multi-shift pauses for float-float base residuals (no shift is measured or rescaled);
     every shift reaches its true residual (oracle-checked) on a ragged lattice with unsorted shifts, the
     graph and eager forms agree bit for bit, and MS_NO_RU runs the loop without updates, to the same
-    tolerance."""
+    tolerance, as do the base updates in FP64 arithmetic (set_update_arithmetic(F64))."""
     L, tol = (8, 10, 12, 14), 1e-8
     fat, lng = links_cache(L, 88)
     shifts = [0.3, 0.0004, 0.02, 0.0012]
@@ -547,10 +547,19 @@ def test_multishift_base_reliable_updates(sqcg, links_cache, monkeypatch):
         got_n = [lat.unpack(x) for x in xn]
         with pytest.raises(sqcg.SqcgError):
             lat.multishift_cg_solve(shifts, db, xn, tol=tol, mode=sqcg.MODE_MIXED | sqcg.MS_NO_RU | sqcg.MS_SHIFT_RU)
-    for s, info, x, i_n, x_n in zip(shifts, infos, got, no_ru, got_n):
+        # the base updates in FP64 arithmetic instead of float-float
+        lat.set_update_arithmetic(sqcg.F64)
+        x64 = [lat.new_spinor() for _ in shifts]
+        i64 = lat.multishift_cg_solve(shifts, db, x64, tol=tol, max_iter=20000, mode=sqcg.MODE_MIXED)
+        rec64 = lat.multishift_ru_record()
+        got64 = [lat.unpack(x) for x in x64]
+        lat.set_update_arithmetic(sqcg.FF)
+    for s, info, x, i_n, x_n, i6, x6 in zip(shifts, infos, got, no_ru, got_n, i64, got64):
         assert info.status == 0 and info.true_rel_resid <= tol
         assert oracle.true_rel_residual(L, fat, lng, s, b, x) <= tol
         assert i_n.status == 0 and oracle.true_rel_residual(L, fat, lng, s, b, x_n) <= tol
+        assert i6.status == 0 and oracle.true_rel_residual(L, fat, lng, s, b, x6) <= tol
+    assert len(rec64) >= 2
     assert len(rec) >= 2
     prev = 1.0
     for it, r0, loss in rec:
