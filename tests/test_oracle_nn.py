@@ -105,3 +105,26 @@ def test_residual_norm_loss_is_the_preconditioned_residual():
     z = nn.apply(L, fat, params, r)
     want = np.linalg.norm(oracle.normal_op(L, fat, lng, sigma, z) - r) ** 2 / np.linalg.norm(r) ** 2
     assert abs(loss - want) <= 1e-10 * want
+
+
+def test_bf16_rounding_of_the_rounded_oracle_test_is_round_to_nearest_even():
+    """The tensor-core network test inserts BF16 rounding into the oracle with its own bit arithmetic;
+    that rounding must be the conversion the GPU's cvt.rn.bf16x2 performs: round to nearest, ties to
+    even (the same as PyTorch's float32 -> bfloat16 cast on the CPU), on random values and exact ties."""
+    torch = pytest.importorskip("torch")
+    from tests.test_gpu_nn import bf16c
+
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(4096) * 10.0 ** rng.integers(-20, 20, 4096),
+                        [0.0, -0.0, 1.0, -1.0, 3.0e38, -3.0e38, 1e-40]]).astype(np.float32)
+    # exact ties: the 16 dropped bits are 0x8000; the kept upper halves (sign, exponent, 7 mantissa bits)
+    # are drawn over both signs and exponents 2^-64 .. 2^63, so the kept last bit is even and odd
+    upper = rng.integers(0x1F80, 0x5F00, 1024, dtype=np.uint32) | (rng.integers(0, 2, 1024, dtype=np.uint32) << 15)
+    ties = ((upper << np.uint32(16)) | np.uint32(0x8000)).view(np.float32)
+    assert np.all(np.isfinite(ties)) and len(set(upper & 1)) == 2
+    for v in (x, ties):
+        want = torch.from_numpy(v.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+        got = bf16c(v.astype(np.float64) + 0j).real
+        assert np.array_equal(got, want)
+        got_im = bf16c(1j * v.astype(np.float64)).imag
+        assert np.array_equal(got_im, want)
