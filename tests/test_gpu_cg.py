@@ -569,6 +569,33 @@ def test_multishift_base_reliable_updates(sqcg, links_cache, monkeypatch):
     assert infos[base].reliable_updates >= len(rec)
 
 
+def test_multishift_reliable_update_flags_edge_cases(sqcg, links_cache):
+    """One shift with shift-aware updates (the base alone: every update records only its own zero loss),
+    and the rational application with the flag passed through to its multi-shift solve."""
+    L, tol, m = (8, 8, 8, 8), 1e-8, 0.1
+    fat, lng = links_cache(L, 1001)
+    b = synth.gaussian_source(L, 2302)
+    a0, a, beta = synth.inverse_sqrt_rational(9, 4 * m * m, 64.0)
+    shifts = 4 * m * m + beta
+    want = oracle.rational_apply(L, fat, lng, shifts, a, 0.25, b, tol=1e-13)
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng, recon12=True)
+        db = lat.pack(b)
+        x = [lat.new_spinor()]
+        one = lat.multishift_cg_solve([0.01], db, x, tol=tol, max_iter=20000, mode=sqcg.MODE_MIXED | sqcg.MS_SHIFT_RU)
+        rec = lat.multishift_ru_record()
+        x1 = lat.unpack(x[0])
+        out = lat.new_spinor()
+        infos = lat.rational_apply(shifts, a, 0.25, db, out, tol=1e-9, mode=sqcg.MODE_MIXED | sqcg.MS_SHIFT_RU)
+        rec_r = lat.multishift_ru_record()
+        got = lat.unpack(out)
+    assert one[0].status == 0 and oracle.true_rel_residual(L, fat, lng, 0.01, b, x1) <= tol
+    assert len(rec) >= 1 and all(loss == [0.0] for _, _, loss in rec)
+    assert all(i.status == 0 and i.true_rel_resid <= 1e-9 for i in infos)
+    assert rel(got, want) <= 2e3 * 1e-9  # as the rational test without the flag
+    assert len(rec_r) >= 1 and all(len(loss) == len(shifts) for _, _, loss in rec_r)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_multishift_degenerate_and_maximum_shift_counts(sqcg, links_cache, mode):
     """One shift is plain CG; 32 shifts (the maximum) with duplicates all converge; bad arguments are refused."""

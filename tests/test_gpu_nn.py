@@ -144,6 +144,35 @@ def test_loss_and_gradient_match_oracle(sqcg, links_cache, norm):
         assert rel(grad[lo:hi].astype(np.float64), want[lo:hi]) <= 1e-3
 
 
+def test_training_kernels_ignore_the_inference_mixing(sqcg, links_cache):
+    """The BF16 tensor-core mixing is an inference option: the loss and gradient (the training forward
+    pass keeps its pre-activations and runs in FP32) are the same bits with either setting, while the
+    network's inference output changes and comes back bit for bit when FP32 mixing is set again."""
+    L, sigma = (4, 4, 4, 6), 0.05
+    fat, lng = links_cache(L, 56)
+    r = to_f32(synth.gaussian_source(L, 57))
+    e = to_f32(synth.gaussian_source(L, 58))
+    with sqcg.Lattice(L) as lat:
+        lat.load_links(fat, lng)
+        net = sqcg.Network(lat)
+        net.set_params(params_to_flat(onn.init_params(7, scale=0.7)))
+        dr, de = lat.pack(r, sqcg.F32), lat.pack(e, sqcg.F32)
+
+        def infer():
+            return lat.unpack(net.apply(dr, lat.new_spinor(sqcg.F32)), sqcg.F32)
+
+        l32, g32 = net.loss_grad(sigma, dr, de)
+        z32 = infer()
+        net.set_mixing(sqcg.NN_MIX_BF16)
+        l16, g16 = net.loss_grad(sigma, dr, de)
+        z16 = infer()
+        net.set_mixing(sqcg.NN_MIX_FP32)
+        zb = infer()
+        net.close()
+    assert l16 == l32 and np.array_equal(g16, g32)
+    assert not np.array_equal(z16, z32) and np.array_equal(zb, z32)
+
+
 def make_pairs(sqcg, lat, net, fat, lng, m, seeds, ks):
     """(r_k, e_k) pairs from CG iterates x_k (CG from 0 truncated at k iterations) and a tight x*."""
     sigma = 4 * m * m
